@@ -1,0 +1,196 @@
+/*
+ * bdem.h -- C ABI of the GB300 implicit bonded-DEM library (libbdem.so).
+ *
+ * The library advances particles that carry a position p in R^3 and a unit quaternion q
+ * (stored {x, y, z, w}, scalar last) by the implicit bonded discrete element method of
+ * "Implicit Bonded Discrete Element Method with Manifold Optimization":
+ *   - each time step minimises Phi(x) = 1/(2 dt^2) (x - xhat)^T M_s (x - xhat) + V(x)
+ *     (Sec. 3.1, Eq. optimization form; M_s = diag(m I3, 8/5 m r^2 I4), xhat = 2 x_n - x_{n-1}),
+ *   - V is the bond potential of Sec. 3.2 (stretch, shear, bend-twist) plus gravity and the penalty
+ *     contact of Sec. 5.4 (ground plane and self contact),
+ *   - the minimisation is the second-order manifold optimisation of Sec. 4.2 / Alg. 2 inside the stable
+ *     integrator of Alg. 3: Riemannian gradient and Hessian (Eq. manifold-hessian-1..4), nullspace
+ *     reduction to 6 unknowns per particle, per-term eigenvalue clamp (Sec. 5.2), block-Jacobi PCG with
+ *     relative tolerance min(0.5, sqrt|grad f|) (Sec. 5.3), exponential-map retraction with an
+ *     energy-decrease line search (Eq. manifold-update-1/2), velocity update, and a tensile-strain bond
+ *     break test after every converged step.
+ * All arithmetic runs in CUDA kernels on the device; there is no CPU fallback.
+ *
+ * Conventions for every entry point:
+ *   - host pointers are caller-owned and only read (or written, for outputs) during the call; the library
+ *     copies what it keeps;
+ *   - device memory is owned by the library and released by bdem_destroy;
+ *   - no call throws, aborts or traps; each returns a bdem_status and keeps a message readable through
+ *     bdem_last_error(sim);
+ *   - on any status other than BDEM_OK, BDEM_E_NEWTON_MAXITER and BDEM_E_LINESEARCH the simulation state
+ *     is left at the last committed time step;
+ *   - a simulation object must not be used from two host threads at once.
+ */
+#ifndef BDEM_H
+#define BDEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bdem_sim bdem_sim;
+
+typedef enum {
+  BDEM_OK = 0,
+  BDEM_E_INVALID = 1,         /* an argument failed validation; nothing changed */
+  BDEM_E_NOMEM = 2,           /* a device allocation failed */
+  BDEM_E_CUDA = 3,            /* a CUDA runtime call failed */
+  BDEM_E_NEWTON_MAXITER = 4,  /* warning: a scene hit newton_max_iter; its best iterate was committed */
+  BDEM_E_LINESEARCH = 5,      /* warning: no step length in the halving sequence decreased Phi; the scene
+                                 stopped at its current (best) iterate, which was committed */
+  BDEM_E_NONFINITE = 6,       /* a residual norm became NaN/Inf; the step was rolled back */
+  BDEM_E_TIMEOUT = 7          /* a device-side wait gave up; the step was rolled back */
+} bdem_status;
+
+enum { BDEM_FP64 = 0, BDEM_MIXED = 1 };   /* bdem_config.precision */
+enum { BDEM_SPD_EIG = 0 };                /* bdem_config.spd_mode */
+
+/* Bond material (Sec. 3.2). G = E / (2 (1 + nu)) (isotropic relation; the paper does not define G). */
+typedef struct {
+  double E;                 /* Young's modulus > 0 */
+  double nu;                /* Poisson ratio in (-1, 0.5) */
+  double density;           /* > 0; particle mass m = density * 4/3 pi r^3 */
+  double break_strain;      /* tensile strain limit > 0; +inf: unbreakable */
+  double bend_twist_scale;  /* >= 0, multiplies K = diag(GJ, EI, EI)/l0 */
+  double shear_scale;       /* >= 0, multiplies the shear angle: 1 gives 1/2 kt theta^2 as printed (N/m);
+                               a length (e.g. the rest bond length) gives the dimensionally consistent energy */
+} bdem_material;
+
+typedef struct {
+  double dt;                /* time step > 0 */
+  double gravity[3];        /* V_g = -m g.p */
+  double newton_rel_tol;    /* a scene converges when |g_k|_2 <= tol |g_0|_2 (g_0 at the initial guess) */
+  int32_t newton_max_iter;  /* >= 1 */
+  int32_t pcg_max_iter;     /* >= 1 */
+  int32_t ls_max_halvings;  /* >= 0; the line search tries alpha = 1, 1/2, ..., 2^-ls_max_halvings */
+  int32_t precision;        /* BDEM_FP64: every stage in FP64. BDEM_MIXED: bond Hessians, block-sparse matrix,
+                               preconditioner and PCG vectors in FP32; gradient, residual norms, PCG dot
+                               products, line-search energy sums and the state in FP64 */
+  double ground_z;          /* ground plane z = ground_z */
+  double k_ground;          /* ground penalty stiffness; 0 disables the ground */
+  double k_self;            /* particle-particle penalty stiffness; 0 disables self contact */
+  double contact_skin;      /* >= 0; candidate pairs are collected once per step at the initial guess when
+                               |p_i - p_j| < r_i + r_j + contact_skin (same scene, not joined by an intact bond) */
+  int32_t spd_mode;         /* BDEM_SPD_EIG: per-term eigenvalue clamp */
+  int32_t reserved0;
+  void* cuda_stream;        /* cudaStream_t the library launches on (NULL: the legacy default stream) */
+} bdem_config;
+
+/* Per-scene statistics of one bdem_step call (sums over its steps, norms of the last step). */
+typedef struct {
+  int32_t steps;
+  int32_t newton_iters;     /* linear solves performed */
+  int32_t pcg_iters;
+  int32_t ls_halvings;
+  int32_t bonds_broken;
+  int32_t contact_candidates; /* of the last step */
+  int32_t status;           /* worst bdem_status of the scene in this call */
+  int32_t reserved0;
+  double g0_norm;           /* |g_0| of the last step */
+  double g_norm;            /* |g| at exit of the last step */
+} bdem_step_stats;
+
+/* Creates a simulation of n particles split into n_scenes independent scenes: scene s owns particles
+ * [scene_offsets[s], scene_offsets[s+1]) (scene_offsets[0] = 0, non-decreasing, scene_offsets[n_scenes] = n).
+ * Scenes share the configuration but never interact, and each converges on its own.
+ *   pos[n][3], quat[n][4] (unit, +-1e-6; normalised on input), vel[n][3] or NULL (zero), quat_vel[n][4] or NULL
+ *   (zero; dq/dt), radius[n] > 0, particle_material[n] in [0, n_mats), kinematic[n] or NULL: nonzero marks a
+ *   particle that moves with its given velocity and is excluded from the solve (Sec. 3.1 boundary condition).
+ * Returns BDEM_E_INVALID on bad input, BDEM_E_NOMEM / BDEM_E_CUDA on device failure; *out is NULL then. */
+bdem_status bdem_create(const bdem_config* config, int32_t n_scenes, const int64_t* scene_offsets, const double* pos,
+                        const double* quat, const double* vel, const double* quat_vel, const double* radius,
+                        const int32_t* particle_material, const bdem_material* mats, int32_t n_mats,
+                        const uint8_t* kinematic, bdem_sim** out);
+
+/* Adds n bonds (i[k], j[k]) with material bond_material[k] (Sec. 3.2). Rest data comes from the current state:
+ * l0 = |p_j - p_i|, d0 = conj(q_c) (.) (p_j - p_i)/l0 with q_c = (q_i + q_j)/|q_i + q_j|, r0 = (r_i + r_j)/2,
+ * S = pi r0^2, I = pi r0^4/4, J = pi r0^4/2, kn = E S/l0, kt = G S/l0, K = bend_twist_scale diag(GJ, EI, EI)/l0.
+ * Requires i != j, both in the same scene, no duplicate pair (also against earlier calls), l0 > 0 and
+ * q_i . q_j >= 1 - 1e-12 (equal rest orientations); otherwise BDEM_E_INVALID and nothing is added.
+ * The library stores each bond with i < j; bdem_read_state reports bond flags in the order of
+ * bdem_bond_order(). */
+bdem_status bdem_add_bonds(bdem_sim* sim, int64_t n, const int32_t* i, const int32_t* j, const int32_t* bond_material);
+
+/* Advances n_steps >= 0 time steps (Alg. 3). stats: NULL or an array of n_scenes entries. Host-blocking: returns
+ * when the last step has completed on the device. */
+bdem_status bdem_step(bdem_sim* sim, int32_t n_steps, bdem_step_stats* stats);
+
+/* Copies the committed state to caller host buffers; any pointer may be NULL. pos[n][3], quat[n][4], vel[n][3],
+ * quat_vel[n][4], bond_broken[n_bonds] (1 = broken). Synchronises the library's stream. */
+bdem_status bdem_read_state(bdem_sim* sim, double* pos, double* quat, double* vel, double* quat_vel,
+                            uint8_t* bond_broken);
+
+/* Overwrites the dynamic state (for checkpoint / resume); NULL leaves a field unchanged. Rest data is kept.
+ * quat must be unit (+-1e-6). */
+bdem_status bdem_write_state(bdem_sim* sim, const double* pos, const double* quat, const double* vel,
+                             const double* quat_vel, const uint8_t* bond_broken);
+
+/* Sizes: particles, intact + broken bonds, scenes. */
+bdem_status bdem_sizes(const bdem_sim* sim, int64_t* n_particles, int64_t* n_bonds, int32_t* n_scenes);
+
+/* The stored bond order: pairs[2k], pairs[2k+1] (i < j) for k < n_bonds. */
+bdem_status bdem_bond_order(const bdem_sim* sim, int32_t* pairs);
+
+/* Releases every device and host resource of sim (NULL is ignored). */
+void bdem_destroy(bdem_sim* sim);
+
+/* Message of the last failed call on sim ("" if none); valid until the next call on sim. NULL sim: the message of
+ * the last failed bdem_create. */
+const char* bdem_last_error(const bdem_sim* sim);
+
+/* ---- inspection entry points (the Newton system the step builds, for verification) --------------------------
+ * They evaluate at the current committed state x with inertia targets (phat, qhat) given by the caller (host,
+ * [n][3], [n][4]); contact candidates are collected at x. They run the same kernels as bdem_step. */
+
+/* Reduced gradient g[n][6] (FP64), assembled projected diagonal blocks diag[n][6][6], per-bond projected reduced
+ * Hessians bond_hess[n_bonds][12][12] in the order (dp_i, y_i, dp_j, y_j) (zero for broken bonds), and the number
+ * of contact candidates; any output may be NULL. Kinematic rows are not masked. */
+bdem_status bdem_debug_system(bdem_sim* sim, const double* phat, const double* qhat, double* g, double* diag,
+                              double* bond_hess, int64_t* n_candidates);
+
+/* y = H x with the system of the last bdem_debug_system call; x, y host [n][6]. */
+bdem_status bdem_debug_matvec(bdem_sim* sim, const double* x, double* y);
+
+/* PCG (Sec. 5.3) on H dx = b with the system of the last bdem_debug_system call (kinematic rows removed), from
+ * dx = 0 until |r| <= eps_r |b| or max_iter iterations. b, dx host [n][6]; iters[n_scenes] or NULL. */
+bdem_status bdem_debug_pcg(bdem_sim* sim, const double* b, double eps_r, int32_t max_iter, double* dx,
+                           int32_t* iters);
+
+/* Kernel launches issued by this sim since creation (for launch accounting). */
+int64_t bdem_launch_count(const bdem_sim* sim);
+
+/* ---- phase timing: CUDA events recorded on the library's stream around each stage's launches ------------------ */
+enum {
+  BDEM_PH_PREDICT = 0,     /* prediction and step set-up */
+  BDEM_PH_CONTACT = 1,     /* spatial hash and contact candidate lists */
+  BDEM_PH_GRAD = 2,        /* bond gradients, per-particle gradient gather, residual norms */
+  BDEM_PH_HESS = 3,        /* bond Hessians with eigenvalue clamp, diagonal blocks and their inverses */
+  BDEM_PH_PCG = 4,         /* the persistent PCG kernel */
+  BDEM_PH_LINESEARCH = 5,  /* descent check, retraction trials, energy differences, commit */
+  BDEM_PH_FINISH = 6,      /* velocity update and fracture */
+  BDEM_N_PHASES = 7
+};
+typedef struct {
+  double ms[BDEM_N_PHASES];         /* summed event time per phase */
+  int64_t intervals[BDEM_N_PHASES]; /* timed intervals per phase (the PCG phase: one per kernel launch) */
+  int64_t pcg_iters;                /* PCG iterations summed over scenes */
+  int64_t newton_iters;             /* linear solves summed over scenes */
+  int64_t particle_newton_iters;    /* sum over scenes of particles x Newton iterations */
+  int64_t steps;
+} bdem_profile;
+
+/* on != 0 enables timing and clears the counters; on == 0 disables it. */
+bdem_status bdem_profile_enable(bdem_sim* sim, int32_t on);
+bdem_status bdem_profile_read(bdem_sim* sim, bdem_profile* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,280 @@
+"""Python binding of libbdem (include/bdem.h): argument marshalling only.
+
+Every stage of the implicit bonded-DEM step runs in the library's sm_103a CUDA kernels. The binding loads the
+in-tree `_build/libbdem.so` (built by `paper_2308_10459_gb300.build.build()`); if it is missing or cannot be
+loaded, importing a function that needs it raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from . import build as _build_mod
+
+LIB_PATH = _build_mod.LIB
+
+BDEM_OK, BDEM_E_INVALID, BDEM_E_NOMEM, BDEM_E_CUDA = 0, 1, 2, 3
+BDEM_E_NEWTON_MAXITER, BDEM_E_LINESEARCH, BDEM_E_NONFINITE, BDEM_E_TIMEOUT = 4, 5, 6, 7
+BDEM_FP64, BDEM_MIXED = 0, 1
+STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "NOMEM", 3: "CUDA", 4: "NEWTON_MAXITER", 5: "LINESEARCH", 6: "NONFINITE",
+                7: "TIMEOUT"}
+
+
+class bdem_material(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_double), ("nu", ctypes.c_double), ("density", ctypes.c_double),
+                ("break_strain", ctypes.c_double), ("bend_twist_scale", ctypes.c_double),
+                ("shear_scale", ctypes.c_double)]
+
+
+class bdem_config(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("gravity", ctypes.c_double * 3), ("newton_rel_tol", ctypes.c_double),
+                ("newton_max_iter", ctypes.c_int32), ("pcg_max_iter", ctypes.c_int32),
+                ("ls_max_halvings", ctypes.c_int32), ("precision", ctypes.c_int32), ("ground_z", ctypes.c_double),
+                ("k_ground", ctypes.c_double), ("k_self", ctypes.c_double), ("contact_skin", ctypes.c_double),
+                ("spd_mode", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
+
+
+class bdem_step_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int32), ("newton_iters", ctypes.c_int32), ("pcg_iters", ctypes.c_int32),
+                ("ls_halvings", ctypes.c_int32), ("bonds_broken", ctypes.c_int32),
+                ("contact_candidates", ctypes.c_int32), ("status", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("g0_norm", ctypes.c_double), ("g_norm", ctypes.c_double)]
+
+
+PHASES = ["predict", "contact", "grad", "hess", "pcg", "linesearch", "finish"]
+
+
+class bdem_profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 7), ("intervals", ctypes.c_int64 * 7), ("pcg_iters", ctypes.c_int64),
+                ("newton_iters", ctypes.c_int64), ("particle_newton_iters", ctypes.c_int64),
+                ("steps", ctypes.c_int64)]
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+_lp = ctypes.POINTER(ctypes.c_int64)
+_up = ctypes.POINTER(ctypes.c_uint8)
+_vp = ctypes.c_void_p
+
+# C prototypes (names identical to include/bdem.h)
+_PROTOS = {
+    "bdem_create": (ctypes.c_int, [ctypes.POINTER(bdem_config), ctypes.c_int32, _lp, _dp, _dp, _dp, _dp, _dp, _ip,
+                                   ctypes.POINTER(bdem_material), ctypes.c_int32, _up, ctypes.POINTER(_vp)]),
+    "bdem_add_bonds": (ctypes.c_int, [_vp, ctypes.c_int64, _ip, _ip, _ip]),
+    "bdem_step": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(bdem_step_stats)]),
+    "bdem_read_state": (ctypes.c_int, [_vp, _dp, _dp, _dp, _dp, _up]),
+    "bdem_write_state": (ctypes.c_int, [_vp, _dp, _dp, _dp, _dp, _up]),
+    "bdem_sizes": (ctypes.c_int, [_vp, _lp, _lp, _ip]),
+    "bdem_bond_order": (ctypes.c_int, [_vp, _ip]),
+    "bdem_destroy": (None, [_vp]),
+    "bdem_last_error": (ctypes.c_char_p, [_vp]),
+    "bdem_debug_system": (ctypes.c_int, [_vp, _dp, _dp, _dp, _dp, _dp, _lp]),
+    "bdem_debug_matvec": (ctypes.c_int, [_vp, _dp, _dp]),
+    "bdem_debug_pcg": (ctypes.c_int, [_vp, _dp, ctypes.c_double, ctypes.c_int32, _dp, _ip]),
+    "bdem_launch_count": (ctypes.c_int64, [_vp]),
+    "bdem_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "bdem_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(bdem_profile)]),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libbdem.so; raises if it is missing (build it with build.build())."""
+    global _lib
+    if _lib is None:
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libbdem.so not found at {p}; run paper_2308_10459_gb300.build.build()")
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in _PROTOS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return list(_PROTOS)
+
+
+class BdemError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _arr(a, dtype, shape=None):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _ptr(a, ct):
+    return None if a is None else a.ctypes.data_as(ct)
+
+
+def make_config(cfg: dict, precision=BDEM_FP64, cuda_stream=None) -> bdem_config:
+    c = bdem_config()
+    c.dt = cfg["dt"]
+    for k in range(3):
+        c.gravity[k] = cfg["gravity"][k]
+    c.newton_rel_tol = cfg["newton_rel_tol"]
+    c.newton_max_iter = int(cfg["newton_max_iter"])
+    c.pcg_max_iter = int(cfg["pcg_max_iter"])
+    c.ls_max_halvings = int(cfg["ls_max_halvings"])
+    c.precision = int(precision)
+    c.ground_z = cfg["ground_z"]
+    c.k_ground = cfg["k_ground"]
+    c.k_self = cfg["k_self"]
+    c.contact_skin = cfg["contact_skin"]
+    c.spd_mode = 0
+    c.cuda_stream = cuda_stream
+    return c
+
+
+def bdem_create(config: bdem_config, scene_offsets, pos, quat, vel, quat_vel, radius, particle_material, mats,
+                kinematic=None):
+    """Thin wrapper of bdem_create; returns an opaque handle (c_void_p)."""
+    L = load()
+    so = _arr(scene_offsets, np.int64)
+    n = int(so[-1])
+    pos, quat = _arr(pos, np.float64, (n, 3)), _arr(quat, np.float64, (n, 4))
+    vel = None if vel is None else _arr(vel, np.float64, (n, 3))
+    quat_vel = None if quat_vel is None else _arr(quat_vel, np.float64, (n, 4))
+    radius, pm = _arr(radius, np.float64, (n,)), _arr(particle_material, np.int32, (n,))
+    kin = None if kinematic is None else _arr(kinematic, np.uint8, (n,))
+    M = (bdem_material * len(mats))()
+    for k, m in enumerate(mats):
+        M[k] = bdem_material(m.E, m.nu, m.density, m.break_strain, m.bend_twist_scale, m.shear_scale)
+    h = _vp()
+    st = L.bdem_create(ctypes.byref(config), len(so) - 1, _ptr(so, _lp), _ptr(pos, _dp), _ptr(quat, _dp),
+                       _ptr(vel, _dp), _ptr(quat_vel, _dp), _ptr(radius, _dp), _ptr(pm, _ip), M, len(mats),
+                       _ptr(kin, _up), ctypes.byref(h))
+    if st != BDEM_OK:
+        raise BdemError(st, L.bdem_last_error(None).decode())
+    return h
+
+
+class Sim:
+    """Owns one bdem_sim. Methods mirror the C entry points."""
+
+    def __init__(self, scene, precision=BDEM_FP64, config=None, cuda_stream=None):
+        cfg = dict(scene.config)
+        if config:
+            cfg.update(config)
+        self.scene = scene
+        self.cfg = cfg
+        self.precision = precision
+        self.config = make_config(cfg, precision, cuda_stream)
+        self.L = load()
+        self.h = bdem_create(self.config, scene.scene_offsets, scene.pos, scene.quat, scene.vel, scene.quat_vel,
+                             scene.radius, scene.material, scene.materials, scene.kinematic)
+        self.n = scene.n
+        self.n_scenes = scene.n_scenes
+        if scene.nb:
+            self.bdem_add_bonds(scene.bond_i, scene.bond_j, scene.bond_material)
+
+    def _check(self, st, ok=(BDEM_OK,)):
+        if st not in ok:
+            raise BdemError(st, self.L.bdem_last_error(self.h).decode())
+        return st
+
+    def bdem_add_bonds(self, i, j, m):
+        i, j, m = _arr(i, np.int32), _arr(j, np.int32), _arr(m, np.int32)
+        self._check(self.L.bdem_add_bonds(self.h, i.size, _ptr(i, _ip), _ptr(j, _ip), _ptr(m, _ip)))
+
+    def bdem_step(self, n_steps=1, allow_warnings=True):
+        stats = (bdem_step_stats * self.n_scenes)()
+        ok = (BDEM_OK, BDEM_E_NEWTON_MAXITER, BDEM_E_LINESEARCH) if allow_warnings else (BDEM_OK,)
+        st = self._check(self.L.bdem_step(self.h, int(n_steps), stats), ok)
+        self.last_status = st
+        return [{f: getattr(s, f) for f, _ in bdem_step_stats._fields_} for s in stats]
+
+    step = bdem_step
+
+    def sizes(self):
+        n, nb, ns = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        self._check(self.L.bdem_sizes(self.h, ctypes.byref(n), ctypes.byref(nb), ctypes.byref(ns)))
+        return n.value, nb.value, ns.value
+
+    def bond_order(self):
+        nb = self.sizes()[1]
+        pairs = np.zeros((max(nb, 1), 2), np.int32)
+        self._check(self.L.bdem_bond_order(self.h, _ptr(pairs, _ip)))
+        return pairs[:nb]
+
+    def bdem_read_state(self, out=None):
+        n, nb, _ = self.sizes()
+        o = out or dict(pos=np.zeros((n, 3)), quat=np.zeros((n, 4)), vel=np.zeros((n, 3)), quat_vel=np.zeros((n, 4)),
+                        broken=np.zeros(max(nb, 1), np.uint8))
+        self._check(self.L.bdem_read_state(self.h, _ptr(o["pos"], _dp), _ptr(o["quat"], _dp), _ptr(o["vel"], _dp),
+                                           _ptr(o["quat_vel"], _dp), _ptr(o["broken"], _up)))
+        if out is None:
+            o["broken"] = o["broken"][:nb]
+        return o
+
+    read_state = bdem_read_state
+
+    def bdem_write_state(self, pos=None, quat=None, vel=None, quat_vel=None, broken=None):
+        n = self.n
+        a = [None if x is None else _arr(x, np.float64, s) for x, s in
+             ((pos, (n, 3)), (quat, (n, 4)), (vel, (n, 3)), (quat_vel, (n, 4)))]
+        b = None if broken is None else _arr(broken, np.uint8)
+        self._check(self.L.bdem_write_state(self.h, _ptr(a[0], _dp), _ptr(a[1], _dp), _ptr(a[2], _dp),
+                                            _ptr(a[3], _dp), _ptr(b, _up)))
+
+    write_state = bdem_write_state
+
+    def bdem_debug_system(self, phat, qhat, want_bonds=True):
+        n, nb, _ = self.sizes()
+        phat, qhat = _arr(phat, np.float64, (n, 3)), _arr(qhat, np.float64, (n, 4))
+        g, D = np.zeros((n, 6)), np.zeros((n, 6, 6))
+        H = np.zeros((max(nb, 1), 12, 12)) if want_bonds else None
+        nc = ctypes.c_int64()
+        self._check(self.L.bdem_debug_system(self.h, _ptr(phat, _dp), _ptr(qhat, _dp), _ptr(g, _dp), _ptr(D, _dp),
+                                             _ptr(H, _dp) if want_bonds else None, ctypes.byref(nc)))
+        return dict(g=g, diag=D, bondH=None if H is None else H[:nb], n_candidates=nc.value)
+
+    def bdem_debug_matvec(self, x):
+        x = _arr(x, np.float64, (self.n, 6))
+        y = np.zeros((self.n, 6))
+        self._check(self.L.bdem_debug_matvec(self.h, _ptr(x, _dp), _ptr(y, _dp)))
+        return y
+
+    def bdem_debug_pcg(self, b, eps_r, max_iter):
+        b = _arr(b, np.float64, (self.n, 6))
+        x = np.zeros((self.n, 6))
+        it = np.zeros(self.n_scenes, np.int32)
+        self._check(self.L.bdem_debug_pcg(self.h, _ptr(b, _dp), float(eps_r), int(max_iter), _ptr(x, _dp),
+                                          _ptr(it, _ip)))
+        return x, it
+
+    def profile_enable(self, on=True):
+        self._check(self.L.bdem_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self):
+        p = bdem_profile()
+        self._check(self.L.bdem_profile_read(self.h, ctypes.byref(p)))
+        return dict(ms={k: p.ms[i] for i, k in enumerate(PHASES)},
+                    intervals={k: p.intervals[i] for i, k in enumerate(PHASES)}, pcg_iters=p.pcg_iters,
+                    newton_iters=p.newton_iters, particle_newton_iters=p.particle_newton_iters, steps=p.steps)
+
+    def launch_count(self):
+        return int(self.L.bdem_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.bdem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,933 @@
+// bdem_api.cu -- host implementation of the C ABI in include/bdem.h: validation, bond rest data (Sec. 3.2),
+// device memory, and the host-driven Newton / line-search loop of Alg. 3 around the device kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/bdem.h"
+#include "bdem_internal.h"
+
+using namespace bdem;
+
+struct bdem_sim {
+  bdem_config cfg;
+  int32_t n = 0, n_scenes = 0;
+  int64_t nb = 0;
+  cudaStream_t stream = 0;
+  std::vector<int64_t> offsets;
+  std::vector<int32_t> pscene;
+  std::vector<double> radius, mass;
+  std::vector<uint8_t> kin;
+  std::vector<bdem_material> mats;
+  std::vector<int32_t> bi, bj, bmat;  // stored bond order, i < j, sorted by (i, j)
+  std::vector<double4> rest, stiff;   // host copies of the bond rest data (d0, l0), (kn, kt, kb, ktw)
+  std::vector<double> brk;
+  DevArrays d{};
+  std::vector<void*> allocs;          // every device buffer owned by the sim
+  std::string err;
+  int64_t launches = 0;
+  int pcg_blocks = 0;
+  double* dbg_buf = nullptr;          // device scratch of the inspection calls
+  size_t dbg_cap = 0;
+  double* stage = nullptr;            // device staging for [n][3] / [n][6] host layouts
+  bool system_ready = false;
+  // phase timing
+  bool prof_on = false;
+  bdem_profile prof{};
+  std::vector<cudaEvent_t> ev_pool;
+  struct Pending { int ph; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  cudaEvent_t ev_open = nullptr;
+  int ph_open = -1;
+};
+
+static cudaEvent_t ev_get(bdem_sim* s) {
+  if (!s->ev_pool.empty()) {
+    cudaEvent_t e = s->ev_pool.back();
+    s->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+static void phase_begin(bdem_sim* s, int ph) {
+  if (!s->prof_on) return;
+  s->ev_open = ev_get(s);
+  s->ph_open = ph;
+  cudaEventRecord(s->ev_open, s->stream);
+}
+
+static void phase_end(bdem_sim* s) {
+  if (!s->prof_on || s->ph_open < 0) return;
+  cudaEvent_t b = ev_get(s);
+  cudaEventRecord(b, s->stream);
+  s->pending.push_back({s->ph_open, s->ev_open, b});
+  s->ph_open = -1;
+  s->ev_open = nullptr;
+}
+
+// called after a stream synchronisation: every pending interval has completed
+static void phase_collect(bdem_sim* s) {
+  for (auto& p : s->pending) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      s->prof.ms[p.ph] += ms;
+      s->prof.intervals[p.ph] += 1;
+    }
+    s->ev_pool.push_back(p.a);
+    s->ev_pool.push_back(p.b);
+  }
+  s->pending.clear();
+}
+
+static std::string g_create_err;
+
+static bdem_status fail(bdem_sim* s, bdem_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (s) s->err = buf;
+  else g_create_err = buf;
+  return st;
+}
+
+#define CUDA_TRY(sim, call)                                                                            \
+  do {                                                                                                 \
+    cudaError_t e_ = (call);                                                                           \
+    if (e_ != cudaSuccess)                                                                             \
+      return fail(sim, e_ == cudaErrorMemoryAllocation ? BDEM_E_NOMEM : BDEM_E_CUDA, "%s: %s", #call, \
+                  cudaGetErrorString(e_));                                                             \
+  } while (0)
+
+#define TRY(expr)                  \
+  do {                             \
+    bdem_status st_ = (expr);      \
+    if (st_ != BDEM_OK) return st_; \
+  } while (0)
+
+static bdem_status dalloc(bdem_sim* s, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(s, e == cudaErrorMemoryAllocation ? BDEM_E_NOMEM : BDEM_E_CUDA, "cudaMalloc(%zu bytes): %s", bytes,
+                cudaGetErrorString(e));
+  }
+  cudaError_t e2 = cudaMemset(*p, 0, bytes);
+  s->allocs.push_back(*p);
+  if (e2 != cudaSuccess) return fail(s, BDEM_E_CUDA, "cudaMemset: %s", cudaGetErrorString(e2));
+  return BDEM_OK;
+}
+
+template <typename P>
+static bdem_status dalloc_t(bdem_sim* s, P** p, size_t count) {
+  return dalloc(s, reinterpret_cast<void**>(p), sizeof(P) * count);
+}
+
+static void dfree(bdem_sim* s, void* p) {
+  if (!p) return;
+  auto it = std::find(s->allocs.begin(), s->allocs.end(), p);
+  if (it != s->allocs.end()) s->allocs.erase(it);
+  cudaFree(p);
+}
+
+static bool fin(double x) { return std::isfinite(x); }
+
+static bdem_status check_launch(bdem_sim* s, int k) {
+  s->launches += k;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(s, BDEM_E_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+  return BDEM_OK;
+}
+
+static void phase_collect(bdem_sim* s);
+
+static bdem_status sync(bdem_sim* s) {
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return fail(s, BDEM_E_CUDA, "cudaStreamSynchronize: %s", cudaGetErrorString(e));
+  phase_collect(s);
+  return BDEM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// quaternion helpers for the host-side rest data (App. A conventions, scalar last)
+// ------------------------------------------------------------------------------------------------
+
+static void hq_mul(const double a[4], const double b[4], double o[4]) {
+  o[0] = a[3] * b[0] + b[3] * a[0] + a[1] * b[2] - a[2] * b[1];
+  o[1] = a[3] * b[1] + b[3] * a[1] + a[2] * b[0] - a[0] * b[2];
+  o[2] = a[3] * b[2] + b[3] * a[2] + a[0] * b[1] - a[1] * b[0];
+  o[3] = a[3] * b[3] - a[0] * b[0] - a[1] * b[1] - a[2] * b[2];
+}
+
+// d = q (.) v = vec(q (v, 0) conj(q))
+static void hq_rotate(const double q[4], const double v[3], double d[3]) {
+  double x[4] = {v[0], v[1], v[2], 0.0}, t[4], qc[4] = {-q[0], -q[1], -q[2], q[3]}, r[4];
+  hq_mul(q, x, t);
+  hq_mul(t, qc, r);
+  d[0] = r[0];
+  d[1] = r[1];
+  d[2] = r[2];
+}
+
+// ------------------------------------------------------------------------------------------------
+// create
+// ------------------------------------------------------------------------------------------------
+
+static bdem_status check_config(const bdem_config* c) {
+  if (!c) return fail(nullptr, BDEM_E_INVALID, "config is NULL");
+  if (!(c->dt > 0.0) || !fin(c->dt)) return fail(nullptr, BDEM_E_INVALID, "dt must be positive and finite");
+  for (int k = 0; k < 3; ++k)
+    if (!fin(c->gravity[k])) return fail(nullptr, BDEM_E_INVALID, "gravity must be finite");
+  if (!(c->newton_rel_tol >= 0.0) || !fin(c->newton_rel_tol))
+    return fail(nullptr, BDEM_E_INVALID, "newton_rel_tol must be finite and >= 0");
+  if (c->newton_max_iter < 1 || c->pcg_max_iter < 1 || c->ls_max_halvings < 0 || c->ls_max_halvings > 1000)
+    return fail(nullptr, BDEM_E_INVALID, "iteration caps must be newton >= 1, pcg >= 1, 0 <= line search <= 1000");
+  if (c->precision != BDEM_FP64 && c->precision != BDEM_MIXED)
+    return fail(nullptr, BDEM_E_INVALID, "precision must be BDEM_FP64 or BDEM_MIXED");
+  if (c->spd_mode != BDEM_SPD_EIG) return fail(nullptr, BDEM_E_INVALID, "spd_mode must be BDEM_SPD_EIG");
+  if (!(c->k_ground >= 0.0) || !(c->k_self >= 0.0) || !(c->contact_skin >= 0.0) || !fin(c->ground_z) ||
+      !fin(c->k_ground) || !fin(c->k_self) || !fin(c->contact_skin))
+    return fail(nullptr, BDEM_E_INVALID, "contact parameters must be finite and >= 0");
+  return BDEM_OK;
+}
+
+static size_t wsize(const bdem_sim* s) { return s->cfg.precision == BDEM_MIXED ? sizeof(float) : sizeof(double); }
+
+static bdem_status alloc_particles(bdem_sim* s) {
+  DevArrays& d = s->d;
+  size_t n = (size_t)std::max(s->n, 1);
+  double4** p4[] = {&d.xp, &d.xq, &d.x0p, &d.x0q, &d.vp, &d.vq, &d.hp, &d.hq, &d.tp, &d.tq};
+  for (double4** p : p4) TRY(dalloc_t(s, p, n));
+  size_t w = wsize(s);
+  TRY(dalloc_t(s, &d.coef, n));
+  TRY(dalloc_t(s, &d.pscene, n));
+  TRY(dalloc_t(s, &d.kin, n));
+  TRY(dalloc_t(s, &d.g, 6 * n));
+  TRY(dalloc(s, &d.D, w * 21 * n));
+  TRY(dalloc(s, &d.Dinv, w * 21 * n));
+  void** pv[] = {&d.vx, &d.vr, &d.vz, &d.vp_, &d.vq_};
+  for (void** p : pv) TRY(dalloc(s, p, w * 6 * n));
+  int hs = 1024;
+  while (hs < 2 * (int)n) hs <<= 1;
+  d.hash_size = hs;
+  size_t mx = std::max((size_t)hs, n);
+  TRY(dalloc_t(s, &d.c_start, n + 1));
+  TRY(dalloc_t(s, &d.cell_key, n));
+  TRY(dalloc_t(s, &d.hash_count, (size_t)hs));
+  TRY(dalloc_t(s, &d.hash_start, (size_t)hs + 1));
+  TRY(dalloc_t(s, &d.hash_ids, n));
+  TRY(dalloc_t(s, &d.cnt_tmp, mx));
+  TRY(dalloc_t(s, &d.scan_tmp, mx / 1024 + 4));
+  d.c_cap = (int32_t)std::max<size_t>(1024, (s->cfg.k_self > 0.0 ? 16 : 1) * n);
+  TRY(dalloc_t(s, &d.c_nbr, (size_t)d.c_cap));
+  TRY(dalloc(s, &d.c_blk, 4 * w * d.c_cap));
+  TRY(dalloc_t(s, &s->stage, 6 * n));
+  TRY(dalloc_t(s, &d.sc, (size_t)std::max(s->n_scenes, 1)));
+  TRY(dalloc_t(s, &d.cnt, 1));
+  return BDEM_OK;
+}
+
+// particle tiles (<= kTile rows inside one scene) and their per-scene ranges
+static bdem_status build_particle_tiles(bdem_sim* s) {
+  std::vector<int32_t> start, scene, begin(s->n_scenes + 1, 0);
+  for (int sc = 0; sc < s->n_scenes; ++sc) {
+    begin[sc] = (int32_t)scene.size();
+    for (int64_t a = s->offsets[sc]; a < s->offsets[sc + 1]; a += kTile) {
+      start.push_back((int32_t)a);
+      scene.push_back(sc);
+    }
+  }
+  begin[s->n_scenes] = (int32_t)scene.size();
+  start.push_back(s->n);
+  DevArrays& d = s->d;
+  d.n_ptiles = (int32_t)scene.size();
+  TRY(dalloc_t(s, &d.ptile_start, start.size()));
+  TRY(dalloc_t(s, &d.ptile_scene, std::max<size_t>(scene.size(), 1)));
+  TRY(dalloc_t(s, &d.ptile_begin, begin.size()));
+  TRY(dalloc_t(s, &d.part_p, (size_t)kPartials * std::max(d.n_ptiles, 1)));
+  CUDA_TRY(s, cudaMemcpy(d.ptile_start, start.data(), sizeof(int32_t) * start.size(), cudaMemcpyHostToDevice));
+  if (!scene.empty())
+    CUDA_TRY(s, cudaMemcpy(d.ptile_scene, scene.data(), sizeof(int32_t) * scene.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(s, cudaMemcpy(d.ptile_begin, begin.data(), sizeof(int32_t) * begin.size(), cudaMemcpyHostToDevice));
+  return BDEM_OK;
+}
+
+extern "C" bdem_status bdem_create(const bdem_config* config, int32_t n_scenes, const int64_t* scene_offsets,
+                                   const double* pos, const double* quat, const double* vel, const double* quat_vel,
+                                   const double* radius, const int32_t* particle_material, const bdem_material* mats,
+                                   int32_t n_mats, const uint8_t* kinematic, bdem_sim** out) {
+  if (!out) return fail(nullptr, BDEM_E_INVALID, "out is NULL");
+  *out = nullptr;
+  TRY(check_config(config));
+  if (n_scenes < 1 || !scene_offsets) return fail(nullptr, BDEM_E_INVALID, "need n_scenes >= 1 and scene_offsets");
+  if (scene_offsets[0] != 0) return fail(nullptr, BDEM_E_INVALID, "scene_offsets[0] must be 0");
+  for (int s = 0; s < n_scenes; ++s)
+    if (scene_offsets[s + 1] < scene_offsets[s]) return fail(nullptr, BDEM_E_INVALID, "scene_offsets must not decrease");
+  int64_t n = scene_offsets[n_scenes];
+  if (n < 0 || n > (int64_t)1 << 30) return fail(nullptr, BDEM_E_INVALID, "particle count out of range");
+  if (n > 0 && (!pos || !quat || !radius || !particle_material))
+    return fail(nullptr, BDEM_E_INVALID, "pos, quat, radius and particle_material are required");
+  if (n_mats < 1 || !mats) return fail(nullptr, BDEM_E_INVALID, "need at least one material");
+  for (int m = 0; m < n_mats; ++m) {
+    const bdem_material& M = mats[m];
+    if (!(M.E > 0.0) || !fin(M.E) || !(M.nu > -1.0 && M.nu < 0.5) || !(M.density > 0.0) || !fin(M.density) ||
+        !(M.break_strain > 0.0) || !(M.bend_twist_scale >= 0.0) || !fin(M.bend_twist_scale) ||
+        !(M.shear_scale >= 0.0) || !fin(M.shear_scale))
+      return fail(nullptr, BDEM_E_INVALID, "material %d is invalid", m);
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    for (int k = 0; k < 3; ++k)
+      if (!fin(pos[3 * i + k]) || (vel && !fin(vel[3 * i + k])))
+        return fail(nullptr, BDEM_E_INVALID, "particle %lld: non-finite position or velocity", (long long)i);
+    double nq = 0.0;
+    for (int k = 0; k < 4; ++k) {
+      if (!fin(quat[4 * i + k]) || (quat_vel && !fin(quat_vel[4 * i + k])))
+        return fail(nullptr, BDEM_E_INVALID, "particle %lld: non-finite quaternion", (long long)i);
+      nq += quat[4 * i + k] * quat[4 * i + k];
+    }
+    if (std::fabs(std::sqrt(nq) - 1.0) > 1e-6)
+      return fail(nullptr, BDEM_E_INVALID, "particle %lld: quaternion is not unit", (long long)i);
+    if (!(radius[i] > 0.0) || !fin(radius[i]))
+      return fail(nullptr, BDEM_E_INVALID, "particle %lld: radius must be positive", (long long)i);
+    if (particle_material[i] < 0 || particle_material[i] >= n_mats)
+      return fail(nullptr, BDEM_E_INVALID, "particle %lld: material index out of range", (long long)i);
+  }
+  bdem_sim* s = new bdem_sim();
+  s->cfg = *config;
+  s->n = (int32_t)n;
+  s->n_scenes = n_scenes;
+  s->stream = (cudaStream_t)config->cuda_stream;
+  s->offsets.assign(scene_offsets, scene_offsets + n_scenes + 1);
+  s->mats.assign(mats, mats + n_mats);
+  s->pscene.resize(n);
+  for (int sc = 0; sc < n_scenes; ++sc)
+    for (int64_t i = scene_offsets[sc]; i < scene_offsets[sc + 1]; ++i) s->pscene[i] = sc;
+  s->radius.assign(radius, radius + n);
+  s->mass.resize(n);
+  s->kin.assign(n, 0);
+  if (kinematic)
+    for (int64_t i = 0; i < n; ++i) s->kin[i] = kinematic[i] ? 1 : 0;
+  const bdem_config& c = s->cfg;
+  DevArrays& d = s->d;
+  d.n = (int32_t)n;
+  d.nb = 0;
+  d.n_scenes = n_scenes;
+  d.mixed = c.precision == BDEM_MIXED;
+  d.dt = c.dt;
+  d.gx = c.gravity[0];
+  d.gy = c.gravity[1];
+  d.gz = c.gravity[2];
+  d.tol = c.newton_rel_tol;
+  d.ground_z = c.ground_z;
+  d.k_ground = c.k_ground;
+  d.k_self = c.k_self;
+  d.skin = c.contact_skin;
+  double rmax = 0.0;
+  for (int64_t i = 0; i < n; ++i) rmax = std::max(rmax, radius[i]);
+  d.cell_h = std::max(2.0 * rmax + c.contact_skin, 1e-12);
+  d.newton_max = c.newton_max_iter;
+  d.pcg_max = c.pcg_max_iter;
+  d.ls_max = c.ls_max_halvings;
+  bdem_status st = alloc_particles(s);
+  if (st == BDEM_OK) st = build_particle_tiles(s);
+  if (st == BDEM_OK) {
+    std::vector<double4> xp(std::max<int64_t>(n, 1)), xq(std::max<int64_t>(n, 1)), vp(std::max<int64_t>(n, 1)),
+        vq(std::max<int64_t>(n, 1)), hp(std::max<int64_t>(n, 1));
+    std::vector<double2> coef(std::max<int64_t>(n, 1));
+    for (int64_t i = 0; i < n; ++i) {
+      const bdem_material& M = mats[particle_material[i]];
+      double r = radius[i], m = M.density * 4.0 / 3.0 * M_PI * r * r * r;
+      s->mass[i] = m;
+      double qn = std::sqrt(quat[4 * i] * quat[4 * i] + quat[4 * i + 1] * quat[4 * i + 1] +
+                            quat[4 * i + 2] * quat[4 * i + 2] + quat[4 * i + 3] * quat[4 * i + 3]);
+      xp[i] = make_double4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], r);
+      xq[i] = make_double4(quat[4 * i] / qn, quat[4 * i + 1] / qn, quat[4 * i + 2] / qn, quat[4 * i + 3] / qn);
+      vp[i] = vel ? make_double4(vel[3 * i], vel[3 * i + 1], vel[3 * i + 2], 0.0) : make_double4(0, 0, 0, 0);
+      vq[i] = quat_vel ? make_double4(quat_vel[4 * i], quat_vel[4 * i + 1], quat_vel[4 * i + 2], quat_vel[4 * i + 3])
+                       : make_double4(0, 0, 0, 0);
+      hp[i] = make_double4(0, 0, 0, m);
+      coef[i] = make_double2(m / (c.dt * c.dt), 1.6 * m * r * r / (c.dt * c.dt));
+    }
+    size_t nn = (size_t)n;
+    if (nn) {
+      cudaMemcpy(d.x0p, xp.data(), sizeof(double4) * nn, cudaMemcpyHostToDevice);
+      cudaMemcpy(d.x0q, xq.data(), sizeof(double4) * nn, cudaMemcpyHostToDevice);
+      cudaMemcpy(d.xp, xp.data(), sizeof(double4) * nn, cudaMemcpyHostToDevice);
+      cudaMemcpy(d.xq, xq.data(), sizeof(double4) * nn, cudaMemcpyHostToDevice);
+      cudaMemcpy(d.vp, vp.data(), sizeof(double4) * nn, cudaMemcpyHostToDevice);
+      cudaMemcpy(d.vq, vq.data(), sizeof(double4) * nn, cudaMemcpyHostToDevice);
+      cudaMemcpy(d.hp, hp.data(), sizeof(double4) * nn, cudaMemcpyHostToDevice);
+      cudaMemcpy(d.coef, coef.data(), sizeof(double2) * nn, cudaMemcpyHostToDevice);
+      cudaMemcpy(d.pscene, s->pscene.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice);
+      cudaMemcpy(d.kin, s->kin.data(), nn, cudaMemcpyHostToDevice);
+    }
+    // no bonds yet: empty incidence lists and an empty bond-tile table (every scene owns zero bond tiles)
+    st = BDEM_OK;
+    if (dalloc_t(s, &d.inc_start, nn + 1) != BDEM_OK || dalloc_t(s, &d.inc, 1) != BDEM_OK ||
+        dalloc_t(s, &d.btile_start, 1) != BDEM_OK || dalloc_t(s, &d.btile_scene, 1) != BDEM_OK ||
+        dalloc_t(s, &d.btile_begin, (size_t)n_scenes + 1) != BDEM_OK ||
+        dalloc_t(s, &d.part_b, (size_t)kPartials) != BDEM_OK)
+      st = BDEM_E_NOMEM;
+    d.n_btiles = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (st == BDEM_OK && e != cudaSuccess) st = fail(s, BDEM_E_CUDA, "upload: %s", cudaGetErrorString(e));
+    if (st == BDEM_OK) s->pcg_blocks = pcg_max_blocks(d.mixed);
+    if (st == BDEM_OK && s->pcg_blocks < 1) st = fail(s, BDEM_E_CUDA, "no resident blocks for the PCG kernel");
+  }
+  if (st != BDEM_OK) {
+    g_create_err = s->err;
+    bdem_destroy(s);
+    return st;
+  }
+  *out = s;
+  return BDEM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// bonds
+// ------------------------------------------------------------------------------------------------
+
+static bdem_status download_committed(bdem_sim* s, std::vector<double4>& xp, std::vector<double4>& xq) {
+  xp.resize(std::max(s->n, 1));
+  xq.resize(std::max(s->n, 1));
+  if (s->n == 0) return BDEM_OK;
+  CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+  CUDA_TRY(s, cudaMemcpy(xp.data(), s->d.x0p, sizeof(double4) * s->n, cudaMemcpyDeviceToHost));
+  CUDA_TRY(s, cudaMemcpy(xq.data(), s->d.x0q, sizeof(double4) * s->n, cudaMemcpyDeviceToHost));
+  return BDEM_OK;
+}
+
+extern "C" bdem_status bdem_add_bonds(bdem_sim* s, int64_t n, const int32_t* I, const int32_t* J, const int32_t* M) {
+  if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
+  if (n < 0) return fail(s, BDEM_E_INVALID, "negative bond count");
+  if (n == 0) return BDEM_OK;
+  if (!I || !J || !M) return fail(s, BDEM_E_INVALID, "bond arrays are NULL");
+  if (s->nb + n > ((int64_t)1 << 29)) return fail(s, BDEM_E_INVALID, "too many bonds");
+  std::vector<double4> xp, xq;
+  TRY(download_committed(s, xp, xq));
+  struct NB { int32_t a, b, m; int64_t old; };
+  std::vector<NB> all;
+  all.reserve(s->nb + n);
+  for (int64_t k = 0; k < s->nb; ++k) all.push_back({s->bi[k], s->bj[k], s->bmat[k], k});
+  for (int64_t k = 0; k < n; ++k) {
+    int32_t i = I[k], j = J[k], m = M[k];
+    if (i < 0 || j < 0 || i >= s->n || j >= s->n) return fail(s, BDEM_E_INVALID, "bond %lld: index out of range", (long long)k);
+    if (i == j) return fail(s, BDEM_E_INVALID, "bond %lld: i == j", (long long)k);
+    if (s->pscene[i] != s->pscene[j]) return fail(s, BDEM_E_INVALID, "bond %lld joins two scenes", (long long)k);
+    if (m < 0 || m >= (int32_t)s->mats.size()) return fail(s, BDEM_E_INVALID, "bond %lld: material out of range", (long long)k);
+    double4 qi = xq[i], qj = xq[j];
+    double qd = qi.x * qj.x + qi.y * qj.y + qi.z * qj.z + qi.w * qj.w;
+    if (!(qd >= 1.0 - 1e-12))
+      return fail(s, BDEM_E_INVALID, "bond %lld: endpoint orientations differ (q_i.q_j = %.17g)", (long long)k, qd);
+    double dx = xp[j].x - xp[i].x, dy = xp[j].y - xp[i].y, dz = xp[j].z - xp[i].z;
+    if (!(dx * dx + dy * dy + dz * dz > 0.0)) return fail(s, BDEM_E_INVALID, "bond %lld: zero length", (long long)k);
+    all.push_back({std::min(i, j), std::max(i, j), m, -1 - k});
+  }
+  std::sort(all.begin(), all.end(), [](const NB& x, const NB& y) { return x.a != y.a ? x.a < y.a : x.b < y.b; });
+  for (size_t k = 1; k < all.size(); ++k)
+    if (all[k].a == all[k - 1].a && all[k].b == all[k - 1].b)
+      return fail(s, BDEM_E_INVALID, "duplicate bond (%d, %d)", all[k].a, all[k].b);
+  // broken flags of the existing bonds
+  std::vector<uint8_t> old_broken(std::max<int64_t>(s->nb, 1), 0);
+  if (s->nb) CUDA_TRY(s, cudaMemcpy(old_broken.data(), s->d.bbroken, s->nb, cudaMemcpyDeviceToHost));
+  int64_t nb = (int64_t)all.size();
+  std::vector<int2> bij(nb);
+  std::vector<double4> rest(nb), stiff(nb);
+  std::vector<double> brk(nb);
+  std::vector<uint8_t> broken(nb, 0);
+  std::vector<int32_t> bscene(nb), bi(nb), bj(nb), bm(nb);
+  for (int64_t k = 0; k < nb; ++k) {
+    const NB& e = all[k];
+    bij[k] = make_int2(e.a, e.b);
+    bi[k] = e.a;
+    bj[k] = e.b;
+    bm[k] = e.m;
+    bscene[k] = s->pscene[e.a];
+    const bdem_material& mt = s->mats[e.m];
+    brk[k] = mt.break_strain;
+    if (e.old >= 0) {
+      rest[k] = s->rest[e.old];
+      stiff[k] = s->stiff[e.old];
+      broken[k] = old_broken[e.old];
+      continue;
+    }
+    // rest data from the current state (Sec. 3.2 with the readings of the bond frame)
+    double pi[3] = {xp[e.a].x, xp[e.a].y, xp[e.a].z}, pj[3] = {xp[e.b].x, xp[e.b].y, xp[e.b].z};
+    double qi[4] = {xq[e.a].x, xq[e.a].y, xq[e.a].z, xq[e.a].w}, qj[4] = {xq[e.b].x, xq[e.b].y, xq[e.b].z, xq[e.b].w};
+    double dd[3] = {pj[0] - pi[0], pj[1] - pi[1], pj[2] - pi[2]};
+    double l0 = std::sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+    double n0[3] = {dd[0] / l0, dd[1] / l0, dd[2] / l0};
+    double sg = (qi[0] * qj[0] + qi[1] * qj[1] + qi[2] * qj[2] + qi[3] * qj[3]) < 0.0 ? -1.0 : 1.0;
+    double m4[4], mm = 0.0;
+    for (int c = 0; c < 4; ++c) {
+      m4[c] = qi[c] + sg * qj[c];
+      mm += m4[c] * m4[c];
+    }
+    mm = std::sqrt(mm);
+    double qcc[4] = {-m4[0] / mm, -m4[1] / mm, -m4[2] / mm, m4[3] / mm}, d0[3];
+    hq_rotate(qcc, n0, d0);
+    double r0 = 0.5 * (s->radius[e.a] + s->radius[e.b]);
+    double S = M_PI * r0 * r0, Ia = M_PI * r0 * r0 * r0 * r0 / 4.0, Ja = M_PI * r0 * r0 * r0 * r0 / 2.0;
+    double G = mt.E / (2.0 * (1.0 + mt.nu));
+    rest[k] = make_double4(d0[0], d0[1], d0[2], l0);
+    stiff[k] = make_double4(mt.E * S / l0, G * S / l0 * mt.shear_scale * mt.shear_scale,
+                            mt.bend_twist_scale * mt.E * Ia / l0, mt.bend_twist_scale * G * Ja / l0);
+  }
+  // incidence CSR (entries ordered by bond index within each particle)
+  std::vector<int32_t> inc_start(s->n + 1, 0), inc(2 * nb);
+  for (int64_t k = 0; k < nb; ++k) {
+    inc_start[bi[k] + 1]++;
+    inc_start[bj[k] + 1]++;
+  }
+  for (int i = 0; i < s->n; ++i) inc_start[i + 1] += inc_start[i];
+  {
+    std::vector<int32_t> fill(inc_start.begin(), inc_start.end() - 1);
+    for (int64_t k = 0; k < nb; ++k) {
+      inc[fill[bi[k]]++] = (int32_t)(k << 1);
+      inc[fill[bj[k]]++] = (int32_t)((k << 1) | 1);
+    }
+  }
+  // bond tiles per scene
+  std::vector<int32_t> tstart, tscene, tbegin(s->n_scenes + 1, 0);
+  {
+    int64_t k = 0;
+    for (int sc = 0; sc < s->n_scenes; ++sc) {
+      tbegin[sc] = (int32_t)tscene.size();
+      int64_t a = k;
+      while (k < nb && bscene[k] == sc) ++k;
+      for (int64_t t = a; t < k; t += kTile) {
+        tstart.push_back((int32_t)t);
+        tscene.push_back(sc);
+      }
+    }
+    tbegin[s->n_scenes] = (int32_t)tscene.size();
+    tstart.push_back((int32_t)nb);
+  }
+  // replace the device bond arrays
+  DevArrays& d = s->d;
+  void* olds[] = {d.bij, d.brest, d.bstiff, d.bbrk, d.bbroken, d.bscene, d.bg, d.bM, d.bE, d.inc, d.inc_start,
+                  d.btile_start, d.btile_scene, d.btile_begin, d.part_b};
+  for (void* p : olds) dfree(s, p);
+  size_t w = wsize(s);
+  TRY(dalloc_t(s, &d.bij, nb));
+  TRY(dalloc_t(s, &d.brest, nb));
+  TRY(dalloc_t(s, &d.bstiff, nb));
+  TRY(dalloc_t(s, &d.bbrk, nb));
+  TRY(dalloc_t(s, &d.bbroken, nb));
+  TRY(dalloc_t(s, &d.bscene, nb));
+  TRY(dalloc_t(s, &d.bg, 9 * (size_t)nb));
+  TRY(dalloc(s, &d.bM, w * 36 * nb));
+  TRY(dalloc(s, &d.bE, w * 12 * nb));
+  TRY(dalloc_t(s, &d.inc, 2 * (size_t)nb));
+  TRY(dalloc_t(s, &d.inc_start, (size_t)s->n + 1));
+  TRY(dalloc_t(s, &d.btile_start, tstart.size()));
+  TRY(dalloc_t(s, &d.btile_scene, std::max<size_t>(1, tscene.size())));
+  TRY(dalloc_t(s, &d.btile_begin, tbegin.size()));
+  TRY(dalloc_t(s, &d.part_b, (size_t)kPartials * std::max<size_t>(1, tscene.size())));
+  CUDA_TRY(s, cudaMemcpy(d.bij, bij.data(), sizeof(int2) * nb, cudaMemcpyHostToDevice));
+  CUDA_TRY(s, cudaMemcpy(d.brest, rest.data(), sizeof(double4) * nb, cudaMemcpyHostToDevice));
+  CUDA_TRY(s, cudaMemcpy(d.bstiff, stiff.data(), sizeof(double4) * nb, cudaMemcpyHostToDevice));
+  CUDA_TRY(s, cudaMemcpy(d.bbrk, brk.data(), sizeof(double) * nb, cudaMemcpyHostToDevice));
+  CUDA_TRY(s, cudaMemcpy(d.bbroken, broken.data(), nb, cudaMemcpyHostToDevice));
+  CUDA_TRY(s, cudaMemcpy(d.bscene, bscene.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice));
+  CUDA_TRY(s, cudaMemcpy(d.inc, inc.data(), sizeof(int32_t) * 2 * nb, cudaMemcpyHostToDevice));
+  CUDA_TRY(s, cudaMemcpy(d.inc_start, inc_start.data(), sizeof(int32_t) * (s->n + 1), cudaMemcpyHostToDevice));
+  CUDA_TRY(s, cudaMemcpy(d.btile_start, tstart.data(), sizeof(int32_t) * tstart.size(), cudaMemcpyHostToDevice));
+  if (!tscene.empty())
+    CUDA_TRY(s, cudaMemcpy(d.btile_scene, tscene.data(), sizeof(int32_t) * tscene.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(s, cudaMemcpy(d.btile_begin, tbegin.data(), sizeof(int32_t) * tbegin.size(), cudaMemcpyHostToDevice));
+  d.nb = (int32_t)nb;
+  d.n_btiles = (int32_t)tscene.size();
+  s->nb = nb;
+  s->bi.swap(bi);
+  s->bj.swap(bj);
+  s->bmat.swap(bm);
+  s->rest.swap(rest);
+  s->stiff.swap(stiff);
+  s->brk.swap(brk);
+  s->system_ready = false;
+  return BDEM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// step
+// ------------------------------------------------------------------------------------------------
+
+static bdem_status read_counters(bdem_sim* s, Counters* c) {
+  CUDA_TRY(s, cudaMemcpyAsync(c, s->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s->stream));
+  TRY(sync(s));
+  if (c->timeout) {
+    Counters z{};
+    cudaMemcpy(s->d.cnt, &z, sizeof z, cudaMemcpyHostToDevice);
+    return fail(s, BDEM_E_TIMEOUT, "a device-side wait gave up; the step was rolled back");
+  }
+  return BDEM_OK;
+}
+
+static bdem_status build_contacts(bdem_sim* s) {
+  DevArrays& d = s->d;
+  TRY(check_launch(s, launch_contacts(d, 0, s->stream)));
+  int32_t total = 0;
+  CUDA_TRY(s, cudaMemcpyAsync(&total, d.c_start + d.n, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+  TRY(sync(s));
+  if (total < 0) return fail(s, BDEM_E_CUDA, "contact count overflow");
+  if (total > d.c_cap) {
+    dfree(s, d.c_nbr);
+    dfree(s, d.c_blk);
+    d.c_nbr = nullptr;
+    d.c_blk = nullptr;
+    int64_t cap = (int64_t)total + total / 2 + 1024;
+    if (cap > ((int64_t)1 << 31) - 1) return fail(s, BDEM_E_NOMEM, "too many contact candidates");
+    TRY(dalloc_t(s, &d.c_nbr, (size_t)cap));
+    TRY(dalloc(s, &d.c_blk, 4 * wsize(s) * (size_t)cap));
+    d.c_cap = (int32_t)cap;
+  }
+  TRY(check_launch(s, launch_contacts(d, 1, s->stream)));
+  return BDEM_OK;
+}
+
+static bdem_status run_pcg(bdem_sim* s, const DevArrays& d, int rhs_from_g, int mask) {
+  cudaError_t e = cudaSuccess;
+  int k = launch_pcg(d, rhs_from_g, mask, s->pcg_blocks, s->stream, &e);
+  s->launches += k;
+  if (e != cudaSuccess) return fail(s, BDEM_E_CUDA, "cooperative PCG launch: %s", cudaGetErrorString(e));
+  return check_launch(s, 0);
+}
+
+// one time step; on success ctl holds the per-scene control blocks of the step
+static bdem_status do_step(bdem_sim* s, std::vector<SceneCtl>& ctl) {
+  DevArrays& d = s->d;
+  cudaStream_t st = s->stream;
+  phase_begin(s, BDEM_PH_PREDICT);
+  TRY(check_launch(s, launch_predict(d, st)));
+  phase_end(s);
+  phase_begin(s, BDEM_PH_CONTACT);
+  if (d.k_self > 0.0 && d.n > 0) {
+    TRY(build_contacts(s));
+  } else if (d.n > 0) {
+    CUDA_TRY(s, cudaMemsetAsync(d.c_start, 0, sizeof(int32_t) * (d.n + 1), st));
+  }
+  TRY(check_launch(s, launch_scene_reduce(d, RED_CAND, 0, st)));
+  phase_end(s);
+  Counters c{};
+  for (int k = 0;; ++k) {
+    phase_begin(s, BDEM_PH_GRAD);
+    TRY(check_launch(s, launch_bond_grad(d, 0, st)));
+    TRY(check_launch(s, launch_particle_grad(d, 1, 0, st)));
+    TRY(check_launch(s, launch_scene_reduce(d, RED_GRAD, k, st)));
+    phase_end(s);
+    TRY(read_counters(s, &c));
+    if (c.nonfinite) {
+      Counters z{};
+      cudaMemcpy(d.cnt, &z, sizeof z, cudaMemcpyHostToDevice);
+      return fail(s, BDEM_E_NONFINITE, "the Newton residual became non-finite; the step was rolled back");
+    }
+    if (c.n_active == 0) break;
+    if (k > d.newton_max + 1) return fail(s, BDEM_E_CUDA, "Newton loop did not terminate");
+    phase_begin(s, BDEM_PH_HESS);
+    TRY(check_launch(s, launch_bond_hess(d, 0, st)));
+    TRY(check_launch(s, launch_particle_hess(d, 1, 0, st)));
+    phase_end(s);
+    phase_begin(s, BDEM_PH_PCG);
+    TRY(run_pcg(s, d, 1, 1));
+    phase_end(s);
+    phase_begin(s, BDEM_PH_LINESEARCH);
+    TRY(check_launch(s, launch_gdx(d, st)));
+    TRY(check_launch(s, launch_scene_reduce(d, RED_GDX, k, st)));
+    for (int h = 0; h <= d.ls_max + 1; ++h) {
+      TRY(check_launch(s, launch_ls_trial(d, st)));
+      TRY(check_launch(s, launch_ls_energy(d, st)));
+      TRY(check_launch(s, launch_scene_reduce(d, RED_LS, k, st)));
+      phase_end(s);
+      TRY(read_counters(s, &c));
+      if (c.n_pending == 0) break;
+      phase_begin(s, BDEM_PH_LINESEARCH);
+    }
+    phase_begin(s, BDEM_PH_LINESEARCH);
+    TRY(check_launch(s, launch_ls_commit(d, st)));
+    phase_end(s);
+  }
+  phase_begin(s, BDEM_PH_FINISH);
+  TRY(check_launch(s, launch_finish(d, st)));
+  phase_end(s);
+  ctl.resize(s->n_scenes);
+  CUDA_TRY(s, cudaMemcpyAsync(ctl.data(), d.sc, sizeof(SceneCtl) * s->n_scenes, cudaMemcpyDeviceToHost, st));
+  TRY(sync(s));
+  if (s->prof_on) {
+    s->prof.steps += 1;
+    for (int sc = 0; sc < s->n_scenes; ++sc) {
+      s->prof.pcg_iters += ctl[sc].pcg_total;
+      s->prof.newton_iters += ctl[sc].newton_iters;
+      s->prof.particle_newton_iters += (int64_t)ctl[sc].newton_iters * (s->offsets[sc + 1] - s->offsets[sc]);
+    }
+  }
+  return BDEM_OK;
+}
+
+extern "C" bdem_status bdem_step(bdem_sim* s, int32_t n_steps, bdem_step_stats* stats) {
+  if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
+  if (n_steps < 0) return fail(s, BDEM_E_INVALID, "n_steps must be >= 0");
+  if (stats) memset(stats, 0, sizeof(bdem_step_stats) * s->n_scenes);
+  s->system_ready = false;
+  int worst = BDEM_OK;
+  std::vector<SceneCtl> ctl;
+  for (int t = 0; t < n_steps; ++t) {
+    bdem_status st = do_step(s, ctl);
+    if (st != BDEM_OK) return st;
+    for (int sc = 0; sc < s->n_scenes; ++sc) {
+      const SceneCtl& c = ctl[sc];
+      worst = std::max(worst, (int)c.status);
+      if (!stats) continue;
+      bdem_step_stats& o = stats[sc];
+      o.steps += 1;
+      o.newton_iters += c.newton_iters;
+      o.pcg_iters += c.pcg_total;
+      o.ls_halvings += c.ls_halvings;
+      o.bonds_broken += c.bonds_broken;
+      o.contact_candidates = c.pad2;
+      o.status = std::max(o.status, c.status);
+      o.g0_norm = c.g0;
+      o.g_norm = c.gnorm;
+    }
+  }
+  if (worst == BDEM_E_NEWTON_MAXITER) fail(s, BDEM_E_NEWTON_MAXITER, "a scene reached newton_max_iter");
+  if (worst == BDEM_E_LINESEARCH) fail(s, BDEM_E_LINESEARCH, "a line search found no decrease");
+  return (bdem_status)worst;
+}
+
+// ------------------------------------------------------------------------------------------------
+// state access
+// ------------------------------------------------------------------------------------------------
+
+extern "C" bdem_status bdem_read_state(bdem_sim* s, double* pos, double* quat, double* vel, double* quat_vel,
+                                       uint8_t* bond_broken) {
+  if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
+  DevArrays& d = s->d;
+  size_t n = (size_t)s->n;
+  cudaStream_t st = s->stream;
+  if (n) {
+    if (pos || vel) TRY(check_launch(s, launch_pack_state(d, pos ? s->stage : nullptr, vel ? s->stage + 3 * n : nullptr, st)));
+    if (pos) CUDA_TRY(s, cudaMemcpyAsync(pos, s->stage, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+    if (vel) CUDA_TRY(s, cudaMemcpyAsync(vel, s->stage + 3 * n, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+    if (quat) CUDA_TRY(s, cudaMemcpyAsync(quat, d.x0q, sizeof(double4) * n, cudaMemcpyDeviceToHost, st));
+    if (quat_vel) CUDA_TRY(s, cudaMemcpyAsync(quat_vel, d.vq, sizeof(double4) * n, cudaMemcpyDeviceToHost, st));
+  }
+  if (bond_broken && s->nb) CUDA_TRY(s, cudaMemcpyAsync(bond_broken, d.bbroken, s->nb, cudaMemcpyDeviceToHost, st));
+  return sync(s);
+}
+
+extern "C" bdem_status bdem_write_state(bdem_sim* s, const double* pos, const double* quat, const double* vel,
+                                        const double* quat_vel, const uint8_t* bond_broken) {
+  if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
+  size_t n = (size_t)s->n;
+  for (size_t i = 0; i < n; ++i) {
+    if (pos)
+      for (int k = 0; k < 3; ++k)
+        if (!fin(pos[3 * i + k])) return fail(s, BDEM_E_INVALID, "particle %zu: non-finite position", i);
+    if (vel)
+      for (int k = 0; k < 3; ++k)
+        if (!fin(vel[3 * i + k])) return fail(s, BDEM_E_INVALID, "particle %zu: non-finite velocity", i);
+    if (quat_vel)
+      for (int k = 0; k < 4; ++k)
+        if (!fin(quat_vel[4 * i + k])) return fail(s, BDEM_E_INVALID, "particle %zu: non-finite quaternion velocity", i);
+    if (quat) {
+      double nq = 0.0;
+      for (int k = 0; k < 4; ++k) nq += quat[4 * i + k] * quat[4 * i + k];
+      if (!fin(nq) || std::fabs(std::sqrt(nq) - 1.0) > 1e-6)
+        return fail(s, BDEM_E_INVALID, "particle %zu: quaternion is not unit", i);
+    }
+  }
+  DevArrays& d = s->d;
+  cudaStream_t st = s->stream;
+  if (n) {
+    if (pos) CUDA_TRY(s, cudaMemcpyAsync(s->stage, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    if (vel) CUDA_TRY(s, cudaMemcpyAsync(s->stage + 3 * n, vel, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    if (pos || vel)
+      TRY(check_launch(s, launch_unpack_state(d, pos ? s->stage : nullptr, vel ? s->stage + 3 * n : nullptr, st)));
+    if (quat) CUDA_TRY(s, cudaMemcpyAsync(d.x0q, quat, sizeof(double4) * n, cudaMemcpyHostToDevice, st));
+    if (quat_vel) CUDA_TRY(s, cudaMemcpyAsync(d.vq, quat_vel, sizeof(double4) * n, cudaMemcpyHostToDevice, st));
+  }
+  if (bond_broken && s->nb) {
+    std::vector<uint8_t> b(bond_broken, bond_broken + s->nb);
+    for (auto& x : b) x = x ? 1 : 0;
+    CUDA_TRY(s, cudaMemcpyAsync(d.bbroken, b.data(), s->nb, cudaMemcpyHostToDevice, st));
+    TRY(sync(s));
+  }
+  s->system_ready = false;
+  return BDEM_OK;
+}
+
+extern "C" bdem_status bdem_sizes(const bdem_sim* s, int64_t* n_particles, int64_t* n_bonds, int32_t* n_scenes) {
+  if (!s) return BDEM_E_INVALID;
+  if (n_particles) *n_particles = s->n;
+  if (n_bonds) *n_bonds = s->nb;
+  if (n_scenes) *n_scenes = s->n_scenes;
+  return BDEM_OK;
+}
+
+extern "C" bdem_status bdem_bond_order(const bdem_sim* s, int32_t* pairs) {
+  if (!s || (!pairs && s->nb)) return BDEM_E_INVALID;
+  for (int64_t k = 0; k < s->nb; ++k) {
+    pairs[2 * k] = s->bi[k];
+    pairs[2 * k + 1] = s->bj[k];
+  }
+  return BDEM_OK;
+}
+
+extern "C" void bdem_destroy(bdem_sim* s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->stream);
+  phase_collect(s);
+  for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+  for (void* p : s->allocs) cudaFree(p);
+  s->allocs.clear();
+  delete s;
+}
+
+extern "C" const char* bdem_last_error(const bdem_sim* s) { return s ? s->err.c_str() : g_create_err.c_str(); }
+
+extern "C" int64_t bdem_launch_count(const bdem_sim* s) { return s ? s->launches : 0; }
+
+// ------------------------------------------------------------------------------------------------
+// inspection
+// ------------------------------------------------------------------------------------------------
+
+static bdem_status dbg_reserve(bdem_sim* s, size_t count) {
+  if (s->dbg_cap >= count) return BDEM_OK;
+  dfree(s, s->dbg_buf);
+  s->dbg_buf = nullptr;
+  s->dbg_cap = 0;
+  TRY(dalloc_t(s, &s->dbg_buf, count));
+  s->dbg_cap = count;
+  return BDEM_OK;
+}
+
+extern "C" bdem_status bdem_debug_system(bdem_sim* s, const double* phat, const double* qhat, double* g, double* diag,
+                                         double* bond_hess, int64_t* n_candidates) {
+  if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
+  if (!phat || !qhat) return fail(s, BDEM_E_INVALID, "phat and qhat are required");
+  DevArrays& d = s->d;
+  cudaStream_t st = s->stream;
+  size_t n = (size_t)s->n;
+  if (n) {
+    std::vector<double4> hp(n), hq(n);
+    for (size_t i = 0; i < n; ++i) {
+      hp[i] = make_double4(phat[3 * i], phat[3 * i + 1], phat[3 * i + 2], s->mass[i]);
+      hq[i] = make_double4(qhat[4 * i], qhat[4 * i + 1], qhat[4 * i + 2], qhat[4 * i + 3]);
+    }
+    CUDA_TRY(s, cudaMemcpy(d.hp, hp.data(), sizeof(double4) * n, cudaMemcpyHostToDevice));
+    CUDA_TRY(s, cudaMemcpy(d.hq, hq.data(), sizeof(double4) * n, cudaMemcpyHostToDevice));
+    CUDA_TRY(s, cudaMemcpyAsync(d.xp, d.x0p, sizeof(double4) * n, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(s, cudaMemcpyAsync(d.xq, d.x0q, sizeof(double4) * n, cudaMemcpyDeviceToDevice, st));
+  }
+  TRY(check_launch(s, launch_scene_reduce(d, RED_FORCE_ACTIVE, 0, st)));
+  if (d.k_self > 0.0 && d.n > 0) TRY(build_contacts(s));
+  else if (d.n > 0) CUDA_TRY(s, cudaMemsetAsync(d.c_start, 0, sizeof(int32_t) * (d.n + 1), st));
+  TRY(check_launch(s, launch_bond_grad(d, 1, st)));
+  TRY(check_launch(s, launch_particle_grad(d, 0, 1, st)));
+  TRY(check_launch(s, launch_bond_hess(d, 1, st)));
+  TRY(check_launch(s, launch_particle_hess(d, 0, 1, st)));
+  if (g && n) CUDA_TRY(s, cudaMemcpyAsync(g, d.g, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, st));
+  if (diag && n) {
+    TRY(dbg_reserve(s, 36 * n));
+    TRY(check_launch(s, launch_unpack_diag(d, s->dbg_buf, st)));
+    CUDA_TRY(s, cudaMemcpyAsync(diag, s->dbg_buf, sizeof(double) * 36 * n, cudaMemcpyDeviceToHost, st));
+    TRY(sync(s));
+  }
+  if (bond_hess && s->nb) {
+    TRY(dbg_reserve(s, 144 * (size_t)s->nb));
+    TRY(check_launch(s, launch_unpack_bond_hess(d, s->dbg_buf, st)));
+    CUDA_TRY(s, cudaMemcpyAsync(bond_hess, s->dbg_buf, sizeof(double) * 144 * s->nb, cudaMemcpyDeviceToHost, st));
+  }
+  if (n_candidates) {
+    int32_t c = 0;
+    if (n) CUDA_TRY(s, cudaMemcpyAsync(&c, d.c_start + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    TRY(sync(s));
+    *n_candidates = c / 2;  // directed entries: each pair appears in both lists
+  }
+  TRY(sync(s));
+  s->system_ready = true;
+  return BDEM_OK;
+}
+
+extern "C" bdem_status bdem_debug_matvec(bdem_sim* s, const double* x, double* y) {
+  if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
+  if (!s->system_ready) return fail(s, BDEM_E_INVALID, "call bdem_debug_system first");
+  if (!x || !y) return fail(s, BDEM_E_INVALID, "x and y are required");
+  size_t n = (size_t)s->n;
+  if (!n) return BDEM_OK;
+  DevArrays& d = s->d;
+  cudaStream_t st = s->stream;
+  TRY(dbg_reserve(s, 6 * n));
+  CUDA_TRY(s, cudaMemcpyAsync(s->dbg_buf, x, sizeof(double) * 6 * n, cudaMemcpyHostToDevice, st));
+  TRY(check_launch(s, launch_convert(s->dbg_buf, 1, d.vp_, !d.mixed, 6 * n, st)));
+  TRY(check_launch(s, launch_matvec(d, 0, st)));
+  TRY(check_launch(s, launch_convert(d.vq_, !d.mixed, s->dbg_buf, 1, 6 * n, st)));
+  CUDA_TRY(s, cudaMemcpyAsync(y, s->dbg_buf, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, st));
+  return sync(s);
+}
+
+extern "C" bdem_status bdem_debug_pcg(bdem_sim* s, const double* b, double eps_r, int32_t max_iter, double* dx,
+                                      int32_t* iters) {
+  if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
+  if (!s->system_ready) return fail(s, BDEM_E_INVALID, "call bdem_debug_system first");
+  if (!b || !dx || max_iter < 1 || !(eps_r >= 0.0)) return fail(s, BDEM_E_INVALID, "bad PCG arguments");
+  size_t n = (size_t)s->n;
+  if (!n) return BDEM_OK;
+  DevArrays d = s->d;
+  d.pcg_max = max_iter;
+  cudaStream_t st = s->stream;
+  // the solve removes kinematic rows: rebuild the diagonal blocks with them masked
+  TRY(check_launch(s, launch_particle_hess(d, 1, 1, st)));
+  std::vector<SceneCtl> ctl(s->n_scenes);
+  CUDA_TRY(s, cudaMemcpyAsync(ctl.data(), d.sc, sizeof(SceneCtl) * s->n_scenes, cudaMemcpyDeviceToHost, st));
+  TRY(sync(s));
+  for (auto& c : ctl) {
+    c.newton_active = 1;
+    c.eps_r = eps_r;
+  }
+  CUDA_TRY(s, cudaMemcpy(d.sc, ctl.data(), sizeof(SceneCtl) * s->n_scenes, cudaMemcpyHostToDevice));
+  TRY(dbg_reserve(s, 6 * n));
+  CUDA_TRY(s, cudaMemcpyAsync(s->dbg_buf, b, sizeof(double) * 6 * n, cudaMemcpyHostToDevice, st));
+  TRY(check_launch(s, launch_convert(s->dbg_buf, 1, d.vr, !d.mixed, 6 * n, st)));
+  TRY(run_pcg(s, d, 0, 1));
+  Counters c{};
+  TRY(read_counters(s, &c));
+  TRY(check_launch(s, launch_convert(d.vx, !d.mixed, s->dbg_buf, 1, 6 * n, st)));
+  CUDA_TRY(s, cudaMemcpyAsync(dx, s->dbg_buf, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(s, cudaMemcpyAsync(ctl.data(), d.sc, sizeof(SceneCtl) * s->n_scenes, cudaMemcpyDeviceToHost, st));
+  TRY(sync(s));
+  if (iters)
+    for (int sc = 0; sc < s->n_scenes; ++sc) iters[sc] = ctl[sc].pcg_iters;
+  // restore the unmasked diagonal blocks of the inspected system
+  TRY(check_launch(s, launch_particle_hess(s->d, 0, 1, st)));
+  return sync(s);
+}
+
+extern "C" bdem_status bdem_profile_enable(bdem_sim* s, int32_t on) {
+  if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
+  TRY(sync(s));
+  s->prof_on = on != 0;
+  s->prof = bdem_profile{};
+  return BDEM_OK;
+}
+
+extern "C" bdem_status bdem_profile_read(bdem_sim* s, bdem_profile* out) {
+  if (!s || !out) return fail(s, BDEM_E_INVALID, "NULL argument");
+  TRY(sync(s));
+  *out = s->prof;
+  return BDEM_OK;
+}

@@ -1,0 +1,117 @@
+// bdem_internal.h -- device data layout and kernel launchers shared by bdem_kernels.cu and bdem_api.cu.
+//
+// Layout in HBM (N particles, B bonds, S scenes; T = float in the mixed path, double in the FP64 path):
+//   particles, AoS of double4 (32 B, two per particle state): xp = (p, radius), xq = q       current iterate
+//             x0p, x0q committed state of the step; vp = (v, 0), vq = dq/dt; hp = (phat, mass), hq = qhat (raw);
+//             tp, tq line-search trial; coef = (c_p, c_q) = (m/dt^2, 8/5 m r^2/dt^2); g [N][6] FP64 gradient;
+//             D, Dinv [N][21] T packed symmetric diagonal blocks and their inverses (block Jacobi);
+//             PCG vectors [N][6] T (x, r, z, p, q)
+//   bonds, sorted by (i, j) with i < j (so each scene's bonds are contiguous):
+//             bij int2; brest double4 (d0, l0); bstiff double4 (kn, kt s^2, kb, ktw); bbrk double; bbroken u8;
+//             bg [B][9] FP64 gradient in (d = p_j - p_i, y_i, y_j);
+//             bM [B][36] T: the (i, j) off-diagonal 6x6 block in factored form (1/2 A sym6 | B/sqrt2 3x3 |
+//             C/sqrt2 3x3 | F 3x3 | 3 pad) of the clamped 9x9 Hessian in (u = (dp_j - dp_i)/sqrt2, y_i, y_j);
+//             bE [B][12] T: its E (y_i y_i) and G (y_j y_j) blocks, sym6 each
+//   incidence CSR inc_start [N+1], inc [2B] entries (bond << 1 | side), side 0: particle is i, 1: particle is j
+//   contact CSR c_start [N+1], c_nbr [C], c_blk [C] T4 (n, k) of the clamped contact Hessian k n n^T
+//   tiles: particle tiles of <= 256 rows inside one scene, bond tiles of <= 256 bonds inside one scene
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bdem {
+
+constexpr int kTile = 256;      // rows (particles or bonds) per tile = threads per block of tile kernels
+constexpr int kPartials = 4;    // partial sums per tile
+
+struct SceneCtl {
+  double g0, gnorm, eps_r, bnorm;
+  double rz, pq, alpha, beta;
+  double dphi, ls_alpha, gdx, pad0;
+  int32_t newton_active;        // still iterating Newton in this step
+  int32_t pcg_active;
+  int32_t pcg_iters;            // in the current solve
+  int32_t use_neg_grad;         // the PCG direction was not a descent direction
+  int32_t ls_state;             // 0 pending, 1 accepted, 2 failed
+  int32_t newton_iters;         // in this step
+  int32_t pcg_total, ls_halvings;
+  int32_t status;               // bdem_status of the scene in this step
+  int32_t bonds_broken;
+  int32_t pad1;                 // halvings in the current line search
+  int32_t pad2;                 // contact candidates of the step
+};
+
+struct Counters {               // small device-side summary read by the host after reductions
+  int32_t n_active;             // scenes with work left in the current loop
+  int32_t n_pending;
+  int32_t timeout;              // a device wait gave up
+  int32_t nonfinite;
+  unsigned int sync_count;      // grid barrier arrival counter
+  unsigned int sync_gen;        // grid barrier generation
+  int32_t pad[2];
+};
+
+struct DevArrays {
+  int32_t n, nb, n_scenes, n_ptiles, n_btiles;
+  int32_t mixed;                // T = float when 1, double when 0
+  int32_t c_cap;                // capacity of the contact arrays
+  int32_t hash_size;            // power of two
+  double dt, gx, gy, gz, tol, ground_z, k_ground, k_self, skin, cell_h;
+  int32_t newton_max, pcg_max, ls_max, pad0;
+  // particles
+  double4 *xp, *xq, *x0p, *x0q, *vp, *vq, *hp, *hq, *tp, *tq;
+  double2* coef;
+  int32_t* pscene;
+  uint8_t* kin;
+  double* g;
+  void *D, *Dinv;
+  void *vx, *vr, *vz, *vp_, *vq_;
+  // bonds
+  int2* bij;
+  double4 *brest, *bstiff;
+  double* bbrk;
+  uint8_t* bbroken;
+  int32_t* bscene;
+  double* bg;
+  void *bM, *bE;
+  int32_t *inc_start, *inc;
+  // contacts
+  int32_t *c_start, *c_nbr;
+  void* c_blk;
+  int32_t *cell_key, *hash_count, *hash_start, *hash_ids, *cnt_tmp;
+  int64_t* scan_tmp;
+  // tiles
+  int32_t *ptile_start, *ptile_scene, *ptile_begin;   // ptile_begin [S+1]: first tile of each scene
+  int32_t *btile_start, *btile_scene, *btile_begin;
+  double *part_p, *part_b;      // [tiles][kPartials]
+  SceneCtl* sc;
+  Counters* cnt;
+};
+
+// ---- launchers (bdem_kernels.cu); each returns the number of kernels launched -----------------------------------
+int launch_predict(const DevArrays& d, cudaStream_t s);
+int launch_contacts(const DevArrays& d, int stage, cudaStream_t s);  // stage 0: hash+count, 1: fill
+int launch_scan_counts(const DevArrays& d, const int32_t* counts, int32_t* starts, int n, cudaStream_t s);
+int launch_bond_grad(const DevArrays& d, int all_scenes, cudaStream_t s);
+int launch_particle_grad(const DevArrays& d, int mask_kin, int all_scenes, cudaStream_t s);
+int launch_bond_hess(const DevArrays& d, int all_scenes, cudaStream_t s);
+int launch_particle_hess(const DevArrays& d, int mask_kin, int all_scenes, cudaStream_t s);
+// reduction modes of the per-scene reduce kernel
+enum ReduceMode { RED_GRAD = 0, RED_GDX = 1, RED_LS = 2, RED_FORCE_ACTIVE = 3, RED_CAND = 4 };
+int launch_scene_reduce(const DevArrays& d, int mode, int k_iter, cudaStream_t s);
+// PCG: rhs_from_g = 1 uses b = -g; else b is read from vr (already T) and eps from sc.eps_r
+int launch_pcg(const DevArrays& d, int rhs_from_g, int mask_kin, int grid_blocks, cudaStream_t s, cudaError_t* err);
+int pcg_max_blocks(int mixed);
+int launch_gdx(const DevArrays& d, cudaStream_t s);
+int launch_ls_trial(const DevArrays& d, cudaStream_t s);
+int launch_ls_energy(const DevArrays& d, cudaStream_t s);
+int launch_ls_commit(const DevArrays& d, cudaStream_t s);
+int launch_finish(const DevArrays& d, cudaStream_t s);
+int launch_matvec(const DevArrays& d, int mask_kin, cudaStream_t s);  // vq_ = H vp_
+int launch_unpack_bond_hess(const DevArrays& d, double* out /*device [nb][144]*/, cudaStream_t s);
+int launch_unpack_diag(const DevArrays& d, double* out /*device [n][36]*/, cudaStream_t s);
+int launch_pack_state(const DevArrays& d, double* pos3, double* vel3, cudaStream_t s);          // committed -> [n][3]
+int launch_unpack_state(const DevArrays& d, const double* pos3, const double* vel3, cudaStream_t s);
+int launch_convert(const void* src, int src_double, void* dst, int dst_double, int64_t count, cudaStream_t s);
+
+}  // namespace bdem

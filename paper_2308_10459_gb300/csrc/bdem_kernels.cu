@@ -1,0 +1,1305 @@
+// bdem_kernels.cu -- sm_103a kernels of one implicit bonded-DEM time step (Alg. 3) and their launchers.
+//
+// Stage map (one Newton iteration of Alg. 3 / Alg. 2 on every active scene):
+//   k_predict            xhat = x_n + dt v_n, x_0 = (phat, qhat/|qhat|)                       (Alg. 3, Sec. 3.1)
+//   k_cell_* / k_contact spatial hash -> per-particle contact candidate lists at x_0             (Sec. 5.4)
+//   k_bond_grad          per-bond FP64 energy gradient in (d, y_i, y_j)                       (Sec. 3.2, 4.1)
+//   k_particle_grad      per-particle gather: inertia, gravity, ground, bonds, contacts -> g      (Sec. 4.1)
+//   k_bond_hess          per-bond reduced Riemannian Hessian, eigen-clamp, block store     (Eq. manifold-hessian, 5.2)
+//   k_particle_hess      diagonal blocks + block-Jacobi inverses                                (Sec. 5.3)
+//   k_pcg                persistent cooperative PCG, per-scene FP64 dot products              (Sec. 5.3)
+//   k_ls_*               exp-map retraction, term-wise energy difference, accept / halve  (Eq. manifold-update-1/2)
+//   k_finish / k_fracture velocity update, tensile-strain bond breaking                      (Alg. 3)
+// Every reduction is deterministic: per-tile partial sums (fixed order) reduced per scene in tile order.
+#include <math.h>
+
+#include "bdem_device.cuh"
+#include "bdem_internal.h"
+
+namespace bdem {
+
+// ================================================================================================
+// helpers
+// ================================================================================================
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// sum of K values over a 256-thread block; the result is returned to every thread
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K]) {
+  __shared__ double sh[K][kTile / 32];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[k][w] = v[k];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < kTile / 32; ++j) s += sh[k][j];
+    v[k] = s;
+  }
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <typename T>
+struct Vec6 {
+  T v[6];
+};
+
+template <typename T>
+__device__ __forceinline__ Vec6<T> load6(const T* base, int i) {
+  Vec6<T> r;
+  const T* p = base + 6 * (size_t)i;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r.v[k] = p[k];
+  return r;
+}
+
+// L2-coherent load (data written by other blocks of the same persistent kernel)
+template <typename T>
+__device__ __forceinline__ Vec6<T> load6_cg(const T* base, int i);
+template <>
+__device__ __forceinline__ Vec6<float> load6_cg<float>(const float* base, int i) {
+  const float2* p = reinterpret_cast<const float2*>(base + 6 * (size_t)i);
+  float2 a = __ldcg(p), b = __ldcg(p + 1), c = __ldcg(p + 2);
+  return Vec6<float>{{a.x, a.y, b.x, b.y, c.x, c.y}};
+}
+template <>
+__device__ __forceinline__ Vec6<double> load6_cg<double>(const double* base, int i) {
+  const double2* p = reinterpret_cast<const double2*>(base + 6 * (size_t)i);
+  double2 a = __ldcg(p), b = __ldcg(p + 1), c = __ldcg(p + 2);
+  return Vec6<double>{{a.x, a.y, b.x, b.y, c.x, c.y}};
+}
+
+template <typename T>
+__device__ __forceinline__ void store6(T* base, int i, const T (&v)[6]) {
+  T* p = base + 6 * (size_t)i;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) p[k] = v[k];
+}
+
+template <typename T>
+struct T4 {
+  T x, y, z, w;
+};
+
+// ================================================================================================
+// step initialisation and prediction
+// ================================================================================================
+
+__global__ void k_step_init(DevArrays d) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.n_scenes) return;
+  SceneCtl c = {};
+  c.newton_active = 1;
+  d.sc[s] = c;
+}
+
+// xhat = x_n + dt v_n; the initial guess x_0 = (phat, qhat/|qhat|) (Alg. 3; qhat itself stays unnormalised)
+__global__ void k_predict(DevArrays d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  double4 p = d.x0p[i], q = d.x0q[i], v = d.vp[i], u = d.vq[i];
+  double dt = d.dt;
+  double mass = d.hp[i].w;
+  double4 hp = make_double4(p.x + dt * v.x, p.y + dt * v.y, p.z + dt * v.z, mass);
+  double4 hq = make_double4(q.x + dt * u.x, q.y + dt * u.y, q.z + dt * u.z, q.w + dt * u.w);
+  double nq = sqrt(hq.x * hq.x + hq.y * hq.y + hq.z * hq.z + hq.w * hq.w);
+  d.hp[i] = hp;
+  d.hq[i] = hq;
+  d.xp[i] = make_double4(hp.x, hp.y, hp.z, p.w);
+  d.xq[i] = make_double4(hq.x / nq, hq.y / nq, hq.z / nq, hq.w / nq);
+}
+
+// ================================================================================================
+// spatial hash contact candidates (Sec. 5.4 repulsion between elements)
+// ================================================================================================
+
+__device__ __forceinline__ int3 cell_of(const DevArrays& d, double4 p) {
+  double ih = 1.0 / d.cell_h;
+  return make_int3((int)floor(p.x * ih), (int)floor(p.y * ih), (int)floor(p.z * ih));
+}
+
+__device__ __forceinline__ int hash_cell(int3 c, int scene, int size) {
+  unsigned h = (unsigned)c.x * 73856093u ^ (unsigned)c.y * 19349663u ^ (unsigned)c.z * 83492791u ^
+               (unsigned)scene * 2654435761u;
+  return (int)(h & (unsigned)(size - 1));
+}
+
+__global__ void k_cell_count(DevArrays d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  int key = hash_cell(cell_of(d, d.xp[i]), d.pscene[i], d.hash_size);
+  d.cell_key[i] = key;
+  atomicAdd(&d.hash_count[key], 1);
+}
+
+__global__ void k_cell_fill(DevArrays d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  int key = d.cell_key[i];
+  int pos = d.hash_start[key] + atomicAdd(&d.cnt_tmp[key], 1);
+  d.hash_ids[pos] = i;
+}
+
+// order each bucket by particle index so that candidate lists do not depend on atomic order
+__global__ void k_cell_sort(DevArrays d) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.hash_size) return;
+  int a = d.hash_start[k], b = d.hash_start[k + 1];
+  for (int x = a + 1; x < b; ++x) {
+    int v = d.hash_ids[x], y = x - 1;
+    while (y >= a && d.hash_ids[y] > v) {
+      d.hash_ids[y + 1] = d.hash_ids[y];
+      --y;
+    }
+    d.hash_ids[y + 1] = v;
+  }
+}
+
+__device__ __forceinline__ bool bonded_intact(const DevArrays& d, int i, int j) {
+  for (int e = d.inc_start[i]; e < d.inc_start[i + 1]; ++e) {
+    int ent = d.inc[e], b = ent >> 1;
+    int2 ij = d.bij[b];
+    int o = (ent & 1) ? ij.x : ij.y;
+    if (o == j && !d.bbroken[b]) return true;
+  }
+  return false;
+}
+
+// stage 0 counts, stage 1 fills (same traversal order: 27 cells in fixed order, buckets sorted by index)
+template <int FILL>
+__global__ void k_contact_scan(DevArrays d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  double4 pi = d.xp[i];
+  int si = d.pscene[i];
+  int3 ci = cell_of(d, pi);
+  int count = 0, out = FILL ? d.c_start[i] : 0;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        int3 c = make_int3(ci.x + dx, ci.y + dy, ci.z + dz);
+        int key = hash_cell(c, si, d.hash_size);
+        for (int e = d.hash_start[key]; e < d.hash_start[key + 1]; ++e) {
+          int j = d.hash_ids[e];
+          if (j == i || d.pscene[j] != si) continue;
+          double4 pj = d.xp[j];
+          int3 cj = cell_of(d, pj);
+          if (cj.x != c.x || cj.y != c.y || cj.z != c.z) continue;
+          double ex = pi.x - pj.x, ey = pi.y - pj.y, ez = pi.z - pj.z;
+          double lim = pi.w + pj.w + d.skin;
+          if (ex * ex + ey * ey + ez * ez >= lim * lim) continue;
+          if (bonded_intact(d, i, j)) continue;
+          if (FILL) {
+            if (out < d.c_cap) d.c_nbr[out] = j;
+            ++out;
+          } else {
+            ++count;
+          }
+        }
+      }
+  if (!FILL) d.cnt_tmp[i] = count;
+}
+
+// ---- exclusive scan of int32 counts (n) into starts (n+1) --------------------------------------------------------
+__global__ void k_scan_block_sums(const int32_t* in, int n, int64_t* bsum) {
+  __shared__ int64_t sh[1024];
+  int i = blockIdx.x * 1024 + threadIdx.x;
+  sh[threadIdx.x] = (i < n) ? in[i] : 0;
+  __syncthreads();
+  for (int s = 512; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bsum[blockIdx.x] = sh[0];
+}
+
+__global__ void k_scan_top(int64_t* bsum, int nb) {  // one block: exclusive scan of nb block sums in place
+  __shared__ int64_t carry;
+  __shared__ int64_t sh[1024];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += 1024) {
+    int i = base + threadIdx.x;
+    int64_t v = (i < nb) ? bsum[i] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+      int64_t t = (threadIdx.x >= off) ? sh[threadIdx.x - off] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < nb) bsum[i] = carry + sh[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += sh[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bsum[nb] = carry;
+}
+
+__global__ void k_scan_apply(const int32_t* in, int n, const int64_t* bsum, int nblk, int32_t* out) {
+  __shared__ int64_t sh[1024];
+  int i = blockIdx.x * 1024 + threadIdx.x;
+  int64_t v = (i < n) ? in[i] : 0;
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    int64_t t = (threadIdx.x >= off) ? sh[threadIdx.x - off] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  if (i < n) out[i] = (int32_t)(bsum[blockIdx.x] + sh[threadIdx.x] - v);
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = (int32_t)bsum[nblk];
+}
+
+// ================================================================================================
+// gradient
+// ================================================================================================
+
+__global__ void __launch_bounds__(kTile) k_bond_grad(DevArrays d, int all) {
+  int t = blockIdx.x;
+  int b = d.btile_start[t] + threadIdx.x;
+  if (b >= d.btile_start[t + 1]) return;
+  int s = d.btile_scene[t];
+  if (!all && !d.sc[s].newton_active) return;
+  double* g = d.bg + 9 * (size_t)b;
+  if (d.bbroken[b]) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) g[k] = 0.0;
+    return;
+  }
+  int2 ij = d.bij[b];
+  BondParams bp = load_bond(d.brest[b], d.bstiff[b]);
+  BondEval E;
+  bond_first_order(bp, to_v(d.xp[ij.x]), to_q(d.xq[ij.x]), to_v(d.xp[ij.y]), to_q(d.xq[ij.y]), E);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) g[k] = E.g[k];
+}
+
+// inertia + gravity + ground (particle term) reduced gradient: (c_p (p - phat) - m g + ground, -c_q vec(conj(q) qhat))
+__device__ __forceinline__ void particle_term_grad(const DevArrays& d, int i, double g[6]) {
+  double4 p = d.xp[i], q = d.xq[i], hp = d.hp[i], hq = d.hq[i];
+  double2 cf = d.coef[i];
+  double m = hp.w;
+  g[0] = cf.x * (p.x - hp.x) - m * d.gx;
+  g[1] = cf.x * (p.y - hp.y) - m * d.gy;
+  g[2] = cf.x * (p.z - hp.z) - m * d.gz;
+  if (d.k_ground > 0.0) {
+    double gd = p.z - d.ground_z - p.w;
+    if (gd < 0.0) g[2] += d.k_ground * gd;
+  }
+  V3<double> gy = gl_mul(to_q(q), to_q(hq));
+  g[3] = -cf.y * gy.x;
+  g[4] = -cf.y * gy.y;
+  g[5] = -cf.y * gy.z;
+}
+
+__global__ void __launch_bounds__(kTile) k_particle_grad(DevArrays d, int mask, int all) {
+  int t = blockIdx.x;
+  int i = d.ptile_start[t] + threadIdx.x;
+  int s = d.ptile_scene[t];
+  bool act = (i < d.ptile_start[t + 1]) && (all || d.sc[s].newton_active);
+  double acc[1] = {0.0};
+  if (act) {
+    double g[6];
+    particle_term_grad(d, i, g);
+    for (int e = d.inc_start[i]; e < d.inc_start[i + 1]; ++e) {
+      int ent = d.inc[e], b = ent >> 1;
+      if (d.bbroken[b]) continue;
+      const double* bg = d.bg + 9 * (size_t)b;
+      if (ent & 1) {  // particle is j: dV/dp_j = dV/dd
+        g[0] += bg[0]; g[1] += bg[1]; g[2] += bg[2];
+        g[3] += bg[6]; g[4] += bg[7]; g[5] += bg[8];
+      } else {        // particle is i: dV/dp_i = -dV/dd
+        g[0] -= bg[0]; g[1] -= bg[1]; g[2] -= bg[2];
+        g[3] += bg[3]; g[4] += bg[4]; g[5] += bg[5];
+      }
+    }
+    if (d.k_self > 0.0) {
+      double4 pi = d.xp[i];
+      for (int e = d.c_start[i]; e < d.c_start[i + 1]; ++e) {
+        int j = d.c_nbr[e];
+        double4 pj = d.xp[j];
+        double ex = pi.x - pj.x, ey = pi.y - pj.y, ez = pi.z - pj.z;
+        double dd = sqrt(ex * ex + ey * ey + ez * ez), R = pi.w + pj.w;
+        if (dd < R) {
+          double f = d.k_self * (dd - R) / dd;
+          g[0] += f * ex; g[1] += f * ey; g[2] += f * ez;
+        }
+      }
+    }
+    if (mask && d.kin[i])
+#pragma unroll
+      for (int k = 0; k < 6; ++k) g[k] = 0.0;
+    double* go = d.g + 6 * (size_t)i;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) { go[k] = g[k]; acc[0] += g[k] * g[k]; }
+  }
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) d.part_p[kPartials * t] = acc[0];
+}
+
+// ================================================================================================
+// Hessian
+// ================================================================================================
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_bond_hess(DevArrays d, int all) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= d.nb) return;
+  int s = d.bscene[b];
+  if (!all && !d.sc[s].newton_active) return;
+  T* M = reinterpret_cast<T*>(d.bM) + 36 * (size_t)b;
+  T* Eo = reinterpret_cast<T*>(d.bE) + 12 * (size_t)b;
+  if (d.bbroken[b]) {
+#pragma unroll
+    for (int k = 0; k < 36; ++k) M[k] = (T)0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) Eo[k] = (T)0;
+    return;
+  }
+  int2 ij = d.bij[b];
+  BondParams bp = load_bond(d.brest[b], d.bstiff[b]);
+  Q4<double> qi = to_q(d.xq[ij.x]), qj = to_q(d.xq[ij.y]);
+  BondEval E;
+  bond_first_order(bp, to_v(d.xp[ij.x]), qi, to_v(d.xp[ij.y]), qj, E);
+  T H[45];
+  bond_hessian<T>(bp, qi, qj, E, H);
+  // orthonormal coordinates u = d / sqrt(2): H_uu = 2 H_dd, H_uy = sqrt(2) H_dy; clamp; back to d
+  const T r2 = (T)1.4142135623730951;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int c = a; c < 3; ++c) H[sidx<9>(a, c)] *= (T)2;
+#pragma unroll
+    for (int c = 3; c < 9; ++c) H[sidx<9>(a, c)] *= r2;
+  }
+  eig_clamp<T, 9>(H);
+  const T ir2 = (T)0.7071067811865476;
+  // 1/2 A (= clamped H_dd), B/sqrt2, C/sqrt2, F, E, G
+  M[0] = (T)0.5 * H[sidx<9>(0, 0)]; M[1] = (T)0.5 * H[sidx<9>(0, 1)]; M[2] = (T)0.5 * H[sidx<9>(0, 2)];
+  M[3] = (T)0.5 * H[sidx<9>(1, 1)]; M[4] = (T)0.5 * H[sidx<9>(1, 2)]; M[5] = (T)0.5 * H[sidx<9>(2, 2)];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      M[6 + 3 * a + c] = ir2 * H[sidx<9>(a, 3 + c)];
+      M[15 + 3 * a + c] = ir2 * H[sidx<9>(a, 6 + c)];
+      M[24 + 3 * a + c] = H[sidx<9>(3 + a, 6 + c)];
+    }
+  M[33] = M[34] = M[35] = (T)0;
+  int k = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = a; c < 3; ++c) {
+      Eo[k] = H[sidx<9>(3 + a, 3 + c)];
+      Eo[6 + k] = H[sidx<9>(6 + a, 6 + c)];
+      ++k;
+    }
+}
+
+__device__ __forceinline__ int s3(int a, int c) { return sidx<3>(a, c); }
+
+template <typename T>
+__global__ void __launch_bounds__(kTile) k_particle_hess(DevArrays d, int mask, int all) {
+  int t = blockIdx.x;
+  int i = d.ptile_start[t] + threadIdx.x;
+  if (i >= d.ptile_start[t + 1]) return;
+  int s = d.ptile_scene[t];
+  if (!all && !d.sc[s].newton_active) return;
+  T D[21];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) D[k] = (T)0;
+  double4 p = d.xp[i], q = d.xq[i], hq = d.hq[i];
+  double2 cf = d.coef[i];
+  // particle term: diag(c_p I (+ k_ground e_z e_z^T), max(c_q q.qhat, 0) I), already clamped
+  double cy = cf.y * (q.x * hq.x + q.y * hq.y + q.z * hq.z + q.w * hq.w);
+  cy = cy > 0.0 ? cy : 0.0;
+  D[sidx<6>(0, 0)] = (T)cf.x;
+  D[sidx<6>(1, 1)] = (T)cf.x;
+  D[sidx<6>(2, 2)] = (T)cf.x;
+  if (d.k_ground > 0.0 && p.z - d.ground_z - p.w < 0.0) D[sidx<6>(2, 2)] += (T)d.k_ground;
+  D[sidx<6>(3, 3)] = (T)cy;
+  D[sidx<6>(4, 4)] = (T)cy;
+  D[sidx<6>(5, 5)] = (T)cy;
+  const T* Mall = reinterpret_cast<const T*>(d.bM);
+  const T* Eall = reinterpret_cast<const T*>(d.bE);
+  for (int e = d.inc_start[i]; e < d.inc_start[i + 1]; ++e) {
+    int ent = d.inc[e], b = ent >> 1;
+    if (d.bbroken[b]) continue;
+    const T* M = Mall + 36 * (size_t)b;
+    const T* Eb = Eall + 12 * (size_t)b + ((ent & 1) ? 6 : 0);
+    const T* X = M + ((ent & 1) ? 15 : 6);  // Cs for j, Bs for i
+    T sgn = (ent & 1) ? (T)1 : (T)-1;        // D_j += [[Ah, Cs], ...], D_i += [[Ah, -Bs], ...]
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int c = a; c < 3; ++c) {
+        D[sidx<6>(a, c)] += M[s3(a, c)];
+        D[sidx<6>(3 + a, 3 + c)] += Eb[s3(a, c)];
+      }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) D[sidx<6>(a, 3 + c)] += sgn * X[3 * a + c];
+  }
+  if (d.k_self > 0.0) {
+    T4<T>* blk = reinterpret_cast<T4<T>*>(d.c_blk);
+    for (int e = d.c_start[i]; e < d.c_start[i + 1]; ++e) {
+      int j = d.c_nbr[e];
+      double4 pj = d.xp[j];
+      double ex = p.x - pj.x, ey = p.y - pj.y, ez = p.z - pj.z;
+      double dd = sqrt(ex * ex + ey * ey + ez * ez), R = p.w + pj.w;
+      T4<T> o = {(T)0, (T)0, (T)0, (T)0};
+      if (dd < R) {  // clamped penalty Hessian k n n^T (the transverse part k (d - R)/d < 0 is removed)
+        T n[3] = {(T)(ex / dd), (T)(ey / dd), (T)(ez / dd)};
+        T k = (T)d.k_self;
+        o = {n[0], n[1], n[2], k};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int c = a; c < 3; ++c) D[sidx<6>(a, c)] += k * n[a] * n[c];
+      }
+      blk[e] = o;
+    }
+  }
+  if (mask && d.kin[i]) {
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+      for (int c = a; c < 6; ++c) D[sidx<6>(a, c)] = (a == c) ? (T)1 : (T)0;
+  }
+  T* Do = reinterpret_cast<T*>(d.D) + 21 * (size_t)i;
+  T* Io = reinterpret_cast<T*>(d.Dinv) + 21 * (size_t)i;
+  T I[21];
+  spd_inverse6<T>(D, I);
+#pragma unroll
+  for (int k = 0; k < 21; ++k) { Do[k] = D[k]; Io[k] = I[k]; }
+}
+
+// ================================================================================================
+// block-sparse matrix-vector product, one row (particle) per thread: y_i = D_i x_i + sum_b H_ib x_other + contacts
+// ================================================================================================
+
+template <typename T>
+__device__ __forceinline__ void sym6_mul(const T* P, const T (&x)[6], T (&y)[6]) {
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    T s = 0;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s += P[sidx<6>(a, c)] * x[c];
+    y[a] = s;
+  }
+}
+
+template <typename T, bool CG>
+__device__ __forceinline__ void row_matvec(const DevArrays& d, int i, const T* x, T (&y)[6], int mask) {
+  if (mask && d.kin[i]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) y[k] = (T)0;
+    return;
+  }
+  Vec6<T> xi = CG ? load6_cg<T>(x, i) : load6<T>(x, i);
+  const T* Dp = reinterpret_cast<const T*>(d.D) + 21 * (size_t)i;
+  sym6_mul<T>(Dp, xi.v, y);
+  const T* Mall = reinterpret_cast<const T*>(d.bM);
+  for (int e = d.inc_start[i]; e < d.inc_start[i + 1]; ++e) {
+    int ent = d.inc[e], b = ent >> 1;
+    int2 ij = d.bij[b];
+    int side = ent & 1;
+    int o = side ? ij.x : ij.y;
+    Vec6<T> xo = CG ? load6_cg<T>(x, o) : load6<T>(x, o);
+    const T* M = Mall + 36 * (size_t)b;
+    T a0 = xo.v[0], a1 = xo.v[1], a2 = xo.v[2], b0 = xo.v[3], b1 = xo.v[4], b2 = xo.v[5];
+    // -1/2 A a
+    T Ah[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) Ah[k] = M[k];
+    y[0] -= Ah[0] * a0 + Ah[1] * a1 + Ah[2] * a2;
+    y[1] -= Ah[1] * a0 + Ah[3] * a1 + Ah[4] * a2;
+    y[2] -= Ah[2] * a0 + Ah[4] * a1 + Ah[5] * a2;
+    const T* Bs = M + 6;
+    const T* Cs = M + 15;
+    const T* F = M + 24;
+    if (!side) {  // i = bi: H_ij = [[-Ah, -Cs], [Bs^T, F]]
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        y[r] -= Cs[3 * r] * b0 + Cs[3 * r + 1] * b1 + Cs[3 * r + 2] * b2;
+        y[3 + r] += Bs[r] * a0 + Bs[3 + r] * a1 + Bs[6 + r] * a2 + F[3 * r] * b0 + F[3 * r + 1] * b1 + F[3 * r + 2] * b2;
+      }
+    } else {      // i = bj: H_ij^T = [[-Ah, Bs], [-Cs^T, F^T]]
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        y[r] += Bs[3 * r] * b0 + Bs[3 * r + 1] * b1 + Bs[3 * r + 2] * b2;
+        y[3 + r] += -(Cs[r] * a0 + Cs[3 + r] * a1 + Cs[6 + r] * a2) + F[r] * b0 + F[3 + r] * b1 + F[6 + r] * b2;
+      }
+    }
+  }
+  if (d.k_self > 0.0) {
+    const T4<T>* blk = reinterpret_cast<const T4<T>*>(d.c_blk);
+    for (int e = d.c_start[i]; e < d.c_start[i + 1]; ++e) {
+      T4<T> c = blk[e];
+      if (c.w == (T)0) continue;
+      Vec6<T> xo = CG ? load6_cg<T>(x, d.c_nbr[e]) : load6<T>(x, d.c_nbr[e]);
+      T t = c.w * (c.x * xo.v[0] + c.y * xo.v[1] + c.z * xo.v[2]);
+      y[0] -= t * c.x;
+      y[1] -= t * c.y;
+      y[2] -= t * c.z;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTile) k_matvec(DevArrays d, int mask) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  T y[6];
+  row_matvec<T, false>(d, i, reinterpret_cast<const T*>(d.vp_), y, mask);
+  store6<T>(reinterpret_cast<T*>(d.vq_), i, y);
+}
+
+// ================================================================================================
+// persistent PCG (Sec. 5.3): block-Jacobi preconditioner, stop at |r| <= eps_r |b| or the iteration cap
+// ================================================================================================
+
+// grid barrier with a bounded wait; the last block to arrive runs `work` (whole block) before releasing the others
+template <typename F>
+__device__ bool grid_barrier(const DevArrays& d, F&& work) {
+  __shared__ int s_last, s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned gen = ld_acquire(&d.cnt->sync_gen);
+    __threadfence();
+    unsigned arrived = atomicAdd(&d.cnt->sync_count, 1u) + 1u;
+    s_last = (arrived == gridDim.x);
+    s_ok = 1;
+    if (!s_last) {
+      unsigned long long t0 = global_ns();
+      while (ld_acquire(&d.cnt->sync_gen) == gen) {
+        __nanosleep(32);
+        if (global_ns() - t0 > 2000000000ull) {  // 2 s: give up, flag the timeout
+          s_ok = 0;
+          atomicExch(&d.cnt->timeout, 1);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  if (s_last) {
+    work();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      d.cnt->sync_count = 0u;
+      __threadfence();
+      atomicAdd(&d.cnt->sync_gen, 1u);
+    }
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// deterministic per-scene sums of partial slot `k` over a scene's particle tiles, one warp per scene
+__device__ __forceinline__ double scene_partial(const DevArrays& d, int s, int k, int lane) {
+  int a = d.ptile_begin[s], b = d.ptile_begin[s + 1];
+  double v = 0.0;
+  for (int t = a + lane; t < b; t += 32) v += __ldcg(d.part_p + kPartials * t + k);
+  return warp_sum(v);
+}
+
+enum PcgPhase { PH_INIT = 0, PH_A = 1, PH_B = 2 };
+
+__device__ void pcg_reduce(const DevArrays& d, int phase) {
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __shared__ int s_active[kTile / 32];
+  int active = 0;
+  for (int s = warp; s < d.n_scenes; s += nw) {
+    // volatile: another block may have written this scene's control block since this SM last cached it
+    volatile SceneCtl* c = d.sc + s;
+    if (phase == PH_INIT) {
+      double rr = scene_partial(d, s, 0, lane), rz = scene_partial(d, s, 1, lane);
+      if (lane == 0) {
+        c->bnorm = sqrt(rr);
+        c->rz = rz;
+        c->pcg_iters = 0;
+        int a = c->newton_active && (sqrt(rr) > c->eps_r * c->bnorm) && d.pcg_max > 0;
+        c->pcg_active = a;
+        active += a;
+      }
+    } else if (phase == PH_A) {
+      double pq = scene_partial(d, s, 0, lane);
+      if (lane == 0 && c->pcg_active) {
+        c->pcg_iters += 1;
+        c->pq = pq;
+        if (!(pq > 0.0)) {
+          c->pcg_active = 0;
+          c->alpha = 0.0;
+        } else {
+          c->alpha = c->rz / pq;
+        }
+      }
+      if (lane == 0) active += c->pcg_active;
+    } else {
+      double rr = scene_partial(d, s, 0, lane), rz = scene_partial(d, s, 1, lane);
+      if (lane == 0 && c->pcg_active) {
+        if (sqrt(rr) <= c->eps_r * c->bnorm || c->pcg_iters >= d.pcg_max) {
+          c->pcg_active = 0;
+          c->beta = 0.0;
+        } else {
+          c->beta = rz / c->rz;
+          c->rz = rz;
+        }
+      }
+      if (lane == 0) active += c->pcg_active;
+    }
+  }
+  if (lane == 0) s_active[warp] = active;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tot = 0;
+    for (int w = 0; w < nw; ++w) tot += s_active[w];
+    d.cnt->n_active = tot;
+  }
+}
+
+// PH_A sets the per-scene "active" flag before PH_B; a scene that stops in PH_A (breakdown) skips the update
+template <typename T>
+__global__ void __launch_bounds__(kTile) k_pcg(DevArrays d, int rhs_from_g, int mask) {
+  T* X = reinterpret_cast<T*>(d.vx);
+  T* R = reinterpret_cast<T*>(d.vr);
+  T* Z = reinterpret_cast<T*>(d.vz);
+  T* P = reinterpret_cast<T*>(d.vp_);
+  T* Q = reinterpret_cast<T*>(d.vq_);
+  const T* Dinv = reinterpret_cast<const T*>(d.Dinv);
+  // ---- init: x = 0, r = b, z = M^-1 r, p = z
+  for (int t = blockIdx.x; t < d.n_ptiles; t += gridDim.x) {
+    int i = d.ptile_start[t] + threadIdx.x;
+    int s = d.ptile_scene[t];
+    double acc[2] = {0.0, 0.0};
+    if (i < d.ptile_start[t + 1] && d.sc[s].newton_active) {
+      T r[6], z[6], zero[6] = {0, 0, 0, 0, 0, 0};
+      if (rhs_from_g) {
+        const double* g = d.g + 6 * (size_t)i;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) r[k] = (T)(-g[k]);
+      } else {
+        Vec6<T> b = load6<T>(R, i);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) r[k] = b.v[k];
+      }
+      if (mask && d.kin[i])
+#pragma unroll
+        for (int k = 0; k < 6; ++k) r[k] = (T)0;
+      sym6_mul<T>(Dinv + 21 * (size_t)i, r, z);
+      store6<T>(X, i, zero);
+      store6<T>(R, i, r);
+      store6<T>(Z, i, z);
+      store6<T>(P, i, z);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        acc[0] += (double)r[k] * (double)r[k];
+        acc[1] += (double)r[k] * (double)z[k];
+      }
+    }
+    block_sum<2>(acc);
+    if (threadIdx.x == 0) {
+      d.part_p[kPartials * t] = acc[0];
+      d.part_p[kPartials * t + 1] = acc[1];
+    }
+  }
+  if (!grid_barrier(d, [&] { pcg_reduce(d, PH_INIT); })) return;
+  for (;;) {
+    if (__ldcg(&d.cnt->n_active) == 0 || __ldcg(&d.cnt->timeout)) break;
+    // ---- A: q = H p, p.q
+    for (int t = blockIdx.x; t < d.n_ptiles; t += gridDim.x) {
+      int i = d.ptile_start[t] + threadIdx.x;
+      int s = d.ptile_scene[t];
+      double acc[1] = {0.0};
+      if (i < d.ptile_start[t + 1] && __ldcg(&d.sc[s].pcg_active)) {
+        T y[6];
+        row_matvec<T, true>(d, i, P, y, mask);
+        store6<T>(Q, i, y);
+        Vec6<T> p = load6_cg<T>(P, i);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc[0] += (double)p.v[k] * (double)y[k];
+      }
+      block_sum<1>(acc);
+      if (threadIdx.x == 0) d.part_p[kPartials * t] = acc[0];
+    }
+    if (!grid_barrier(d, [&] { pcg_reduce(d, PH_A); })) return;
+    // ---- B: x += alpha p, r -= alpha q, z = M^-1 r, r.r, r.z
+    for (int t = blockIdx.x; t < d.n_ptiles; t += gridDim.x) {
+      int i = d.ptile_start[t] + threadIdx.x;
+      int s = d.ptile_scene[t];
+      double acc[2] = {0.0, 0.0};
+      if (i < d.ptile_start[t + 1] && __ldcg(&d.sc[s].pcg_active)) {
+        T al = (T)__ldcg(&d.sc[s].alpha);
+        Vec6<T> x = load6<T>(X, i), r = load6<T>(R, i), p = load6_cg<T>(P, i), q = load6<T>(Q, i);
+        T xn[6], rn[6], z[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          xn[k] = x.v[k] + al * p.v[k];
+          rn[k] = r.v[k] - al * q.v[k];
+        }
+        sym6_mul<T>(Dinv + 21 * (size_t)i, rn, z);
+        store6<T>(X, i, xn);
+        store6<T>(R, i, rn);
+        store6<T>(Z, i, z);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          acc[0] += (double)rn[k] * (double)rn[k];
+          acc[1] += (double)rn[k] * (double)z[k];
+        }
+      }
+      block_sum<2>(acc);
+      if (threadIdx.x == 0) {
+        d.part_p[kPartials * t] = acc[0];
+        d.part_p[kPartials * t + 1] = acc[1];
+      }
+    }
+    if (!grid_barrier(d, [&] { pcg_reduce(d, PH_B); })) return;
+    // ---- C: p = z + beta p
+    for (int t = blockIdx.x; t < d.n_ptiles; t += gridDim.x) {
+      int i = d.ptile_start[t] + threadIdx.x;
+      int s = d.ptile_scene[t];
+      if (i < d.ptile_start[t + 1] && __ldcg(&d.sc[s].pcg_active)) {
+        T be = (T)__ldcg(&d.sc[s].beta);
+        Vec6<T> z = load6<T>(Z, i), p = load6_cg<T>(P, i);
+        T pn[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) pn[k] = z.v[k] + be * p.v[k];
+        store6<T>(P, i, pn);
+      }
+    }
+    if (!grid_barrier(d, [] {})) return;
+  }
+}
+
+// ================================================================================================
+// per-scene reductions outside the PCG (Newton residual, descent check, line search decision)
+// ================================================================================================
+
+__global__ void k_scene_reduce(DevArrays d, int mode, int k_iter) {
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __shared__ int s_cnt[32];
+  int cnt = 0;
+  for (int s = warp; s < d.n_scenes; s += nw) {
+    SceneCtl* c = d.sc + s;
+    double v = scene_partial(d, s, 0, lane);
+    if (mode == RED_LS) {
+      int a = d.btile_begin[s], b = d.btile_begin[s + 1];
+      double w = 0.0;
+      for (int t = a + lane; t < b; t += 32) w += d.part_b[kPartials * t];
+      v += warp_sum(w);
+    }
+    if (lane != 0) continue;
+    if (mode == RED_GRAD) {
+      if (!c->newton_active) continue;
+      if (!isfinite(v)) {
+        c->newton_active = 0;
+        c->status = 6;
+        d.cnt->nonfinite = 1;
+        continue;
+      }
+      double gn = sqrt(v);
+      if (k_iter == 0) c->g0 = gn;
+      c->gnorm = gn;
+      if (gn <= d.tol * c->g0) {
+        c->newton_active = 0;
+      } else if (c->newton_iters >= d.newton_max) {
+        c->newton_active = 0;
+        c->status = 4;
+      } else {
+        c->eps_r = fmin(0.5, sqrt(gn));
+        ++cnt;
+      }
+    } else if (mode == RED_GDX) {
+      if (!c->newton_active) continue;
+      c->gdx = v;
+      c->use_neg_grad = !(v < 0.0);
+      c->ls_alpha = 1.0;
+      c->ls_state = 0;
+      c->pad1 = 0;  // halvings in this line search
+      c->newton_iters += 1;
+      c->pcg_total += c->pcg_iters;
+      ++cnt;
+    } else if (mode == RED_LS) {
+      if (!c->newton_active || c->ls_state != 0) continue;
+      c->dphi = v;
+      if (v <= 0.0) {
+        c->ls_state = 1;
+      } else {
+        if (c->pad1 >= d.ls_max) {
+          c->ls_state = 2;
+          c->status = c->status > 5 ? c->status : 5;
+          c->newton_active = 0;
+        } else {
+          c->pad1 += 1;
+          c->ls_halvings += 1;
+          c->ls_alpha *= 0.5;
+          ++cnt;
+        }
+      }
+    } else if (mode == RED_FORCE_ACTIVE) {
+      c->newton_active = 1;
+      ++cnt;
+    } else if (mode == RED_CAND) {
+      int a = d.ptile_start[d.ptile_begin[s]], b = d.ptile_start[d.ptile_begin[s + 1]];
+      c->pad2 = d.c_start[b] - d.c_start[a];
+    }
+  }
+  if (lane == 0) s_cnt[warp] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tot = 0;
+    for (int w = 0; w < nw; ++w) tot += s_cnt[w];
+    if (mode == RED_LS) d.cnt->n_pending = tot;
+    else d.cnt->n_active = tot;
+  }
+}
+
+// partial g . dx for the descent check
+template <typename T>
+__global__ void __launch_bounds__(kTile) k_gdx(DevArrays d) {
+  int t = blockIdx.x;
+  int i = d.ptile_start[t] + threadIdx.x;
+  int s = d.ptile_scene[t];
+  double acc[1] = {0.0};
+  if (i < d.ptile_start[t + 1] && d.sc[s].newton_active) {
+    const double* g = d.g + 6 * (size_t)i;
+    Vec6<T> x = load6<T>(reinterpret_cast<const T*>(d.vx), i);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[0] += g[k] * (double)x.v[k];
+  }
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) d.part_p[kPartials * t] = acc[0];
+}
+
+// ================================================================================================
+// line search along the retraction (Eq. manifold-update-1/2, then normalisation)
+// ================================================================================================
+
+template <typename T>
+__global__ void k_ls_trial(DevArrays d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  const SceneCtl& c = d.sc[d.pscene[i]];
+  if (!c.newton_active || c.ls_state != 0) return;
+  double4 p = d.xp[i], q = d.xq[i];
+  if (d.kin[i]) {
+    d.tp[i] = p;
+    d.tq[i] = q;
+    return;
+  }
+  double st[6];
+  if (c.use_neg_grad) {
+    const double* g = d.g + 6 * (size_t)i;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) st[k] = -g[k];
+  } else {
+    Vec6<T> x = load6<T>(reinterpret_cast<const T*>(d.vx), i);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) st[k] = (double)x.v[k];
+  }
+  double al = c.ls_alpha;
+  double4 pn = make_double4(p.x + al * st[0], p.y + al * st[1], p.z + al * st[2], p.w);
+  // dq = G_l(q)^T (alpha y) = q (x) (alpha y, 0)
+  Q4<double> qq = to_q(q);
+  Q4<double> dq = qmul(qq, Q4<double>{al * st[3], al * st[4], al * st[5], 0.0});
+  double a = sqrt(qdot(dq, dq));
+  Q4<double> qn = qq;
+  if (a != 0.0) {
+    double sa, ca;
+    sincos(a, &sa, &ca);
+    double f = sa / a;
+    qn = {qq.x * ca + dq.x * f, qq.y * ca + dq.y * f, qq.z * ca + dq.z * f, qq.w * ca + dq.w * f};
+  }
+  double nq = sqrt(qdot(qn, qn));
+  d.tp[i] = pn;
+  d.tq[i] = make_double4(qn.x / nq, qn.y / nq, qn.z / nq, qn.w / nq);
+}
+
+// particle-term difference with dp = p1 - p0: c dp.((p0 - phat) + dp/2) - m g.dp (+ ground), the same for q
+__device__ __forceinline__ double particle_dphi(const DevArrays& d, int i) {
+  double4 p0 = d.xp[i], q0 = d.xq[i], p1 = d.tp[i], q1 = d.tq[i], hp = d.hp[i], hq = d.hq[i];
+  double2 cf = d.coef[i];
+  double m = hp.w;
+  double dpx = p1.x - p0.x, dpy = p1.y - p0.y, dpz = p1.z - p0.z;
+  double e = cf.x * (dpx * ((p0.x - hp.x) + 0.5 * dpx) + dpy * ((p0.y - hp.y) + 0.5 * dpy) + dpz * ((p0.z - hp.z) + 0.5 * dpz));
+  e -= m * (d.gx * dpx + d.gy * dpy + d.gz * dpz);
+  double dqx = q1.x - q0.x, dqy = q1.y - q0.y, dqz = q1.z - q0.z, dqw = q1.w - q0.w;
+  e += cf.y * (dqx * ((q0.x - hq.x) + 0.5 * dqx) + dqy * ((q0.y - hq.y) + 0.5 * dqy) + dqz * ((q0.z - hq.z) + 0.5 * dqz) +
+               dqw * ((q0.w - hq.w) + 0.5 * dqw));
+  if (d.k_ground > 0.0) {
+    double g0 = p0.z - d.ground_z - p0.w, g1 = p1.z - d.ground_z - p0.w;
+    if (g0 < 0.0 && g1 < 0.0) e += 0.5 * d.k_ground * dpz * (g0 + g1);
+    else e += 0.5 * d.k_ground * ((g1 < 0.0 ? g1 * g1 : 0.0) - (g0 < 0.0 ? g0 * g0 : 0.0));
+  }
+  return e;
+}
+
+// contact difference; when overlapping at both states 1/2 k (d1 - d0)(e1 + e0), d1 - d0 = (x1 - x0).(x1 + x0)/(d1 + d0)
+__device__ __forceinline__ double contact_dphi(const DevArrays& d, int i, int j) {
+  double4 a0 = d.xp[i], b0 = d.xp[j], a1 = d.tp[i], b1 = d.tp[j];
+  double x0[3] = {a0.x - b0.x, a0.y - b0.y, a0.z - b0.z}, x1[3] = {a1.x - b1.x, a1.y - b1.y, a1.z - b1.z};
+  double dx[3] = {(a1.x - a0.x) - (b1.x - b0.x), (a1.y - a0.y) - (b1.y - b0.y), (a1.z - a0.z) - (b1.z - b0.z)};
+  double d0 = sqrt(x0[0] * x0[0] + x0[1] * x0[1] + x0[2] * x0[2]);
+  double d1 = sqrt(x1[0] * x1[0] + x1[1] * x1[1] + x1[2] * x1[2]);
+  double R = a0.w + b0.w, k = d.k_self;
+  if (d0 < R && d1 < R) {
+    double dd = (dx[0] * (x0[0] + x1[0]) + dx[1] * (x0[1] + x1[1]) + dx[2] * (x0[2] + x1[2])) / (d0 + d1);
+    return 0.5 * k * dd * ((d0 - R) + (d1 - R));
+  }
+  double e1 = d1 < R ? 0.5 * k * (d1 - R) * (d1 - R) : 0.0;
+  double e0 = d0 < R ? 0.5 * k * (d0 - R) * (d0 - R) : 0.0;
+  return e1 - e0;
+}
+
+__global__ void __launch_bounds__(kTile) k_ls_energy_particles(DevArrays d) {
+  int t = blockIdx.x;
+  int i = d.ptile_start[t] + threadIdx.x;
+  int s = d.ptile_scene[t];
+  double acc[1] = {0.0};
+  if (i < d.ptile_start[t + 1] && d.sc[s].newton_active && d.sc[s].ls_state == 0) {
+    acc[0] = particle_dphi(d, i);
+    if (d.k_self > 0.0)
+      for (int e = d.c_start[i]; e < d.c_start[i + 1]; ++e) {
+        int j = d.c_nbr[e];
+        if (j > i) acc[0] += contact_dphi(d, i, j);
+      }
+  }
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) d.part_p[kPartials * t] = acc[0];
+}
+
+// bond difference: stretch via l1 - l0 = (d1 - d0).(d1 + d0)/(l1 + l0); bend-twist via the bilinear identity
+// r1 - r0 = vec((conj q_j1 - conj q_j0) q_i1) + vec(conj q_j0 (q_i1 - q_i0)); shear differenced directly
+__global__ void __launch_bounds__(kTile) k_ls_energy_bonds(DevArrays d) {
+  int t = blockIdx.x;
+  int b = d.btile_start[t] + threadIdx.x;
+  int s = d.btile_scene[t];
+  double acc[1] = {0.0};
+  if (b < d.btile_start[t + 1] && d.sc[s].newton_active && d.sc[s].ls_state == 0 && !d.bbroken[b]) {
+    int2 ij = d.bij[b];
+    BondParams bp = load_bond(d.brest[b], d.bstiff[b]);
+    double4 pi0 = d.xp[ij.x], pj0 = d.xp[ij.y], pi1 = d.tp[ij.x], pj1 = d.tp[ij.y];
+    Q4<double> qi0 = to_q(d.xq[ij.x]), qj0 = to_q(d.xq[ij.y]), qi1 = to_q(d.tq[ij.x]), qj1 = to_q(d.tq[ij.y]);
+    // stretch
+    V3<double> dd0 = to_v(pj0) - to_v(pi0), dd1 = to_v(pj1) - to_v(pi1);
+    V3<double> ddd = (to_v(pj1) - to_v(pj0)) - (to_v(pi1) - to_v(pi0));
+    double l0 = sqrt(dot(dd0, dd0)), l1 = sqrt(dot(dd1, dd1));
+    double dl = dot(ddd, dd0 + dd1) / (l0 + l1);
+    double e = 0.5 * bp.kn * dl * ((l0 - bp.l0) + (l1 - bp.l0));
+    // bend-twist
+    V3<double> r0 = qvec(qmul(qconj(qj0), qi0)), r1 = qvec(qmul(qconj(qj1), qi1));
+    Q4<double> dqj = {qj1.x - qj0.x, qj1.y - qj0.y, qj1.z - qj0.z, qj1.w - qj0.w};
+    Q4<double> dqi = {qi1.x - qi0.x, qi1.y - qi0.y, qi1.z - qi0.z, qi1.w - qi0.w};
+    V3<double> dr = qvec(qmul(qconj(dqj), qi1)) + qvec(qmul(qconj(qj0), dqi));
+    e += 0.5 * dot(dr, kmul(bp, r0 + r1));
+    // shear
+    BondEval E0, E1;
+    bond_first_order(bp, to_v(pi0), qi0, to_v(pj0), qj0, E0);
+    bond_first_order(bp, to_v(pi1), qi1, to_v(pj1), qj1, E1);
+    e += E1.e_shear - E0.e_shear;
+    acc[0] = e;
+  }
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) d.part_b[kPartials * t] = acc[0];
+}
+
+__global__ void k_ls_commit(DevArrays d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  const SceneCtl& c = d.sc[d.pscene[i]];
+  if (c.ls_state == 1 && c.newton_active) {
+    d.xp[i] = d.tp[i];
+    d.xq[i] = d.tq[i];
+  }
+}
+
+// ================================================================================================
+// end of step: velocities (Alg. 3) and tensile-strain fracture (bond state update)
+// ================================================================================================
+
+__global__ void k_finish(DevArrays d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  double4 p = d.xp[i], q = d.xq[i], p0 = d.x0p[i], q0 = d.x0q[i];
+  double idt = 1.0 / d.dt;
+  d.vp[i] = make_double4((p.x - p0.x) * idt, (p.y - p0.y) * idt, (p.z - p0.z) * idt, 0.0);
+  d.vq[i] = make_double4((q.x - q0.x) * idt, (q.y - q0.y) * idt, (q.z - q0.z) * idt, (q.w - q0.w) * idt);
+  d.x0p[i] = p;
+  d.x0q[i] = q;
+}
+
+__global__ void k_fracture(DevArrays d) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= d.nb || d.bbroken[b]) return;
+  int2 ij = d.bij[b];
+  double4 pi = d.x0p[ij.x], pj = d.x0p[ij.y];
+  double ex = pj.x - pi.x, ey = pj.y - pi.y, ez = pj.z - pi.z;
+  double l0 = d.brest[b].w;
+  double strain = (sqrt(ex * ex + ey * ey + ez * ez) - l0) / l0;
+  if (strain > d.bbrk[b]) {
+    d.bbroken[b] = 1;
+    atomicAdd(&d.sc[d.bscene[b]].bonds_broken, 1);
+  }
+}
+
+// ================================================================================================
+// inspection helpers
+// ================================================================================================
+
+template <typename T>
+__global__ void k_unpack_bond_hess(DevArrays d, double* out) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= d.nb) return;
+  const T* M = reinterpret_cast<const T*>(d.bM) + 36 * (size_t)b;
+  const T* E = reinterpret_cast<const T*>(d.bE) + 12 * (size_t)b;
+  double H[12][12];
+  for (int a = 0; a < 12; ++a)
+    for (int c = 0; c < 12; ++c) H[a][c] = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) {
+      double ah = M[s3(a, c)], bs = M[6 + 3 * a + c], cs = M[15 + 3 * a + c], f = M[24 + 3 * a + c];
+      double e = E[s3(a, c)], g = E[6 + s3(a, c)];
+      H[a][c] = ah; H[6 + a][6 + c] = ah; H[a][6 + c] = -ah; H[6 + a][c] = -ah;   // p_i, p_j
+      H[a][3 + c] = -bs; H[3 + c][a] = -bs;                                        // p_i y_i
+      H[6 + a][3 + c] = bs; H[3 + c][6 + a] = bs;                                  // p_j y_i
+      H[a][9 + c] = -cs; H[9 + c][a] = -cs;                                        // p_i y_j
+      H[6 + a][9 + c] = cs; H[9 + c][6 + a] = cs;                                  // p_j y_j
+      H[3 + a][3 + c] = e; H[9 + a][9 + c] = g;
+      H[3 + a][9 + c] = f; H[9 + c][3 + a] = f;
+    }
+  double* o = out + 144 * (size_t)b;
+  for (int a = 0; a < 12; ++a)
+    for (int c = 0; c < 12; ++c) o[12 * a + c] = H[a][c];
+}
+
+template <typename T>
+__global__ void k_unpack_diag(DevArrays d, double* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  const T* D = reinterpret_cast<const T*>(d.D) + 21 * (size_t)i;
+  for (int a = 0; a < 6; ++a)
+    for (int c = 0; c < 6; ++c) out[36 * (size_t)i + 6 * a + c] = (double)D[sidx<6>(a, c)];
+}
+
+__global__ void k_convert(const void* src, int sd, void* dst, int dd, int64_t count) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  double v = sd ? reinterpret_cast<const double*>(src)[k] : (double)reinterpret_cast<const float*>(src)[k];
+  if (dd) reinterpret_cast<double*>(dst)[k] = v;
+  else reinterpret_cast<float*>(dst)[k] = (float)v;
+}
+
+// ================================================================================================
+// launchers
+// ================================================================================================
+
+static inline int blocks_for(int64_t n, int bs) { return (int)((n + bs - 1) / bs); }
+
+int launch_predict(const DevArrays& d, cudaStream_t s) {
+  k_step_init<<<blocks_for(d.n_scenes, 128), 128, 0, s>>>(d);
+  if (d.n == 0) return 1;
+  k_predict<<<blocks_for(d.n, 256), 256, 0, s>>>(d);
+  return 2;
+}
+
+int launch_contacts(const DevArrays& d, int stage, cudaStream_t s) {
+  if (d.n == 0) return 0;
+  if (stage == 0) {
+    cudaMemsetAsync(d.hash_count, 0, sizeof(int32_t) * d.hash_size, s);
+    cudaMemsetAsync(d.cnt_tmp, 0, sizeof(int32_t) * (d.hash_size > d.n ? d.hash_size : d.n), s);
+    k_cell_count<<<blocks_for(d.n, 256), 256, 0, s>>>(d);
+    int k = 1 + launch_scan_counts(d, d.hash_count, d.hash_start, d.hash_size, s);
+    k_cell_fill<<<blocks_for(d.n, 256), 256, 0, s>>>(d);
+    k_cell_sort<<<blocks_for(d.hash_size, 256), 256, 0, s>>>(d);
+    k_contact_scan<0><<<blocks_for(d.n, 128), 128, 0, s>>>(d);
+    k += 3 + launch_scan_counts(d, d.cnt_tmp, d.c_start, d.n, s);
+    return k;
+  }
+  k_contact_scan<1><<<blocks_for(d.n, 128), 128, 0, s>>>(d);
+  return 1;
+}
+
+int launch_scan_counts(const DevArrays& d, const int32_t* counts, int32_t* starts, int n, cudaStream_t s) {
+  int nblk = blocks_for(n, 1024);
+  if (nblk == 0) {
+    cudaMemsetAsync(starts, 0, sizeof(int32_t), s);
+    return 0;
+  }
+  k_scan_block_sums<<<nblk, 1024, 0, s>>>(counts, n, d.scan_tmp);
+  k_scan_top<<<1, 1024, 0, s>>>(d.scan_tmp, nblk);
+  k_scan_apply<<<nblk, 1024, 0, s>>>(counts, n, d.scan_tmp, nblk, starts);
+  return 3;
+}
+
+int launch_bond_grad(const DevArrays& d, int all, cudaStream_t s) {
+  if (d.n_btiles == 0) return 0;
+  k_bond_grad<<<d.n_btiles, kTile, 0, s>>>(d, all);
+  return 1;
+}
+
+int launch_particle_grad(const DevArrays& d, int mask, int all, cudaStream_t s) {
+  if (d.n_ptiles == 0) return 0;
+  k_particle_grad<<<d.n_ptiles, kTile, 0, s>>>(d, mask, all);
+  return 1;
+}
+
+int launch_bond_hess(const DevArrays& d, int all, cudaStream_t s) {
+  if (d.nb == 0) return 0;
+  if (d.mixed) k_bond_hess<float><<<blocks_for(d.nb, 128), 128, 0, s>>>(d, all);
+  else k_bond_hess<double><<<blocks_for(d.nb, 128), 128, 0, s>>>(d, all);
+  return 1;
+}
+
+int launch_particle_hess(const DevArrays& d, int mask, int all, cudaStream_t s) {
+  if (d.n_ptiles == 0) return 0;
+  if (d.mixed) k_particle_hess<float><<<d.n_ptiles, kTile, 0, s>>>(d, mask, all);
+  else k_particle_hess<double><<<d.n_ptiles, kTile, 0, s>>>(d, mask, all);
+  return 1;
+}
+
+int launch_scene_reduce(const DevArrays& d, int mode, int k_iter, cudaStream_t s) {
+  k_scene_reduce<<<1, 1024, 0, s>>>(d, mode, k_iter);
+  return 1;
+}
+
+int pcg_max_blocks(int mixed) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (mixed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg<float>, kTile, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg<double>, kTile, 0);
+  return sms * per;
+}
+
+int launch_pcg(const DevArrays& d, int rhs_from_g, int mask, int grid_blocks, cudaStream_t s, cudaError_t* err) {
+  if (d.n_ptiles == 0) {
+    *err = cudaSuccess;
+    return 0;
+  }
+  int grid = grid_blocks < d.n_ptiles ? grid_blocks : d.n_ptiles;
+  if (grid < 1) grid = 1;
+  DevArrays dd = d;
+  void* args[] = {&dd, &rhs_from_g, &mask};
+  if (d.mixed) *err = cudaLaunchCooperativeKernel((void*)k_pcg<float>, grid, kTile, args, 0, s);
+  else *err = cudaLaunchCooperativeKernel((void*)k_pcg<double>, grid, kTile, args, 0, s);
+  return 1;
+}
+
+int launch_gdx(const DevArrays& d, cudaStream_t s) {
+  if (d.n_ptiles == 0) return 0;
+  if (d.mixed) k_gdx<float><<<d.n_ptiles, kTile, 0, s>>>(d);
+  else k_gdx<double><<<d.n_ptiles, kTile, 0, s>>>(d);
+  return 1;
+}
+
+int launch_ls_trial(const DevArrays& d, cudaStream_t s) {
+  if (d.n == 0) return 0;
+  if (d.mixed) k_ls_trial<float><<<blocks_for(d.n, 256), 256, 0, s>>>(d);
+  else k_ls_trial<double><<<blocks_for(d.n, 256), 256, 0, s>>>(d);
+  return 1;
+}
+
+int launch_ls_energy(const DevArrays& d, cudaStream_t s) {
+  int k = 0;
+  if (d.n_ptiles) { k_ls_energy_particles<<<d.n_ptiles, kTile, 0, s>>>(d); ++k; }
+  if (d.n_btiles) { k_ls_energy_bonds<<<d.n_btiles, kTile, 0, s>>>(d); ++k; }
+  return k;
+}
+
+int launch_ls_commit(const DevArrays& d, cudaStream_t s) {
+  if (d.n == 0) return 0;
+  k_ls_commit<<<blocks_for(d.n, 256), 256, 0, s>>>(d);
+  return 1;
+}
+
+int launch_finish(const DevArrays& d, cudaStream_t s) {
+  int k = 0;
+  if (d.n) { k_finish<<<blocks_for(d.n, 256), 256, 0, s>>>(d); ++k; }
+  if (d.nb) { k_fracture<<<blocks_for(d.nb, 256), 256, 0, s>>>(d); ++k; }
+  return k;
+}
+
+int launch_matvec(const DevArrays& d, int mask, cudaStream_t s) {
+  if (d.n == 0) return 0;
+  if (d.mixed) k_matvec<float><<<blocks_for(d.n, kTile), kTile, 0, s>>>(d, mask);
+  else k_matvec<double><<<blocks_for(d.n, kTile), kTile, 0, s>>>(d, mask);
+  return 1;
+}
+
+int launch_unpack_bond_hess(const DevArrays& d, double* out, cudaStream_t s) {
+  if (d.nb == 0) return 0;
+  if (d.mixed) k_unpack_bond_hess<float><<<blocks_for(d.nb, 64), 64, 0, s>>>(d, out);
+  else k_unpack_bond_hess<double><<<blocks_for(d.nb, 64), 64, 0, s>>>(d, out);
+  return 1;
+}
+
+int launch_unpack_diag(const DevArrays& d, double* out, cudaStream_t s) {
+  if (d.n == 0) return 0;
+  if (d.mixed) k_unpack_diag<float><<<blocks_for(d.n, 128), 128, 0, s>>>(d, out);
+  else k_unpack_diag<double><<<blocks_for(d.n, 128), 128, 0, s>>>(d, out);
+  return 1;
+}
+
+__global__ void k_pack_state(DevArrays d, double* pos3, double* vel3) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  if (pos3) { double4 p = d.x0p[i]; pos3[3 * i] = p.x; pos3[3 * i + 1] = p.y; pos3[3 * i + 2] = p.z; }
+  if (vel3) { double4 v = d.vp[i]; vel3[3 * i] = v.x; vel3[3 * i + 1] = v.y; vel3[3 * i + 2] = v.z; }
+}
+
+__global__ void k_unpack_state(DevArrays d, const double* pos3, const double* vel3) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  if (pos3) { double r = d.x0p[i].w; d.x0p[i] = make_double4(pos3[3 * i], pos3[3 * i + 1], pos3[3 * i + 2], r); }
+  if (vel3) d.vp[i] = make_double4(vel3[3 * i], vel3[3 * i + 1], vel3[3 * i + 2], 0.0);
+}
+
+int launch_pack_state(const DevArrays& d, double* pos3, double* vel3, cudaStream_t s) {
+  if (d.n == 0) return 0;
+  k_pack_state<<<blocks_for(d.n, 256), 256, 0, s>>>(d, pos3, vel3);
+  return 1;
+}
+
+int launch_unpack_state(const DevArrays& d, const double* pos3, const double* vel3, cudaStream_t s) {
+  if (d.n == 0) return 0;
+  k_unpack_state<<<blocks_for(d.n, 256), 256, 0, s>>>(d, pos3, vel3);
+  return 1;
+}
+
+int launch_convert(const void* src, int sd, void* dst, int dd, int64_t count, cudaStream_t s) {
+  if (count == 0) return 0;
+  k_convert<<<blocks_for(count, 256), 256, 0, s>>>(src, sd, dst, dd, count);
+  return 1;
+}
+
+}  // namespace bdem
