@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark of the implicit bonded-DEM step (GB300).
+
+Workload: the ceramic-plate fracture scene (hexagonal-close-packed disk, 219,314 particles, 1,092,558 bonds, E = 5e9,
+dt = 5e-4, tensile break strain 1e-3, dropped at 3 m/s onto the ground with penalty contact), FP32-mixed path.
+A "step" is one full time step (prediction, contact candidates, the Newton loop with its PCG solves and line
+searches, velocity update, fracture). Metric: particle-Newton-iterations per second (sum over steps of
+particles x Newton iterations, divided by time); sim steps/s is reported beside it, and the FP64 GPU path is timed
+on the same workload for the mixed-over-FP64 speedup at equal Newton residual (1e-6 relative).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own replica of the workload (replicas only: the path has no
+cross-GPU exchange); the wall time is the maximum over ranks and the value counts every rank's work.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-Newton-iters/s & sim steps/s, FP32-mixed vs FP64 GPU at 1e-6 residual"
+UNIT = "particle-Newton-iters/s"
+WORKLOAD = ("ceramic plate fracture: HCP disk R=0.284 m, 3 layers, r=1 mm, bonds within 1.05*2r, jitter 1e-5 m, "
+            "E=5e9 Pa, nu=0.3, rho=2500, break strain 1e-3, dropped at 3 m/s tilted 10 deg, ground and self "
+            "penalty contact k=E*r, dt=5e-4 s, Newton tol 1e-6 relative")
+SAMPLE_R = 0.02  # radius of the bounded CPU sample of the same plate construction
+
+
+# ------------------------------------------------------------------------------------------------
+# algorithmic bytes of one PCG iteration (the dominant kernel)
+# ------------------------------------------------------------------------------------------------
+
+def pcg_bytes_per_iter(n, nb, n_contact_entries, w):
+    """Bytes one PCG iteration must move at minimum in this layout: the factored bond blocks (33 words per bond)
+    with their incidence entries (8 B per bond) and endpoint pairs (8 B), the diagonal blocks and their inverses
+    (2 x 21 words per particle), twelve 6-word vector streams per particle (q = H p: read p, write q; x, r update:
+    read x r p q, write x r z; p update: read z p, write p), the row starts and kinematic flags (5 B), and the
+    contact entries (index 4 B + rank-one block 4 words)."""
+    return nb * (33 * w + 16) + n * (42 * w + 72 * w + 5) + n_contact_entries * (4 + 4 * w)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def traffic_record():
+    """ncu DRAM bytes per PCG iteration, if captured for the current kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_pcg_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        src = open(os.path.join(ROOT, "paper_2308_10459_gb300", "csrc", "bdem_kernels.cu"), "rb").read()
+        if rec.get("kernels_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return rec
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------------------
+# distributed helpers (replicas only)
+# ------------------------------------------------------------------------------------------------
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_timing(elapsed_s, units, world):
+    """Max of the timed region over ranks, sum of the work units (torch.distributed must be initialised if
+    world > 1)."""
+    if world <= 1:
+        return elapsed_s, units
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([elapsed_s], dtype=torch.float64, device=dev)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle legs
+# ------------------------------------------------------------------------------------------------
+
+def oracle_sample_rate(n_steps=1):
+    """The CPU oracle (single thread) on the bounded sample; returns (rate, seconds, particles, newton iters)."""
+    import oracle
+    from paper_2308_10459_gb300 import scenes
+    sc = scenes.c2_plate_small(R=SAMPLE_R)
+    o = oracle.OracleSim(sc)
+    t0 = time.perf_counter()
+    res = o.step(n_steps)
+    t = time.perf_counter() - t0
+    its = sum(s[0]["newton_iters"] for s in res)
+    return sc.n * its / t, t, sc.n, its
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2308_10459_gb300 import scenes
+    oracle.build()
+    sc = scenes.c2_plate_small(R=SAMPLE_R)
+    o = oracle.OracleSim(sc)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    res = o.step(args.steps)
+    t = time.perf_counter() - t0
+    its = sum(s[0]["newton_iters"] for s in res)
+    value = sc.n * its / t
+    sample = (f"{args.steps} consecutive steps (after {args.warmup} warm-up steps) of the same plate construction "
+              f"at R={SAMPLE_R} m ({sc.n} particles, {sc.nb} bonds)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "sim_steps_per_s": args.steps / t,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------------
+# main (our CUDA path)
+# ------------------------------------------------------------------------------------------------
+
+def timed_steps(sim, K, world, torch):
+    launches0 = sim.launch_count()
+    sim.profile_enable(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    stats = []
+    for _ in range(K):
+        stats.append(sim.step(1)[0])
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    prof = sim.profile_read()
+    return elapsed, prof, sim.launch_count() - launches0, stats
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=4)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--radius", type=float, default=0.284,
+                    help="plate radius; anything but 0.284 m is a smaller profiling case, not the benchmark workload")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+
+    import paper_2308_10459_gb300 as pkg
+    from paper_2308_10459_gb300 import build as bmod
+    from paper_2308_10459_gb300 import scenes
+
+    torch.cuda.set_device(local)
+    bmod.build()
+    pkg.load()
+    sc = scenes.c2_plate(R=args.radius)
+
+    # ---- FP32-mixed path, inputs resident ----
+    sim = pkg.Sim(sc, precision=pkg.BDEM_MIXED)
+    sim.step(args.warmup)
+    clocks = ClockSampler(local)
+    clocks.start()
+    elapsed, prof, launches, stats = timed_steps(sim, args.steps, world, torch)
+    clk = clocks.stop()
+    t_max, units = reduce_timing(elapsed, prof["particle_newton_iters"], world)
+    value = units / t_max
+
+    # roofline of the dominant kernel (persistent PCG): algorithmic bytes per launch / average launch time
+    cand = max(int(s["contact_candidates"]) for s in stats)
+    bytes_iter = pcg_bytes_per_iter(sc.n, sc.nb, 2 * cand, 4)
+    pcg_launches = max(prof["intervals"]["pcg"], 1)
+    pcg_iters_launch = prof["pcg_iters"] / pcg_launches
+    pcg_ms_launch = prof["ms"]["pcg"] / pcg_launches
+    achieved = bytes_iter * pcg_iters_launch / (pcg_ms_launch * 1e-3) / 1e9
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    trec = traffic_record()
+    traffic = None if trec is None else trec["bytes_per_pcg_iter"] * pcg_iters_launch
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region ----
+    e2e = None
+    if args.e2e_steps > 0:
+        st = sim.read_state()
+        n, nb = sc.n, sc.nb
+        pin = {k: torch.empty(v.shape, dtype=torch.float64 if v.dtype == np.float64 else torch.uint8,
+                              pin_memory=True).numpy() for k, v in st.items()}
+        for k in pin:
+            pin[k][...] = st[k]
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        pni = 0
+        for _ in range(args.e2e_steps):
+            sim.write_state(pin["pos"], pin["quat"], pin["vel"], pin["quat_vel"], pin["broken"])
+            s = sim.step(1)[0]
+            pni += s["newton_iters"] * n
+            sim.read_state(pin)
+        t_e2e = time.perf_counter() - t0
+        barrier(world)
+        t_e2e, pni = reduce_timing(t_e2e, pni, world)
+        e2e = {"value": pni / t_e2e, "unit": UNIT, "h2d_bytes_per_step": n * (3 + 4 + 3 + 4) * 8 + nb,
+               "d2h_bytes_per_step": n * (3 + 4 + 3 + 4) * 8 + nb}
+    sim.close()
+
+    # ---- FP64 GPU path on the same workload ----
+    fp64 = None
+    if args.fp64_steps > 0:
+        sim64 = pkg.Sim(sc, precision=pkg.BDEM_FP64)
+        sim64.step(args.warmup)
+        e64, p64, _, _ = timed_steps(sim64, args.fp64_steps, world, torch)
+        t64, u64 = reduce_timing(e64, p64["particle_newton_iters"], world)
+        fp64 = {"value": u64 / t64, "unit": UNIT, "steps": args.fp64_steps, "ms_per_step": 1e3 * t64 / args.fp64_steps,
+                "sim_steps_per_s": args.fp64_steps * world / t64,
+                "newton_iters_per_step": p64["newton_iters"] / max(p64["steps"], 1),
+                "phase_ms_per_step": {k: v / max(p64["steps"], 1) for k, v in p64["ms"].items()}}
+        sim64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        rate, secs, npart, its = oracle_sample_rate(1)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one time step of the same plate construction at R={SAMPLE_R} m ({npart} particles, "
+                         f"{its} Newton iterations, {secs:.1f} s on one host core)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.radius == 0.284 else f"profiling case R={args.radius} m",
+                       "precision": "FP32-mixed (f32 Hessian/PCG, f64 gradient/reductions/state)",
+                       "n_particles": sc.n, "n_bonds": sc.nb, "replicas": world,
+                       "l2": "working set of every timed stage exceeds the 129 MB L2; no flush between steps"},
+            "sim_steps_per_s": args.steps * world / t_max,
+            "newton_iters_per_step": prof["newton_iters"] / max(prof["steps"], 1),
+            "pcg_iters_per_newton": prof["pcg_iters"] / max(prof["newton_iters"], 1),
+            "phase_ms_per_step": {k: v / max(prof["steps"], 1) for k, v in prof["ms"].items()},
+            "roofline": {"bound": "hbm", "kernel": "k_pcg (persistent PCG)", "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "algorithmic_bytes_per_pcg_iter": bytes_iter, "pcg_iters_per_launch": pcg_iters_launch,
+                         "launch_ms": pcg_ms_launch},
+            "fp64": fp64,
+            "mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
