@@ -166,6 +166,25 @@ bdem_status bdem_debug_pcg(bdem_sim* sim, const double* b, double eps_r, int32_t
 /* Kernel launches issued by this sim since creation (for launch accounting). */
 int64_t bdem_launch_count(const bdem_sim* sim);
 
+/* ---- allocation-free solve ---------------------------------------------------------------------------------------
+ * The paper has no counterpart: this entry point exists for callers that cannot allocate device memory, for
+ * example code running under an external memory pool that forbids extra cudaMalloc calls, or a host thread that
+ * must not trigger allocation while other work is being captured or scheduled.
+ * It runs the same PCG solve as bdem_debug_pcg (Sec. 5.3 block-Jacobi PCG, kinematic rows removed) on the system
+ * assembled by the last bdem_debug_system call, but keeps all of its scratch (per-scene control blocks, barrier
+ * counters, partial sums, PCG vectors) in one static device array of 24 MiB inside the library, so the call itself
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine). That caps the system at about 100,000
+ * particles in BDEM_FP64 and 200,000 in BDEM_MIXED; larger systems get BDEM_E_INVALID with the byte counts.
+ *   b_dev, x_dev: caller-owned DEVICE arrays [n][6] of double (right-hand side in, solution out).
+ *   iters: NULL or host int32_t[n_scenes] receiving the iterations per scene.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that device current
+ * and caches it, so make that first call before any stream capture. Every GPU that loads the library holds the
+ * array until the process exits. All calls share the array and each call overwrites it, clearing what must start
+ * at zero; calls whose work overlaps on the GPU (other host threads, other streams, other sims) race on it and
+ * must be serialised by the caller. Host-blocking: returns after the solve has completed. */
+bdem_status bdem_pcg_static(bdem_sim* sim, const double* b_dev, double* x_dev, double eps_r, int32_t max_iter,
+                            int32_t* iters);
+
 /* ---- phase timing: CUDA events recorded on the library's stream around each stage's launches ------------------ */
 enum {
   BDEM_PH_PREDICT = 0,     /* prediction and step set-up */

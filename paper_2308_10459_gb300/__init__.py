@@ -75,6 +75,7 @@ _PROTOS = {
     "bdem_debug_matvec": (ctypes.c_int, [_vp, _dp, _dp]),
     "bdem_debug_pcg": (ctypes.c_int, [_vp, _dp, ctypes.c_double, ctypes.c_int32, _dp, _ip]),
     "bdem_launch_count": (ctypes.c_int64, [_vp]),
+    "bdem_pcg_static": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int32, _ip]),
     "bdem_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "bdem_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(bdem_profile)]),
 }
@@ -254,6 +255,13 @@ class Sim:
         self._check(self.L.bdem_debug_pcg(self.h, _ptr(b, _dp), float(eps_r), int(max_iter), _ptr(x, _dp),
                                           _ptr(it, _ip)))
         return x, it
+
+    def bdem_pcg_static(self, b_dev_ptr, x_dev_ptr, eps_r, max_iter):
+        """Allocation-free PCG (see include/bdem.h): b and x are device addresses of [n][6] float64 arrays."""
+        it = np.zeros(self.n_scenes, np.int32)
+        self._check(self.L.bdem_pcg_static(self.h, ctypes.c_void_p(b_dev_ptr), ctypes.c_void_p(x_dev_ptr),
+                                           float(eps_r), int(max_iter), _ptr(it, _ip)))
+        return it
 
     def profile_enable(self, on=True):
         self._check(self.L.bdem_profile_enable(self.h, 1 if on else 0))

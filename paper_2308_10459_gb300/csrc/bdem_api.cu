@@ -931,3 +931,55 @@ extern "C" bdem_status bdem_profile_read(bdem_sim* s, bdem_profile* out) {
   *out = s->prof;
   return BDEM_OK;
 }
+
+// ------------------------------------------------------------------------------------------------
+// allocation-free PCG solve (scratch in the library's static device array)
+// ------------------------------------------------------------------------------------------------
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+extern "C" bdem_status bdem_pcg_static(bdem_sim* s, const double* b_dev, double* x_dev, double eps_r,
+                                       int32_t max_iter, int32_t* iters) {
+  if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
+  if (!b_dev || !x_dev || max_iter < 1 || !(eps_r >= 0.0)) return fail(s, BDEM_E_INVALID, "bad PCG arguments");
+  DevArrays d = s->d;
+  size_t n = (size_t)s->n, w = wsize(s);
+  // scratch layout: scene control blocks | counters | tile partials | PCG vectors x r z p q
+  size_t off_sc = 0;
+  size_t off_cnt = off_sc + align256(sizeof(SceneCtl) * (size_t)std::max(s->n_scenes, 1));
+  size_t off_part = off_cnt + align256(sizeof(Counters));
+  size_t off_vec = off_part + align256(sizeof(double) * kPartials * (size_t)std::max(d.n_ptiles, 1));
+  size_t vec_bytes = align256(w * 6 * std::max<size_t>(n, 1));
+  size_t need = off_vec + 5 * vec_bytes;
+  if (need > static_pcg_capacity())
+    return fail(s, BDEM_E_INVALID,
+                "system too large for the static PCG scratch: needs %zu bytes, the array holds %zu bytes "
+                "(about %zu particles in this precision)",
+                need, static_pcg_capacity(), (size_t)(static_pcg_capacity() / (5 * 6 * w + 1)));
+  if (!s->system_ready) return fail(s, BDEM_E_INVALID, "call bdem_debug_system first");
+  if (n == 0) return BDEM_OK;
+  void* base = nullptr;
+  cudaError_t e = static_pcg_address(&base);
+  if (e != cudaSuccess) return fail(s, BDEM_E_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+  unsigned char* b8 = static_cast<unsigned char*>(base);
+  d.sc = reinterpret_cast<SceneCtl*>(b8 + off_sc);
+  d.cnt = reinterpret_cast<Counters*>(b8 + off_cnt);
+  d.part_p = reinterpret_cast<double*>(b8 + off_part);
+  void** vecs[] = {&d.vx, &d.vr, &d.vz, &d.vp_, &d.vq_};
+  for (int k = 0; k < 5; ++k) *vecs[k] = b8 + off_vec + k * vec_bytes;
+  d.pcg_max = max_iter;
+  cudaStream_t st = s->stream;
+  int k = launch_static_pcg_init(d, eps_r, st);
+  k += launch_convert(b_dev, 1, d.vr, !d.mixed, 6 * (int64_t)n, st);
+  TRY(check_launch(s, k));
+  TRY(run_pcg(s, d, 0, 1));
+  TRY(check_launch(s, launch_convert(d.vx, !d.mixed, x_dev, 1, 6 * (int64_t)n, st)));
+  Counters c{};
+  CUDA_TRY(s, cudaMemcpyAsync(&c, d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+  if (iters)
+    for (int sc = 0; sc < s->n_scenes; ++sc)
+      CUDA_TRY(s, cudaMemcpyAsync(iters + sc, &d.sc[sc].pcg_iters, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+  if (c.timeout) return fail(s, BDEM_E_TIMEOUT, "a device-side wait gave up");
+  return BDEM_OK;
+}

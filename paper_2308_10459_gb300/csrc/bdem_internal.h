@@ -112,6 +112,10 @@ int launch_unpack_bond_hess(const DevArrays& d, double* out /*device [nb][144]*/
 int launch_unpack_diag(const DevArrays& d, double* out /*device [n][36]*/, cudaStream_t s);
 int launch_pack_state(const DevArrays& d, double* pos3, double* vel3, cudaStream_t s);          // committed -> [n][3]
 int launch_unpack_state(const DevArrays& d, const double* pos3, const double* vel3, cudaStream_t s);
+// allocation-free PCG scratch (static device array in bdem_kernels.cu)
+size_t static_pcg_capacity();
+cudaError_t static_pcg_address(void** out);
+int launch_static_pcg_init(const DevArrays& d, double eps_r, cudaStream_t s);
 int launch_convert(const void* src, int src_double, void* dst, int dst_double, int64_t count, cudaStream_t s);
 
 }  // namespace bdem

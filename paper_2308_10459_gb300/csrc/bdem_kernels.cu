@@ -1119,11 +1119,58 @@ __global__ void k_convert(const void* src, int sd, void* dst, int dd, int64_t co
   else reinterpret_cast<float*>(dst)[k] = (float)v;
 }
 
+static inline int blocks_for(int64_t n, int bs) { return (int)((n + bs - 1) / bs); }
+
+// ================================================================================================
+// Allocation-free PCG: the solver's scratch (per-scene control blocks, barrier counters, partial sums and the
+// PCG vectors) lives in this fixed static device array instead of memory the library allocates. Every GPU that
+// loads the library holds the array until the process exits. All calls share it.
+// ================================================================================================
+
+constexpr size_t kStaticPcgBytes = size_t(24) << 20;  // 24 MiB
+static __device__ __align__(256) unsigned char g_static_pcg_scratch[kStaticPcgBytes];
+
+size_t static_pcg_capacity() { return kStaticPcgBytes; }
+
+// Device address of the static array for the current device. The first call on a device looks the symbol up
+// (cudaGetSymbolAddress) with that device current and caches it; later calls reuse the cached address.
+cudaError_t static_pcg_address(void** out) {
+  static void* cache[256] = {nullptr};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  if (cache[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_pcg_scratch);
+    if (e != cudaSuccess) return e;
+    cache[dev] = p;
+  }
+  *out = cache[dev];
+  return cudaSuccess;
+}
+
+// clears the control blocks and counters that must start at zero and sets every scene active with eps_r
+__global__ void k_static_pcg_init(DevArrays d, double eps_r) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s == 0) *d.cnt = Counters{};
+  if (s >= d.n_scenes) return;
+  SceneCtl c = {};
+  c.newton_active = 1;
+  c.eps_r = eps_r;
+  d.sc[s] = c;
+}
+
+int launch_static_pcg_init(const DevArrays& d, double eps_r, cudaStream_t s) {
+  int n = d.n_scenes > 1 ? d.n_scenes : 1;
+  k_static_pcg_init<<<blocks_for(n, 128), 128, 0, s>>>(d, eps_r);
+  return 1;
+}
+
 // ================================================================================================
 // launchers
 // ================================================================================================
 
-static inline int blocks_for(int64_t n, int bs) { return (int)((n + bs - 1) / bs); }
 
 int launch_predict(const DevArrays& d, cudaStream_t s) {
   k_step_init<<<blocks_for(d.n_scenes, 128), 128, 0, s>>>(d);
