@@ -43,12 +43,13 @@ SAMPLE_R = 0.02  # radius of the bounded CPU sample of the same plate constructi
 # ------------------------------------------------------------------------------------------------
 
 def pcg_bytes_per_iter(n, nb, n_contact_entries, w):
-    """Bytes one PCG iteration must move at minimum in this layout: the factored bond blocks (33 words per bond)
-    with their incidence entries (8 B per bond) and endpoint pairs (8 B), the diagonal blocks and their inverses
-    (2 x 21 words per particle), twelve 6-word vector streams per particle (q = H p: read p, write q; x, r update:
-    read x r p q, write x r z; p update: read z p, write p), the row starts and kinematic flags (5 B), and the
-    contact entries (index 4 B + rank-one block 4 words)."""
-    return nb * (33 * w + 16) + n * (42 * w + 72 * w + 5) + n_contact_entries * (4 + 4 * w)
+    """Bytes one PCG iteration must move at minimum in this layout (Chronopoulos-Gear arrangement): the factored
+    bond blocks (33 words per bond, read once) with their two incidence entries (8 B each), the diagonal blocks and
+    their inverses (2 x 21 words per particle), fourteen 6-word vector streams per particle (w = H z: read z r,
+    write w; update: read z w p s x r, write p s x r z, plus z once more for the product's own row), the row
+    starts, active-contact counts and kinematic flags (9 B), and the active contact entries (index 4 B + rank-one
+    block 4 words)."""
+    return nb * (33 * w + 16) + n * (42 * w + 84 * w + 9) + n_contact_entries * (4 + 4 * w)
 
 
 def measured_peaks():
@@ -224,6 +225,30 @@ def timed_steps(sim, K, world, torch):
     return elapsed, prof, sim.launch_count() - launches0, stats
 
 
+def pcg_probe(args, sc, sim, pkg, torch):
+    """One PCG solve of exactly N iterations (eps_r = 0) on the system at the state after `warmup` steps; prints the
+    time per iteration and the algorithmic bytes (the command the k_pcg ncu captures use)."""
+    import numpy as np
+    if args.warmup:
+        sim.step(args.warmup)
+    if args.pcg_lanes:
+        sim.set_pcg_shape(args.pcg_lanes, args.pcg_blocks)
+    st = sim.read_state()
+    dt = sc.config["dt"]
+    sys_ = sim.bdem_debug_system(st["pos"] + dt * st["vel"], st["quat"] + dt * st["quat_vel"], want_bonds=False)
+    b = -sys_["g"]
+    sim.profile_enable(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, it = sim.bdem_debug_pcg(b, 0.0, args.pcg_probe)
+    t = time.perf_counter() - t0
+    line = {"probe": "pcg", "iters": int(it[0]), "seconds_incl_transfers": t, "n": sc.n, "nb": sc.nb,
+            "algorithmic_bytes_per_iter": pcg_bytes_per_iter(sc.n, sc.nb, 2 * sys_["n_candidates"], 4),
+            "lanes": args.pcg_lanes}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -233,10 +258,14 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=4)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pcg-lanes", type=int, default=0, help="lanes per row of the PCG product (0: autotune)")
+    ap.add_argument("--pcg-blocks", type=int, default=0, help="PCG grid size with --pcg-lanes (0: all resident)")
+    ap.add_argument("--pcg-probe", type=int, default=0,
+                    help="time N PCG iterations of one solve (eps 0) on the workload's system and exit (profiling)")
     ap.add_argument("--radius", type=float, default=0.284,
                     help="plate radius; anything but 0.284 m is a smaller profiling case, not the benchmark workload")
     args = ap.parse_args()
-    if args.warmup < 3:
+    if args.warmup < 3 and not args.pcg_probe:
         args.warmup = 3
     world, rank, local = dist_env()
     if world > 1:
@@ -262,7 +291,15 @@ def main():
 
     # ---- FP32-mixed path, inputs resident ----
     sim = pkg.Sim(sc, precision=pkg.BDEM_MIXED)
+    if args.pcg_probe:
+        return pcg_probe(args, sc, sim, pkg, torch)
     sim.step(args.warmup)
+    if args.pcg_lanes:
+        sim.set_pcg_shape(args.pcg_lanes, args.pcg_blocks)
+        shape = {"lanes_per_row": args.pcg_lanes, "blocks": args.pcg_blocks, "autotuned": False}
+    else:
+        lanes, blocks = sim.autotune_pcg(30)
+        shape = {"lanes_per_row": lanes, "blocks": blocks, "autotuned": True}
     clocks = ClockSampler(local)
     clocks.start()
     elapsed, prof, launches, stats = timed_steps(sim, args.steps, world, torch)
@@ -342,6 +379,7 @@ def main():
             "newton_iters_per_step": prof["newton_iters"] / max(prof["steps"], 1),
             "pcg_iters_per_newton": prof["pcg_iters"] / max(prof["newton_iters"], 1),
             "phase_ms_per_step": {k: v / max(prof["steps"], 1) for k, v in prof["ms"].items()},
+            "pcg_shape": shape,
             "roofline": {"bound": "hbm", "kernel": "k_pcg (persistent PCG)", "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "algorithmic_bytes_per_pcg_iter": bytes_iter, "pcg_iters_per_launch": pcg_iters_launch,

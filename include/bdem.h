@@ -114,8 +114,8 @@ bdem_status bdem_create(const bdem_config* config, int32_t n_scenes, const int64
  * S = pi r0^2, I = pi r0^4/4, J = pi r0^4/2, kn = E S/l0, kt = G S/l0, K = bend_twist_scale diag(GJ, EI, EI)/l0.
  * Requires i != j, both in the same scene, no duplicate pair (also against earlier calls), l0 > 0 and
  * q_i . q_j >= 1 - 1e-12 (equal rest orientations); otherwise BDEM_E_INVALID and nothing is added.
- * The library stores each bond with i < j; bdem_read_state reports bond flags in the order of
- * bdem_bond_order(). */
+ * Bond flags (bdem_read_state, bdem_write_state) and per-bond outputs are in the order of addition across all calls,
+ * which bdem_bond_order() lists. */
 bdem_status bdem_add_bonds(bdem_sim* sim, int64_t n, const int32_t* i, const int32_t* j, const int32_t* bond_material);
 
 /* Advances n_steps >= 0 time steps (Alg. 3). stats: NULL or an array of n_scenes entries. Host-blocking: returns
@@ -135,7 +135,7 @@ bdem_status bdem_write_state(bdem_sim* sim, const double* pos, const double* qua
 /* Sizes: particles, intact + broken bonds, scenes. */
 bdem_status bdem_sizes(const bdem_sim* sim, int64_t* n_particles, int64_t* n_bonds, int32_t* n_scenes);
 
-/* The stored bond order: pairs[2k], pairs[2k+1] (i < j) for k < n_bonds. */
+/* The bonds in their order of addition: pairs[2k], pairs[2k+1] = (min(i, j), max(i, j)) of the k-th bond added. */
 bdem_status bdem_bond_order(const bdem_sim* sim, int32_t* pairs);
 
 /* Releases every device and host resource of sim (NULL is ignored). */
@@ -151,7 +151,8 @@ const char* bdem_last_error(const bdem_sim* sim);
 
 /* Reduced gradient g[n][6] (FP64), assembled projected diagonal blocks diag[n][6][6], per-bond projected reduced
  * Hessians bond_hess[n_bonds][12][12] in the order (dp_i, y_i, dp_j, y_j) (zero for broken bonds), and the number
- * of contact candidates; any output may be NULL. Kinematic rows are not masked. */
+ * of contact candidates; any output may be NULL. Kinematic rows are not masked. Rows and particles are in the
+ * caller's order, bonds in their order of addition. */
 bdem_status bdem_debug_system(bdem_sim* sim, const double* phat, const double* qhat, double* g, double* diag,
                               double* bond_hess, int64_t* n_candidates);
 
@@ -166,6 +167,18 @@ bdem_status bdem_debug_pcg(bdem_sim* sim, const double* b, double eps_r, int32_t
 /* Kernel launches issued by this sim since creation (for launch accounting). */
 int64_t bdem_launch_count(const bdem_sim* sim);
 
+/* ---- launch shape of the persistent PCG kernel ---------------------------------------------------------------------
+ * lanes_per_row in {1, 2, 4, 8}: threads that share one block row of the product (the rows of a warp = 32 / lanes);
+ * blocks: PCG grid size, 0 = every co-resident block (capped at one block per 64 rows). Changing the shape changes
+ * the grouping of the FP64 partial sums, so results differ at rounding level between shapes; a fixed shape gives
+ * bit-identical runs. */
+bdem_status bdem_set_pcg_shape(bdem_sim* sim, int32_t lanes_per_row, int32_t blocks);
+
+/* Times the PCG kernel for `iters` iterations on the system at the current committed state for each candidate shape
+ * (lanes 1, 2, 4, 8 x 1..all co-resident blocks per SM), keeps the fastest, and reports it (either pointer may be
+ * NULL). Host-blocking. */
+bdem_status bdem_autotune_pcg(bdem_sim* sim, int32_t iters, int32_t* lanes_per_row, int32_t* blocks);
+
 /* ---- allocation-free solve ---------------------------------------------------------------------------------------
  * The paper has no counterpart: this entry point exists for callers that cannot allocate device memory, for
  * example code running under an external memory pool that forbids extra cudaMalloc calls, or a host thread that
@@ -173,8 +186,8 @@ int64_t bdem_launch_count(const bdem_sim* sim);
  * It runs the same PCG solve as bdem_debug_pcg (Sec. 5.3 block-Jacobi PCG, kinematic rows removed) on the system
  * assembled by the last bdem_debug_system call, but keeps all of its scratch (per-scene control blocks, barrier
  * counters, partial sums, PCG vectors) in one static device array of 24 MiB inside the library, so the call itself
- * allocates nothing (no cudaMalloc, cudaFree or allocating library routine). That caps the system at about 100,000
- * particles in BDEM_FP64 and 200,000 in BDEM_MIXED; larger systems get BDEM_E_INVALID with the byte counts.
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine). That caps the system at about 87,000
+ * particles in BDEM_FP64 and 174,000 in BDEM_MIXED; larger systems get BDEM_E_INVALID with the byte counts.
  *   b_dev, x_dev: caller-owned DEVICE arrays [n][6] of double (right-hand side in, solution out).
  *   iters: NULL or host int32_t[n_scenes] receiving the iterations per scene.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that device current

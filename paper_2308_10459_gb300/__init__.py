@@ -76,6 +76,8 @@ _PROTOS = {
     "bdem_debug_pcg": (ctypes.c_int, [_vp, _dp, ctypes.c_double, ctypes.c_int32, _dp, _ip]),
     "bdem_launch_count": (ctypes.c_int64, [_vp]),
     "bdem_pcg_static": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int32, _ip]),
+    "bdem_set_pcg_shape": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
+    "bdem_autotune_pcg": (ctypes.c_int, [_vp, ctypes.c_int32, _ip, _ip]),
     "bdem_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "bdem_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(bdem_profile)]),
 }
@@ -262,6 +264,14 @@ class Sim:
         self._check(self.L.bdem_pcg_static(self.h, ctypes.c_void_p(b_dev_ptr), ctypes.c_void_p(x_dev_ptr),
                                            float(eps_r), int(max_iter), _ptr(it, _ip)))
         return it
+
+    def set_pcg_shape(self, lanes_per_row, blocks=0):
+        self._check(self.L.bdem_set_pcg_shape(self.h, int(lanes_per_row), int(blocks)))
+
+    def autotune_pcg(self, iters=30):
+        l, g = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self.L.bdem_autotune_pcg(self.h, int(iters), ctypes.byref(l), ctypes.byref(g)))
+        return l.value, g.value
 
     def profile_enable(self, on=True):
         self._check(self.L.bdem_profile_enable(self.h, 1 if on else 0))

@@ -25,7 +25,11 @@ struct bdem_sim {
   std::vector<double> radius, mass;
   std::vector<uint8_t> kin;
   std::vector<bdem_material> mats;
-  std::vector<int32_t> bi, bj, bmat;  // stored bond order, i < j, sorted by (i, j)
+  std::vector<int32_t> perm, iperm;  // internal -> caller particle index, caller -> internal
+  std::vector<int32_t> deg;          // bonds per particle (internal order), weights of the PCG partition
+  std::vector<int32_t> ext_i, ext_j;  // bonds in the caller's order of addition (caller indices, i < j)
+  std::vector<int32_t> bond_ext2int_h;
+  std::vector<int32_t> bi, bj, bmat;  // stored bond order (internal indices), i < j, sorted by (i, j)
   std::vector<double4> rest, stiff;   // host copies of the bond rest data (d0, l0), (kn, kt, kb, ktw)
   std::vector<double> brk;
   DevArrays d{};
@@ -35,7 +39,8 @@ struct bdem_sim {
   int pcg_blocks = 0;
   double* dbg_buf = nullptr;          // device scratch of the inspection calls
   size_t dbg_cap = 0;
-  double* stage = nullptr;            // device staging for [n][3] / [n][6] host layouts
+  double* stage = nullptr;            // device staging for the caller-order state arrays (14 doubles per particle)
+  uint8_t* flag_stage = nullptr;      // device staging for bond flags
   bool system_ready = false;
   // phase timing
   bool prof_on = false;
@@ -216,9 +221,9 @@ static bdem_status alloc_particles(bdem_sim* s) {
   TRY(dalloc_t(s, &d.pscene, n));
   TRY(dalloc_t(s, &d.kin, n));
   TRY(dalloc_t(s, &d.g, 6 * n));
-  TRY(dalloc(s, &d.D, w * 21 * n));
-  TRY(dalloc(s, &d.Dinv, w * 21 * n));
-  void** pv[] = {&d.vx, &d.vr, &d.vz, &d.vp_, &d.vq_};
+  TRY(dalloc(s, &d.D, w * kDiagStride * n));
+  TRY(dalloc(s, &d.Dinv, w * kDiagStride * n));
+  void** pv[] = {&d.vx, &d.vr, &d.vz, &d.vp_, &d.vq_, &d.vs};
   for (void** p : pv) TRY(dalloc(s, p, w * 6 * n));
   int hs = 1024;
   while (hs < 2 * (int)n) hs <<= 1;
@@ -233,8 +238,11 @@ static bdem_status alloc_particles(bdem_sim* s) {
   TRY(dalloc_t(s, &d.scan_tmp, mx / 1024 + 4));
   d.c_cap = (int32_t)std::max<size_t>(1024, (s->cfg.k_self > 0.0 ? 16 : 1) * n);
   TRY(dalloc_t(s, &d.c_nbr, (size_t)d.c_cap));
+  TRY(dalloc_t(s, &d.c_anbr, (size_t)d.c_cap));
   TRY(dalloc(s, &d.c_blk, 4 * w * d.c_cap));
-  TRY(dalloc_t(s, &s->stage, 6 * n));
+  TRY(dalloc_t(s, &d.c_act, n));
+  TRY(dalloc_t(s, &s->stage, 14 * n + 128));
+  TRY(dalloc_t(s, &d.perm, n));
   TRY(dalloc_t(s, &d.sc, (size_t)std::max(s->n_scenes, 1)));
   TRY(dalloc_t(s, &d.cnt, 1));
   return BDEM_OK;
@@ -263,6 +271,132 @@ static bdem_status build_particle_tiles(bdem_sim* s) {
     CUDA_TRY(s, cudaMemcpy(d.ptile_scene, scene.data(), sizeof(int32_t) * scene.size(), cudaMemcpyHostToDevice));
   CUDA_TRY(s, cudaMemcpy(d.ptile_begin, begin.data(), sizeof(int32_t) * begin.size(), cudaMemcpyHostToDevice));
   return BDEM_OK;
+}
+
+// 21-bit spread for 3-D Morton codes (bits of x land at every third position)
+static uint64_t spread3(uint64_t x) {
+  x &= 0x1fffff;
+  x = (x | x << 32) & 0x1f00000000ffffull;
+  x = (x | x << 16) & 0x1f0000ff0000ffull;
+  x = (x | x << 8) & 0x100f00f00f00f00full;
+  x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+  x = (x | x << 2) & 0x1249249249249249ull;
+  return x;
+}
+
+// internal order: inside each scene, particles sorted by the Morton code of their initial position (ties by index)
+static void morton_order(const int64_t* offsets, int n_scenes, const double* pos, std::vector<int32_t>& perm) {
+  int64_t n = offsets[n_scenes];
+  perm.resize(n);
+  std::vector<uint64_t> code(n);
+  for (int sc = 0; sc < n_scenes; ++sc) {
+    int64_t a = offsets[sc], b = offsets[sc + 1];
+    if (b <= a) continue;
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t i = a; i < b; ++i)
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = std::min(lo[k], pos[3 * i + k]);
+        hi[k] = std::max(hi[k], pos[3 * i + k]);
+      }
+    double ext = std::max({hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2], 1e-300});
+    double sc_q = 2097151.0 / ext;
+    for (int64_t i = a; i < b; ++i) {
+      uint64_t q[3];
+      for (int k = 0; k < 3; ++k) q[k] = (uint64_t)std::min(2097151.0, std::max(0.0, (pos[3 * i + k] - lo[k]) * sc_q));
+      code[i] = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
+      perm[i] = (int32_t)i;
+    }
+    std::sort(perm.begin() + a, perm.begin() + b, [&](int32_t x, int32_t y) {
+      return code[x] != code[y] ? code[x] < code[y] : x < y;
+    });
+  }
+}
+
+// balanced PCG row ranges per block and their intersections with the scenes (segments)
+static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
+  DevArrays& d = s->d;
+  int64_t n = s->n;
+  if (grid < 1) grid = 1;
+  if (n > 0 && grid > n) grid = (int)n;
+  std::vector<int32_t> seg_row, seg_scene, block_seg(grid + 1, 0), scene_seg(s->n_scenes + 1, 0);
+  // block boundaries at equal cumulative work, a row weighing 4 + its bond count (the product's entries)
+  std::vector<int64_t> cum(n + 1, 0), bounds(grid + 1, 0);
+  for (int64_t i = 0; i < n; ++i) cum[i + 1] = cum[i] + 4 + s->deg[i];
+  for (int b = 1; b < grid; ++b) {
+    int64_t target = cum[n] * b / grid;
+    bounds[b] = std::lower_bound(cum.begin(), cum.end(), target) - cum.begin();
+    bounds[b] = std::max(bounds[b], bounds[b - 1]);
+  }
+  bounds[grid] = n;
+  int64_t max_rows = 0;
+  for (int b = 0; b < grid; ++b) max_rows = std::max(max_rows, bounds[b + 1] - bounds[b]);
+  if (max_rows * (int64_t)sizeof(int4) > (int64_t)160 * 1024)
+    return fail(s, BDEM_E_INVALID, "PCG grid of %d blocks leaves %lld rows in one block; use more blocks", grid,
+                (long long)max_rows);
+  int sc = 0;
+  for (int b = 0; b < grid; ++b) {
+    int64_t r0 = bounds[b], r1 = bounds[b + 1];
+    block_seg[b] = (int32_t)seg_scene.size();
+    int64_t r = r0;
+    while (r < r1) {
+      while (sc < s->n_scenes && s->offsets[sc + 1] <= r) ++sc;
+      int64_t e = std::min<int64_t>(r1, s->offsets[sc + 1]);
+      seg_row.push_back((int32_t)r);
+      seg_scene.push_back(sc);
+      r = e;
+    }
+  }
+  block_seg[grid] = (int32_t)seg_scene.size();
+  seg_row.push_back((int32_t)n);
+  for (int x = 0, k = 0; x <= s->n_scenes; ++x) {  // first segment of each scene (segments are in row order)
+    while (k < (int)seg_scene.size() && seg_scene[k] < x) ++k;
+    scene_seg[x] = k;
+  }
+  void* olds[] = {d.seg_row, d.seg_scene, d.block_seg, d.scene_seg, d.part_s};
+  for (void* p : olds) dfree(s, p);
+  size_t ns = std::max<size_t>(seg_scene.size(), 1);
+  TRY(dalloc_t(s, &d.seg_row, seg_row.size()));
+  TRY(dalloc_t(s, &d.seg_scene, ns));
+  TRY(dalloc_t(s, &d.block_seg, block_seg.size()));
+  TRY(dalloc_t(s, &d.scene_seg, scene_seg.size()));
+  TRY(dalloc_t(s, &d.part_s, (size_t)kPartials * ns));
+  CUDA_TRY(s, cudaMemcpy(d.seg_row, seg_row.data(), sizeof(int32_t) * seg_row.size(), cudaMemcpyHostToDevice));
+  if (!seg_scene.empty())
+    CUDA_TRY(s, cudaMemcpy(d.seg_scene, seg_scene.data(), sizeof(int32_t) * seg_scene.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(s, cudaMemcpy(d.block_seg, block_seg.data(), sizeof(int32_t) * block_seg.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(s, cudaMemcpy(d.scene_seg, scene_seg.data(), sizeof(int32_t) * scene_seg.size(), cudaMemcpyHostToDevice));
+  d.n_seg = (int32_t)seg_scene.size();
+  d.pcg_grid = n > 0 ? grid : 0;
+  d.pcg_lanes = lanes;
+  d.pcg_max_rows = (int32_t)std::max<int64_t>(max_rows, 1);
+  return BDEM_OK;
+}
+
+// default PCG launch shape: 4 lanes per row, every co-resident block, at least 64 rows per block
+static size_t pcg_smem_for(const bdem_sim* s, int grid) {
+  return sizeof(int4) * (size_t)std::max<int64_t>(1, 2 * (s->n / std::max(grid, 1) + 64));
+}
+
+// builds the partition for (lanes, grid) and shrinks the grid until every block is co-resident with the partition's
+// actual shared-memory need (a cooperative launch requires it)
+static bdem_status apply_pcg_shape(bdem_sim* s, int lanes, int grid) {
+  for (int tries = 0; tries < 16; ++tries) {
+    TRY(build_pcg_segments(s, lanes, grid));
+    int mx = pcg_max_blocks(s->d.mixed, lanes, sizeof(int4) * (size_t)s->d.pcg_max_rows);
+    if (mx < 1) return fail(s, BDEM_E_CUDA, "no resident blocks for the PCG kernel");
+    if (s->d.pcg_grid <= mx) return BDEM_OK;
+    grid = mx;
+  }
+  return fail(s, BDEM_E_CUDA, "could not fit the PCG grid on the device");
+}
+
+static bdem_status default_pcg_shape(bdem_sim* s) {
+  int lanes = 2;
+  int mx = pcg_max_blocks(s->d.mixed, lanes, pcg_smem_for(s, 608));
+  if (mx < 1) return fail(s, BDEM_E_CUDA, "no resident blocks for the PCG kernel");
+  int grid = (int)std::min<int64_t>(mx, std::max<int64_t>(1, (s->n + 63) / 64));
+  s->pcg_blocks = mx;
+  return apply_pcg_shape(s, lanes, grid);
 }
 
 extern "C" bdem_status bdem_create(const bdem_config* config, int32_t n_scenes, const int64_t* scene_offsets,
@@ -315,11 +449,17 @@ extern "C" bdem_status bdem_create(const bdem_config* config, int32_t n_scenes, 
   s->pscene.resize(n);
   for (int sc = 0; sc < n_scenes; ++sc)
     for (int64_t i = scene_offsets[sc]; i < scene_offsets[sc + 1]; ++i) s->pscene[i] = sc;
-  s->radius.assign(radius, radius + n);
+  morton_order(scene_offsets, n_scenes, pos, s->perm);
+  s->iperm.resize(n);
+  s->deg.assign(n, 0);
+  for (int64_t k = 0; k < n; ++k) s->iperm[s->perm[k]] = (int32_t)k;
+  s->radius.resize(n);
   s->mass.resize(n);
   s->kin.assign(n, 0);
-  if (kinematic)
-    for (int64_t i = 0; i < n; ++i) s->kin[i] = kinematic[i] ? 1 : 0;
+  for (int64_t k = 0; k < n; ++k) {
+    s->radius[k] = radius[s->perm[k]];
+    if (kinematic) s->kin[k] = kinematic[s->perm[k]] ? 1 : 0;
+  }
   const bdem_config& c = s->cfg;
   DevArrays& d = s->d;
   d.n = (int32_t)n;
@@ -347,16 +487,17 @@ extern "C" bdem_status bdem_create(const bdem_config* config, int32_t n_scenes, 
     std::vector<double4> xp(std::max<int64_t>(n, 1)), xq(std::max<int64_t>(n, 1)), vp(std::max<int64_t>(n, 1)),
         vq(std::max<int64_t>(n, 1)), hp(std::max<int64_t>(n, 1));
     std::vector<double2> coef(std::max<int64_t>(n, 1));
-    for (int64_t i = 0; i < n; ++i) {
-      const bdem_material& M = mats[particle_material[i]];
-      double r = radius[i], m = M.density * 4.0 / 3.0 * M_PI * r * r * r;
+    for (int64_t i = 0; i < n; ++i) {  // i internal, u the caller's index
+      int64_t u = s->perm[i];
+      const bdem_material& M = mats[particle_material[u]];
+      double r = radius[u], m = M.density * 4.0 / 3.0 * M_PI * r * r * r;
       s->mass[i] = m;
-      double qn = std::sqrt(quat[4 * i] * quat[4 * i] + quat[4 * i + 1] * quat[4 * i + 1] +
-                            quat[4 * i + 2] * quat[4 * i + 2] + quat[4 * i + 3] * quat[4 * i + 3]);
-      xp[i] = make_double4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], r);
-      xq[i] = make_double4(quat[4 * i] / qn, quat[4 * i + 1] / qn, quat[4 * i + 2] / qn, quat[4 * i + 3] / qn);
-      vp[i] = vel ? make_double4(vel[3 * i], vel[3 * i + 1], vel[3 * i + 2], 0.0) : make_double4(0, 0, 0, 0);
-      vq[i] = quat_vel ? make_double4(quat_vel[4 * i], quat_vel[4 * i + 1], quat_vel[4 * i + 2], quat_vel[4 * i + 3])
+      double qn = std::sqrt(quat[4 * u] * quat[4 * u] + quat[4 * u + 1] * quat[4 * u + 1] +
+                            quat[4 * u + 2] * quat[4 * u + 2] + quat[4 * u + 3] * quat[4 * u + 3]);
+      xp[i] = make_double4(pos[3 * u], pos[3 * u + 1], pos[3 * u + 2], r);
+      xq[i] = make_double4(quat[4 * u] / qn, quat[4 * u + 1] / qn, quat[4 * u + 2] / qn, quat[4 * u + 3] / qn);
+      vp[i] = vel ? make_double4(vel[3 * u], vel[3 * u + 1], vel[3 * u + 2], 0.0) : make_double4(0, 0, 0, 0);
+      vq[i] = quat_vel ? make_double4(quat_vel[4 * u], quat_vel[4 * u + 1], quat_vel[4 * u + 2], quat_vel[4 * u + 3])
                        : make_double4(0, 0, 0, 0);
       hp[i] = make_double4(0, 0, 0, m);
       coef[i] = make_double2(m / (c.dt * c.dt), 1.6 * m * r * r / (c.dt * c.dt));
@@ -373,10 +514,11 @@ extern "C" bdem_status bdem_create(const bdem_config* config, int32_t n_scenes, 
       cudaMemcpy(d.coef, coef.data(), sizeof(double2) * nn, cudaMemcpyHostToDevice);
       cudaMemcpy(d.pscene, s->pscene.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice);
       cudaMemcpy(d.kin, s->kin.data(), nn, cudaMemcpyHostToDevice);
+      cudaMemcpy(d.perm, s->perm.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice);
     }
     // no bonds yet: empty incidence lists and an empty bond-tile table (every scene owns zero bond tiles)
     st = BDEM_OK;
-    if (dalloc_t(s, &d.inc_start, nn + 1) != BDEM_OK || dalloc_t(s, &d.inc, 1) != BDEM_OK ||
+    if (dalloc_t(s, &d.inc_start, nn + 1) != BDEM_OK || dalloc_t(s, &d.inc2, 1) != BDEM_OK ||
         dalloc_t(s, &d.btile_start, 1) != BDEM_OK || dalloc_t(s, &d.btile_scene, 1) != BDEM_OK ||
         dalloc_t(s, &d.btile_begin, (size_t)n_scenes + 1) != BDEM_OK ||
         dalloc_t(s, &d.part_b, (size_t)kPartials) != BDEM_OK)
@@ -384,8 +526,7 @@ extern "C" bdem_status bdem_create(const bdem_config* config, int32_t n_scenes, 
     d.n_btiles = 0;
     cudaError_t e = cudaDeviceSynchronize();
     if (st == BDEM_OK && e != cudaSuccess) st = fail(s, BDEM_E_CUDA, "upload: %s", cudaGetErrorString(e));
-    if (st == BDEM_OK) s->pcg_blocks = pcg_max_blocks(d.mixed);
-    if (st == BDEM_OK && s->pcg_blocks < 1) st = fail(s, BDEM_E_CUDA, "no resident blocks for the PCG kernel");
+    if (st == BDEM_OK) st = default_pcg_shape(s);
   }
   if (st != BDEM_OK) {
     g_create_err = s->err;
@@ -399,6 +540,15 @@ extern "C" bdem_status bdem_create(const bdem_config* config, int32_t n_scenes, 
 // ------------------------------------------------------------------------------------------------
 // bonds
 // ------------------------------------------------------------------------------------------------
+
+// staging sub-arrays of the caller-order state: pos [n][3], quat [n][4], vel [n][3], quat_vel [n][4], each starting
+// on a 256-byte boundary
+static size_t stage_off(size_t n, int k) {
+  const size_t len[4] = {3 * n, 4 * n, 3 * n, 4 * n};
+  size_t off = 0;
+  for (int i = 0; i < k; ++i) off += (len[i] + 31) & ~(size_t)31;
+  return off;
+}
 
 static bdem_status download_committed(bdem_sim* s, std::vector<double4>& xp, std::vector<double4>& xq) {
   xp.resize(std::max(s->n, 1));
@@ -418,14 +568,18 @@ extern "C" bdem_status bdem_add_bonds(bdem_sim* s, int64_t n, const int32_t* I, 
   if (s->nb + n > ((int64_t)1 << 29)) return fail(s, BDEM_E_INVALID, "too many bonds");
   std::vector<double4> xp, xq;
   TRY(download_committed(s, xp, xq));
-  struct NB { int32_t a, b, m; int64_t old; };
+  struct NB { int32_t a, b, m; int64_t old, ext; };
   std::vector<NB> all;
   all.reserve(s->nb + n);
-  for (int64_t k = 0; k < s->nb; ++k) all.push_back({s->bi[k], s->bj[k], s->bmat[k], k});
+  std::vector<int64_t> old_ext(s->nb);  // stored index -> caller index of the existing bonds
+  for (int64_t e = 0; e < s->nb; ++e) old_ext[s->bond_ext2int_h[e]] = e;
+  for (int64_t k = 0; k < s->nb; ++k) all.push_back({s->bi[k], s->bj[k], s->bmat[k], k, old_ext[k]});
   for (int64_t k = 0; k < n; ++k) {
-    int32_t i = I[k], j = J[k], m = M[k];
-    if (i < 0 || j < 0 || i >= s->n || j >= s->n) return fail(s, BDEM_E_INVALID, "bond %lld: index out of range", (long long)k);
-    if (i == j) return fail(s, BDEM_E_INVALID, "bond %lld: i == j", (long long)k);
+    int32_t iu = I[k], ju = J[k], m = M[k];
+    if (iu < 0 || ju < 0 || iu >= s->n || ju >= s->n)
+      return fail(s, BDEM_E_INVALID, "bond %lld: index out of range", (long long)k);
+    if (iu == ju) return fail(s, BDEM_E_INVALID, "bond %lld: i == j", (long long)k);
+    int32_t i = s->iperm[iu], j = s->iperm[ju];
     if (s->pscene[i] != s->pscene[j]) return fail(s, BDEM_E_INVALID, "bond %lld joins two scenes", (long long)k);
     if (m < 0 || m >= (int32_t)s->mats.size()) return fail(s, BDEM_E_INVALID, "bond %lld: material out of range", (long long)k);
     double4 qi = xq[i], qj = xq[j];
@@ -434,12 +588,12 @@ extern "C" bdem_status bdem_add_bonds(bdem_sim* s, int64_t n, const int32_t* I, 
       return fail(s, BDEM_E_INVALID, "bond %lld: endpoint orientations differ (q_i.q_j = %.17g)", (long long)k, qd);
     double dx = xp[j].x - xp[i].x, dy = xp[j].y - xp[i].y, dz = xp[j].z - xp[i].z;
     if (!(dx * dx + dy * dy + dz * dz > 0.0)) return fail(s, BDEM_E_INVALID, "bond %lld: zero length", (long long)k);
-    all.push_back({std::min(i, j), std::max(i, j), m, -1 - k});
+    all.push_back({std::min(i, j), std::max(i, j), m, -1 - k, s->nb + k});
   }
   std::sort(all.begin(), all.end(), [](const NB& x, const NB& y) { return x.a != y.a ? x.a < y.a : x.b < y.b; });
   for (size_t k = 1; k < all.size(); ++k)
     if (all[k].a == all[k - 1].a && all[k].b == all[k - 1].b)
-      return fail(s, BDEM_E_INVALID, "duplicate bond (%d, %d)", all[k].a, all[k].b);
+      return fail(s, BDEM_E_INVALID, "duplicate bond (%d, %d)", s->perm[all[k].a], s->perm[all[k].b]);
   // broken flags of the existing bonds
   std::vector<uint8_t> old_broken(std::max<int64_t>(s->nb, 1), 0);
   if (s->nb) CUDA_TRY(s, cudaMemcpy(old_broken.data(), s->d.bbroken, s->nb, cudaMemcpyDeviceToHost));
@@ -448,9 +602,11 @@ extern "C" bdem_status bdem_add_bonds(bdem_sim* s, int64_t n, const int32_t* I, 
   std::vector<double4> rest(nb), stiff(nb);
   std::vector<double> brk(nb);
   std::vector<uint8_t> broken(nb, 0);
-  std::vector<int32_t> bscene(nb), bi(nb), bj(nb), bm(nb);
+  std::vector<int32_t> bscene(nb), bi(nb), bj(nb), bm(nb), e2i(nb), i2e(nb);
   for (int64_t k = 0; k < nb; ++k) {
     const NB& e = all[k];
+    e2i[e.ext] = (int32_t)k;
+    i2e[k] = (int32_t)e.ext;
     bij[k] = make_int2(e.a, e.b);
     bi[k] = e.a;
     bj[k] = e.b;
@@ -487,7 +643,8 @@ extern "C" bdem_status bdem_add_bonds(bdem_sim* s, int64_t n, const int32_t* I, 
                             mt.bend_twist_scale * mt.E * Ia / l0, mt.bend_twist_scale * G * Ja / l0);
   }
   // incidence CSR (entries ordered by bond index within each particle)
-  std::vector<int32_t> inc_start(s->n + 1, 0), inc(2 * nb);
+  std::vector<int32_t> inc_start(s->n + 1, 0);
+  std::vector<int2> inc(2 * nb);
   for (int64_t k = 0; k < nb; ++k) {
     inc_start[bi[k] + 1]++;
     inc_start[bj[k] + 1]++;
@@ -496,8 +653,8 @@ extern "C" bdem_status bdem_add_bonds(bdem_sim* s, int64_t n, const int32_t* I, 
   {
     std::vector<int32_t> fill(inc_start.begin(), inc_start.end() - 1);
     for (int64_t k = 0; k < nb; ++k) {
-      inc[fill[bi[k]]++] = (int32_t)(k << 1);
-      inc[fill[bj[k]]++] = (int32_t)((k << 1) | 1);
+      inc[fill[bi[k]]++] = make_int2((int32_t)(k << 1), bj[k]);
+      inc[fill[bj[k]]++] = make_int2((int32_t)((k << 1) | 1), bi[k]);
     }
   }
   // bond tiles per scene
@@ -518,7 +675,7 @@ extern "C" bdem_status bdem_add_bonds(bdem_sim* s, int64_t n, const int32_t* I, 
   }
   // replace the device bond arrays
   DevArrays& d = s->d;
-  void* olds[] = {d.bij, d.brest, d.bstiff, d.bbrk, d.bbroken, d.bscene, d.bg, d.bM, d.bE, d.inc, d.inc_start,
+  void* olds[] = {d.bij, d.brest, d.bstiff, d.bbrk, d.bbroken, d.bscene, d.bg, d.bM, d.bE, d.inc2, d.inc_start, d.bond_ext2int, d.bond_int2ext, s->flag_stage,
                   d.btile_start, d.btile_scene, d.btile_begin, d.part_b};
   for (void* p : olds) dfree(s, p);
   size_t w = wsize(s);
@@ -531,7 +688,10 @@ extern "C" bdem_status bdem_add_bonds(bdem_sim* s, int64_t n, const int32_t* I, 
   TRY(dalloc_t(s, &d.bg, 9 * (size_t)nb));
   TRY(dalloc(s, &d.bM, w * 36 * nb));
   TRY(dalloc(s, &d.bE, w * 12 * nb));
-  TRY(dalloc_t(s, &d.inc, 2 * (size_t)nb));
+  TRY(dalloc_t(s, &d.inc2, 2 * (size_t)nb));
+  TRY(dalloc_t(s, &d.bond_ext2int, nb));
+  TRY(dalloc_t(s, &d.bond_int2ext, nb));
+  TRY(dalloc_t(s, &s->flag_stage, nb));
   TRY(dalloc_t(s, &d.inc_start, (size_t)s->n + 1));
   TRY(dalloc_t(s, &d.btile_start, tstart.size()));
   TRY(dalloc_t(s, &d.btile_scene, std::max<size_t>(1, tscene.size())));
@@ -543,7 +703,9 @@ extern "C" bdem_status bdem_add_bonds(bdem_sim* s, int64_t n, const int32_t* I, 
   CUDA_TRY(s, cudaMemcpy(d.bbrk, brk.data(), sizeof(double) * nb, cudaMemcpyHostToDevice));
   CUDA_TRY(s, cudaMemcpy(d.bbroken, broken.data(), nb, cudaMemcpyHostToDevice));
   CUDA_TRY(s, cudaMemcpy(d.bscene, bscene.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice));
-  CUDA_TRY(s, cudaMemcpy(d.inc, inc.data(), sizeof(int32_t) * 2 * nb, cudaMemcpyHostToDevice));
+  CUDA_TRY(s, cudaMemcpy(d.inc2, inc.data(), sizeof(int2) * 2 * nb, cudaMemcpyHostToDevice));
+  CUDA_TRY(s, cudaMemcpy(d.bond_ext2int, e2i.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice));
+  CUDA_TRY(s, cudaMemcpy(d.bond_int2ext, i2e.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice));
   CUDA_TRY(s, cudaMemcpy(d.inc_start, inc_start.data(), sizeof(int32_t) * (s->n + 1), cudaMemcpyHostToDevice));
   CUDA_TRY(s, cudaMemcpy(d.btile_start, tstart.data(), sizeof(int32_t) * tstart.size(), cudaMemcpyHostToDevice));
   if (!tscene.empty())
@@ -552,6 +714,12 @@ extern "C" bdem_status bdem_add_bonds(bdem_sim* s, int64_t n, const int32_t* I, 
   d.nb = (int32_t)nb;
   d.n_btiles = (int32_t)tscene.size();
   s->nb = nb;
+  for (int64_t k = 0; k < n; ++k) {
+    s->ext_i.push_back(std::min(I[k], J[k]));
+    s->ext_j.push_back(std::max(I[k], J[k]));
+  }
+  s->bond_ext2int_h.swap(e2i);
+  for (int i = 0; i < s->n; ++i) s->deg[i] = inc_start[i + 1] - inc_start[i];
   s->bi.swap(bi);
   s->bj.swap(bj);
   s->bmat.swap(bm);
@@ -559,7 +727,8 @@ extern "C" bdem_status bdem_add_bonds(bdem_sim* s, int64_t n, const int32_t* I, 
   s->stiff.swap(stiff);
   s->brk.swap(brk);
   s->system_ready = false;
-  return BDEM_OK;
+  // the PCG partition weighs rows by their bond counts: rebuild it for the new bonds (same shape)
+  return apply_pcg_shape(s, s->d.pcg_lanes, s->d.pcg_grid);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -586,12 +755,14 @@ static bdem_status build_contacts(bdem_sim* s) {
   if (total < 0) return fail(s, BDEM_E_CUDA, "contact count overflow");
   if (total > d.c_cap) {
     dfree(s, d.c_nbr);
+    dfree(s, d.c_anbr);
     dfree(s, d.c_blk);
-    d.c_nbr = nullptr;
+    d.c_nbr = d.c_anbr = nullptr;
     d.c_blk = nullptr;
     int64_t cap = (int64_t)total + total / 2 + 1024;
     if (cap > ((int64_t)1 << 31) - 1) return fail(s, BDEM_E_NOMEM, "too many contact candidates");
     TRY(dalloc_t(s, &d.c_nbr, (size_t)cap));
+    TRY(dalloc_t(s, &d.c_anbr, (size_t)cap));
     TRY(dalloc(s, &d.c_blk, 4 * wsize(s) * (size_t)cap));
     d.c_cap = (int32_t)cap;
   }
@@ -601,7 +772,7 @@ static bdem_status build_contacts(bdem_sim* s) {
 
 static bdem_status run_pcg(bdem_sim* s, const DevArrays& d, int rhs_from_g, int mask) {
   cudaError_t e = cudaSuccess;
-  int k = launch_pcg(d, rhs_from_g, mask, s->pcg_blocks, s->stream, &e);
+  int k = launch_pcg(d, rhs_from_g, mask, s->stream, &e);
   s->launches += k;
   if (e != cudaSuccess) return fail(s, BDEM_E_CUDA, "cooperative PCG launch: %s", cudaGetErrorString(e));
   return check_launch(s, 0);
@@ -718,14 +889,20 @@ extern "C" bdem_status bdem_read_state(bdem_sim* s, double* pos, double* quat, d
   DevArrays& d = s->d;
   size_t n = (size_t)s->n;
   cudaStream_t st = s->stream;
-  if (n) {
-    if (pos || vel) TRY(check_launch(s, launch_pack_state(d, pos ? s->stage : nullptr, vel ? s->stage + 3 * n : nullptr, st)));
-    if (pos) CUDA_TRY(s, cudaMemcpyAsync(pos, s->stage, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
-    if (vel) CUDA_TRY(s, cudaMemcpyAsync(vel, s->stage + 3 * n, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
-    if (quat) CUDA_TRY(s, cudaMemcpyAsync(quat, d.x0q, sizeof(double4) * n, cudaMemcpyDeviceToHost, st));
-    if (quat_vel) CUDA_TRY(s, cudaMemcpyAsync(quat_vel, d.vq, sizeof(double4) * n, cudaMemcpyDeviceToHost, st));
+  double *sp = s->stage + stage_off(n, 0), *sq = s->stage + stage_off(n, 1), *sv = s->stage + stage_off(n, 2),
+         *su = s->stage + stage_off(n, 3);
+  if (n && (pos || quat || vel || quat_vel)) {
+    TRY(check_launch(s, launch_pack_state(d, pos ? sp : nullptr, quat ? sq : nullptr, vel ? sv : nullptr,
+                                          quat_vel ? su : nullptr, st)));
+    if (pos) CUDA_TRY(s, cudaMemcpyAsync(pos, sp, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+    if (quat) CUDA_TRY(s, cudaMemcpyAsync(quat, sq, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, st));
+    if (vel) CUDA_TRY(s, cudaMemcpyAsync(vel, sv, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+    if (quat_vel) CUDA_TRY(s, cudaMemcpyAsync(quat_vel, su, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, st));
   }
-  if (bond_broken && s->nb) CUDA_TRY(s, cudaMemcpyAsync(bond_broken, d.bbroken, s->nb, cudaMemcpyDeviceToHost, st));
+  if (bond_broken && s->nb) {
+    TRY(check_launch(s, launch_bond_flags(d, s->flag_stage, 0, st)));
+    CUDA_TRY(s, cudaMemcpyAsync(bond_broken, s->flag_stage, s->nb, cudaMemcpyDeviceToHost, st));
+  }
   return sync(s);
 }
 
@@ -752,22 +929,22 @@ extern "C" bdem_status bdem_write_state(bdem_sim* s, const double* pos, const do
   }
   DevArrays& d = s->d;
   cudaStream_t st = s->stream;
-  if (n) {
-    if (pos) CUDA_TRY(s, cudaMemcpyAsync(s->stage, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
-    if (vel) CUDA_TRY(s, cudaMemcpyAsync(s->stage + 3 * n, vel, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
-    if (pos || vel)
-      TRY(check_launch(s, launch_unpack_state(d, pos ? s->stage : nullptr, vel ? s->stage + 3 * n : nullptr, st)));
-    if (quat) CUDA_TRY(s, cudaMemcpyAsync(d.x0q, quat, sizeof(double4) * n, cudaMemcpyHostToDevice, st));
-    if (quat_vel) CUDA_TRY(s, cudaMemcpyAsync(d.vq, quat_vel, sizeof(double4) * n, cudaMemcpyHostToDevice, st));
+  double *sp = s->stage + stage_off(n, 0), *sq = s->stage + stage_off(n, 1), *sv = s->stage + stage_off(n, 2),
+         *su = s->stage + stage_off(n, 3);
+  if (n && (pos || quat || vel || quat_vel)) {
+    if (pos) CUDA_TRY(s, cudaMemcpyAsync(sp, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    if (quat) CUDA_TRY(s, cudaMemcpyAsync(sq, quat, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, st));
+    if (vel) CUDA_TRY(s, cudaMemcpyAsync(sv, vel, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    if (quat_vel) CUDA_TRY(s, cudaMemcpyAsync(su, quat_vel, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, st));
+    TRY(check_launch(s, launch_unpack_state(d, pos ? sp : nullptr, quat ? sq : nullptr, vel ? sv : nullptr,
+                                            quat_vel ? su : nullptr, st)));
   }
   if (bond_broken && s->nb) {
-    std::vector<uint8_t> b(bond_broken, bond_broken + s->nb);
-    for (auto& x : b) x = x ? 1 : 0;
-    CUDA_TRY(s, cudaMemcpyAsync(d.bbroken, b.data(), s->nb, cudaMemcpyHostToDevice, st));
-    TRY(sync(s));
+    CUDA_TRY(s, cudaMemcpyAsync(s->flag_stage, bond_broken, s->nb, cudaMemcpyHostToDevice, st));
+    TRY(check_launch(s, launch_bond_flags(d, s->flag_stage, 1, st)));
   }
   s->system_ready = false;
-  return BDEM_OK;
+  return sync(s);
 }
 
 extern "C" bdem_status bdem_sizes(const bdem_sim* s, int64_t* n_particles, int64_t* n_bonds, int32_t* n_scenes) {
@@ -780,9 +957,9 @@ extern "C" bdem_status bdem_sizes(const bdem_sim* s, int64_t* n_particles, int64
 
 extern "C" bdem_status bdem_bond_order(const bdem_sim* s, int32_t* pairs) {
   if (!s || (!pairs && s->nb)) return BDEM_E_INVALID;
-  for (int64_t k = 0; k < s->nb; ++k) {
-    pairs[2 * k] = s->bi[k];
-    pairs[2 * k + 1] = s->bj[k];
+  for (int64_t k = 0; k < s->nb; ++k) {  // the caller's order of addition, caller indices
+    pairs[2 * k] = s->ext_i[k];
+    pairs[2 * k + 1] = s->ext_j[k];
   }
   return BDEM_OK;
 }
@@ -823,13 +1000,10 @@ extern "C" bdem_status bdem_debug_system(bdem_sim* s, const double* phat, const 
   cudaStream_t st = s->stream;
   size_t n = (size_t)s->n;
   if (n) {
-    std::vector<double4> hp(n), hq(n);
-    for (size_t i = 0; i < n; ++i) {
-      hp[i] = make_double4(phat[3 * i], phat[3 * i + 1], phat[3 * i + 2], s->mass[i]);
-      hq[i] = make_double4(qhat[4 * i], qhat[4 * i + 1], qhat[4 * i + 2], qhat[4 * i + 3]);
-    }
-    CUDA_TRY(s, cudaMemcpy(d.hp, hp.data(), sizeof(double4) * n, cudaMemcpyHostToDevice));
-    CUDA_TRY(s, cudaMemcpy(d.hq, hq.data(), sizeof(double4) * n, cudaMemcpyHostToDevice));
+    double *sp = s->stage + stage_off(n, 0), *sq = s->stage + stage_off(n, 1);
+    CUDA_TRY(s, cudaMemcpyAsync(sp, phat, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(s, cudaMemcpyAsync(sq, qhat, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, st));
+    TRY(check_launch(s, launch_set_hat(d, sp, sq, st)));
     CUDA_TRY(s, cudaMemcpyAsync(d.xp, d.x0p, sizeof(double4) * n, cudaMemcpyDeviceToDevice, st));
     CUDA_TRY(s, cudaMemcpyAsync(d.xq, d.x0q, sizeof(double4) * n, cudaMemcpyDeviceToDevice, st));
   }
@@ -840,7 +1014,12 @@ extern "C" bdem_status bdem_debug_system(bdem_sim* s, const double* phat, const 
   TRY(check_launch(s, launch_particle_grad(d, 0, 1, st)));
   TRY(check_launch(s, launch_bond_hess(d, 1, st)));
   TRY(check_launch(s, launch_particle_hess(d, 0, 1, st)));
-  if (g && n) CUDA_TRY(s, cudaMemcpyAsync(g, d.g, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, st));
+  if (g && n) {
+    TRY(dbg_reserve(s, 6 * n));
+    TRY(check_launch(s, launch_convert_perm(d.g, 1, s->dbg_buf, 1, d.perm, 1, (int)n, st)));
+    CUDA_TRY(s, cudaMemcpyAsync(g, s->dbg_buf, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, st));
+    TRY(sync(s));
+  }
   if (diag && n) {
     TRY(dbg_reserve(s, 36 * n));
     TRY(check_launch(s, launch_unpack_diag(d, s->dbg_buf, st)));
@@ -871,12 +1050,12 @@ extern "C" bdem_status bdem_debug_matvec(bdem_sim* s, const double* x, double* y
   if (!n) return BDEM_OK;
   DevArrays& d = s->d;
   cudaStream_t st = s->stream;
-  TRY(dbg_reserve(s, 6 * n));
+  TRY(dbg_reserve(s, 12 * n));
   CUDA_TRY(s, cudaMemcpyAsync(s->dbg_buf, x, sizeof(double) * 6 * n, cudaMemcpyHostToDevice, st));
-  TRY(check_launch(s, launch_convert(s->dbg_buf, 1, d.vp_, !d.mixed, 6 * n, st)));
+  TRY(check_launch(s, launch_convert_perm(s->dbg_buf, 1, d.vp_, !d.mixed, d.perm, 0, (int)n, st)));
   TRY(check_launch(s, launch_matvec(d, 0, st)));
-  TRY(check_launch(s, launch_convert(d.vq_, !d.mixed, s->dbg_buf, 1, 6 * n, st)));
-  CUDA_TRY(s, cudaMemcpyAsync(y, s->dbg_buf, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, st));
+  TRY(check_launch(s, launch_convert_perm(d.vq_, !d.mixed, s->dbg_buf + 6 * n, 1, d.perm, 1, (int)n, st)));
+  CUDA_TRY(s, cudaMemcpyAsync(y, s->dbg_buf + 6 * n, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, st));
   return sync(s);
 }
 
@@ -900,14 +1079,14 @@ extern "C" bdem_status bdem_debug_pcg(bdem_sim* s, const double* b, double eps_r
     c.eps_r = eps_r;
   }
   CUDA_TRY(s, cudaMemcpy(d.sc, ctl.data(), sizeof(SceneCtl) * s->n_scenes, cudaMemcpyHostToDevice));
-  TRY(dbg_reserve(s, 6 * n));
+  TRY(dbg_reserve(s, 12 * n));
   CUDA_TRY(s, cudaMemcpyAsync(s->dbg_buf, b, sizeof(double) * 6 * n, cudaMemcpyHostToDevice, st));
-  TRY(check_launch(s, launch_convert(s->dbg_buf, 1, d.vr, !d.mixed, 6 * n, st)));
+  TRY(check_launch(s, launch_convert_perm(s->dbg_buf, 1, d.vr, !d.mixed, d.perm, 0, (int)n, st)));
   TRY(run_pcg(s, d, 0, 1));
   Counters c{};
   TRY(read_counters(s, &c));
-  TRY(check_launch(s, launch_convert(d.vx, !d.mixed, s->dbg_buf, 1, 6 * n, st)));
-  CUDA_TRY(s, cudaMemcpyAsync(dx, s->dbg_buf, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, st));
+  TRY(check_launch(s, launch_convert_perm(d.vx, !d.mixed, s->dbg_buf + 6 * n, 1, d.perm, 1, (int)n, st)));
+  CUDA_TRY(s, cudaMemcpyAsync(dx, s->dbg_buf + 6 * n, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(s, cudaMemcpyAsync(ctl.data(), d.sc, sizeof(SceneCtl) * s->n_scenes, cudaMemcpyDeviceToHost, st));
   TRY(sync(s));
   if (iters)
@@ -944,18 +1123,19 @@ extern "C" bdem_status bdem_pcg_static(bdem_sim* s, const double* b_dev, double*
   if (!b_dev || !x_dev || max_iter < 1 || !(eps_r >= 0.0)) return fail(s, BDEM_E_INVALID, "bad PCG arguments");
   DevArrays d = s->d;
   size_t n = (size_t)s->n, w = wsize(s);
-  // scratch layout: scene control blocks | counters | tile partials | PCG vectors x r z p q
+  // scratch layout: scene control blocks | counters | segment partials | PCG vectors x r z p w s
+  constexpr int kVecs = 6;
   size_t off_sc = 0;
   size_t off_cnt = off_sc + align256(sizeof(SceneCtl) * (size_t)std::max(s->n_scenes, 1));
   size_t off_part = off_cnt + align256(sizeof(Counters));
-  size_t off_vec = off_part + align256(sizeof(double) * kPartials * (size_t)std::max(d.n_ptiles, 1));
+  size_t off_vec = off_part + align256(sizeof(double) * kPartials * (size_t)std::max(d.n_seg, 1));
   size_t vec_bytes = align256(w * 6 * std::max<size_t>(n, 1));
-  size_t need = off_vec + 5 * vec_bytes;
+  size_t need = off_vec + kVecs * vec_bytes;
   if (need > static_pcg_capacity())
     return fail(s, BDEM_E_INVALID,
                 "system too large for the static PCG scratch: needs %zu bytes, the array holds %zu bytes "
                 "(about %zu particles in this precision)",
-                need, static_pcg_capacity(), (size_t)(static_pcg_capacity() / (5 * 6 * w + 1)));
+                need, static_pcg_capacity(), (size_t)(static_pcg_capacity() / (kVecs * 6 * w + 1)));
   if (!s->system_ready) return fail(s, BDEM_E_INVALID, "call bdem_debug_system first");
   if (n == 0) return BDEM_OK;
   void* base = nullptr;
@@ -964,16 +1144,16 @@ extern "C" bdem_status bdem_pcg_static(bdem_sim* s, const double* b_dev, double*
   unsigned char* b8 = static_cast<unsigned char*>(base);
   d.sc = reinterpret_cast<SceneCtl*>(b8 + off_sc);
   d.cnt = reinterpret_cast<Counters*>(b8 + off_cnt);
-  d.part_p = reinterpret_cast<double*>(b8 + off_part);
-  void** vecs[] = {&d.vx, &d.vr, &d.vz, &d.vp_, &d.vq_};
-  for (int k = 0; k < 5; ++k) *vecs[k] = b8 + off_vec + k * vec_bytes;
+  d.part_s = reinterpret_cast<double*>(b8 + off_part);
+  void** vecs[] = {&d.vx, &d.vr, &d.vz, &d.vp_, &d.vq_, &d.vs};
+  for (int k = 0; k < kVecs; ++k) *vecs[k] = b8 + off_vec + k * vec_bytes;
   d.pcg_max = max_iter;
   cudaStream_t st = s->stream;
   int k = launch_static_pcg_init(d, eps_r, st);
-  k += launch_convert(b_dev, 1, d.vr, !d.mixed, 6 * (int64_t)n, st);
+  k += launch_convert_perm(b_dev, 1, d.vr, !d.mixed, d.perm, 0, (int)n, st);
   TRY(check_launch(s, k));
   TRY(run_pcg(s, d, 0, 1));
-  TRY(check_launch(s, launch_convert(d.vx, !d.mixed, x_dev, 1, 6 * (int64_t)n, st)));
+  TRY(check_launch(s, launch_convert_perm(d.vx, !d.mixed, x_dev, 1, d.perm, 1, (int)n, st)));
   Counters c{};
   CUDA_TRY(s, cudaMemcpyAsync(&c, d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
   if (iters)
@@ -981,5 +1161,82 @@ extern "C" bdem_status bdem_pcg_static(bdem_sim* s, const double* b_dev, double*
       CUDA_TRY(s, cudaMemcpyAsync(iters + sc, &d.sc[sc].pcg_iters, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(s, cudaStreamSynchronize(s->stream));
   if (c.timeout) return fail(s, BDEM_E_TIMEOUT, "a device-side wait gave up");
+  return BDEM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// PCG launch shape and its autotuner
+// ------------------------------------------------------------------------------------------------
+
+extern "C" bdem_status bdem_set_pcg_shape(bdem_sim* s, int32_t lanes, int32_t blocks) {
+  if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
+  if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8) return fail(s, BDEM_E_INVALID, "lanes must be 1, 2, 4 or 8");
+  if (blocks < 0) return fail(s, BDEM_E_INVALID, "blocks must be >= 0");
+  int mx = pcg_max_blocks(s->d.mixed, lanes, pcg_smem_for(s, blocks > 0 ? blocks : 608));
+  if (mx < 1) return fail(s, BDEM_E_CUDA, "no resident blocks for the PCG kernel");
+  int cap = (int)std::min<int64_t>(mx, std::max<int64_t>(1, (s->n + 63) / 64));
+  int grid = blocks == 0 ? cap : std::min(blocks, cap);
+  TRY(sync(s));
+  TRY(apply_pcg_shape(s, lanes, grid));
+  s->pcg_blocks = mx;
+  return BDEM_OK;
+}
+
+// assemble the Newton system at the committed state with xhat = x + dt v (the step's prediction)
+static bdem_status assemble_at_committed(bdem_sim* s) {
+  DevArrays& d = s->d;
+  cudaStream_t st = s->stream;
+  TRY(check_launch(s, launch_predict(d, st)));
+  if (d.k_self > 0.0 && d.n > 0) TRY(build_contacts(s));
+  else if (d.n > 0) CUDA_TRY(s, cudaMemsetAsync(d.c_start, 0, sizeof(int32_t) * (d.n + 1), st));
+  TRY(check_launch(s, launch_scene_reduce(d, RED_FORCE_ACTIVE, 0, st)));
+  TRY(check_launch(s, launch_bond_grad(d, 1, st)));
+  TRY(check_launch(s, launch_particle_grad(d, 1, 1, st)));
+  TRY(check_launch(s, launch_bond_hess(d, 1, st)));
+  TRY(check_launch(s, launch_particle_hess(d, 1, 1, st)));
+  return sync(s);
+}
+
+extern "C" bdem_status bdem_autotune_pcg(bdem_sim* s, int32_t iters, int32_t* lanes_out, int32_t* blocks_out) {
+  if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
+  if (iters < 1) return fail(s, BDEM_E_INVALID, "iters must be >= 1");
+  if (s->n == 0) return BDEM_OK;
+  TRY(assemble_at_committed(s));
+  cudaEvent_t a = ev_get(s), b = ev_get(s);
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  float best = 1e30f;
+  int best_l = s->d.pcg_lanes, best_g = s->d.pcg_grid;
+  const int lanes_c[] = {1, 2, 4, 8};
+  for (int lanes : lanes_c) {
+    int mx = pcg_max_blocks(s->d.mixed, lanes, pcg_smem_for(s, 4 * sms));
+    for (int per = 1; per <= std::max(1, mx / sms); ++per) {
+      TRY(bdem_set_pcg_shape(s, lanes, per * sms));
+      DevArrays d = s->d;
+      d.pcg_max = iters;
+      float t_min = 1e30f;
+      for (int rep = 0; rep < 2; ++rep) {
+        std::vector<SceneCtl> ctl(s->n_scenes);
+        CUDA_TRY(s, cudaMemcpy(ctl.data(), d.sc, sizeof(SceneCtl) * s->n_scenes, cudaMemcpyDeviceToHost));
+        for (auto& c : ctl) { c.newton_active = 1; c.eps_r = 0.0; }
+        CUDA_TRY(s, cudaMemcpy(d.sc, ctl.data(), sizeof(SceneCtl) * s->n_scenes, cudaMemcpyHostToDevice));
+        cudaEventRecord(a, s->stream);
+        TRY(run_pcg(s, d, 1, 1));
+        cudaEventRecord(b, s->stream);
+        TRY(sync(s));
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, a, b);
+        t_min = std::min(t_min, ms);
+      }
+      if (t_min < best) { best = t_min; best_l = lanes; best_g = s->d.pcg_grid; }
+      if (s->d.pcg_grid >= (s->n + 63) / 64) break;  // larger grids are capped to the same shape
+    }
+  }
+  s->ev_pool.push_back(a);
+  s->ev_pool.push_back(b);
+  TRY(bdem_set_pcg_shape(s, best_l, best_g));
+  if (lanes_out) *lanes_out = best_l;
+  if (blocks_out) *blocks_out = best_g;
   return BDEM_OK;
 }

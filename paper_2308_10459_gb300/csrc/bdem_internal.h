@@ -1,10 +1,12 @@
 // bdem_internal.h -- device data layout and kernel launchers shared by bdem_kernels.cu and bdem_api.cu.
 //
 // Layout in HBM (N particles, B bonds, S scenes; T = float in the mixed path, double in the FP64 path):
+//   particles are stored in a space-filling-curve (Morton) order inside each scene, so that bonded and contacting
+//             particles are close in memory; every transfer across the ABI is reordered on the device
 //   particles, AoS of double4 (32 B, two per particle state): xp = (p, radius), xq = q       current iterate
 //             x0p, x0q committed state of the step; vp = (v, 0), vq = dq/dt; hp = (phat, mass), hq = qhat (raw);
 //             tp, tq line-search trial; coef = (c_p, c_q) = (m/dt^2, 8/5 m r^2/dt^2); g [N][6] FP64 gradient;
-//             D, Dinv [N][21] T packed symmetric diagonal blocks and their inverses (block Jacobi);
+//             D, Dinv [N][24] T packed symmetric diagonal blocks (21 words + 3 pad) and their inverses (block Jacobi);
 //             PCG vectors [N][6] T (x, r, z, p, q)
 //   bonds, sorted by (i, j) with i < j (so each scene's bonds are contiguous):
 //             bij int2; brest double4 (d0, l0); bstiff double4 (kn, kt s^2, kb, ktw); bbrk double; bbroken u8;
@@ -12,9 +14,15 @@
 //             bM [B][36] T: the (i, j) off-diagonal 6x6 block in factored form (1/2 A sym6 | B/sqrt2 3x3 |
 //             C/sqrt2 3x3 | F 3x3 | 3 pad) of the clamped 9x9 Hessian in (u = (dp_j - dp_i)/sqrt2, y_i, y_j);
 //             bE [B][12] T: its E (y_i y_i) and G (y_j y_j) blocks, sym6 each
-//   incidence CSR inc_start [N+1], inc [2B] entries (bond << 1 | side), side 0: particle is i, 1: particle is j
-//   contact CSR c_start [N+1], c_nbr [C], c_blk [C] T4 (n, k) of the clamped contact Hessian k n n^T
+//   incidence CSR inc_start [N+1], inc2 [2B] int2 entries (bond << 1 | side, other particle), side 0: particle is
+//             i, 1: particle is j; entries of a particle are in bond order
+//   contact CSR c_start [N+1], c_nbr [C] candidates; per Newton iteration the active ones are compacted to the front
+//             of each particle's range: c_anbr [C], c_blk [C] T4 (n, k) of the clamped contact Hessian k n n^T,
+//             c_act [N] counts
 //   tiles: particle tiles of <= 256 rows inside one scene, bond tiles of <= 256 bonds inside one scene
+//   PCG segments: the persistent PCG grid gives block b the balanced row range [b N / P, (b+1) N / P); its
+//             intersections with the scenes are the segments (seg_row [nseg+1], seg_scene, block_seg [P+1],
+//             scene_seg [S+1]); one partial per segment and quantity (part_s [nseg][4])
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -23,6 +31,7 @@ namespace bdem {
 
 constexpr int kTile = 256;      // rows (particles or bonds) per tile = threads per block of tile kernels
 constexpr int kPartials = 4;    // partial sums per tile
+constexpr int kDiagStride = 24; // words per stored 6x6 symmetric block (21 used, padded for 128-bit loads)
 
 struct SceneCtl {
   double g0, gnorm, eps_r, bnorm;
@@ -62,21 +71,24 @@ struct DevArrays {
   double4 *xp, *xq, *x0p, *x0q, *vp, *vq, *hp, *hq, *tp, *tq;
   double2* coef;
   int32_t* pscene;
+  int32_t* perm;                // caller index of internal particle k (internal order: Morton order per scene)
   uint8_t* kin;
   double* g;
   void *D, *Dinv;
-  void *vx, *vr, *vz, *vp_, *vq_;
+  void *vx, *vr, *vz, *vp_, *vq_, *vs;   // x, r, z, p, w (= H z; also the inspection product), s (= H p)
   // bonds
   int2* bij;
   double4 *brest, *bstiff;
   double* bbrk;
   uint8_t* bbroken;
   int32_t* bscene;
+  int32_t *bond_ext2int, *bond_int2ext;  // caller bond order (order of addition) <-> stored order
   double* bg;
   void *bM, *bE;
-  int32_t *inc_start, *inc;
+  int32_t* inc_start;
+  int2* inc2;
   // contacts
-  int32_t *c_start, *c_nbr;
+  int32_t *c_start, *c_nbr, *c_anbr, *c_act;
   void* c_blk;
   int32_t *cell_key, *hash_count, *hash_start, *hash_ids, *cnt_tmp;
   int64_t* scan_tmp;
@@ -84,6 +96,9 @@ struct DevArrays {
   int32_t *ptile_start, *ptile_scene, *ptile_begin;   // ptile_begin [S+1]: first tile of each scene
   int32_t *btile_start, *btile_scene, *btile_begin;
   double *part_p, *part_b;      // [tiles][kPartials]
+  int32_t n_seg, pcg_grid, pcg_lanes, pcg_max_rows;  // pcg_max_rows: most rows of one PCG block
+  int32_t *seg_row, *seg_scene, *block_seg, *scene_seg;
+  double* part_s;               // [n_seg][kPartials]
   SceneCtl* sc;
   Counters* cnt;
 };
@@ -100,8 +115,8 @@ int launch_particle_hess(const DevArrays& d, int mask_kin, int all_scenes, cudaS
 enum ReduceMode { RED_GRAD = 0, RED_GDX = 1, RED_LS = 2, RED_FORCE_ACTIVE = 3, RED_CAND = 4 };
 int launch_scene_reduce(const DevArrays& d, int mode, int k_iter, cudaStream_t s);
 // PCG: rhs_from_g = 1 uses b = -g; else b is read from vr (already T) and eps from sc.eps_r
-int launch_pcg(const DevArrays& d, int rhs_from_g, int mask_kin, int grid_blocks, cudaStream_t s, cudaError_t* err);
-int pcg_max_blocks(int mixed);
+int launch_pcg(const DevArrays& d, int rhs_from_g, int mask_kin, cudaStream_t s, cudaError_t* err);
+int pcg_max_blocks(int mixed, int lanes, size_t smem);  // co-resident PCG blocks on this device (0: none)
 int launch_gdx(const DevArrays& d, cudaStream_t s);
 int launch_ls_trial(const DevArrays& d, cudaStream_t s);
 int launch_ls_energy(const DevArrays& d, cudaStream_t s);
@@ -110,8 +125,14 @@ int launch_finish(const DevArrays& d, cudaStream_t s);
 int launch_matvec(const DevArrays& d, int mask_kin, cudaStream_t s);  // vq_ = H vp_
 int launch_unpack_bond_hess(const DevArrays& d, double* out /*device [nb][144]*/, cudaStream_t s);
 int launch_unpack_diag(const DevArrays& d, double* out /*device [n][36]*/, cudaStream_t s);
-int launch_pack_state(const DevArrays& d, double* pos3, double* vel3, cudaStream_t s);          // committed -> [n][3]
-int launch_unpack_state(const DevArrays& d, const double* pos3, const double* vel3, cudaStream_t s);
+// transfers in the caller's particle order (any pointer may be NULL): committed state <-> [n][3] / [n][4] arrays
+int launch_pack_state(const DevArrays& d, double* pos3, double* quat4, double* vel3, double* qvel4, cudaStream_t s);
+int launch_unpack_state(const DevArrays& d, const double* pos3, const double* quat4, const double* vel3,
+                        const double* qvel4, cudaStream_t s);
+int launch_set_hat(const DevArrays& d, const double* phat3, const double* qhat4, cudaStream_t s);
+int launch_bond_flags(const DevArrays& d, uint8_t* ext, int to_device, cudaStream_t s);
+int launch_convert_perm(const void* src, int src_double, void* dst, int dst_double, const int32_t* perm, int dir,
+                        int n, cudaStream_t s);
 // allocation-free PCG scratch (static device array in bdem_kernels.cu)
 size_t static_pcg_capacity();
 cudaError_t static_pcg_address(void** out);

@@ -103,6 +103,33 @@ struct T4 {
   T x, y, z, w;
 };
 
+// Dot products of FP32 vectors accumulated without FP64 arithmetic per element: each product is split exactly into
+// p + e (p = a b rounded, e = fma(a, b, -p)) and summed with error-free two-sums (the Dot2 scheme of Ogita, Rump
+// and Oishi, "Accurate sum and dot product", 2005); the result carries about twice the FP32 precision and is
+// converted to FP64 once per thread before the FP64 reductions. For FP64 vectors plain FP64 products are used.
+template <typename T>
+struct DotAcc;
+template <>
+struct DotAcc<float> {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add(float a, float b) {
+    float p = a * b;
+    float e = fmaf(a, b, -p);
+    float s = hi + p;
+    float z = s - hi;
+    float t = (hi - (s - z)) + (p - z);
+    hi = s;
+    lo += t + e;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+template <>
+struct DotAcc<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { v = fma(a, b, v); }
+  __device__ __forceinline__ double value() const { return v; }
+};
+
 // ================================================================================================
 // step initialisation and prediction
 // ================================================================================================
@@ -179,10 +206,8 @@ __global__ void k_cell_sort(DevArrays d) {
 
 __device__ __forceinline__ bool bonded_intact(const DevArrays& d, int i, int j) {
   for (int e = d.inc_start[i]; e < d.inc_start[i + 1]; ++e) {
-    int ent = d.inc[e], b = ent >> 1;
-    int2 ij = d.bij[b];
-    int o = (ent & 1) ? ij.x : ij.y;
-    if (o == j && !d.bbroken[b]) return true;
+    int2 ent = d.inc2[e];
+    if (ent.y == j && !d.bbroken[ent.x >> 1]) return true;
   }
   return false;
 }
@@ -327,7 +352,7 @@ __global__ void __launch_bounds__(kTile) k_particle_grad(DevArrays d, int mask, 
     double g[6];
     particle_term_grad(d, i, g);
     for (int e = d.inc_start[i]; e < d.inc_start[i + 1]; ++e) {
-      int ent = d.inc[e], b = ent >> 1;
+      int ent = d.inc2[e].x, b = ent >> 1;
       if (d.bbroken[b]) continue;
       const double* bg = d.bg + 9 * (size_t)b;
       if (ent & 1) {  // particle is j: dV/dp_j = dV/dd
@@ -449,7 +474,7 @@ __global__ void __launch_bounds__(kTile) k_particle_hess(DevArrays d, int mask, 
   const T* Mall = reinterpret_cast<const T*>(d.bM);
   const T* Eall = reinterpret_cast<const T*>(d.bE);
   for (int e = d.inc_start[i]; e < d.inc_start[i + 1]; ++e) {
-    int ent = d.inc[e], b = ent >> 1;
+    int ent = d.inc2[e].x, b = ent >> 1;
     if (d.bbroken[b]) continue;
     const T* M = Mall + 36 * (size_t)b;
     const T* Eb = Eall + 12 * (size_t)b + ((ent & 1) ? 6 : 0);
@@ -467,46 +492,76 @@ __global__ void __launch_bounds__(kTile) k_particle_hess(DevArrays d, int mask, 
 #pragma unroll
       for (int c = 0; c < 3; ++c) D[sidx<6>(a, 3 + c)] += sgn * X[3 * a + c];
   }
+  int nact = 0;
   if (d.k_self > 0.0) {
+    // active contacts (overlapping candidates) compacted to the front of the particle's candidate range
     T4<T>* blk = reinterpret_cast<T4<T>*>(d.c_blk);
-    for (int e = d.c_start[i]; e < d.c_start[i + 1]; ++e) {
+    int c0 = d.c_start[i];
+    for (int e = c0; e < d.c_start[i + 1]; ++e) {
       int j = d.c_nbr[e];
       double4 pj = d.xp[j];
       double ex = p.x - pj.x, ey = p.y - pj.y, ez = p.z - pj.z;
       double dd = sqrt(ex * ex + ey * ey + ez * ez), R = p.w + pj.w;
-      T4<T> o = {(T)0, (T)0, (T)0, (T)0};
       if (dd < R) {  // clamped penalty Hessian k n n^T (the transverse part k (d - R)/d < 0 is removed)
         T n[3] = {(T)(ex / dd), (T)(ey / dd), (T)(ez / dd)};
         T k = (T)d.k_self;
-        o = {n[0], n[1], n[2], k};
+        blk[c0 + nact] = T4<T>{n[0], n[1], n[2], k};
+        d.c_anbr[c0 + nact] = j;
+        ++nact;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
           for (int c = a; c < 3; ++c) D[sidx<6>(a, c)] += k * n[a] * n[c];
       }
-      blk[e] = o;
     }
   }
+  d.c_act[i] = nact;
   if (mask && d.kin[i]) {
 #pragma unroll
     for (int a = 0; a < 6; ++a)
 #pragma unroll
       for (int c = a; c < 6; ++c) D[sidx<6>(a, c)] = (a == c) ? (T)1 : (T)0;
   }
-  T* Do = reinterpret_cast<T*>(d.D) + 21 * (size_t)i;
-  T* Io = reinterpret_cast<T*>(d.Dinv) + 21 * (size_t)i;
+  T* Do = reinterpret_cast<T*>(d.D) + kDiagStride * (size_t)i;
+  T* Io = reinterpret_cast<T*>(d.Dinv) + kDiagStride * (size_t)i;
   T I[21];
   spd_inverse6<T>(D, I);
 #pragma unroll
   for (int k = 0; k < 21; ++k) { Do[k] = D[k]; Io[k] = I[k]; }
+#pragma unroll
+  for (int k = 21; k < kDiagStride; ++k) { Do[k] = (T)0; Io[k] = (T)0; }
 }
 
 // ================================================================================================
-// block-sparse matrix-vector product, one row (particle) per thread: y_i = D_i x_i + sum_b H_ib x_other + contacts
+// block-sparse matrix-vector product: y_i = D_i x_i + sum_b H_ib x_other + sum_c (-k n n^T) x_c
 // ================================================================================================
 
+// 128-bit loads of a padded block of n words (n a multiple of 4 floats / 2 doubles; 16-byte aligned)
+template <int NW>
+__device__ __forceinline__ void load_words(const float* src, float (&dst)[NW]) {
+  static_assert(NW % 4 == 0, "float blocks load in float4");
+  const float4* p = reinterpret_cast<const float4*>(src);
+#pragma unroll
+  for (int k = 0; k < NW / 4; ++k) {
+    float4 v = __ldg(p + k);
+    dst[4 * k] = v.x; dst[4 * k + 1] = v.y; dst[4 * k + 2] = v.z; dst[4 * k + 3] = v.w;
+  }
+}
+template <int NW>
+__device__ __forceinline__ void load_words(const double* src, double (&dst)[NW]) {
+  static_assert(NW % 2 == 0, "double blocks load in double2");
+  const double2* p = reinterpret_cast<const double2*>(src);
+#pragma unroll
+  for (int k = 0; k < NW / 2; ++k) {
+    double2 v = __ldg(p + k);
+    dst[2 * k] = v.x; dst[2 * k + 1] = v.y;
+  }
+}
+
 template <typename T>
-__device__ __forceinline__ void sym6_mul(const T* P, const T (&x)[6], T (&y)[6]) {
+__device__ __forceinline__ void sym6_mul(const T* Pg, const T (&x)[6], T (&y)[6]) {
+  T P[kDiagStride];
+  load_words<kDiagStride>(Pg, P);
 #pragma unroll
   for (int a = 0; a < 6; ++a) {
     T s = 0;
@@ -516,74 +571,76 @@ __device__ __forceinline__ void sym6_mul(const T* P, const T (&x)[6], T (&y)[6])
   }
 }
 
-template <typename T, bool CG>
-__device__ __forceinline__ void row_matvec(const DevArrays& d, int i, const T* x, T (&y)[6], int mask) {
-  if (mask && d.kin[i]) {
+// one off-diagonal bond block times the other endpoint's vector, added to y
+template <typename T>
+__device__ __forceinline__ void bond_block_mul(const T* Mg, int side, const Vec6<T>& xo, T (&y)[6]) {
+  T M[36];
+  load_words<36>(Mg, M);
+  T a0 = xo.v[0], a1 = xo.v[1], a2 = xo.v[2], b0 = xo.v[3], b1 = xo.v[4], b2 = xo.v[5];
+  T Ah[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) y[k] = (T)0;
-    return;
-  }
-  Vec6<T> xi = CG ? load6_cg<T>(x, i) : load6<T>(x, i);
-  const T* Dp = reinterpret_cast<const T*>(d.D) + 21 * (size_t)i;
-  sym6_mul<T>(Dp, xi.v, y);
-  const T* Mall = reinterpret_cast<const T*>(d.bM);
-  for (int e = d.inc_start[i]; e < d.inc_start[i + 1]; ++e) {
-    int ent = d.inc[e], b = ent >> 1;
-    int2 ij = d.bij[b];
-    int side = ent & 1;
-    int o = side ? ij.x : ij.y;
-    Vec6<T> xo = CG ? load6_cg<T>(x, o) : load6<T>(x, o);
-    const T* M = Mall + 36 * (size_t)b;
-    T a0 = xo.v[0], a1 = xo.v[1], a2 = xo.v[2], b0 = xo.v[3], b1 = xo.v[4], b2 = xo.v[5];
-    // -1/2 A a
-    T Ah[6];
+  for (int k = 0; k < 6; ++k) Ah[k] = M[k];
+  y[0] -= Ah[0] * a0 + Ah[1] * a1 + Ah[2] * a2;
+  y[1] -= Ah[1] * a0 + Ah[3] * a1 + Ah[4] * a2;
+  y[2] -= Ah[2] * a0 + Ah[4] * a1 + Ah[5] * a2;
+  const T* Bs = M + 6;
+  const T* Cs = M + 15;
+  const T* F = M + 24;
+  if (!side) {  // the row is i (= bi): H_ij = [[-Ah, -Cs], [Bs^T, F]]
 #pragma unroll
-    for (int k = 0; k < 6; ++k) Ah[k] = M[k];
-    y[0] -= Ah[0] * a0 + Ah[1] * a1 + Ah[2] * a2;
-    y[1] -= Ah[1] * a0 + Ah[3] * a1 + Ah[4] * a2;
-    y[2] -= Ah[2] * a0 + Ah[4] * a1 + Ah[5] * a2;
-    const T* Bs = M + 6;
-    const T* Cs = M + 15;
-    const T* F = M + 24;
-    if (!side) {  // i = bi: H_ij = [[-Ah, -Cs], [Bs^T, F]]
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        y[r] -= Cs[3 * r] * b0 + Cs[3 * r + 1] * b1 + Cs[3 * r + 2] * b2;
-        y[3 + r] += Bs[r] * a0 + Bs[3 + r] * a1 + Bs[6 + r] * a2 + F[3 * r] * b0 + F[3 * r + 1] * b1 + F[3 * r + 2] * b2;
-      }
-    } else {      // i = bj: H_ij^T = [[-Ah, Bs], [-Cs^T, F^T]]
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        y[r] += Bs[3 * r] * b0 + Bs[3 * r + 1] * b1 + Bs[3 * r + 2] * b2;
-        y[3 + r] += -(Cs[r] * a0 + Cs[3 + r] * a1 + Cs[6 + r] * a2) + F[r] * b0 + F[3 + r] * b1 + F[6 + r] * b2;
-      }
+    for (int r = 0; r < 3; ++r) {
+      y[r] -= Cs[3 * r] * b0 + Cs[3 * r + 1] * b1 + Cs[3 * r + 2] * b2;
+      y[3 + r] += Bs[r] * a0 + Bs[3 + r] * a1 + Bs[6 + r] * a2 + F[3 * r] * b0 + F[3 * r + 1] * b1 + F[3 * r + 2] * b2;
     }
-  }
-  if (d.k_self > 0.0) {
-    const T4<T>* blk = reinterpret_cast<const T4<T>*>(d.c_blk);
-    for (int e = d.c_start[i]; e < d.c_start[i + 1]; ++e) {
-      T4<T> c = blk[e];
-      if (c.w == (T)0) continue;
-      Vec6<T> xo = CG ? load6_cg<T>(x, d.c_nbr[e]) : load6<T>(x, d.c_nbr[e]);
-      T t = c.w * (c.x * xo.v[0] + c.y * xo.v[1] + c.z * xo.v[2]);
-      y[0] -= t * c.x;
-      y[1] -= t * c.y;
-      y[2] -= t * c.z;
+  } else {      // the row is j (= bj): H_ij^T = [[-Ah, Bs], [-Cs^T, F^T]]
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      y[r] += Bs[3 * r] * b0 + Bs[3 * r + 1] * b1 + Bs[3 * r + 2] * b2;
+      y[3 + r] += -(Cs[r] * a0 + Cs[3 + r] * a1 + Cs[6 + r] * a2) + F[r] * b0 + F[3 + r] * b1 + F[6 + r] * b2;
     }
   }
 }
 
+// entry k of row i (bonds first, then active contacts), added to y
+template <typename T, bool CG>
+__device__ __forceinline__ void row_entry(const DevArrays& d, int i, int k, int nbond, const T* x, T (&y)[6]) {
+  if (k < nbond) {
+    int2 ent = d.inc2[d.inc_start[i] + k];
+    Vec6<T> xo = CG ? load6_cg<T>(x, ent.y) : load6<T>(x, ent.y);
+    bond_block_mul<T>(reinterpret_cast<const T*>(d.bM) + 36 * (size_t)(ent.x >> 1), ent.x & 1, xo, y);
+  } else {
+    int e = d.c_start[i] + (k - nbond);
+    T4<T> c = reinterpret_cast<const T4<T>*>(d.c_blk)[e];
+    Vec6<T> xo = CG ? load6_cg<T>(x, d.c_anbr[e]) : load6<T>(x, d.c_anbr[e]);
+    T t = c.w * (c.x * xo.v[0] + c.y * xo.v[1] + c.z * xo.v[2]);
+    y[0] -= t * c.x;
+    y[1] -= t * c.y;
+    y[2] -= t * c.z;
+  }
+}
+
+// one thread per row (inspection product)
 template <typename T>
 __global__ void __launch_bounds__(kTile) k_matvec(DevArrays d, int mask) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
-  T y[6];
-  row_matvec<T, false>(d, i, reinterpret_cast<const T*>(d.vp_), y, mask);
+  T y[6] = {0, 0, 0, 0, 0, 0};
+  if (!(mask && d.kin[i])) {
+    Vec6<T> xi = load6<T>(reinterpret_cast<const T*>(d.vp_), i);
+    sym6_mul<T>(reinterpret_cast<const T*>(d.D) + kDiagStride * (size_t)i, xi.v, y);
+    int nbond = d.inc_start[i + 1] - d.inc_start[i];
+    int nent = nbond + (d.k_self > 0.0 ? d.c_act[i] : 0);
+    for (int k = 0; k < nent; ++k) row_entry<T, false>(d, i, k, nbond, reinterpret_cast<const T*>(d.vp_), y);
+  }
   store6<T>(reinterpret_cast<T*>(d.vq_), i, y);
 }
 
 // ================================================================================================
-// persistent PCG (Sec. 5.3): block-Jacobi preconditioner, stop at |r| <= eps_r |b| or the iteration cap
+// persistent PCG (Sec. 5.3) in the Chronopoulos-Gear arrangement: per iteration one product w = H z fused with the
+// three dot products (r.z, w.z, r.r) and one grid-wide reduction, then one vector update. In exact arithmetic it
+// produces the iterates of the textbook PCG (x0 = 0, block-Jacobi preconditioner, stop at |r| <= eps_r |b| or the
+// iteration cap): alpha_k = gamma_k / (delta_k - beta_k gamma_k / alpha_{k-1}), beta_k = gamma_k / gamma_{k-1},
+// p = z + beta p, s = w + beta s (= H p), x += alpha p, r -= alpha s, z = M^-1 r.
 // ================================================================================================
 
 // grid barrier with a bounded wait; the last block to arrive runs `work` (whole block) before releasing the others
@@ -625,7 +682,7 @@ __device__ bool grid_barrier(const DevArrays& d, F&& work) {
   return s_ok != 0;
 }
 
-// deterministic per-scene sums of partial slot `k` over a scene's particle tiles, one warp per scene
+// deterministic per-scene sums of partial slot k over a scene's tiles (particle tiles), one warp per scene
 __device__ __forceinline__ double scene_partial(const DevArrays& d, int s, int k, int lane) {
   int a = d.ptile_begin[s], b = d.ptile_begin[s + 1];
   double v = 0.0;
@@ -633,51 +690,47 @@ __device__ __forceinline__ double scene_partial(const DevArrays& d, int s, int k
   return warp_sum(v);
 }
 
-enum PcgPhase { PH_INIT = 0, PH_A = 1, PH_B = 2 };
-
-__device__ void pcg_reduce(const DevArrays& d, int phase) {
+// per-scene decision after the fused product (run by the last block to reach the barrier): one warp per scene,
+// lanes stride over the scene's segments in order
+__device__ void pcg_decide(const DevArrays& d, int k_iter) {
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   __shared__ int s_active[kTile / 32];
   int active = 0;
   for (int s = warp; s < d.n_scenes; s += nw) {
-    // volatile: another block may have written this scene's control block since this SM last cached it
-    volatile SceneCtl* c = d.sc + s;
-    if (phase == PH_INIT) {
-      double rr = scene_partial(d, s, 0, lane), rz = scene_partial(d, s, 1, lane);
-      if (lane == 0) {
-        c->bnorm = sqrt(rr);
-        c->rz = rz;
-        c->pcg_iters = 0;
-        int a = c->newton_active && (sqrt(rr) > c->eps_r * c->bnorm) && d.pcg_max > 0;
-        c->pcg_active = a;
-        active += a;
-      }
-    } else if (phase == PH_A) {
-      double pq = scene_partial(d, s, 0, lane);
-      if (lane == 0 && c->pcg_active) {
-        c->pcg_iters += 1;
-        c->pq = pq;
-        if (!(pq > 0.0)) {
-          c->pcg_active = 0;
-          c->alpha = 0.0;
-        } else {
-          c->alpha = c->rz / pq;
-        }
-      }
-      if (lane == 0) active += c->pcg_active;
-    } else {
-      double rr = scene_partial(d, s, 0, lane), rz = scene_partial(d, s, 1, lane);
-      if (lane == 0 && c->pcg_active) {
-        if (sqrt(rr) <= c->eps_r * c->bnorm || c->pcg_iters >= d.pcg_max) {
-          c->pcg_active = 0;
-          c->beta = 0.0;
-        } else {
-          c->beta = rz / c->rz;
-          c->rz = rz;
-        }
-      }
-      if (lane == 0) active += c->pcg_active;
+    volatile SceneCtl* c = d.sc + s;  // volatile: written by other blocks since this SM last cached it
+    int a = d.scene_seg[s], b = d.scene_seg[s + 1];
+    double gam = 0.0, del = 0.0, rho = 0.0;
+    for (int t = a + lane; t < b; t += 32) {
+      gam += __ldcg(d.part_s + kPartials * t);
+      del += __ldcg(d.part_s + kPartials * t + 1);
+      rho += __ldcg(d.part_s + kPartials * t + 2);
     }
+    gam = warp_sum(gam);
+    del = warp_sum(del);
+    rho = warp_sum(rho);
+    if (lane != 0 || !c->newton_active) continue;
+    if (k_iter == 0) {
+      c->bnorm = sqrt(rho);
+      c->pcg_iters = 0;
+      c->pcg_active = 1;
+    }
+    if (!c->pcg_active) continue;
+    bool stop = !(sqrt(rho) > c->eps_r * c->bnorm) || c->pcg_iters >= d.pcg_max;
+    if (!stop) {
+      double beta = (c->pcg_iters == 0) ? 0.0 : gam / c->rz;
+      double den = (c->pcg_iters == 0) ? del : del - beta * gam / c->alpha;
+      if (!(den > 0.0) || !(gam > 0.0)) {
+        stop = true;  // breakdown: no further decrease along this Krylov space
+      } else {
+        c->beta = beta;
+        c->alpha = gam / den;
+        c->rz = gam;
+        c->pq = den;
+        c->pcg_iters += 1;
+      }
+    }
+    if (stop) c->pcg_active = 0;
+    else ++active;
   }
   if (lane == 0) s_active[warp] = active;
   __syncthreads();
@@ -688,26 +741,38 @@ __device__ void pcg_reduce(const DevArrays& d, int phase) {
   }
 }
 
-// PH_A sets the per-scene "active" flag before PH_B; a scene that stops in PH_A (breakdown) skips the update
-template <typename T>
+template <typename T, int G>
 __global__ void __launch_bounds__(kTile) k_pcg(DevArrays d, int rhs_from_g, int mask) {
   T* X = reinterpret_cast<T*>(d.vx);
   T* R = reinterpret_cast<T*>(d.vr);
   T* Z = reinterpret_cast<T*>(d.vz);
   T* P = reinterpret_cast<T*>(d.vp_);
-  T* Q = reinterpret_cast<T*>(d.vq_);
+  T* W = reinterpret_cast<T*>(d.vq_);
+  T* S = reinterpret_cast<T*>(d.vs);
   const T* Dinv = reinterpret_cast<const T*>(d.Dinv);
-  // ---- init: x = 0, r = b, z = M^-1 r, p = z
-  for (int t = blockIdx.x; t < d.n_ptiles; t += gridDim.x) {
-    int i = d.ptile_start[t] + threadIdx.x;
-    int s = d.ptile_scene[t];
-    double acc[2] = {0.0, 0.0};
-    if (i < d.ptile_start[t + 1] && d.sc[s].newton_active) {
-      T r[6], z[6], zero[6] = {0, 0, 0, 0, 0, 0};
+  const T* Dm = reinterpret_cast<const T*>(d.D);
+  const int seg0 = d.block_seg[blockIdx.x], seg1 = d.block_seg[blockIdx.x + 1];
+  const T zero6[6] = {0, 0, 0, 0, 0, 0};
+  // per-row descriptors of the block's rows, fixed for the whole solve: first incidence entry, bond count,
+  // active-contact count with the kinematic flag in bit 30, first contact entry
+  extern __shared__ int4 s_rows[];
+  const int R0 = d.seg_row[seg0], R1 = d.seg_row[seg1];
+  for (int i = R0 + threadIdx.x; i < R1; i += blockDim.x) {
+    int a = d.inc_start[i];
+    int na = (d.k_self > 0.0) ? d.c_act[i] : 0;
+    int kin = (mask && d.kin[i]) ? (1 << 30) : 0;
+    s_rows[i - R0] = make_int4(a, d.inc_start[i + 1] - a, na | kin, d.c_start[i]);
+  }
+  // ---- init: x = p = s = 0, r = b, z = M^-1 r
+  for (int g = seg0; g < seg1; ++g) {
+    int sc = d.seg_scene[g];
+    if (!d.sc[sc].newton_active) continue;
+    for (int i = d.seg_row[g] + threadIdx.x; i < d.seg_row[g + 1]; i += blockDim.x) {
+      T r[6], z[6];
       if (rhs_from_g) {
-        const double* g = d.g + 6 * (size_t)i;
+        const double* gg = d.g + 6 * (size_t)i;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) r[k] = (T)(-g[k]);
+        for (int k = 0; k < 6; ++k) r[k] = (T)(-gg[k]);
       } else {
         Vec6<T> b = load6<T>(R, i);
 #pragma unroll
@@ -716,85 +781,102 @@ __global__ void __launch_bounds__(kTile) k_pcg(DevArrays d, int rhs_from_g, int 
       if (mask && d.kin[i])
 #pragma unroll
         for (int k = 0; k < 6; ++k) r[k] = (T)0;
-      sym6_mul<T>(Dinv + 21 * (size_t)i, r, z);
-      store6<T>(X, i, zero);
+      sym6_mul<T>(Dinv + kDiagStride * (size_t)i, r, z);
+      store6<T>(X, i, zero6);
+      store6<T>(P, i, zero6);
+      store6<T>(S, i, zero6);
       store6<T>(R, i, r);
       store6<T>(Z, i, z);
-      store6<T>(P, i, z);
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        acc[0] += (double)r[k] * (double)r[k];
-        acc[1] += (double)r[k] * (double)z[k];
-      }
-    }
-    block_sum<2>(acc);
-    if (threadIdx.x == 0) {
-      d.part_p[kPartials * t] = acc[0];
-      d.part_p[kPartials * t + 1] = acc[1];
     }
   }
-  if (!grid_barrier(d, [&] { pcg_reduce(d, PH_INIT); })) return;
-  for (;;) {
-    if (__ldcg(&d.cnt->n_active) == 0 || __ldcg(&d.cnt->timeout)) break;
-    // ---- A: q = H p, p.q
-    for (int t = blockIdx.x; t < d.n_ptiles; t += gridDim.x) {
-      int i = d.ptile_start[t] + threadIdx.x;
-      int s = d.ptile_scene[t];
-      double acc[1] = {0.0};
-      if (i < d.ptile_start[t + 1] && __ldcg(&d.sc[s].pcg_active)) {
-        T y[6];
-        row_matvec<T, true>(d, i, P, y, mask);
-        store6<T>(Q, i, y);
-        Vec6<T> p = load6_cg<T>(P, i);
+  if (!grid_barrier(d, [] {})) return;
+  const int sub = threadIdx.x % G, grp = threadIdx.x / G, rows_per_pass = blockDim.x / G;
+  for (int k_iter = 0;; ++k_iter) {
+    // ---- A: w = H z, gamma = r.z, delta = w.z, rho = r.r (per segment, deterministic)
+    for (int g = seg0; g < seg1; ++g) {
+      int sc = d.seg_scene[g];
+      bool act = d.sc[sc].newton_active && (k_iter == 0 || __ldcg(&d.sc[sc].pcg_active));
+      DotAcc<T> dg, dd, dr;
+      if (act) {
+        int r0 = d.seg_row[g], r1 = d.seg_row[g + 1];
+        for (int base = r0; base < r1; base += rows_per_pass) {
+          int i = base + grp;
+          bool valid = i < r1;
+          T y[6] = {0, 0, 0, 0, 0, 0};
+          int4 rd = valid ? s_rows[i - R0] : make_int4(0, 0, 1 << 30, 0);
+          bool live = valid && !(rd.z & (1 << 30));
+          if (live) {
+            if (sub == 0) {
+              Vec6<T> zi = load6_cg<T>(Z, i);
+              sym6_mul<T>(Dm + kDiagStride * (size_t)i, zi.v, y);
+            }
+            const int2* ent = d.inc2 + rd.x;
+            const T* Mall = reinterpret_cast<const T*>(d.bM);
+#pragma unroll 2
+            for (int k = sub; k < rd.y; k += G) {
+              int2 e = ent[k];
+              Vec6<T> xo = load6_cg<T>(Z, e.y);
+              bond_block_mul<T>(Mall + 36 * (size_t)(e.x >> 1), e.x & 1, xo, y);
+            }
+            int nact = rd.z & ((1 << 30) - 1);
+            for (int k = sub; k < nact; k += G) {
+              int e = rd.w + k;
+              T4<T> c = reinterpret_cast<const T4<T>*>(d.c_blk)[e];
+              Vec6<T> xo = load6_cg<T>(Z, d.c_anbr[e]);
+              T t = c.w * (c.x * xo.v[0] + c.y * xo.v[1] + c.z * xo.v[2]);
+              y[0] -= t * c.x;
+              y[1] -= t * c.y;
+              y[2] -= t * c.z;
+            }
+          }
 #pragma unroll
-        for (int k = 0; k < 6; ++k) acc[0] += (double)p.v[k] * (double)y[k];
+          for (int o = G / 2; o >= 1; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) y[k] += __shfl_xor_sync(0xffffffffu, y[k], o, G);
+          if (valid && sub == 0) {
+            store6<T>(W, i, y);
+            Vec6<T> zi = load6_cg<T>(Z, i), ri = load6_cg<T>(R, i);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+              dg.add(ri.v[k], zi.v[k]);
+              dd.add(y[k], zi.v[k]);
+              dr.add(ri.v[k], ri.v[k]);
+            }
+          }
+        }
       }
-      block_sum<1>(acc);
-      if (threadIdx.x == 0) d.part_p[kPartials * t] = acc[0];
+      double acc[3] = {dg.value(), dd.value(), dr.value()};
+      block_sum<3>(acc);
+      if (threadIdx.x == 0) {
+        d.part_s[kPartials * g] = acc[0];
+        d.part_s[kPartials * g + 1] = acc[1];
+        d.part_s[kPartials * g + 2] = acc[2];
+      }
     }
-    if (!grid_barrier(d, [&] { pcg_reduce(d, PH_A); })) return;
-    // ---- B: x += alpha p, r -= alpha q, z = M^-1 r, r.r, r.z
-    for (int t = blockIdx.x; t < d.n_ptiles; t += gridDim.x) {
-      int i = d.ptile_start[t] + threadIdx.x;
-      int s = d.ptile_scene[t];
-      double acc[2] = {0.0, 0.0};
-      if (i < d.ptile_start[t + 1] && __ldcg(&d.sc[s].pcg_active)) {
-        T al = (T)__ldcg(&d.sc[s].alpha);
-        Vec6<T> x = load6<T>(X, i), r = load6<T>(R, i), p = load6_cg<T>(P, i), q = load6<T>(Q, i);
-        T xn[6], rn[6], z[6];
+    if (!grid_barrier(d, [&] { pcg_decide(d, k_iter); })) return;
+    if (__ldcg(&d.cnt->n_active) == 0 || __ldcg(&d.cnt->timeout)) break;
+    // ---- B: p = z + beta p, s = w + beta s, x += alpha p, r -= alpha s, z = M^-1 r
+    for (int g = seg0; g < seg1; ++g) {
+      int sc = d.seg_scene[g];
+      if (!d.sc[sc].newton_active || !__ldcg(&d.sc[sc].pcg_active)) continue;
+      T al = (T)__ldcg(&d.sc[sc].alpha), be = (T)__ldcg(&d.sc[sc].beta);
+      for (int i = d.seg_row[g] + threadIdx.x; i < d.seg_row[g + 1]; i += blockDim.x) {
+        Vec6<T> z = load6_cg<T>(Z, i), w = load6_cg<T>(W, i), p = load6_cg<T>(P, i), s = load6_cg<T>(S, i);
+        Vec6<T> x = load6_cg<T>(X, i), r = load6_cg<T>(R, i);
+        T pn[6], sn[6], xn[6], rn[6], zn[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-          xn[k] = x.v[k] + al * p.v[k];
-          rn[k] = r.v[k] - al * q.v[k];
+          pn[k] = z.v[k] + be * p.v[k];
+          sn[k] = w.v[k] + be * s.v[k];
+          xn[k] = x.v[k] + al * pn[k];
+          rn[k] = r.v[k] - al * sn[k];
         }
-        sym6_mul<T>(Dinv + 21 * (size_t)i, rn, z);
+        sym6_mul<T>(Dinv + kDiagStride * (size_t)i, rn, zn);
+        store6<T>(P, i, pn);
+        store6<T>(S, i, sn);
         store6<T>(X, i, xn);
         store6<T>(R, i, rn);
-        store6<T>(Z, i, z);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-          acc[0] += (double)rn[k] * (double)rn[k];
-          acc[1] += (double)rn[k] * (double)z[k];
-        }
-      }
-      block_sum<2>(acc);
-      if (threadIdx.x == 0) {
-        d.part_p[kPartials * t] = acc[0];
-        d.part_p[kPartials * t + 1] = acc[1];
-      }
-    }
-    if (!grid_barrier(d, [&] { pcg_reduce(d, PH_B); })) return;
-    // ---- C: p = z + beta p
-    for (int t = blockIdx.x; t < d.n_ptiles; t += gridDim.x) {
-      int i = d.ptile_start[t] + threadIdx.x;
-      int s = d.ptile_scene[t];
-      if (i < d.ptile_start[t + 1] && __ldcg(&d.sc[s].pcg_active)) {
-        T be = (T)__ldcg(&d.sc[s].beta);
-        Vec6<T> z = load6<T>(Z, i), p = load6_cg<T>(P, i);
-        T pn[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) pn[k] = z.v[k] + be * p.v[k];
-        store6<T>(P, i, pn);
+        store6<T>(Z, i, zn);
       }
     }
     if (!grid_barrier(d, [] {})) return;
@@ -1097,7 +1179,7 @@ __global__ void k_unpack_bond_hess(DevArrays d, double* out) {
       H[3 + a][3 + c] = e; H[9 + a][9 + c] = g;
       H[3 + a][9 + c] = f; H[9 + c][3 + a] = f;
     }
-  double* o = out + 144 * (size_t)b;
+  double* o = out + 144 * (size_t)d.bond_int2ext[b];
   for (int a = 0; a < 12; ++a)
     for (int c = 0; c < 12; ++c) o[12 * a + c] = H[a][c];
 }
@@ -1106,9 +1188,10 @@ template <typename T>
 __global__ void k_unpack_diag(DevArrays d, double* out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
-  const T* D = reinterpret_cast<const T*>(d.D) + 21 * (size_t)i;
+  const T* D = reinterpret_cast<const T*>(d.D) + kDiagStride * (size_t)i;
+  size_t u = (size_t)d.perm[i];
   for (int a = 0; a < 6; ++a)
-    for (int c = 0; c < 6; ++c) out[36 * (size_t)i + 6 * a + c] = (double)D[sidx<6>(a, c)];
+    for (int c = 0; c < 6; ++c) out[36 * u + 6 * a + c] = (double)D[sidx<6>(a, c)];
 }
 
 __global__ void k_convert(const void* src, int sd, void* dst, int dd, int64_t count) {
@@ -1239,26 +1322,37 @@ int launch_scene_reduce(const DevArrays& d, int mode, int k_iter, cudaStream_t s
   return 1;
 }
 
-int pcg_max_blocks(int mixed) {
+template <typename T>
+static const void* pcg_kernel(int lanes) {
+  switch (lanes) {
+    case 1: return (const void*)k_pcg<T, 1>;
+    case 2: return (const void*)k_pcg<T, 2>;
+    case 8: return (const void*)k_pcg<T, 8>;
+    default: return (const void*)k_pcg<T, 4>;
+  }
+}
+
+int pcg_max_blocks(int mixed, int lanes, size_t smem) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (mixed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg<float>, kTile, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg<double>, kTile, 0);
+  const void* k = mixed ? pcg_kernel<float>(lanes) : pcg_kernel<double>(lanes);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kTile, smem) != cudaSuccess) return 0;
   return sms * per;
 }
 
-int launch_pcg(const DevArrays& d, int rhs_from_g, int mask, int grid_blocks, cudaStream_t s, cudaError_t* err) {
-  if (d.n_ptiles == 0) {
+int launch_pcg(const DevArrays& d, int rhs_from_g, int mask, cudaStream_t s, cudaError_t* err) {
+  if (d.n == 0 || d.pcg_grid < 1) {
     *err = cudaSuccess;
     return 0;
   }
-  int grid = grid_blocks < d.n_ptiles ? grid_blocks : d.n_ptiles;
-  if (grid < 1) grid = 1;
   DevArrays dd = d;
   void* args[] = {&dd, &rhs_from_g, &mask};
-  if (d.mixed) *err = cudaLaunchCooperativeKernel((void*)k_pcg<float>, grid, kTile, args, 0, s);
-  else *err = cudaLaunchCooperativeKernel((void*)k_pcg<double>, grid, kTile, args, 0, s);
+  const void* k = d.mixed ? pcg_kernel<float>(d.pcg_lanes) : pcg_kernel<double>(d.pcg_lanes);
+  size_t smem = sizeof(int4) * (size_t)(d.pcg_max_rows > 0 ? d.pcg_max_rows : 1);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  *err = cudaLaunchCooperativeKernel(k, d.pcg_grid, kTile, args, smem, s);
   return 1;
 }
 
@@ -1317,29 +1411,90 @@ int launch_unpack_diag(const DevArrays& d, double* out, cudaStream_t s) {
   return 1;
 }
 
-__global__ void k_pack_state(DevArrays d, double* pos3, double* vel3) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d.n) return;
-  if (pos3) { double4 p = d.x0p[i]; pos3[3 * i] = p.x; pos3[3 * i + 1] = p.y; pos3[3 * i + 2] = p.z; }
-  if (vel3) { double4 v = d.vp[i]; vel3[3 * i] = v.x; vel3[3 * i + 1] = v.y; vel3[3 * i + 2] = v.z; }
+// state transfers between the caller's particle order (perm[k] = caller index of internal particle k) and the
+// library's internal space-filling-curve order
+__global__ void k_pack_state(DevArrays d, double* pos3, double* quat4, double* vel3, double* qvel4) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.n) return;
+  size_t u = (size_t)d.perm[k];
+  if (pos3) { double4 p = d.x0p[k]; pos3[3 * u] = p.x; pos3[3 * u + 1] = p.y; pos3[3 * u + 2] = p.z; }
+  if (vel3) { double4 v = d.vp[k]; vel3[3 * u] = v.x; vel3[3 * u + 1] = v.y; vel3[3 * u + 2] = v.z; }
+  // [n][4] arrays are accessed element by element: the caller layout guarantees only 8-byte alignment
+  if (quat4) { double4 q = d.x0q[k]; quat4[4 * u] = q.x; quat4[4 * u + 1] = q.y; quat4[4 * u + 2] = q.z; quat4[4 * u + 3] = q.w; }
+  if (qvel4) { double4 q = d.vq[k]; qvel4[4 * u] = q.x; qvel4[4 * u + 1] = q.y; qvel4[4 * u + 2] = q.z; qvel4[4 * u + 3] = q.w; }
 }
 
-__global__ void k_unpack_state(DevArrays d, const double* pos3, const double* vel3) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d.n) return;
-  if (pos3) { double r = d.x0p[i].w; d.x0p[i] = make_double4(pos3[3 * i], pos3[3 * i + 1], pos3[3 * i + 2], r); }
-  if (vel3) d.vp[i] = make_double4(vel3[3 * i], vel3[3 * i + 1], vel3[3 * i + 2], 0.0);
+__global__ void k_unpack_state(DevArrays d, const double* pos3, const double* quat4, const double* vel3,
+                               const double* qvel4) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.n) return;
+  size_t u = (size_t)d.perm[k];
+  if (pos3) { double r = d.x0p[k].w; d.x0p[k] = make_double4(pos3[3 * u], pos3[3 * u + 1], pos3[3 * u + 2], r); }
+  if (vel3) d.vp[k] = make_double4(vel3[3 * u], vel3[3 * u + 1], vel3[3 * u + 2], 0.0);
+  if (quat4) d.x0q[k] = make_double4(quat4[4 * u], quat4[4 * u + 1], quat4[4 * u + 2], quat4[4 * u + 3]);
+  if (qvel4) d.vq[k] = make_double4(qvel4[4 * u], qvel4[4 * u + 1], qvel4[4 * u + 2], qvel4[4 * u + 3]);
 }
 
-int launch_pack_state(const DevArrays& d, double* pos3, double* vel3, cudaStream_t s) {
+// inertia targets given in the caller's order (inspection calls); the mass in hp.w is kept
+__global__ void k_set_hat(DevArrays d, const double* phat3, const double* qhat4) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.n) return;
+  size_t u = (size_t)d.perm[k];
+  double m = d.hp[k].w;
+  d.hp[k] = make_double4(phat3[3 * u], phat3[3 * u + 1], phat3[3 * u + 2], m);
+  d.hq[k] = make_double4(qhat4[4 * u], qhat4[4 * u + 1], qhat4[4 * u + 2], qhat4[4 * u + 3]);
+}
+
+// bond flags between the caller's bond order (order of addition) and the stored order: ext2int[e] = stored index
+__global__ void k_bond_flags(DevArrays d, uint8_t* ext, int to_device) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.nb) return;
+  int b = d.bond_ext2int[e];
+  if (to_device) d.bbroken[b] = ext[e] ? 1 : 0;
+  else ext[e] = d.bbroken[b];
+}
+
+int launch_pack_state(const DevArrays& d, double* pos3, double* quat4, double* vel3, double* qvel4, cudaStream_t s) {
   if (d.n == 0) return 0;
-  k_pack_state<<<blocks_for(d.n, 256), 256, 0, s>>>(d, pos3, vel3);
+  k_pack_state<<<blocks_for(d.n, 256), 256, 0, s>>>(d, pos3, quat4, vel3, qvel4);
   return 1;
 }
 
-int launch_unpack_state(const DevArrays& d, const double* pos3, const double* vel3, cudaStream_t s) {
+int launch_unpack_state(const DevArrays& d, const double* pos3, const double* quat4, const double* vel3,
+                        const double* qvel4, cudaStream_t s) {
   if (d.n == 0) return 0;
-  k_unpack_state<<<blocks_for(d.n, 256), 256, 0, s>>>(d, pos3, vel3);
+  k_unpack_state<<<blocks_for(d.n, 256), 256, 0, s>>>(d, pos3, quat4, vel3, qvel4);
+  return 1;
+}
+
+int launch_set_hat(const DevArrays& d, const double* phat3, const double* qhat4, cudaStream_t s) {
+  if (d.n == 0) return 0;
+  k_set_hat<<<blocks_for(d.n, 256), 256, 0, s>>>(d, phat3, qhat4);
+  return 1;
+}
+
+int launch_bond_flags(const DevArrays& d, uint8_t* ext, int to_device, cudaStream_t s) {
+  if (d.nb == 0) return 0;
+  k_bond_flags<<<blocks_for(d.nb, 256), 256, 0, s>>>(d, ext, to_device);
+  return 1;
+}
+
+// [n][6] vectors with precision conversion and reordering: dir 0 caller -> internal, dir 1 internal -> caller
+__global__ void k_convert_perm(const void* src, int sd, void* dst, int dd, const int32_t* perm, int dir, int n) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= 6 * (int64_t)n) return;
+  int64_t k = t / 6, c = t % 6;
+  int64_t u = perm[k];
+  int64_t si = dir ? t : 6 * u + c, di = dir ? 6 * u + c : t;
+  double v = sd ? reinterpret_cast<const double*>(src)[si] : (double)reinterpret_cast<const float*>(src)[si];
+  if (dd) reinterpret_cast<double*>(dst)[di] = v;
+  else reinterpret_cast<float*>(dst)[di] = (float)v;
+}
+
+int launch_convert_perm(const void* src, int sd, void* dst, int dd, const int32_t* perm, int dir, int n,
+                        cudaStream_t s) {
+  if (n == 0) return 0;
+  k_convert_perm<<<blocks_for(6 * (int64_t)n, 256), 256, 0, s>>>(src, sd, dst, dd, perm, dir, n);
   return 1;
 }
 
