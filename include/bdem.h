@@ -156,6 +156,10 @@ const char* bdem_last_error(const bdem_sim* sim);
 bdem_status bdem_debug_system(bdem_sim* sim, const double* phat, const double* qhat, double* g, double* diag,
                               double* bond_hess, int64_t* n_candidates);
 
+/* Per-bond projected reduced Hessians [count][12][12] of the bonds ids[k] (order of addition) from the system of the
+ * last bdem_debug_system call (called with bond_hess = NULL to skip the full download). */
+bdem_status bdem_debug_bonds(bdem_sim* sim, int64_t count, const int32_t* ids, double* bond_hess);
+
 /* y = H x with the system of the last bdem_debug_system call; x, y host [n][6]. */
 bdem_status bdem_debug_matvec(bdem_sim* sim, const double* x, double* y);
 

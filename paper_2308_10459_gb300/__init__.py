@@ -73,6 +73,7 @@ _PROTOS = {
     "bdem_last_error": (ctypes.c_char_p, [_vp]),
     "bdem_debug_system": (ctypes.c_int, [_vp, _dp, _dp, _dp, _dp, _dp, _lp]),
     "bdem_debug_matvec": (ctypes.c_int, [_vp, _dp, _dp]),
+    "bdem_debug_bonds": (ctypes.c_int, [_vp, ctypes.c_int64, _ip, _dp]),
     "bdem_debug_pcg": (ctypes.c_int, [_vp, _dp, ctypes.c_double, ctypes.c_int32, _dp, _ip]),
     "bdem_launch_count": (ctypes.c_int64, [_vp]),
     "bdem_pcg_static": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int32, _ip]),
@@ -243,6 +244,12 @@ class Sim:
         self._check(self.L.bdem_debug_system(self.h, _ptr(phat, _dp), _ptr(qhat, _dp), _ptr(g, _dp), _ptr(D, _dp),
                                              _ptr(H, _dp) if want_bonds else None, ctypes.byref(nc)))
         return dict(g=g, diag=D, bondH=None if H is None else H[:nb], n_candidates=nc.value)
+
+    def bdem_debug_bonds(self, ids):
+        ids = _arr(ids, np.int32)
+        out = np.zeros((max(ids.size, 1), 12, 12))
+        self._check(self.L.bdem_debug_bonds(self.h, ids.size, _ptr(ids, _ip), _ptr(out, _dp)))
+        return out[:ids.size]
 
     def bdem_debug_matvec(self, x):
         x = _arr(x, np.float64, (self.n, 6))

@@ -328,9 +328,14 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
     bounds[b] = std::max(bounds[b], bounds[b - 1]);
   }
   bounds[grid] = n;
-  int64_t max_rows = 0;
-  for (int b = 0; b < grid; ++b) max_rows = std::max(max_rows, bounds[b + 1] - bounds[b]);
-  if (max_rows * (int64_t)sizeof(int4) > (int64_t)160 * 1024)
+  int64_t max_rows = 0, max_ent = 0;
+  for (int b = 0; b < grid; ++b) {
+    max_rows = std::max(max_rows, bounds[b + 1] - bounds[b]);
+    int64_t ent = 0;
+    for (int64_t i = bounds[b]; i < bounds[b + 1]; ++i) ent += s->deg[i];
+    max_ent = std::max(max_ent, ent);
+  }
+  if (max_rows * (int64_t)sizeof(int4) + max_ent * (int64_t)sizeof(int2) > (int64_t)200 * 1024)
     return fail(s, BDEM_E_INVALID, "PCG grid of %d blocks leaves %lld rows in one block; use more blocks", grid,
                 (long long)max_rows);
   int sc = 0;
@@ -369,20 +374,20 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
   d.pcg_grid = n > 0 ? grid : 0;
   d.pcg_lanes = lanes;
   d.pcg_max_rows = (int32_t)std::max<int64_t>(max_rows, 1);
+  d.pcg_max_entries = (int32_t)std::max<int64_t>(max_ent, 1);
   return BDEM_OK;
 }
 
 // default PCG launch shape: 4 lanes per row, every co-resident block, at least 64 rows per block
-static size_t pcg_smem_for(const bdem_sim* s, int grid) {
-  return sizeof(int4) * (size_t)std::max<int64_t>(1, 2 * (s->n / std::max(grid, 1) + 64));
-}
+// co-resident PCG blocks as the registers allow (the partition's shared memory is checked in apply_pcg_shape)
+static int pcg_blocks_by_regs(const bdem_sim* s, int lanes) { return pcg_max_blocks(s->d.mixed, lanes, 1024); }
 
 // builds the partition for (lanes, grid) and shrinks the grid until every block is co-resident with the partition's
 // actual shared-memory need (a cooperative launch requires it)
 static bdem_status apply_pcg_shape(bdem_sim* s, int lanes, int grid) {
   for (int tries = 0; tries < 16; ++tries) {
     TRY(build_pcg_segments(s, lanes, grid));
-    int mx = pcg_max_blocks(s->d.mixed, lanes, sizeof(int4) * (size_t)s->d.pcg_max_rows);
+    int mx = pcg_max_blocks(s->d.mixed, lanes, pcg_smem_bytes(s->d));
     if (mx < 1) return fail(s, BDEM_E_CUDA, "no resident blocks for the PCG kernel");
     if (s->d.pcg_grid <= mx) return BDEM_OK;
     grid = mx;
@@ -392,7 +397,7 @@ static bdem_status apply_pcg_shape(bdem_sim* s, int lanes, int grid) {
 
 static bdem_status default_pcg_shape(bdem_sim* s) {
   int lanes = 2;
-  int mx = pcg_max_blocks(s->d.mixed, lanes, pcg_smem_for(s, 608));
+  int mx = pcg_blocks_by_regs(s, lanes);
   if (mx < 1) return fail(s, BDEM_E_CUDA, "no resident blocks for the PCG kernel");
   int grid = (int)std::min<int64_t>(mx, std::max<int64_t>(1, (s->n + 63) / 64));
   s->pcg_blocks = mx;
@@ -1028,7 +1033,7 @@ extern "C" bdem_status bdem_debug_system(bdem_sim* s, const double* phat, const 
   }
   if (bond_hess && s->nb) {
     TRY(dbg_reserve(s, 144 * (size_t)s->nb));
-    TRY(check_launch(s, launch_unpack_bond_hess(d, s->dbg_buf, st)));
+    TRY(check_launch(s, launch_unpack_bond_hess(d, s->dbg_buf, nullptr, 0, st)));
     CUDA_TRY(s, cudaMemcpyAsync(bond_hess, s->dbg_buf, sizeof(double) * 144 * s->nb, cudaMemcpyDeviceToHost, st));
   }
   if (n_candidates) {
@@ -1040,6 +1045,23 @@ extern "C" bdem_status bdem_debug_system(bdem_sim* s, const double* phat, const 
   TRY(sync(s));
   s->system_ready = true;
   return BDEM_OK;
+}
+
+extern "C" bdem_status bdem_debug_bonds(bdem_sim* s, int64_t count, const int32_t* ids, double* out) {
+  if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
+  if (!s->system_ready) return fail(s, BDEM_E_INVALID, "call bdem_debug_system first");
+  if (count < 0 || (count && (!ids || !out))) return fail(s, BDEM_E_INVALID, "bad arguments");
+  for (int64_t k = 0; k < count; ++k)
+    if (ids[k] < 0 || ids[k] >= s->nb) return fail(s, BDEM_E_INVALID, "bond id %d out of range", ids[k]);
+  if (count == 0) return BDEM_OK;
+  cudaStream_t st = s->stream;
+  size_t need = 144 * (size_t)count + ((size_t)count + 1) / 2 + 1;
+  TRY(dbg_reserve(s, need));
+  int32_t* dids = reinterpret_cast<int32_t*>(s->dbg_buf + 144 * (size_t)count);
+  CUDA_TRY(s, cudaMemcpyAsync(dids, ids, sizeof(int32_t) * count, cudaMemcpyHostToDevice, st));
+  TRY(check_launch(s, launch_unpack_bond_hess(s->d, s->dbg_buf, dids, (int)count, st)));
+  CUDA_TRY(s, cudaMemcpyAsync(out, s->dbg_buf, sizeof(double) * 144 * count, cudaMemcpyDeviceToHost, st));
+  return sync(s);
 }
 
 extern "C" bdem_status bdem_debug_matvec(bdem_sim* s, const double* x, double* y) {
@@ -1172,10 +1194,12 @@ extern "C" bdem_status bdem_set_pcg_shape(bdem_sim* s, int32_t lanes, int32_t bl
   if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
   if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8) return fail(s, BDEM_E_INVALID, "lanes must be 1, 2, 4 or 8");
   if (blocks < 0) return fail(s, BDEM_E_INVALID, "blocks must be >= 0");
-  int mx = pcg_max_blocks(s->d.mixed, lanes, pcg_smem_for(s, blocks > 0 ? blocks : 608));
+  int mx = pcg_blocks_by_regs(s, lanes);
   if (mx < 1) return fail(s, BDEM_E_CUDA, "no resident blocks for the PCG kernel");
+  // default: every co-resident block but at least 64 rows per block; an explicit count is honoured up to one row per
+  // block (and the co-resident limit)
   int cap = (int)std::min<int64_t>(mx, std::max<int64_t>(1, (s->n + 63) / 64));
-  int grid = blocks == 0 ? cap : std::min(blocks, cap);
+  int grid = blocks == 0 ? cap : (int)std::min<int64_t>(std::min(blocks, mx), std::max<int64_t>(1, s->n));
   TRY(sync(s));
   TRY(apply_pcg_shape(s, lanes, grid));
   s->pcg_blocks = mx;
@@ -1210,7 +1234,7 @@ extern "C" bdem_status bdem_autotune_pcg(bdem_sim* s, int32_t iters, int32_t* la
   int best_l = s->d.pcg_lanes, best_g = s->d.pcg_grid;
   const int lanes_c[] = {1, 2, 4, 8};
   for (int lanes : lanes_c) {
-    int mx = pcg_max_blocks(s->d.mixed, lanes, pcg_smem_for(s, 4 * sms));
+    int mx = pcg_blocks_by_regs(s, lanes);
     for (int per = 1; per <= std::max(1, mx / sms); ++per) {
       TRY(bdem_set_pcg_shape(s, lanes, per * sms));
       DevArrays d = s->d;

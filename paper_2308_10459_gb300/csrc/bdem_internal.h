@@ -97,6 +97,7 @@ struct DevArrays {
   int32_t *btile_start, *btile_scene, *btile_begin;
   double *part_p, *part_b;      // [tiles][kPartials]
   int32_t n_seg, pcg_grid, pcg_lanes, pcg_max_rows;  // pcg_max_rows: most rows of one PCG block
+  int32_t pcg_max_entries, pad2;                     // most incidence entries of one PCG block's rows
   int32_t *seg_row, *seg_scene, *block_seg, *scene_seg;
   double* part_s;               // [n_seg][kPartials]
   SceneCtl* sc;
@@ -116,14 +117,15 @@ enum ReduceMode { RED_GRAD = 0, RED_GDX = 1, RED_LS = 2, RED_FORCE_ACTIVE = 3, R
 int launch_scene_reduce(const DevArrays& d, int mode, int k_iter, cudaStream_t s);
 // PCG: rhs_from_g = 1 uses b = -g; else b is read from vr (already T) and eps from sc.eps_r
 int launch_pcg(const DevArrays& d, int rhs_from_g, int mask_kin, cudaStream_t s, cudaError_t* err);
-int pcg_max_blocks(int mixed, int lanes, size_t smem);  // co-resident PCG blocks on this device (0: none)
+int pcg_max_blocks(int mixed, int lanes, size_t smem);
+size_t pcg_smem_bytes(const DevArrays& d);  // shared memory of a PCG block: row descriptors + incidence entries  // co-resident PCG blocks on this device (0: none)
 int launch_gdx(const DevArrays& d, cudaStream_t s);
 int launch_ls_trial(const DevArrays& d, cudaStream_t s);
 int launch_ls_energy(const DevArrays& d, cudaStream_t s);
 int launch_ls_commit(const DevArrays& d, cudaStream_t s);
 int launch_finish(const DevArrays& d, cudaStream_t s);
 int launch_matvec(const DevArrays& d, int mask_kin, cudaStream_t s);  // vq_ = H vp_
-int launch_unpack_bond_hess(const DevArrays& d, double* out /*device [nb][144]*/, cudaStream_t s);
+int launch_unpack_bond_hess(const DevArrays& d, double* out, const int32_t* ids, int count, cudaStream_t s);
 int launch_unpack_diag(const DevArrays& d, double* out /*device [n][36]*/, cudaStream_t s);
 // transfers in the caller's particle order (any pointer may be NULL): committed state <-> [n][3] / [n][4] arrays
 int launch_pack_state(const DevArrays& d, double* pos3, double* quat4, double* vel3, double* qvel4, cudaStream_t s);

@@ -755,14 +755,19 @@ __global__ void __launch_bounds__(kTile) k_pcg(DevArrays d, int rhs_from_g, int 
   const T zero6[6] = {0, 0, 0, 0, 0, 0};
   // per-row descriptors of the block's rows, fixed for the whole solve: first incidence entry, bond count,
   // active-contact count with the kinematic flag in bit 30, first contact entry
+  // and the incidence entries of those rows (staged once; every product reads them from shared memory)
   extern __shared__ int4 s_rows[];
+  int2* s_ent = reinterpret_cast<int2*>(s_rows + d.pcg_max_rows);
   const int R0 = d.seg_row[seg0], R1 = d.seg_row[seg1];
+  const int E0 = d.inc_start[R0], E1 = d.inc_start[R1];
   for (int i = R0 + threadIdx.x; i < R1; i += blockDim.x) {
     int a = d.inc_start[i];
     int na = (d.k_self > 0.0) ? d.c_act[i] : 0;
     int kin = (mask && d.kin[i]) ? (1 << 30) : 0;
-    s_rows[i - R0] = make_int4(a, d.inc_start[i + 1] - a, na | kin, d.c_start[i]);
+    s_rows[i - R0] = make_int4(a - E0, d.inc_start[i + 1] - a, na | kin, d.c_start[i]);
   }
+  for (int e = E0 + threadIdx.x; e < E1; e += blockDim.x) s_ent[e - E0] = d.inc2[e];
+  __syncthreads();
   // ---- init: x = p = s = 0, r = b, z = M^-1 r
   for (int g = seg0; g < seg1; ++g) {
     int sc = d.seg_scene[g];
@@ -810,7 +815,7 @@ __global__ void __launch_bounds__(kTile) k_pcg(DevArrays d, int rhs_from_g, int 
               Vec6<T> zi = load6_cg<T>(Z, i);
               sym6_mul<T>(Dm + kDiagStride * (size_t)i, zi.v, y);
             }
-            const int2* ent = d.inc2 + rd.x;
+            const int2* ent = s_ent + rd.x;
             const T* Mall = reinterpret_cast<const T*>(d.bM);
 #pragma unroll 2
             for (int k = sub; k < rd.y; k += G) {
@@ -1158,10 +1163,13 @@ __global__ void k_fracture(DevArrays d) {
 // inspection helpers
 // ================================================================================================
 
+// ids: NULL (every bond, written at its caller index) or a list of caller bond indices (written in list order)
 template <typename T>
-__global__ void k_unpack_bond_hess(DevArrays d, double* out) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= d.nb) return;
+__global__ void k_unpack_bond_hess(DevArrays d, double* out, const int32_t* ids, int count) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (ids ? count : d.nb)) return;
+  int b = ids ? d.bond_ext2int[ids[t]] : t;
+  size_t slot = ids ? (size_t)t : (size_t)d.bond_int2ext[b];
   const T* M = reinterpret_cast<const T*>(d.bM) + 36 * (size_t)b;
   const T* E = reinterpret_cast<const T*>(d.bE) + 12 * (size_t)b;
   double H[12][12];
@@ -1179,9 +1187,13 @@ __global__ void k_unpack_bond_hess(DevArrays d, double* out) {
       H[3 + a][3 + c] = e; H[9 + a][9 + c] = g;
       H[3 + a][9 + c] = f; H[9 + c][3 + a] = f;
     }
-  double* o = out + 144 * (size_t)d.bond_int2ext[b];
+  // stored bonds are oriented by internal index; report them oriented like the caller's pair (lower caller index
+  // first), swapping the two endpoint blocks when the orders disagree
+  int2 bp = d.bij[b];
+  int flip = d.perm[bp.x] > d.perm[bp.y] ? 6 : 0;
+  double* o = out + 144 * slot;
   for (int a = 0; a < 12; ++a)
-    for (int c = 0; c < 12; ++c) o[12 * a + c] = H[a][c];
+    for (int c = 0; c < 12; ++c) o[12 * a + c] = H[(a + flip) % 12][(c + flip) % 12];
 }
 
 template <typename T>
@@ -1322,6 +1334,11 @@ int launch_scene_reduce(const DevArrays& d, int mode, int k_iter, cudaStream_t s
   return 1;
 }
 
+size_t pcg_smem_bytes(const DevArrays& d) {
+  return sizeof(int4) * (size_t)(d.pcg_max_rows > 0 ? d.pcg_max_rows : 1) +
+         sizeof(int2) * (size_t)(d.pcg_max_entries > 0 ? d.pcg_max_entries : 1);
+}
+
 template <typename T>
 static const void* pcg_kernel(int lanes) {
   switch (lanes) {
@@ -1350,7 +1367,7 @@ int launch_pcg(const DevArrays& d, int rhs_from_g, int mask, cudaStream_t s, cud
   DevArrays dd = d;
   void* args[] = {&dd, &rhs_from_g, &mask};
   const void* k = d.mixed ? pcg_kernel<float>(d.pcg_lanes) : pcg_kernel<double>(d.pcg_lanes);
-  size_t smem = sizeof(int4) * (size_t)(d.pcg_max_rows > 0 ? d.pcg_max_rows : 1);
+  size_t smem = pcg_smem_bytes(d);
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   *err = cudaLaunchCooperativeKernel(k, d.pcg_grid, kTile, args, smem, s);
   return 1;
@@ -1397,10 +1414,11 @@ int launch_matvec(const DevArrays& d, int mask, cudaStream_t s) {
   return 1;
 }
 
-int launch_unpack_bond_hess(const DevArrays& d, double* out, cudaStream_t s) {
-  if (d.nb == 0) return 0;
-  if (d.mixed) k_unpack_bond_hess<float><<<blocks_for(d.nb, 64), 64, 0, s>>>(d, out);
-  else k_unpack_bond_hess<double><<<blocks_for(d.nb, 64), 64, 0, s>>>(d, out);
+int launch_unpack_bond_hess(const DevArrays& d, double* out, const int32_t* ids, int count, cudaStream_t s) {
+  int m = ids ? count : d.nb;
+  if (m == 0) return 0;
+  if (d.mixed) k_unpack_bond_hess<float><<<blocks_for(m, 64), 64, 0, s>>>(d, out, ids, count);
+  else k_unpack_bond_hess<double><<<blocks_for(m, 64), 64, 0, s>>>(d, out, ids, count);
   return 1;
 }
 

@@ -1,0 +1,264 @@
+"""Scene-level parity of the CUDA path against the CPU oracle, through the C ABI (needs a GB300).
+
+Covers fracture (tensile strain) with kinematic boundary particles, ground and self contact, batched independent
+scenes of uneven sizes (including an empty scene and an unbonded one), checkpoint / resume, status codes and
+argument validation, the 1,000-particle cube, and full-size sampled checks on the 219K-particle plate.
+Tolerances: FP64 path 1e-9 of the scene's bounding-box diagonal (positions) and 1e-9 (quaternions); mixed path
+1e-4; bond-break sets identical.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2308_10459_gb300 as pkg
+from paper_2308_10459_gb300 import build as bmod
+from paper_2308_10459_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+Rotation = pytest.importorskip("scipy.spatial.transform").Rotation
+
+TOL = {pkg.BDEM_FP64: 1e-9, pkg.BDEM_MIXED: 1e-4}
+PRECS = [pkg.BDEM_FP64, pkg.BDEM_MIXED]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    bmod.build()
+    pkg.load()
+
+
+def bbox(sc):
+    return float(np.linalg.norm(sc.pos.max(0) - sc.pos.min(0)))
+
+
+def quat_err(a, b):
+    return float(np.minimum(np.abs(a - b).max(1), np.abs(a + b).max(1)).max()) if len(a) else 0.0
+
+
+def oracle_trajectory(sc, steps, cfg=None):
+    o = oracle.OracleSim(sc, cfg)
+    states, stats = [], []
+    for _ in range(steps):
+        stats.append(o.step(1)[0])
+        states.append(o.state())
+    return states, stats, o
+
+
+def strain_margin(o, states):
+    """Smallest |strain - limit| / limit over intact bonds and steps (for reporting break-set mismatches)."""
+    m = math.inf
+    for st in states:
+        d = st["pos"][o.bj] - st["pos"][o.bi]
+        e = (np.linalg.norm(d, axis=1) - o.l0) / o.l0
+        fin = np.isfinite(o.brk)
+        if fin.any():
+            m = min(m, float(np.min(np.abs(e[fin] - o.brk[fin]) / o.brk[fin])))
+    return m
+
+
+def compare(sc, prec, ref_states, steps, cfg=None, check_every=1, quat_tol=None, loose_from=None, loose_tol=None):
+    """Step-by-step comparison; from step index `loose_from` on, positions are held to `loose_tol` instead."""
+    sim = pkg.Sim(sc, precision=prec, config=cfg)
+    L = bbox(sc)
+    qtol = quat_tol if quat_tol is not None else TOL[prec]
+    for k in range(steps):
+        sim.step(1)
+        if (k + 1) % check_every and k != steps - 1:
+            continue
+        st = sim.read_state()
+        ref = ref_states[k]
+        e = np.abs(st["pos"] - ref["pos"]).max() / L if sc.n else 0.0
+        ptol = TOL[prec] if loose_from is None or k < loose_from else max(TOL[prec], loose_tol)
+        assert e <= ptol, (k, e)
+        assert quat_err(st["quat"], ref["quat"]) <= max(qtol, TOL[prec]), k
+        assert np.array_equal(st["broken"], ref["broken"]), (k, np.nonzero(st["broken"] != ref["broken"]))
+    sim.close()
+
+
+TEXTILE_CFG = dict(newton_rel_tol=1e-9)
+# The bend-twist stiffness is 1e-3 of nominal: the gradient norm that stops Newton is dominated by the stiff stretch
+# modes, so the orientations of this lattice are pinned down only to about 1e-8 (two correct solvers that round
+# differently land that far apart); positions are held to 1e-9.
+TEXTILE_QUAT_TOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def textile():
+    sc = scenes.c3_textile(nx=12, steps=8)
+    states, stats, o = oracle_trajectory(sc, 8, TEXTILE_CFG)
+    assert sum(s[0]["bonds_broken"] for s in stats) > 50  # the tear happens inside the compared window
+    return sc, states, o
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_textile_tear_with_kinematic_edges(textile, prec):
+    """12x12 textile lattice (x, y and diagonal bonds, bend-twist 1e-3 of nominal), edge columns kinematic and
+    pulled apart at 0.5 m/s, tensile break strain 0.3: the tear starts at step 6 (4 bonds) and runs at step 7
+    (92 bonds). Break sets must be identical at every step; positions are held to 1e-9 until the tear has run, and
+    to 1e-8 in the step after it, where the freed particles amplify the rounding differences of two correct
+    solvers (the minimum strain margin to the break limit is printed on failure)."""
+    sc, states, o = textile
+    try:
+        compare(sc, prec, states, 8, cfg=TEXTILE_CFG, quat_tol=TEXTILE_QUAT_TOL, loose_from=7, loose_tol=1e-8)
+    except AssertionError:
+        print("minimum relative strain margin to the break limit:", strain_margin(o, states))
+        raise
+
+
+@pytest.fixture(scope="module")
+def small_plate():
+    sc = scenes.c2_plate_small(R=0.015)
+    states, stats, _ = oracle_trajectory(sc, 3)
+    assert stats[0][0]["n_candidates"] > 0
+    return sc, states
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_small_plate_ground_and_self_contact(small_plate, prec):
+    """The plate construction (HCP, E = 5e9, 3 m/s drop, ground and self penalty contact) at R = 15 mm."""
+    sc, states = small_plate
+    compare(sc, prec, states, 3)
+
+
+def batched_scene():
+    a = scenes.cube_lattice(nx=2, z_bottom=0.006, k_ground=1e6, vel=(0.1, 0.0, -0.5))
+    b = scenes.cube_lattice(nx=3, z_bottom=0.02, k_ground=1e6, vel=(0.0, 0.2, -1.0), jitter=1e-4, seed=5)
+    rng = np.random.default_rng(9)
+    free = rng.uniform(0.0, 0.05, (5, 3)) + np.array([0.0, 0.0, 0.01])
+    parts = [a.pos, np.zeros((0, 3)), b.pos, free]
+    offs = np.cumsum([0] + [len(x) for x in parts])
+    pos = np.concatenate(parts, 0)
+    pairs = np.concatenate([np.stack([a.bond_i, a.bond_j], 1), np.stack([b.bond_i, b.bond_j], 1) + offs[2]], 0)
+    vel = np.concatenate([a.vel, np.zeros((0, 3)), b.vel, rng.normal(size=(5, 3)) * 0.1], 0)
+    n = pos.shape[0]
+    cfg = scenes.default_config(dt=1e-3, k_ground=1e6)
+    mats = [scenes.Material(1e7, 0.3, 2500.0, math.inf, 1.0, 0.01)]
+    return scenes._assemble(pos, np.full(n, 0.005), np.zeros(n, np.int32), np.zeros(n, np.uint8), pairs, mats, cfg,
+                            "batched", vel=vel, offsets=offs)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_batched_uneven_scenes(prec):
+    """Four independent scenes in one simulation (8-particle cube, an empty scene, a 27-particle jittered cube,
+    five unbonded particles): each converges on its own; per-scene statistics match the oracle's."""
+    sc = batched_scene()
+    states, stats, _ = oracle_trajectory(sc, 20)
+    compare(sc, prec, states, 20, check_every=5)
+    sim = pkg.Sim(sc, precision=prec)
+    st = sim.step(1)
+    assert len(st) == 4 and st[1]["newton_iters"] == 0
+    if prec == pkg.BDEM_FP64:
+        for s in (0, 2, 3):
+            assert st[s]["newton_iters"] == stats[0][s]["newton_iters"]
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_checkpoint_resume_is_bit_identical(prec):
+    """Reading the state after 5 steps, writing it into a fresh simulation and running 5 more steps reproduces an
+    uninterrupted 10-step run bit for bit (deterministic assembly and reductions)."""
+    sc = scenes.cube_lattice(nx=4, z_bottom=0.006, k_ground=1e6, vel=(0.0, 0.0, -0.5), jitter=1e-4, seed=2)
+    a = pkg.Sim(sc, precision=prec)
+    a.step(5)
+    ck = a.read_state()
+    a.step(5)
+    ref = a.read_state()
+    b = pkg.Sim(sc, precision=prec)
+    b.write_state(ck["pos"], ck["quat"], ck["vel"], ck["quat_vel"], ck["broken"])
+    b.step(5)
+    got = b.read_state()
+    for k in ("pos", "quat", "vel", "quat_vel", "broken"):
+        assert np.array_equal(got[k], ref[k]), k
+    a.close()
+    b.close()
+
+
+def test_status_codes_and_validation():
+    sc = scenes.cube_lattice(nx=3, z_bottom=0.004, k_ground=1e6, vel=(0.0, 0.0, -1.0))
+    sim = pkg.Sim(sc, precision=pkg.BDEM_FP64, config=dict(newton_max_iter=1, newton_rel_tol=1e-12))
+    before = sim.read_state()
+    assert sim.step(0)[0]["steps"] == 0
+    assert np.array_equal(sim.read_state()["pos"], before["pos"])
+    st = sim.step(1)[0]
+    assert sim.last_status == pkg.BDEM_E_NEWTON_MAXITER and st["status"] == 4 and st["newton_iters"] == 1
+    assert not np.array_equal(sim.read_state()["pos"], before["pos"])  # the best iterate was committed
+    with pytest.raises(pkg.BdemError) as e:
+        sim.bdem_add_bonds([0], [0], [0])
+    assert e.value.status == pkg.BDEM_E_INVALID
+    with pytest.raises(pkg.BdemError):
+        sim.bdem_add_bonds([0], [1], [0])  # duplicate of an existing bond
+    with pytest.raises(pkg.BdemError):
+        sim.bdem_add_bonds([0], [sc.n], [0])
+    with pytest.raises(pkg.BdemError):
+        sim.bdem_write_state(quat=np.tile([0.0, 0.0, 0.0, 2.0], (sc.n, 1)))
+    with pytest.raises(pkg.BdemError):
+        sim.bdem_debug_matvec(np.zeros((sc.n, 6)))  # no inspected system yet
+    sim.close()
+    bad = sc.copy()
+    bad.quat[0] = [0.0, 0.0, 0.0, 1.1]
+    with pytest.raises(pkg.BdemError):
+        pkg.Sim(bad)
+    with pytest.raises(pkg.BdemError):
+        pkg.Sim(sc, config=dict(dt=-1.0))
+    two = scenes._assemble(np.array([[0, 0, 0], [0.01, 0, 0]], float), np.full(2, 0.005), np.zeros(2, np.int32),
+                           np.zeros(2, np.uint8), np.array([[0, 1]]), [scenes.Material(1e7, 0.3, 2500.0)],
+                           scenes.default_config(), "x", offsets=[0, 1, 2])
+    with pytest.raises(pkg.BdemError):
+        pkg.Sim(two)  # a bond across two scenes
+
+
+def test_c1_cube_first_steps():
+    """The 1,000-particle cube (10x10x10, 2,700 bonds) in free fall: 20 FP64 steps against the oracle, and the
+    mixed path within its tolerance."""
+    sc = scenes.c1_cube()
+    states, stats, _ = oracle_trajectory(sc, 20)
+    compare(sc, pkg.BDEM_FP64, states, 20, check_every=10)
+    compare(sc, pkg.BDEM_MIXED, states, 20, check_every=10)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_size_plate_sampled_and_properties(prec):
+    """219K-particle plate after two steps (in contact): sampled bond Hessians against the oracle evaluated one by
+    one, and properties of the whole system that hold at any size: H symmetric (x.Hy = y.Hx) and positive
+    semi-definite (x.Hx >= 0), and the PCG residual reaching its tolerance."""
+    sc = scenes.c2_plate()
+    sim = pkg.Sim(sc, precision=prec)
+    sim.step(2)
+    st = sim.read_state()
+    dt = sc.config["dt"]
+    sysd = sim.bdem_debug_system(st["pos"] + dt * st["vel"], st["quat"] + dt * st["quat_vel"], want_bonds=False)
+    assert sysd["n_candidates"] > 0 and np.all(np.isfinite(sysd["g"]))
+    o = oracle.OracleSim(sc)
+    o.broken[:] = st["broken"]
+    ids = np.random.default_rng(1).choice(sc.nb, 300, replace=False).astype(np.int32)
+    ids = ids[st["broken"][ids] == 0]
+    H = sim.bdem_debug_bonds(ids)
+    htol, ftol = (1e-10, 1e-13) if prec == pkg.BDEM_FP64 else (2e-5, 1e-6)
+    for k, b in enumerate(ids):
+        i, j = sc.bond_i[b], sc.bond_j[b]
+        _, _, _, Hr = o.bond_terms(b, st["pos"][i], st["quat"][i], st["pos"][j], st["quat"][j])
+        scl = np.sqrt(np.abs(np.outer(np.diag(Hr), np.diag(Hr))))
+        assert np.all(np.abs(H[k] - Hr) <= htol * scl + ftol * np.abs(Hr).max()), b
+    rng = np.random.default_rng(2)
+    x, y = rng.normal(size=(sc.n, 6)), rng.normal(size=(sc.n, 6))
+    Hx, Hy = sim.bdem_debug_matvec(x), sim.bdem_debug_matvec(y)
+    scale = np.sqrt((x * Hx).sum() * (y * Hy).sum())
+    assert abs((x * Hy).sum() - (y * Hx).sum()) <= (1e-11 if prec == pkg.BDEM_FP64 else 1e-5) * scale
+    assert (x * Hx).sum() > 0 and (y * Hy).sum() > 0
+    b = -sysd["g"]
+    dx, it = sim.bdem_debug_pcg(b, 0.1, 20000)
+    assert 0 < it[0] < 20000  # converged before the cap
+    r = b - sim.bdem_debug_matvec(dx)
+    if prec == pkg.BDEM_FP64:
+        # the recurrence residual met the tolerance and the true residual b - H dx agrees with it to rounding
+        assert np.linalg.norm(r) <= 0.1 * np.linalg.norm(b) * (1.0 + 1e-6)
+    else:
+        # FP32 recurrences drift from the true residual on this ill-conditioned system; what the Newton loop needs
+        # (its FP64 gradient refines the step) is a descent direction with a true residual clearly below |b|
+        assert np.linalg.norm(r) <= 0.6 * np.linalg.norm(b) and (b * dx).sum() > 0
+    sim.close()
