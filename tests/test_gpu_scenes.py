@@ -82,9 +82,10 @@ def compare(sc, prec, ref_states, steps, cfg=None, check_every=1, quat_tol=None,
 
 TEXTILE_CFG = dict(newton_rel_tol=1e-9)
 # The bend-twist stiffness is 1e-3 of nominal: the gradient norm that stops Newton is dominated by the stiff stretch
-# modes, so the orientations of this lattice are pinned down only to about 1e-8 (two correct solvers that round
-# differently land that far apart); positions are held to 1e-9.
-TEXTILE_QUAT_TOL = 1e-8
+# modes, so the orientations of this lattice are pinned down only loosely by the stopping test. The oracle itself,
+# run at Newton tolerances 1e-9 and 1e-12 on this scene, gives orientations up to 5.2e-8 apart over steps 0-5
+# (positions up to 2.6e-9 of the diagonal); quaternions are therefore held to 1e-7, positions to 1e-9.
+TEXTILE_QUAT_TOL = 1e-7
 
 
 @pytest.fixture(scope="module")
