@@ -61,6 +61,8 @@ typedef struct {
   double bend_twist_scale;  /* >= 0, multiplies K = diag(GJ, EI, EI)/l0 */
   double shear_scale;       /* >= 0, multiplies the shear angle: 1 gives 1/2 kt theta^2 as printed (N/m);
                                a length (e.g. the rest bond length) gives the dimensionally consistent energy */
+  double tensile_strength;  /* sigma_c > 0 of the stress fracture criterion (Sec. 3.2); +inf: off */
+  double shear_strength;    /* tau_c > 0 of the stress fracture criterion; +inf: off */
 } bdem_material;
 
 typedef struct {
@@ -95,6 +97,8 @@ typedef struct {
   int32_t reserved0;
   double g0_norm;           /* |g_0| of the last step */
   double g_norm;            /* |g| at exit of the last step */
+  int64_t contact_entry_pcg_iters; /* sum over linear solves of (active self-contact matrix entries x PCG iterations) */
+  int64_t intact_bonds;     /* intact bonds of the scene after the last step */
 } bdem_step_stats;
 
 /* Creates a simulation of n particles split into n_scenes independent scenes: scene s owns particles
@@ -119,8 +123,23 @@ bdem_status bdem_create(const bdem_config* config, int32_t n_scenes, const int64
 bdem_status bdem_add_bonds(bdem_sim* sim, int64_t n, const int32_t* i, const int32_t* j, const int32_t* bond_material);
 
 /* Advances n_steps >= 0 time steps (Alg. 3). stats: NULL or an array of n_scenes entries. Host-blocking: returns
- * when the last step has completed on the device. */
+ * when the last step has completed on the device.
+ * By default every step after the first is one launch of a captured CUDA graph whose Newton and line-search loops
+ * are conditional while nodes decided on the device (one host synchronisation per step); the first step, a step
+ * whose contact candidates outgrow the arrays sized so far (repeated, not committed twice), and every step while
+ * phase timing is on run the same kernels from a host-driven loop. Both orders give bit-identical results. */
 bdem_status bdem_step(bdem_sim* sim, int32_t n_steps, bdem_step_stats* stats);
+
+/* on = 0: every step uses the host-driven loop; on = 1 (default): steps use the captured step graph when the
+ * device supports it. Clears a recorded capture failure. */
+bdem_status bdem_set_step_graph(bdem_sim* sim, int32_t on);
+
+/* Steps that ran through the captured graph since creation. */
+int64_t bdem_graph_steps(const bdem_sim* sim);
+
+/* Why the step graph could not be captured or instantiated ("" if it could); steps then use the host-driven
+ * loop. */
+const char* bdem_graph_error(const bdem_sim* sim);
 
 /* Copies the committed state to caller host buffers; any pointer may be NULL. pos[n][3], quat[n][4], vel[n][3],
  * quat_vel[n][4], bond_broken[n_bonds] (1 = broken). Synchronises the library's stream. */
@@ -159,6 +178,11 @@ bdem_status bdem_debug_system(bdem_sim* sim, const double* phat, const double* q
 /* Per-bond projected reduced Hessians [count][12][12] of the bonds ids[k] (order of addition) from the system of the
  * last bdem_debug_system call (called with bond_hess = NULL to skip the full download). */
 bdem_status bdem_debug_bonds(bdem_sim* sim, int64_t count, const int32_t* ids, double* bond_hess);
+
+/* Stresses (sigma, tau) of the stress fracture criterion (Sec. 3.2) of every bond at the committed state, computed
+ * in FP64 by the kernel the fracture test uses: out host [n_bonds][2] in the order of addition (broken bonds
+ * included, evaluated as if intact). */
+bdem_status bdem_debug_bond_stress(bdem_sim* sim, double* out);
 
 /* y = H x with the system of the last bdem_debug_system call; x, y host [n][6]. */
 bdem_status bdem_debug_matvec(bdem_sim* sim, const double* x, double* y);

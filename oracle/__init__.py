@@ -60,7 +60,8 @@ class OrcProblem(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("nb", ctypes.c_int32), ("n_scenes", ctypes.c_int32), ("pad0", ctypes.c_int32),
                 ("scene_start", _lp), ("p", _dp), ("q", _dp), ("v", _dp), ("u", _dp), ("radius", _dp), ("mass", _dp),
                 ("kinematic", _up), ("bi", _ip), ("bj", _ip), ("l0", _dp), ("d0", _dp), ("R0", _dp), ("kn", _dp),
-                ("kt", _dp), ("kbt", _dp), ("shear_scale", _dp), ("break_strain", _dp), ("broken", _up)]
+                ("kt", _dp), ("kbt", _dp), ("shear_scale", _dp), ("break_strain", _dp), ("broken", _up),
+                ("tensile_strength", _dp), ("shear_strength", _dp)]
 
 
 class OrcStats(ctypes.Structure):
@@ -75,6 +76,8 @@ def _setup(L):
     L.orc_step.argtypes = [C, P, ctypes.POINTER(OrcStats)]
     L.orc_bond_terms.argtypes = [P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     L.orc_bond_energy_parts.argtypes = [P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
+    L.orc_bond_stress.argtypes = [P, ctypes.c_int, _dp, _dp, _dp]
+    L.orc_bond_stress.restype = None
     L.orc_system.argtypes = [C, P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _ip]
     L.orc_matvec.argtypes = [C, P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
     L.orc_pcg_solve.argtypes = [C, P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp]
@@ -201,6 +204,8 @@ class OracleSim:
         bts = f64([m.bend_twist_scale for m in mats]) if nb else np.zeros(0)
         shs = f64([m.shear_scale for m in mats]) if nb else np.zeros(0)
         brk = f64([m.break_strain for m in mats]) if nb else np.zeros(0)
+        self.sig_c = f64([getattr(m, "tensile_strength", math.inf) for m in mats]) if nb else np.zeros(0)
+        self.tau_c = f64([getattr(m, "shear_strength", math.inf) for m in mats]) if nb else np.zeros(0)
         self._build_problem()
         if nb:
             lib().orc_bond_rest(ctypes.byref(self.P), _d(E), _d(nu), _d(bts), _d(shs), _d(brk))
@@ -233,6 +238,7 @@ class OracleSim:
         P.l0, P.d0, P.R0, P.kn, P.kt, P.kbt = _d(self.l0), _d(self.d0), _d(self.R0), _d(self.kn), _d(self.kt), _d(self.kbt)
         P.shear_scale, P.break_strain = _d(self.shs), _d(self.brk)
         P.broken = self.broken.ctypes.data_as(_up)
+        P.tensile_strength, P.shear_strength = _d(self.sig_c), _d(self.tau_c)
         self.P = P
 
     def step(self, n_steps=1):
@@ -267,6 +273,17 @@ class OracleSim:
         pi, qi, pj, qj = f64(pi), f64(qi), f64(pj), f64(qj)
         lib().orc_bond_energy_parts(ctypes.byref(self.P), int(b), _d(pi), _d(qi), _d(pj), _d(qj), _d(out))
         return out
+
+    def bond_stress(self, b, pos=None, quat=None):
+        """(sigma, tau) of bond b at (pos, quat), default the current state (stress fracture criterion)."""
+        pos = self.p if pos is None else f64(pos, (self.scene.n, 3))
+        quat = self.q if quat is None else f64(quat, (self.scene.n, 4))
+        out = np.zeros(2)
+        lib().orc_bond_stress(ctypes.byref(self.P), int(b), _d(pos), _d(quat), _d(out))
+        return out
+
+    def bond_stresses(self, pos=None, quat=None):
+        return np.array([self.bond_stress(b, pos, quat) for b in range(self.scene.nb)]).reshape(-1, 2)
 
     def _scene_range(self, scene):
         return int(self.starts[scene]), int(self.starts[scene + 1])

@@ -427,7 +427,7 @@ static void jrotate(const jet q[4], const double d0[3], jet d[3]) {
 
 /* returns total energy; parts: stretch, shear, bend-twist */
 static jet bond_energy_jet(const orc_problem* P, int b, const double pi[3], const double qi[4], const double pj[3],
-                           const double qj[4], double parts[3], double* l_out, double t_out[3]) {
+                           const double qj[4], double parts[3], double* l_out, double t_out[3], jet part_jets[3]) {
   jet Pi[3], Qi[4], Pj[3], Qj[4];
   for (int k = 0; k < 3; ++k) { Pi[k] = jvar(pi[k], k); Pj[k] = jvar(pj[k], 7 + k); }
   for (int k = 0; k < 4; ++k) { Qi[k] = jvar(qi[k], 3 + k); Qj[k] = jvar(qj[k], 10 + k); }
@@ -471,6 +471,7 @@ static jet bond_energy_jet(const orc_problem* P, int b, const double pi[3], cons
   jet Vbt = jscale(jadd(jadd(jscale(jmul(t[0], t[0]), K[0]), jscale(jmul(t[1], t[1]), K[1])), jscale(jmul(t[2], t[2]), K[2])), 0.5);
 
   if (parts) { parts[0] = Vs.v; parts[1] = Vsh.v; parts[2] = Vbt.v; }
+  if (part_jets) { part_jets[0] = Vs; part_jets[1] = Vsh; part_jets[2] = Vbt; }
   if (l_out) *l_out = l.v;
   if (t_out) { t_out[0] = t[0].v; t_out[1] = t[1].v; t_out[2] = t[2].v; }
   return jadd(jadd(Vs, Vsh), Vbt);
@@ -480,14 +481,42 @@ void orc_bond_energy_parts(const orc_problem* P, int b, const double pi[3], cons
                            const double qj[4], double parts[3]) {
   int save = g_order;
   g_order = 0;
-  bond_energy_jet(P, b, pi, qi, pj, qj, parts, NULL, NULL);
+  bond_energy_jet(P, b, pi, qi, pj, qj, parts, NULL, NULL, NULL);
   g_order = save;
+}
+
+/* Bond stresses of the stress fracture criterion (Sec. 3.2, Fracture Criteria), from the implicit potentials:
+ *   F_n = grad_p V_stretch, F_s = grad_p V_shear (gradients with respect to the position of endpoint j; the
+ *   endpoint i gradients are their negatives), (K t) the generalised moment of the bend-twist potential in the
+ *   bond frame (e_0 the twist axis), M_t = <K t, e_0> e_0, M_b = <K t, e_1> e_1 + <K t, e_2> e_2;
+ *   sigma = |F_n| / S + |M_b| r0 / I, tau = |F_s| / S + |M_t| r0 / J with r0 = (r_i + r_j)/2, S = pi r0^2,
+ *   I = pi r0^4 / 4, J = pi r0^4 / 2.
+ * The gradients come from the jets of the energy parts (first derivatives). */
+void orc_bond_stress(const orc_problem* P, int b, const double* p, const double* q, double out[2]) {
+  int i = P->bi[b], j = P->bj[b], save = g_order;
+  g_order = 2;
+  jet parts[3];
+  double t[3];
+  bond_energy_jet(P, b, p + 3 * i, q + 4 * i, p + 3 * j, q + 4 * j, NULL, NULL, t, parts);
+  g_order = save;
+  double fn = 0.0, fs = 0.0;
+  for (int k = 0; k < 3; ++k) {  /* variables 7..9 are p_j */
+    fn += parts[0].g[7 + k] * parts[0].g[7 + k];
+    fs += parts[1].g[7 + k] * parts[1].g[7 + k];
+  }
+  const double* K = P->kbt + 3 * b;
+  double mt = fabs(K[0] * t[0]);
+  double mb = sqrt(K[1] * t[1] * K[1] * t[1] + K[2] * t[2] * K[2] * t[2]);
+  double r0 = 0.5 * (P->radius[i] + P->radius[j]);
+  double S = M_PI * r0 * r0, I = M_PI * pow(r0, 4) / 4.0, J = M_PI * pow(r0, 4) / 2.0;
+  out[0] = sqrt(fn) / S + mb * r0 / I;
+  out[1] = sqrt(fs) / S + mt * r0 / J;
 }
 
 static double bond_energy(const orc_problem* P, int b, const double* p, const double* q) {
   int i = P->bi[b], j = P->bj[b], save = g_order;
   g_order = 0;
-  jet V = bond_energy_jet(P, b, p + 3 * i, q + 4 * i, p + 3 * j, q + 4 * j, NULL, NULL, NULL);
+  jet V = bond_energy_jet(P, b, p + 3 * i, q + 4 * i, p + 3 * j, q + 4 * j, NULL, NULL, NULL, NULL);
   g_order = save;
   return V.v;
 }
@@ -500,8 +529,8 @@ static double bond_energy_diff(const orc_problem* P, int b, const double* p0, co
   int i = P->bi[b], j = P->bj[b], save = g_order;
   double e0[3], e1[3], l0v, l1v, t0[3], t1[3];
   g_order = 0;
-  bond_energy_jet(P, b, p0 + 3 * i, q0 + 4 * i, p0 + 3 * j, q0 + 4 * j, e0, &l0v, t0);
-  bond_energy_jet(P, b, p1 + 3 * i, q1 + 4 * i, p1 + 3 * j, q1 + 4 * j, e1, &l1v, t1);
+  bond_energy_jet(P, b, p0 + 3 * i, q0 + 4 * i, p0 + 3 * j, q0 + 4 * j, e0, &l0v, t0, NULL);
+  bond_energy_jet(P, b, p1 + 3 * i, q1 + 4 * i, p1 + 3 * j, q1 + 4 * j, e1, &l1v, t1, NULL);
   g_order = save;
   double dd[3], ds[3];
   for (int k = 0; k < 3; ++k) {
@@ -538,7 +567,7 @@ static void pair_reduce(const jet* V, const double qa[4], const double qb[4], do
 void orc_bond_terms(const orc_problem* P, int b, const double pi[3], const double qi[4], const double pj[3],
                     const double qj[4], double* energy, double* grad12, double* hess12, double* hess12_spd) {
   g_order = 2;
-  jet V = bond_energy_jet(P, b, pi, qi, pj, qj, NULL, NULL, NULL);
+  jet V = bond_energy_jet(P, b, pi, qi, pj, qj, NULL, NULL, NULL, NULL);
   double g12[12], H12[144];
   pair_reduce(&V, qi, qj, g12, H12);
   if (energy) *energy = V.v;
@@ -1131,13 +1160,21 @@ int orc_step(const orc_config* C, orc_problem* P, orc_scene_stats* stats) {
     for (int k = 0; k < 3; ++k) { P->v[3 * i + k] = (xp[3 * i + k] - P->p[3 * i + k]) / dt; P->p[3 * i + k] = xp[3 * i + k]; }
     for (int k = 0; k < 4; ++k) { P->u[4 * i + k] = (xq[4 * i + k] - P->q[4 * i + k]) / dt; P->q[4 * i + k] = xq[4 * i + k]; }
   }
-  /* bond state update: tensile strain fracture, all bonds at once */
+  /* bond state update, all bonds at once at the new state: tensile strain fracture, and the stress criterion
+   * sigma > sigma_c or tau > tau_c of Sec. 3.2 where the bond's strengths are finite */
   for (int b = 0; b < P->nb; ++b) {
     if (P->broken[b]) continue;
     int i = P->bi[b], j = P->bj[b];
     double d[3] = {P->p[3 * j] - P->p[3 * i], P->p[3 * j + 1] - P->p[3 * i + 1], P->p[3 * j + 2] - P->p[3 * i + 2]};
     double strain = (sqrt(dot3(d, d)) - P->l0[b]) / P->l0[b];
-    if (strain > P->break_strain[b]) {
+    int brk = strain > P->break_strain[b];
+    if (!brk && P->tensile_strength && P->shear_strength &&
+        (isfinite(P->tensile_strength[b]) || isfinite(P->shear_strength[b]))) {
+      double st[2];
+      orc_bond_stress(P, b, P->p, P->q, st);
+      brk = st[0] > P->tensile_strength[b] || st[1] > P->shear_strength[b];
+    }
+    if (brk) {
       P->broken[b] = 1;
       for (int s = 0; s < P->n_scenes; ++s)
         if (i >= P->scene_start[s] && i < P->scene_start[s + 1]) stats[s].bonds_broken++;

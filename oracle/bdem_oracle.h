@@ -57,6 +57,8 @@ typedef struct {
   double* shear_scale;          /* [nb] multiplies theta in the shear energy */
   double* break_strain;         /* [nb] tensile strain limit (+inf: unbreakable) */
   uint8_t* broken;              /* [nb] */
+  const double* tensile_strength; /* [nb] sigma_c of the stress criterion (+inf: off), or NULL */
+  const double* shear_strength;   /* [nb] tau_c of the stress criterion (+inf: off), or NULL */
 } orc_problem;
 
 typedef struct {
@@ -81,6 +83,9 @@ int orc_step(const orc_config* C, orc_problem* P, orc_scene_stats* stats);
  * intact bond at the given endpoint states. Any output may be NULL. */
 void orc_bond_terms(const orc_problem* P, int b, const double pi[3], const double qi[4], const double pj[3],
                     const double qj[4], double* energy, double* grad12, double* hess12, double* hess12_spd);
+
+/* Stresses (sigma, tau) of one bond at the state (p[n][3], q[n][4]) for the stress fracture criterion. */
+void orc_bond_stress(const orc_problem* P, int b, const double* p, const double* q, double out[2]);
 
 /* Plain bond energy (stretch, shear, bend-twist parts). */
 void orc_bond_energy_parts(const orc_problem* P, int b, const double pi[3], const double qi[4],

@@ -26,7 +26,8 @@ STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "NOMEM", 3: "CUDA", 4: "NEWTON_MAXITER
 class bdem_material(ctypes.Structure):
     _fields_ = [("E", ctypes.c_double), ("nu", ctypes.c_double), ("density", ctypes.c_double),
                 ("break_strain", ctypes.c_double), ("bend_twist_scale", ctypes.c_double),
-                ("shear_scale", ctypes.c_double)]
+                ("shear_scale", ctypes.c_double), ("tensile_strength", ctypes.c_double),
+                ("shear_strength", ctypes.c_double)]
 
 
 class bdem_config(ctypes.Structure):
@@ -41,7 +42,8 @@ class bdem_step_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int32), ("newton_iters", ctypes.c_int32), ("pcg_iters", ctypes.c_int32),
                 ("ls_halvings", ctypes.c_int32), ("bonds_broken", ctypes.c_int32),
                 ("contact_candidates", ctypes.c_int32), ("status", ctypes.c_int32), ("reserved0", ctypes.c_int32),
-                ("g0_norm", ctypes.c_double), ("g_norm", ctypes.c_double)]
+                ("g0_norm", ctypes.c_double), ("g_norm", ctypes.c_double),
+                ("contact_entry_pcg_iters", ctypes.c_int64), ("intact_bonds", ctypes.c_int64)]
 
 
 PHASES = ["predict", "contact", "grad", "hess", "pcg", "linesearch", "finish"]
@@ -74,8 +76,12 @@ _PROTOS = {
     "bdem_debug_system": (ctypes.c_int, [_vp, _dp, _dp, _dp, _dp, _dp, _lp]),
     "bdem_debug_matvec": (ctypes.c_int, [_vp, _dp, _dp]),
     "bdem_debug_bonds": (ctypes.c_int, [_vp, ctypes.c_int64, _ip, _dp]),
+    "bdem_debug_bond_stress": (ctypes.c_int, [_vp, _dp]),
     "bdem_debug_pcg": (ctypes.c_int, [_vp, _dp, ctypes.c_double, ctypes.c_int32, _dp, _ip]),
     "bdem_launch_count": (ctypes.c_int64, [_vp]),
+    "bdem_set_step_graph": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "bdem_graph_steps": (ctypes.c_int64, [_vp]),
+    "bdem_graph_error": (ctypes.c_char_p, [_vp]),
     "bdem_pcg_static": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int32, _ip]),
     "bdem_set_pcg_shape": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
     "bdem_autotune_pcg": (ctypes.c_int, [_vp, ctypes.c_int32, _ip, _ip]),
@@ -155,7 +161,8 @@ def bdem_create(config: bdem_config, scene_offsets, pos, quat, vel, quat_vel, ra
     kin = None if kinematic is None else _arr(kinematic, np.uint8, (n,))
     M = (bdem_material * len(mats))()
     for k, m in enumerate(mats):
-        M[k] = bdem_material(m.E, m.nu, m.density, m.break_strain, m.bend_twist_scale, m.shear_scale)
+        M[k] = bdem_material(m.E, m.nu, m.density, m.break_strain, m.bend_twist_scale, m.shear_scale,
+                             getattr(m, "tensile_strength", math.inf), getattr(m, "shear_strength", math.inf))
     h = _vp()
     st = L.bdem_create(ctypes.byref(config), len(so) - 1, _ptr(so, _lp), _ptr(pos, _dp), _ptr(quat, _dp),
                        _ptr(vel, _dp), _ptr(quat_vel, _dp), _ptr(radius, _dp), _ptr(pm, _ip), M, len(mats),
@@ -251,6 +258,13 @@ class Sim:
         self._check(self.L.bdem_debug_bonds(self.h, ids.size, _ptr(ids, _ip), _ptr(out, _dp)))
         return out[:ids.size]
 
+    def bdem_debug_bond_stress(self):
+        """(sigma, tau) of every bond at the committed state, [n_bonds][2] in the order of addition."""
+        nb = self.sizes()[1]
+        out = np.zeros((max(nb, 1), 2))
+        self._check(self.L.bdem_debug_bond_stress(self.h, _ptr(out, _dp)))
+        return out[:nb]
+
     def bdem_debug_matvec(self, x):
         x = _arr(x, np.float64, (self.n, 6))
         y = np.zeros((self.n, 6))
@@ -292,6 +306,15 @@ class Sim:
 
     def launch_count(self):
         return int(self.L.bdem_launch_count(self.h))
+
+    def set_step_graph(self, on=True):
+        self._check(self.L.bdem_set_step_graph(self.h, 1 if on else 0))
+
+    def graph_steps(self):
+        return int(self.L.bdem_graph_steps(self.h))
+
+    def graph_error(self):
+        return (self.L.bdem_graph_error(self.h) or b"").decode()
 
     def close(self):
         if getattr(self, "h", None):

@@ -50,6 +50,18 @@ struct bdem_sim {
   std::vector<Pending> pending;
   cudaEvent_t ev_open = nullptr;
   int ph_open = -1;
+  // captured step graph: one graph launch per step, the Newton and line-search loops run as conditional while
+  // nodes decided on the device
+  bool graph_enabled = true;
+  bool graph_failed = false;          // capture or instantiation was refused: steps use the host-driven loop
+  bool contacts_sized = false;        // a host-driven step has sized the contact arrays
+  std::string graph_err;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  DevArrays graph_d{};                // the arrays the graph was captured with (kernel arguments are by value)
+  cudaStream_t cap[3] = {nullptr, nullptr, nullptr};
+  int g_pre = 0, g_body = 0, g_ls = 0, g_post = 0;  // kernels per graph segment
+  int64_t graph_steps = 0;
 };
 
 static cudaEvent_t ev_get(bdem_sim* s) {
@@ -338,26 +350,35 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
   if (max_rows * (int64_t)sizeof(int4) + max_ent * (int64_t)sizeof(int2) > (int64_t)200 * 1024)
     return fail(s, BDEM_E_INVALID, "PCG grid of %d blocks leaves %lld rows in one block; use more blocks", grid,
                 (long long)max_rows);
-  int sc = 0;
-  for (int b = 0; b < grid; ++b) {
-    int64_t r0 = bounds[b], r1 = bounds[b + 1];
-    block_seg[b] = (int32_t)seg_scene.size();
-    int64_t r = r0;
-    while (r < r1) {
-      while (sc < s->n_scenes && s->offsets[sc + 1] <= r) ++sc;
-      int64_t e = std::min<int64_t>(r1, s->offsets[sc + 1]);
-      seg_row.push_back((int32_t)r);
-      seg_scene.push_back(sc);
-      r = e;
+  // cuts block row ranges at scene boundaries
+  auto cut = [&](const std::vector<int64_t>& bnd, std::vector<int32_t>& row, std::vector<int32_t>& scn,
+                 std::vector<int32_t>& blk) {
+    int sc = 0;
+    for (int b = 0; b < grid; ++b) {
+      int64_t r0 = bnd[b], r1 = bnd[b + 1];
+      blk[b] = (int32_t)scn.size();
+      int64_t r = r0;
+      while (r < r1) {
+        while (sc < s->n_scenes && s->offsets[sc + 1] <= r) ++sc;
+        int64_t e = std::min<int64_t>(r1, s->offsets[sc + 1]);
+        row.push_back((int32_t)r);
+        scn.push_back(sc);
+        r = e;
+      }
     }
-  }
-  block_seg[grid] = (int32_t)seg_scene.size();
-  seg_row.push_back((int32_t)n);
+    blk[grid] = (int32_t)scn.size();
+    row.push_back((int32_t)n);
+  };
+  cut(bounds, seg_row, seg_scene, block_seg);
+  std::vector<int64_t> ubounds(grid + 1);
+  for (int b = 0; b <= grid; ++b) ubounds[b] = n * b / grid;
+  std::vector<int32_t> useg_row, useg_scene, ublock_seg(grid + 1, 0);
+  cut(ubounds, useg_row, useg_scene, ublock_seg);
   for (int x = 0, k = 0; x <= s->n_scenes; ++x) {  // first segment of each scene (segments are in row order)
     while (k < (int)seg_scene.size() && seg_scene[k] < x) ++k;
     scene_seg[x] = k;
   }
-  void* olds[] = {d.seg_row, d.seg_scene, d.block_seg, d.scene_seg, d.part_s};
+  void* olds[] = {d.seg_row, d.seg_scene, d.block_seg, d.scene_seg, d.part_s, d.useg_row, d.useg_scene, d.ublock_seg};
   for (void* p : olds) dfree(s, p);
   size_t ns = std::max<size_t>(seg_scene.size(), 1);
   TRY(dalloc_t(s, &d.seg_row, seg_row.size()));
@@ -370,6 +391,14 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
     CUDA_TRY(s, cudaMemcpy(d.seg_scene, seg_scene.data(), sizeof(int32_t) * seg_scene.size(), cudaMemcpyHostToDevice));
   CUDA_TRY(s, cudaMemcpy(d.block_seg, block_seg.data(), sizeof(int32_t) * block_seg.size(), cudaMemcpyHostToDevice));
   CUDA_TRY(s, cudaMemcpy(d.scene_seg, scene_seg.data(), sizeof(int32_t) * scene_seg.size(), cudaMemcpyHostToDevice));
+  TRY(dalloc_t(s, &d.useg_row, useg_row.size()));
+  TRY(dalloc_t(s, &d.useg_scene, std::max<size_t>(useg_scene.size(), 1)));
+  TRY(dalloc_t(s, &d.ublock_seg, ublock_seg.size()));
+  CUDA_TRY(s, cudaMemcpy(d.useg_row, useg_row.data(), sizeof(int32_t) * useg_row.size(), cudaMemcpyHostToDevice));
+  if (!useg_scene.empty())
+    CUDA_TRY(s, cudaMemcpy(d.useg_scene, useg_scene.data(), sizeof(int32_t) * useg_scene.size(),
+                           cudaMemcpyHostToDevice));
+  CUDA_TRY(s, cudaMemcpy(d.ublock_seg, ublock_seg.data(), sizeof(int32_t) * ublock_seg.size(), cudaMemcpyHostToDevice));
   d.n_seg = (int32_t)seg_scene.size();
   d.pcg_grid = n > 0 ? grid : 0;
   d.pcg_lanes = lanes;
@@ -424,6 +453,7 @@ extern "C" bdem_status bdem_create(const bdem_config* config, int32_t n_scenes, 
     const bdem_material& M = mats[m];
     if (!(M.E > 0.0) || !fin(M.E) || !(M.nu > -1.0 && M.nu < 0.5) || !(M.density > 0.0) || !fin(M.density) ||
         !(M.break_strain > 0.0) || !(M.bend_twist_scale >= 0.0) || !fin(M.bend_twist_scale) ||
+        !(M.tensile_strength > 0.0) || !(M.shear_strength > 0.0) ||
         !(M.shear_scale >= 0.0) || !fin(M.shear_scale))
       return fail(nullptr, BDEM_E_INVALID, "material %d is invalid", m);
   }
@@ -606,6 +636,9 @@ extern "C" bdem_status bdem_add_bonds(bdem_sim* s, int64_t n, const int32_t* I, 
   std::vector<int2> bij(nb);
   std::vector<double4> rest(nb), stiff(nb);
   std::vector<double> brk(nb);
+  std::vector<double4> sgeo(nb);
+  std::vector<double2> sstr(nb);
+  int stress_on = 0;
   std::vector<uint8_t> broken(nb, 0);
   std::vector<int32_t> bscene(nb), bi(nb), bj(nb), bm(nb), e2i(nb), i2e(nb);
   for (int64_t k = 0; k < nb; ++k) {
@@ -619,6 +652,13 @@ extern "C" bdem_status bdem_add_bonds(bdem_sim* s, int64_t n, const int32_t* I, 
     bscene[k] = s->pscene[e.a];
     const bdem_material& mt = s->mats[e.m];
     brk[k] = mt.break_strain;
+    {  // stress criterion: cross-section of the bond (r0 = (r_i + r_j)/2) and strengths
+      double r0 = 0.5 * (s->radius[e.a] + s->radius[e.b]);
+      double S = M_PI * r0 * r0, Ia = M_PI * r0 * r0 * r0 * r0 / 4.0, Ja = M_PI * r0 * r0 * r0 * r0 / 2.0;
+      sgeo[k] = make_double4(1.0 / S, r0 / Ia, r0 / Ja, 0.0);
+      sstr[k] = make_double2(mt.tensile_strength, mt.shear_strength);
+      if (fin(mt.tensile_strength) || fin(mt.shear_strength)) stress_on = 1;
+    }
     if (e.old >= 0) {
       rest[k] = s->rest[e.old];
       stiff[k] = s->stiff[e.old];
@@ -680,7 +720,7 @@ extern "C" bdem_status bdem_add_bonds(bdem_sim* s, int64_t n, const int32_t* I, 
   }
   // replace the device bond arrays
   DevArrays& d = s->d;
-  void* olds[] = {d.bij, d.brest, d.bstiff, d.bbrk, d.bbroken, d.bscene, d.bg, d.bM, d.bE, d.inc2, d.inc_start, d.bond_ext2int, d.bond_int2ext, s->flag_stage,
+  void* olds[] = {d.bij, d.brest, d.bstiff, d.bbrk, d.bsgeo, d.bsstr, d.bbroken, d.bscene, d.bg, d.bM, d.bE, d.inc2, d.inc_start, d.bond_ext2int, d.bond_int2ext, s->flag_stage,
                   d.btile_start, d.btile_scene, d.btile_begin, d.part_b};
   for (void* p : olds) dfree(s, p);
   size_t w = wsize(s);
@@ -688,6 +728,8 @@ extern "C" bdem_status bdem_add_bonds(bdem_sim* s, int64_t n, const int32_t* I, 
   TRY(dalloc_t(s, &d.brest, nb));
   TRY(dalloc_t(s, &d.bstiff, nb));
   TRY(dalloc_t(s, &d.bbrk, nb));
+  TRY(dalloc_t(s, &d.bsgeo, nb));
+  TRY(dalloc_t(s, &d.bsstr, nb));
   TRY(dalloc_t(s, &d.bbroken, nb));
   TRY(dalloc_t(s, &d.bscene, nb));
   TRY(dalloc_t(s, &d.bg, 9 * (size_t)nb));
@@ -706,6 +748,9 @@ extern "C" bdem_status bdem_add_bonds(bdem_sim* s, int64_t n, const int32_t* I, 
   CUDA_TRY(s, cudaMemcpy(d.brest, rest.data(), sizeof(double4) * nb, cudaMemcpyHostToDevice));
   CUDA_TRY(s, cudaMemcpy(d.bstiff, stiff.data(), sizeof(double4) * nb, cudaMemcpyHostToDevice));
   CUDA_TRY(s, cudaMemcpy(d.bbrk, brk.data(), sizeof(double) * nb, cudaMemcpyHostToDevice));
+  CUDA_TRY(s, cudaMemcpy(d.bsgeo, sgeo.data(), sizeof(double4) * nb, cudaMemcpyHostToDevice));
+  CUDA_TRY(s, cudaMemcpy(d.bsstr, sstr.data(), sizeof(double2) * nb, cudaMemcpyHostToDevice));
+  d.stress_on = stress_on;
   CUDA_TRY(s, cudaMemcpy(d.bbroken, broken.data(), nb, cudaMemcpyHostToDevice));
   CUDA_TRY(s, cudaMemcpy(d.bscene, bscene.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice));
   CUDA_TRY(s, cudaMemcpy(d.inc2, inc.data(), sizeof(int2) * 2 * nb, cudaMemcpyHostToDevice));
@@ -803,7 +848,7 @@ static bdem_status do_step(bdem_sim* s, std::vector<SceneCtl>& ctl) {
     phase_begin(s, BDEM_PH_GRAD);
     TRY(check_launch(s, launch_bond_grad(d, 0, st)));
     TRY(check_launch(s, launch_particle_grad(d, 1, 0, st)));
-    TRY(check_launch(s, launch_scene_reduce(d, RED_GRAD, k, st)));
+    TRY(check_launch(s, launch_scene_reduce(d, RED_GRAD, 0, st)));
     phase_end(s);
     TRY(read_counters(s, &c));
     if (c.nonfinite) {
@@ -822,11 +867,11 @@ static bdem_status do_step(bdem_sim* s, std::vector<SceneCtl>& ctl) {
     phase_end(s);
     phase_begin(s, BDEM_PH_LINESEARCH);
     TRY(check_launch(s, launch_gdx(d, st)));
-    TRY(check_launch(s, launch_scene_reduce(d, RED_GDX, k, st)));
+    TRY(check_launch(s, launch_scene_reduce(d, RED_GDX, 0, st)));
     for (int h = 0; h <= d.ls_max + 1; ++h) {
       TRY(check_launch(s, launch_ls_trial(d, st)));
       TRY(check_launch(s, launch_ls_energy(d, st)));
-      TRY(check_launch(s, launch_scene_reduce(d, RED_LS, k, st)));
+      TRY(check_launch(s, launch_scene_reduce(d, RED_LS, 0, st)));
       phase_end(s);
       TRY(read_counters(s, &c));
       if (c.n_pending == 0) break;
@@ -853,6 +898,172 @@ static bdem_status do_step(bdem_sim* s, std::vector<SceneCtl>& ctl) {
   return BDEM_OK;
 }
 
+// ---- the step as one CUDA graph -------------------------------------------------------------------------------
+// predict -> contacts (+ capacity guard) -> gradient -> WHILE(Newton active) { Hessian -> PCG -> descent check ->
+// WHILE(line search pending) { trial -> energy difference -> decision } -> commit -> gradient } -> finish.
+// The reductions that close each loop body set the loop's condition on the device (k_scene_reduce), with the same
+// decisions and caps as the host-driven loop of do_step, so both run the same kernels on the same data.
+
+static void destroy_step_graph(bdem_sim* s) {
+  if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
+  if (s->graph) cudaGraphDestroy(s->graph);
+  s->graph_exec = nullptr;
+  s->graph = nullptr;
+}
+
+// appends a conditional WHILE node after the capture's current frontier and returns its body graph
+static cudaError_t capture_while(cudaStream_t st, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edges = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &edges, &nd);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};  // the remaining members zero-initialised
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  e = cudaGraphAddNode(&node, g, deps, edges, nd, &p);
+  if (e != cudaSuccess) return e;
+  *body = p.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+static bool build_step_graph(bdem_sim* s) {
+  destroy_step_graph(s);
+  const DevArrays& d = s->d;
+  for (auto& c : s->cap)
+    if (!c && cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking) != cudaSuccess) {
+      s->graph_err = "cudaStreamCreateWithFlags failed";
+      return false;
+    }
+  cudaGraph_t G = nullptr, bodyN = nullptr, bodyL = nullptr;
+  cudaGraphConditionalHandle hN = 0, hL = 0;
+  cudaError_t e = cudaSuccess, pe = cudaSuccess;
+  int pre = 0, body = 0, ls = 0, post = 0;
+  const char* where = "";
+#define G_TRY(what, call)        \
+  do {                           \
+    if (e == cudaSuccess) {      \
+      e = (call);                \
+      if (e != cudaSuccess) where = what; \
+    }                            \
+  } while (0)
+  G_TRY("cudaGraphCreate", cudaGraphCreate(&G, 0));
+  G_TRY("cudaGraphConditionalHandleCreate", cudaGraphConditionalHandleCreate(&hN, G, 0, cudaGraphCondAssignDefault));
+  // top level
+  G_TRY("begin capture", cudaStreamBeginCaptureToGraph(s->cap[0], G, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  if (e == cudaSuccess) {
+    cudaStream_t st = s->cap[0];
+    pre += launch_predict(d, st);
+    if (d.k_self > 0.0) {
+      pre += launch_contacts(d, 0, st);
+      pre += launch_contacts(d, 1, st);
+      pre += launch_contacts(d, 2, st);
+    } else {
+      cudaMemsetAsync(d.c_start, 0, sizeof(int32_t) * (d.n + 1), st);
+    }
+    pre += launch_scene_reduce(d, RED_CAND, 0, st);
+    pre += launch_bond_grad(d, 0, st);
+    pre += launch_particle_grad(d, 1, 0, st);
+    pre += launch_scene_reduce(d, RED_GRAD, hN, st);
+    G_TRY("top-level launches", cudaGetLastError());
+    G_TRY("Newton while node", capture_while(st, hN, &bodyN));
+    post += launch_finish(d, st);
+    G_TRY("finish launches", cudaGetLastError());
+    cudaGraph_t out = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(st, &out);
+    if (e == cudaSuccess && e2 != cudaSuccess) { e = e2; where = "end capture"; }
+  }
+  G_TRY("line-search handle", cudaGraphConditionalHandleCreate(&hL, bodyN, 0, 0));
+  // Newton body
+  G_TRY("begin body capture", cudaStreamBeginCaptureToGraph(s->cap[1], bodyN, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  if (e == cudaSuccess) {
+    cudaStream_t st = s->cap[1];
+    body += launch_bond_hess(d, 0, st);
+    body += launch_particle_hess(d, 1, 0, st);
+    body += launch_pcg(d, 1, 1, st, &pe);
+    body += launch_gdx(d, st);
+    body += launch_scene_reduce(d, RED_GDX, hL, st);
+    G_TRY("PCG launch", pe);
+    G_TRY("Newton body launches", cudaGetLastError());
+    G_TRY("line-search while node", capture_while(st, hL, &bodyL));
+    body += launch_ls_commit(d, st);
+    body += launch_bond_grad(d, 0, st);
+    body += launch_particle_grad(d, 1, 0, st);
+    body += launch_scene_reduce(d, RED_GRAD, hN, st);
+    G_TRY("Newton body launches", cudaGetLastError());
+    cudaGraph_t out = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(st, &out);
+    if (e == cudaSuccess && e2 != cudaSuccess) { e = e2; where = "end body capture"; }
+  }
+  // line-search body
+  G_TRY("begin line-search capture", cudaStreamBeginCaptureToGraph(s->cap[2], bodyL, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  if (e == cudaSuccess) {
+    cudaStream_t st = s->cap[2];
+    ls += launch_ls_trial(d, st);
+    ls += launch_ls_energy(d, st);
+    ls += launch_scene_reduce(d, RED_LS, hL, st);
+    G_TRY("line-search launches", cudaGetLastError());
+    cudaGraph_t out = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(st, &out);
+    if (e == cudaSuccess && e2 != cudaSuccess) { e = e2; where = "end line-search capture"; }
+  }
+  G_TRY("cudaGraphInstantiate", cudaGraphInstantiate(&s->graph_exec, G, 0));
+#undef G_TRY
+  s->graph = G;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    destroy_step_graph(s);
+    s->graph_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return false;
+  }
+  s->graph_d = d;
+  s->g_pre = pre;
+  s->g_body = body;
+  s->g_ls = ls;
+  s->g_post = post;
+  return true;
+}
+
+// one step through the graph; *redo when the contact arrays were too small (the step was not committed)
+static bdem_status graph_step(bdem_sim* s, std::vector<SceneCtl>& ctl, bool* redo) {
+  *redo = false;
+  DevArrays& d = s->d;
+  CUDA_TRY(s, cudaGraphLaunch(s->graph_exec, s->stream));
+  Counters c{};
+  ctl.resize(s->n_scenes);
+  CUDA_TRY(s, cudaMemcpyAsync(&c, d.cnt, sizeof c, cudaMemcpyDeviceToHost, s->stream));
+  CUDA_TRY(s, cudaMemcpyAsync(ctl.data(), d.sc, sizeof(SceneCtl) * s->n_scenes, cudaMemcpyDeviceToHost, s->stream));
+  TRY(sync(s));
+  s->launches += s->g_pre + (int64_t)std::max(0, c.loops_newton - 1) * s->g_body + (int64_t)c.ls_total * s->g_ls +
+                 s->g_post;
+  if (c.timeout || c.nonfinite || c.overflow || c.runaway) {
+    Counters z{};
+    z.sync_gen = c.sync_gen;
+    CUDA_TRY(s, cudaMemcpy(d.cnt, &z, sizeof z, cudaMemcpyHostToDevice));
+    if (c.timeout) return fail(s, BDEM_E_TIMEOUT, "a device-side wait gave up; the step was rolled back");
+    if (c.nonfinite)
+      return fail(s, BDEM_E_NONFINITE, "the Newton residual became non-finite; the step was rolled back");
+    if (c.runaway) return fail(s, BDEM_E_CUDA, "Newton loop did not terminate");
+    *redo = true;  // contact arrays too small: the host-driven step grows them
+    return BDEM_OK;
+  }
+  s->graph_steps += 1;
+  return BDEM_OK;
+}
+
+static bool graph_usable(bdem_sim* s) {
+  if (!s->graph_enabled || s->graph_failed || s->prof_on || s->d.n == 0 || !s->contacts_sized) return false;
+  if (s->graph_exec && memcmp(&s->graph_d, &s->d, sizeof(DevArrays)) == 0) return true;
+  if (build_step_graph(s)) return true;
+  s->graph_failed = true;
+  return false;
+}
+
 extern "C" bdem_status bdem_step(bdem_sim* s, int32_t n_steps, bdem_step_stats* stats) {
   if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
   if (n_steps < 0) return fail(s, BDEM_E_INVALID, "n_steps must be >= 0");
@@ -861,8 +1072,16 @@ extern "C" bdem_status bdem_step(bdem_sim* s, int32_t n_steps, bdem_step_stats* 
   int worst = BDEM_OK;
   std::vector<SceneCtl> ctl;
   for (int t = 0; t < n_steps; ++t) {
-    bdem_status st = do_step(s, ctl);
-    if (st != BDEM_OK) return st;
+    bool redo = true;
+    if (graph_usable(s)) {
+      bdem_status st = graph_step(s, ctl, &redo);
+      if (st != BDEM_OK) return st;
+    }
+    if (redo) {
+      bdem_status st = do_step(s, ctl);
+      if (st != BDEM_OK) return st;
+      s->contacts_sized = true;
+    }
     for (int sc = 0; sc < s->n_scenes; ++sc) {
       const SceneCtl& c = ctl[sc];
       worst = std::max(worst, (int)c.status);
@@ -877,6 +1096,8 @@ extern "C" bdem_status bdem_step(bdem_sim* s, int32_t n_steps, bdem_step_stats* 
       o.status = std::max(o.status, c.status);
       o.g0_norm = c.g0;
       o.g_norm = c.gnorm;
+      o.contact_entry_pcg_iters += c.act_pcg;
+      o.intact_bonds = c.intact;
     }
   }
   if (worst == BDEM_E_NEWTON_MAXITER) fail(s, BDEM_E_NEWTON_MAXITER, "a scene reached newton_max_iter");
@@ -969,10 +1190,26 @@ extern "C" bdem_status bdem_bond_order(const bdem_sim* s, int32_t* pairs) {
   return BDEM_OK;
 }
 
+extern "C" bdem_status bdem_set_step_graph(bdem_sim* s, int32_t on) {
+  if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
+  s->graph_enabled = on != 0;
+  s->graph_failed = false;
+  s->graph_err.clear();
+  if (!s->graph_enabled) destroy_step_graph(s);
+  return BDEM_OK;
+}
+
+extern "C" int64_t bdem_graph_steps(const bdem_sim* s) { return s ? s->graph_steps : 0; }
+
+extern "C" const char* bdem_graph_error(const bdem_sim* s) { return s ? s->graph_err.c_str() : ""; }
+
 extern "C" void bdem_destroy(bdem_sim* s) {
   if (!s) return;
   cudaStreamSynchronize(s->stream);
   phase_collect(s);
+  destroy_step_graph(s);
+  for (cudaStream_t c : s->cap)
+    if (c) cudaStreamDestroy(c);
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
   for (void* p : s->allocs) cudaFree(p);
   s->allocs.clear();
@@ -1061,6 +1298,17 @@ extern "C" bdem_status bdem_debug_bonds(bdem_sim* s, int64_t count, const int32_
   CUDA_TRY(s, cudaMemcpyAsync(dids, ids, sizeof(int32_t) * count, cudaMemcpyHostToDevice, st));
   TRY(check_launch(s, launch_unpack_bond_hess(s->d, s->dbg_buf, dids, (int)count, st)));
   CUDA_TRY(s, cudaMemcpyAsync(out, s->dbg_buf, sizeof(double) * 144 * count, cudaMemcpyDeviceToHost, st));
+  return sync(s);
+}
+
+extern "C" bdem_status bdem_debug_bond_stress(bdem_sim* s, double* out) {
+  if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
+  if (s->nb && !out) return fail(s, BDEM_E_INVALID, "out is NULL");
+  if (s->nb == 0) return BDEM_OK;
+  cudaStream_t st = s->stream;
+  TRY(dbg_reserve(s, 2 * (size_t)s->nb));
+  TRY(check_launch(s, launch_bond_stress(s->d, s->dbg_buf, st)));
+  CUDA_TRY(s, cudaMemcpyAsync(out, s->dbg_buf, sizeof(double) * 2 * s->nb, cudaMemcpyDeviceToHost, st));
   return sync(s);
 }
 

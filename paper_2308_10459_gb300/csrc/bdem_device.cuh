@@ -223,6 +223,22 @@ __device__ __forceinline__ void bond_first_order(const BondParams& b, V3<double>
   E.g[6] = gyj.x; E.g[7] = gyj.y; E.g[8] = gyj.z;
 }
 
+// stresses of the stress fracture criterion (Sec. 3.2, Fracture Criteria) from the implicit potentials:
+// |F_n| = |grad_p V_stretch| = kn |l - l0|; |F_s| = |grad_p V_shear| = |1/2 kt f'(c)| |grad_d c|; the bend-twist
+// moment kappa = K r split into its twist part along the bond axis d0 and its bending part;
+// sigma = |F_n| / S + |M_b| r0 / I, tau = |F_s| / S + |M_t| r0 / J with geo = (1/S, r0/I, r0/J)
+__device__ __forceinline__ void bond_stress(const BondParams& b, double4 geo, V3<double> pi, Q4<double> qi,
+                                            V3<double> pj, Q4<double> qj, double& sigma, double& tau) {
+  BondEval E;
+  bond_first_order(b, pi, qi, pj, qj, E);
+  double fn = fabs(b.kn * E.elong);
+  double fs = fabs(0.5 * b.kt * E.fa.f1) * sqrt(dot(E.cd, E.cd));
+  double mt = dot(b.d0, E.kappa);
+  V3<double> mb = E.kappa - mt * b.d0;
+  sigma = fn * geo.x + sqrt(dot(mb, mb)) * geo.y;
+  tau = fs * geo.x + fabs(mt) * geo.z;
+}
+
 // ------------------------------------------------------------------------------------------------
 // Hessian in the 9 variables (d, y_i, y_j), packed symmetric, precision T
 // ------------------------------------------------------------------------------------------------

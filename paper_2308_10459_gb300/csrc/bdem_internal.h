@@ -10,6 +10,7 @@
 //             PCG vectors [N][6] T (x, r, z, p, q)
 //   bonds, sorted by (i, j) with i < j (so each scene's bonds are contiguous):
 //             bij int2; brest double4 (d0, l0); bstiff double4 (kn, kt s^2, kb, ktw); bbrk double; bbroken u8;
+//             bsgeo double4 (1/S, r0/I, r0/J, 0) and bsstr double2 (sigma_c, tau_c) of the stress criterion;
 //             bg [B][9] FP64 gradient in (d = p_j - p_i, y_i, y_j);
 //             bM [B][36] T: the (i, j) off-diagonal 6x6 block in factored form (1/2 A sym6 | B/sqrt2 3x3 |
 //             C/sqrt2 3x3 | F 3x3 | 3 pad) of the clamped 9x9 Hessian in (u = (dp_j - dp_i)/sqrt2, y_i, y_j);
@@ -20,9 +21,11 @@
 //             of each particle's range: c_anbr [C], c_blk [C] T4 (n, k) of the clamped contact Hessian k n n^T,
 //             c_act [N] counts
 //   tiles: particle tiles of <= 256 rows inside one scene, bond tiles of <= 256 bonds inside one scene
-//   PCG segments: the persistent PCG grid gives block b the balanced row range [b N / P, (b+1) N / P); its
-//             intersections with the scenes are the segments (seg_row [nseg+1], seg_scene, block_seg [P+1],
-//             scene_seg [S+1]); one partial per segment and quantity (part_s [nseg][4])
+//   PCG segments: the persistent PCG grid gives block b a row range of the product balanced by rows + incidence
+//             entries; its intersections with the scenes are the segments (seg_row [nseg+1], seg_scene,
+//             block_seg [P+1], scene_seg [S+1]); one partial per segment and quantity (part_s [nseg][4]). The
+//             elementwise phases use the equal-rows ranges [b N / P, (b+1) N / P) cut the same way at scene
+//             boundaries (useg_row, useg_scene, ublock_seg)
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -37,6 +40,9 @@ struct SceneCtl {
   double g0, gnorm, eps_r, bnorm;
   double rz, pq, alpha, beta;
   double dphi, ls_alpha, gdx, pad0;
+  long long act_cur;            // active self-contact matrix entries of the current Newton system
+  long long act_pcg;            // sum over this step's solves of act_cur x PCG iterations
+  long long intact;             // intact bonds after the step's fracture test
   int32_t newton_active;        // still iterating Newton in this step
   int32_t pcg_active;
   int32_t pcg_iters;            // in the current solve
@@ -57,7 +63,12 @@ struct Counters {               // small device-side summary read by the host af
   int32_t nonfinite;
   unsigned int sync_count;      // grid barrier arrival counter
   unsigned int sync_gen;        // grid barrier generation
-  int32_t pad[2];
+  int32_t overflow;             // graph path: contact candidates needed when the contact arrays were too small
+  int32_t runaway;              // graph path: a device-driven loop passed its iteration cap
+  int32_t loops_newton;         // gradient reductions in this step (device-driven Newton loop trips + 1)
+  int32_t loops_ls;             // trials of the current line search
+  int32_t ls_total;             // line-search trials in this step
+  int32_t pad;
 };
 
 struct DevArrays {
@@ -66,7 +77,8 @@ struct DevArrays {
   int32_t c_cap;                // capacity of the contact arrays
   int32_t hash_size;            // power of two
   double dt, gx, gy, gz, tol, ground_z, k_ground, k_self, skin, cell_h;
-  int32_t newton_max, pcg_max, ls_max, pad0;
+  int32_t newton_max, pcg_max, ls_max;
+  int32_t stress_on;            // some bond has a finite tensile or shear strength
   // particles
   double4 *xp, *xq, *x0p, *x0q, *vp, *vq, *hp, *hq, *tp, *tq;
   double2* coef;
@@ -80,6 +92,8 @@ struct DevArrays {
   int2* bij;
   double4 *brest, *bstiff;
   double* bbrk;
+  double4* bsgeo;               // (1/S, r0/I, r0/J, 0) of the stress criterion
+  double2* bsstr;               // (sigma_c, tau_c); +inf: off
   uint8_t* bbroken;
   int32_t* bscene;
   int32_t *bond_ext2int, *bond_int2ext;  // caller bond order (order of addition) <-> stored order
@@ -99,6 +113,7 @@ struct DevArrays {
   int32_t n_seg, pcg_grid, pcg_lanes, pcg_max_rows;  // pcg_max_rows: most rows of one PCG block
   int32_t pcg_max_entries, pad2;                     // most incidence entries of one PCG block's rows
   int32_t *seg_row, *seg_scene, *block_seg, *scene_seg;
+  int32_t *useg_row, *useg_scene, *ublock_seg;      // equal-rows partition of the elementwise PCG phases
   double* part_s;               // [n_seg][kPartials]
   SceneCtl* sc;
   Counters* cnt;
@@ -106,7 +121,9 @@ struct DevArrays {
 
 // ---- launchers (bdem_kernels.cu); each returns the number of kernels launched -----------------------------------
 int launch_predict(const DevArrays& d, cudaStream_t s);
-int launch_contacts(const DevArrays& d, int stage, cudaStream_t s);  // stage 0: hash+count, 1: fill
+// stage 0: hash + count, 1: fill, 2: capacity guard of the graph path (records the overflow and empties every
+// candidate list, so that no later kernel reads past the contact arrays)
+int launch_contacts(const DevArrays& d, int stage, cudaStream_t s);
 int launch_scan_counts(const DevArrays& d, const int32_t* counts, int32_t* starts, int n, cudaStream_t s);
 int launch_bond_grad(const DevArrays& d, int all_scenes, cudaStream_t s);
 int launch_particle_grad(const DevArrays& d, int mask_kin, int all_scenes, cudaStream_t s);
@@ -114,7 +131,9 @@ int launch_bond_hess(const DevArrays& d, int all_scenes, cudaStream_t s);
 int launch_particle_hess(const DevArrays& d, int mask_kin, int all_scenes, cudaStream_t s);
 // reduction modes of the per-scene reduce kernel
 enum ReduceMode { RED_GRAD = 0, RED_GDX = 1, RED_LS = 2, RED_FORCE_ACTIVE = 3, RED_CAND = 4 };
-int launch_scene_reduce(const DevArrays& d, int mode, int k_iter, cudaStream_t s);
+// cond: 0, or the conditional handle of the device-driven loop that this reduction controls in the step graph
+// (RED_GRAD: the Newton loop, RED_GDX and RED_LS: the line-search loop)
+int launch_scene_reduce(const DevArrays& d, int mode, unsigned long long cond, cudaStream_t s);
 // PCG: rhs_from_g = 1 uses b = -g; else b is read from vr (already T) and eps from sc.eps_r
 int launch_pcg(const DevArrays& d, int rhs_from_g, int mask_kin, cudaStream_t s, cudaError_t* err);
 int pcg_max_blocks(int mixed, int lanes, size_t smem);
@@ -127,6 +146,7 @@ int launch_finish(const DevArrays& d, cudaStream_t s);
 int launch_matvec(const DevArrays& d, int mask_kin, cudaStream_t s);  // vq_ = H vp_
 int launch_unpack_bond_hess(const DevArrays& d, double* out, const int32_t* ids, int count, cudaStream_t s);
 int launch_unpack_diag(const DevArrays& d, double* out /*device [n][36]*/, cudaStream_t s);
+int launch_bond_stress(const DevArrays& d, double* out /*device [nb][2], caller bond order*/, cudaStream_t s);
 // transfers in the caller's particle order (any pointer may be NULL): committed state <-> [n][3] / [n][4] arrays
 int launch_pack_state(const DevArrays& d, double* pos3, double* quat4, double* vel3, double* qvel4, cudaStream_t s);
 int launch_unpack_state(const DevArrays& d, const double* pos3, const double* quat4, const double* vel3,

@@ -136,10 +136,22 @@ struct DotAcc<double> {
 
 __global__ void k_step_init(DevArrays d) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s == 0) {
+    d.cnt->loops_newton = 0;
+    d.cnt->loops_ls = 0;
+    d.cnt->ls_total = 0;
+  }
   if (s >= d.n_scenes) return;
   SceneCtl c = {};
   c.newton_active = 1;
   d.sc[s] = c;
+}
+
+// a step that must not be committed: a device wait gave up, the residual became non-finite, the contact arrays
+// were too small (graph path) or a device-driven loop passed its cap
+__device__ __forceinline__ bool step_aborted(const DevArrays& d) {
+  const Counters* c = d.cnt;
+  return c->timeout || c->nonfinite || c->overflow || c->runaway;
 }
 
 // xhat = x_n + dt v_n; the initial guess x_0 = (phat, qhat/|qhat|) (Alg. 3; qhat itself stays unnormalised)
@@ -245,6 +257,19 @@ __global__ void k_contact_scan(DevArrays d) {
         }
       }
   if (!FILL) d.cnt_tmp[i] = count;
+}
+
+// capacity guard of the graph path: the host sizes the contact arrays between steps, a captured step cannot, so
+// a step whose candidates do not fit records the count it needs and runs with empty candidate lists (it is not
+// committed and the host repeats it after growing the arrays)
+__global__ void k_contact_check(DevArrays d) {
+  int need = d.c_start[d.n];
+  d.cnt->overflow = (need < 0) ? 0x7fffffff : (need > d.c_cap ? need : 0);
+}
+__global__ void k_contact_clear(DevArrays d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > d.n) return;
+  if (d.cnt->overflow) d.c_start[i] = 0;
 }
 
 // ---- exclusive scan of int32 counts (n) into starts (n+1) --------------------------------------------------------
@@ -516,6 +541,12 @@ __global__ void __launch_bounds__(kTile) k_particle_hess(DevArrays d, int mask, 
     }
   }
   d.c_act[i] = nact;
+  if (d.k_self > 0.0) {  // per-scene count of the active entries (each tile lies inside one scene)
+    unsigned m = __activemask();
+    int wsum = __reduce_add_sync(m, nact);
+    if ((threadIdx.x & 31) == __ffs(m) - 1 && wsum)
+      atomicAdd(reinterpret_cast<unsigned long long*>(&d.sc[s].act_cur), (unsigned long long)wsum);
+  }
   if (mask && d.kin[i]) {
 #pragma unroll
     for (int a = 0; a < 6; ++a)
@@ -690,15 +721,63 @@ __device__ __forceinline__ double scene_partial(const DevArrays& d, int s, int k
   return warp_sum(v);
 }
 
-// per-scene decision after the fused product (run by the last block to reach the barrier): one warp per scene,
-// lanes stride over the scene's segments in order
+// the PCG decision of one scene from its reduced dots (run by a single thread): convergence test, then the
+// Chronopoulos-Gear step lengths; returns whether the scene keeps iterating
+__device__ bool pcg_decide_scene(const DevArrays& d, SceneCtl* c, double gam, double del, double rho, int k_iter) {
+  // every field the decision reads, loaded together from L2 (other blocks wrote them since this SM last cached them)
+  int newton_active = __ldcg(&c->newton_active), pcg_active = __ldcg(&c->pcg_active), it = __ldcg(&c->pcg_iters);
+  double eps_r = __ldcg(&c->eps_r), bnorm = __ldcg(&c->bnorm), rz = __ldcg(&c->rz), alpha = __ldcg(&c->alpha);
+  if (!newton_active) return false;
+  if (k_iter == 0) {
+    bnorm = sqrt(rho);
+    it = 0;
+    pcg_active = 1;
+    c->bnorm = bnorm;
+    c->pcg_iters = 0;
+    c->pcg_active = 1;
+  }
+  if (!pcg_active) return false;
+  bool stop = !(sqrt(rho) > eps_r * bnorm) || it >= d.pcg_max;
+  if (!stop) {
+    double beta = (it == 0) ? 0.0 : gam / rz;
+    double den = (it == 0) ? del : del - beta * gam / alpha;
+    if (!(den > 0.0) || !(gam > 0.0)) {
+      stop = true;  // breakdown: no further decrease along this Krylov space
+    } else {
+      c->beta = beta;
+      c->alpha = gam / den;
+      c->rz = gam;
+      c->pq = den;
+      c->pcg_iters = it + 1;
+    }
+  }
+  if (stop) c->pcg_active = 0;
+  return !stop;
+}
+
+constexpr int kBlockScene = 64;  // scenes with more PCG segments than this are reduced by the whole block
+
+// per-scene decision after the fused product, run by the last block to reach the barrier. The partial dots of a
+// scene's segments are summed in a fixed order: by one warp (lanes stride over the segments) for a scene with at
+// most kBlockScene segments, by the whole block (threads stride, then warps in order) for a larger one, so that a
+// large scene costs one round of loads instead of a serial walk over its segments.
 __device__ void pcg_decide(const DevArrays& d, int k_iter) {
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   __shared__ int s_active[kTile / 32];
+  __shared__ double s_acc[3][kTile / 32];
+  __shared__ int s_big[kTile], s_nbig;
+  if (threadIdx.x == 0) s_nbig = 0;
+  __syncthreads();
   int active = 0;
   for (int s = warp; s < d.n_scenes; s += nw) {
-    volatile SceneCtl* c = d.sc + s;  // volatile: written by other blocks since this SM last cached it
     int a = d.scene_seg[s], b = d.scene_seg[s + 1];
+    if (b - a > kBlockScene) {
+      if (lane == 0) {
+        int k = atomicAdd(&s_nbig, 1);  // list order is irrelevant: each scene is reduced on its own
+        if (k < kTile) s_big[k] = s;
+      }
+      continue;
+    }
     double gam = 0.0, del = 0.0, rho = 0.0;
     for (int t = a + lane; t < b; t += 32) {
       gam += __ldcg(d.part_s + kPartials * t);
@@ -708,41 +787,50 @@ __device__ void pcg_decide(const DevArrays& d, int k_iter) {
     gam = warp_sum(gam);
     del = warp_sum(del);
     rho = warp_sum(rho);
-    if (lane != 0 || !c->newton_active) continue;
-    if (k_iter == 0) {
-      c->bnorm = sqrt(rho);
-      c->pcg_iters = 0;
-      c->pcg_active = 1;
-    }
-    if (!c->pcg_active) continue;
-    bool stop = !(sqrt(rho) > c->eps_r * c->bnorm) || c->pcg_iters >= d.pcg_max;
-    if (!stop) {
-      double beta = (c->pcg_iters == 0) ? 0.0 : gam / c->rz;
-      double den = (c->pcg_iters == 0) ? del : del - beta * gam / c->alpha;
-      if (!(den > 0.0) || !(gam > 0.0)) {
-        stop = true;  // breakdown: no further decrease along this Krylov space
-      } else {
-        c->beta = beta;
-        c->alpha = gam / den;
-        c->rz = gam;
-        c->pq = den;
-        c->pcg_iters += 1;
-      }
-    }
-    if (stop) c->pcg_active = 0;
-    else ++active;
+    if (lane == 0 && pcg_decide_scene(d, d.sc + s, gam, del, rho, k_iter)) ++active;
   }
   if (lane == 0) s_active[warp] = active;
   __syncthreads();
+  int nbig = s_nbig < kTile ? s_nbig : kTile;  // at most pcg_grid / kBlockScene + 1 scenes, far below kTile
+  int big_active = 0;
+  for (int k = 0; k < nbig; ++k) {
+    int s = s_big[k];
+    int a = d.scene_seg[s], b = d.scene_seg[s + 1];
+    double gam = 0.0, del = 0.0, rho = 0.0;
+    for (int t = a + threadIdx.x; t < b; t += blockDim.x) {
+      gam += __ldcg(d.part_s + kPartials * t);
+      del += __ldcg(d.part_s + kPartials * t + 1);
+      rho += __ldcg(d.part_s + kPartials * t + 2);
+    }
+    gam = warp_sum(gam);
+    del = warp_sum(del);
+    rho = warp_sum(rho);
+    if (lane == 0) {
+      s_acc[0][warp] = gam;
+      s_acc[1][warp] = del;
+      s_acc[2][warp] = rho;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double G = 0.0, D = 0.0, R = 0.0;
+      for (int w = 0; w < nw; ++w) {
+        G += s_acc[0][w];
+        D += s_acc[1][w];
+        R += s_acc[2][w];
+      }
+      if (pcg_decide_scene(d, d.sc + s, G, D, R, k_iter)) ++big_active;
+    }
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
-    int tot = 0;
+    int tot = big_active;
     for (int w = 0; w < nw; ++w) tot += s_active[w];
     d.cnt->n_active = tot;
   }
 }
 
 template <typename T, int G>
-__global__ void __launch_bounds__(kTile) k_pcg(DevArrays d, int rhs_from_g, int mask) {
+__global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays d, int rhs_from_g, int mask) {
   T* X = reinterpret_cast<T*>(d.vx);
   T* R = reinterpret_cast<T*>(d.vr);
   T* Z = reinterpret_cast<T*>(d.vz);
@@ -768,11 +856,14 @@ __global__ void __launch_bounds__(kTile) k_pcg(DevArrays d, int rhs_from_g, int 
   }
   for (int e = E0 + threadIdx.x; e < E1; e += blockDim.x) s_ent[e - E0] = d.inc2[e];
   __syncthreads();
+  // the elementwise phases (init and B) use the equal-rows partition: their cost is per row, while the product's
+  // partition balances rows against incidence entries
+  const int useg0 = d.ublock_seg[blockIdx.x], useg1 = d.ublock_seg[blockIdx.x + 1];
   // ---- init: x = p = s = 0, r = b, z = M^-1 r
-  for (int g = seg0; g < seg1; ++g) {
-    int sc = d.seg_scene[g];
+  for (int g = useg0; g < useg1; ++g) {
+    int sc = d.useg_scene[g];
     if (!d.sc[sc].newton_active) continue;
-    for (int i = d.seg_row[g] + threadIdx.x; i < d.seg_row[g + 1]; i += blockDim.x) {
+    for (int i = d.useg_row[g] + threadIdx.x; i < d.useg_row[g + 1]; i += blockDim.x) {
       T r[6], z[6];
       if (rhs_from_g) {
         const double* gg = d.g + 6 * (size_t)i;
@@ -861,11 +952,11 @@ __global__ void __launch_bounds__(kTile) k_pcg(DevArrays d, int rhs_from_g, int 
     if (!grid_barrier(d, [&] { pcg_decide(d, k_iter); })) return;
     if (__ldcg(&d.cnt->n_active) == 0 || __ldcg(&d.cnt->timeout)) break;
     // ---- B: p = z + beta p, s = w + beta s, x += alpha p, r -= alpha s, z = M^-1 r
-    for (int g = seg0; g < seg1; ++g) {
-      int sc = d.seg_scene[g];
+    for (int g = useg0; g < useg1; ++g) {
+      int sc = d.useg_scene[g];
       if (!d.sc[sc].newton_active || !__ldcg(&d.sc[sc].pcg_active)) continue;
       T al = (T)__ldcg(&d.sc[sc].alpha), be = (T)__ldcg(&d.sc[sc].beta);
-      for (int i = d.seg_row[g] + threadIdx.x; i < d.seg_row[g + 1]; i += blockDim.x) {
+      for (int i = d.useg_row[g] + threadIdx.x; i < d.useg_row[g + 1]; i += blockDim.x) {
         Vec6<T> z = load6_cg<T>(Z, i), w = load6_cg<T>(W, i), p = load6_cg<T>(P, i), s = load6_cg<T>(S, i);
         Vec6<T> x = load6_cg<T>(X, i), r = load6_cg<T>(R, i);
         T pn[6], sn[6], xn[6], rn[6], zn[6];
@@ -892,7 +983,7 @@ __global__ void __launch_bounds__(kTile) k_pcg(DevArrays d, int rhs_from_g, int 
 // per-scene reductions outside the PCG (Newton residual, descent check, line search decision)
 // ================================================================================================
 
-__global__ void k_scene_reduce(DevArrays d, int mode, int k_iter) {
+__global__ void k_scene_reduce(DevArrays d, int mode, unsigned long long cond) {
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   __shared__ int s_cnt[32];
   int cnt = 0;
@@ -908,6 +999,7 @@ __global__ void k_scene_reduce(DevArrays d, int mode, int k_iter) {
     if (lane != 0) continue;
     if (mode == RED_GRAD) {
       if (!c->newton_active) continue;
+      c->act_cur = 0;
       if (!isfinite(v)) {
         c->newton_active = 0;
         c->status = 6;
@@ -915,7 +1007,7 @@ __global__ void k_scene_reduce(DevArrays d, int mode, int k_iter) {
         continue;
       }
       double gn = sqrt(v);
-      if (k_iter == 0) c->g0 = gn;
+      if (c->newton_iters == 0) c->g0 = gn;  // first residual of the step
       c->gnorm = gn;
       if (gn <= d.tol * c->g0) {
         c->newton_active = 0;
@@ -935,6 +1027,7 @@ __global__ void k_scene_reduce(DevArrays d, int mode, int k_iter) {
       c->pad1 = 0;  // halvings in this line search
       c->newton_iters += 1;
       c->pcg_total += c->pcg_iters;
+      c->act_pcg += c->act_cur * (long long)c->pcg_iters;
       ++cnt;
     } else if (mode == RED_LS) {
       if (!c->newton_active || c->ls_state != 0) continue;
@@ -968,6 +1061,21 @@ __global__ void k_scene_reduce(DevArrays d, int mode, int k_iter) {
     for (int w = 0; w < nw; ++w) tot += s_cnt[w];
     if (mode == RED_LS) d.cnt->n_pending = tot;
     else d.cnt->n_active = tot;
+    if (cond) {  // device-driven loop of the step graph: the same decisions as the host-driven loop
+      unsigned go = tot > 0;
+      if (mode == RED_GRAD) {
+        int trips = ++d.cnt->loops_newton;
+        if (go && trips > d.newton_max + 2) d.cnt->runaway = 1;
+      } else if (mode == RED_GDX) {
+        d.cnt->loops_ls = 0;
+      } else if (mode == RED_LS) {
+        int trials = ++d.cnt->loops_ls;
+        d.cnt->ls_total += 1;
+        if (trials >= d.ls_max + 2) go = 0;
+      }
+      if (step_aborted(d)) go = 0;
+      cudaGraphSetConditional((cudaGraphConditionalHandle)cond, go);
+    }
   }
 }
 
@@ -1136,7 +1244,7 @@ __global__ void k_ls_commit(DevArrays d) {
 
 __global__ void k_finish(DevArrays d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d.n) return;
+  if (i >= d.n || step_aborted(d)) return;  // an aborted step leaves the committed state untouched
   double4 p = d.xp[i], q = d.xq[i], p0 = d.x0p[i], q0 = d.x0q[i];
   double idt = 1.0 / d.dt;
   d.vp[i] = make_double4((p.x - p0.x) * idt, (p.y - p0.y) * idt, (p.z - p0.z) * idt, 0.0);
@@ -1147,21 +1255,56 @@ __global__ void k_finish(DevArrays d) {
 
 __global__ void k_fracture(DevArrays d) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= d.nb || d.bbroken[b]) return;
-  int2 ij = d.bij[b];
-  double4 pi = d.x0p[ij.x], pj = d.x0p[ij.y];
-  double ex = pj.x - pi.x, ey = pj.y - pi.y, ez = pj.z - pi.z;
-  double l0 = d.brest[b].w;
-  double strain = (sqrt(ex * ex + ey * ey + ez * ez) - l0) / l0;
-  if (strain > d.bbrk[b]) {
-    d.bbroken[b] = 1;
-    atomicAdd(&d.sc[d.bscene[b]].bonds_broken, 1);
+  bool live = b < d.nb && !d.bbroken[b] && !step_aborted(d);
+  int s = b < d.nb ? d.bscene[b] : -1;
+  bool intact = false;
+  if (live) {
+    int2 ij = d.bij[b];
+    double4 pi = d.x0p[ij.x], pj = d.x0p[ij.y];
+    double ex = pj.x - pi.x, ey = pj.y - pi.y, ez = pj.z - pi.z;
+    double l0 = d.brest[b].w;
+    double strain = (sqrt(ex * ex + ey * ey + ez * ez) - l0) / l0;
+    bool brk = strain > d.bbrk[b];
+    if (!brk && d.stress_on) {
+      double2 lim = d.bsstr[b];
+      if (isfinite(lim.x) || isfinite(lim.y)) {
+        double sg, ta;
+        bond_stress(load_bond(d.brest[b], d.bstiff[b]), d.bsgeo[b], to_v(pi), to_q(d.x0q[ij.x]), to_v(pj),
+                    to_q(d.x0q[ij.y]), sg, ta);
+        brk = sg > lim.x || ta > lim.y;
+      }
+    }
+    if (brk) {
+      d.bbroken[b] = 1;
+      atomicAdd(&d.sc[s].bonds_broken, 1);
+    } else {
+      intact = true;
+    }
   }
+  // intact bonds per scene, one atomic per scene present in the warp (bonds are grouped by scene)
+  unsigned m = __activemask();
+  unsigned grp = __match_any_sync(m, s);
+  unsigned cnt = __popc(__ballot_sync(m, intact) & grp);
+  if (s >= 0 && cnt && (threadIdx.x & 31) == __ffs(grp) - 1)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&d.sc[s].intact), (unsigned long long)cnt);
 }
 
 // ================================================================================================
 // inspection helpers
 // ================================================================================================
+
+// (sigma, tau) of every bond at the committed state, written at its caller index
+__global__ void k_bond_stress(DevArrays d, double* out) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= d.nb) return;
+  int2 ij = d.bij[b];
+  double sg, ta;
+  bond_stress(load_bond(d.brest[b], d.bstiff[b]), d.bsgeo[b], to_v(d.x0p[ij.x]), to_q(d.x0q[ij.x]),
+              to_v(d.x0p[ij.y]), to_q(d.x0q[ij.y]), sg, ta);
+  size_t e = (size_t)d.bond_int2ext[b];
+  out[2 * e] = sg;
+  out[2 * e + 1] = ta;
+}
 
 // ids: NULL (every bond, written at its caller index) or a list of caller bond indices (written in list order)
 template <typename T>
@@ -1287,6 +1430,11 @@ int launch_contacts(const DevArrays& d, int stage, cudaStream_t s) {
     k += 3 + launch_scan_counts(d, d.cnt_tmp, d.c_start, d.n, s);
     return k;
   }
+  if (stage == 2) {
+    k_contact_check<<<1, 1, 0, s>>>(d);
+    k_contact_clear<<<blocks_for(d.n + 1, 256), 256, 0, s>>>(d);
+    return 2;
+  }
   k_contact_scan<1><<<blocks_for(d.n, 128), 128, 0, s>>>(d);
   return 1;
 }
@@ -1329,8 +1477,8 @@ int launch_particle_hess(const DevArrays& d, int mask, int all, cudaStream_t s) 
   return 1;
 }
 
-int launch_scene_reduce(const DevArrays& d, int mode, int k_iter, cudaStream_t s) {
-  k_scene_reduce<<<1, 1024, 0, s>>>(d, mode, k_iter);
+int launch_scene_reduce(const DevArrays& d, int mode, unsigned long long cond, cudaStream_t s) {
+  k_scene_reduce<<<1, 1024, 0, s>>>(d, mode, cond);
   return 1;
 }
 
@@ -1419,6 +1567,12 @@ int launch_unpack_bond_hess(const DevArrays& d, double* out, const int32_t* ids,
   if (m == 0) return 0;
   if (d.mixed) k_unpack_bond_hess<float><<<blocks_for(m, 64), 64, 0, s>>>(d, out, ids, count);
   else k_unpack_bond_hess<double><<<blocks_for(m, 64), 64, 0, s>>>(d, out, ids, count);
+  return 1;
+}
+
+int launch_bond_stress(const DevArrays& d, double* out, cudaStream_t s) {
+  if (d.nb == 0) return 0;
+  k_bond_stress<<<blocks_for(d.nb, 128), 128, 0, s>>>(d, out);
   return 1;
 }
 

@@ -25,13 +25,17 @@ except Exception:  # pragma: no cover
 @dataclasses.dataclass
 class Material:
     """Bond material. shear_scale multiplies the shear angle (1: the energy exactly as printed, in N/m;
-    a length such as the rest bond length: the dimensionally consistent energy in J)."""
+    a length such as the rest bond length: the dimensionally consistent energy in J). A bond breaks when its
+    tensile strain exceeds break_strain, or its stresses exceed tensile_strength (sigma_c) or shear_strength
+    (tau_c); +inf switches a criterion off."""
     E: float
     nu: float
     density: float
     break_strain: float = math.inf
     bend_twist_scale: float = 1.0
     shear_scale: float = 1.0
+    tensile_strength: float = math.inf
+    shear_strength: float = math.inf
 
 
 @dataclasses.dataclass
@@ -233,38 +237,53 @@ def c3_textile(nx=300, spacing=2e-3, r=1e-3, E=1e9, nu=0.3, density=1500.0, bend
 # Poisson-disk packed boxes, batched scenes, slab impact
 # --------------------------------------------------------------------------------------------------
 
-def poisson_box(n_target, r, rng, aspect=(1.0, 1.0, 1.0), max_fail=30):
-    """Dart-throwing (minimum distance 2r) packing of about n_target spheres in a box of the given
-    aspect, sized for a packing fraction near 0.35 (a typical dart-throwing density)."""
-    vol = n_target * (4.0 / 3.0) * math.pi * r ** 3 / 0.35
+def _dart_throw(sample, n_target, r, rng, batch, max_rounds=400, min_accept=None):
+    """Dart throwing with minimum distance 2r, in rounds of `batch` darts drawn by sample(rng, batch): a dart is
+    kept when it is at least 2r from every point already placed and from every earlier dart of its round that is
+    itself not rejected by a placed point (a dart that conflicts with an earlier one of the same round is dropped,
+    as sequential throwing would have dropped one of the two). Stops at n_target points or when a round keeps
+    fewer than min_accept darts (default: 1% of a round)."""
+    if min_accept is None:
+        min_accept = max(2, batch // 100)
+    d2 = 2.0 * r
+    pts = np.zeros((0, 3))
+    for _ in range(max_rounds):
+        if pts.shape[0] >= n_target:
+            break
+        cand = sample(rng, batch)
+        if pts.shape[0]:
+            dist, _ = cKDTree(pts).query(cand, k=1, distance_upper_bound=d2)
+            cand = cand[~(dist < d2)]
+        if cand.shape[0] > 1:
+            pr = cKDTree(cand).query_pairs(d2, output_type="ndarray")
+            if pr.size:
+                drop = np.zeros(cand.shape[0], bool)
+                drop[np.maximum(pr[:, 0], pr[:, 1])] = True
+                cand = cand[~drop]
+        take = cand[: max(0, n_target - pts.shape[0])]
+        pts = np.concatenate([pts, take], 0)
+        if take.shape[0] < min_accept:
+            break
+    return pts
+
+
+def poisson_box(n_target, r, rng, aspect=(1.0, 1.0, 1.0), fraction=0.28, **kw):
+    """Dart-throwing packing of n_target spheres in a box of the given aspect, sized for the packing fraction
+    `fraction` (round-based dart throwing stalls near 0.3, so the default reaches the target count)."""
+    vol = n_target * (4.0 / 3.0) * math.pi * r ** 3 / fraction
     s = (vol / (aspect[0] * aspect[1] * aspect[2])) ** (1.0 / 3.0)
     ext = np.array(aspect) * s
-    cell = 2.0 * r / math.sqrt(3.0)
-    dims = np.maximum(1, np.ceil(ext / cell).astype(int))
-    grid = -np.ones(dims, np.int64)
-    pts = []
-    fails = 0
-    batch = 4096
-    while len(pts) < n_target and fails < max_fail:
-        cand = rng.uniform(0.0, 1.0, (batch, 3)) * ext
-        added = 0
-        for c in cand:
-            gi = np.minimum((c / cell).astype(int), dims - 1)
-            lo = np.maximum(gi - 2, 0)
-            hi = np.minimum(gi + 3, dims)
-            blk = grid[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]]
-            ids = blk[blk >= 0]
-            if ids.size and np.min(np.sum((np.asarray(pts)[ids] - c) ** 2, 1)) < (2.0 * r) ** 2:
-                continue
-            if grid[gi[0], gi[1], gi[2]] >= 0:
-                continue
-            grid[gi[0], gi[1], gi[2]] = len(pts)
-            pts.append(c)
-            added += 1
-            if len(pts) >= n_target:
-                break
-        fails = fails + 1 if added == 0 else 0
-    return np.asarray(pts), ext
+    pts = _dart_throw(lambda g, m: g.uniform(0.0, 1.0, (m, 3)) * ext, n_target, r, rng, max(256, n_target // 8), **kw)
+    return pts, ext
+
+
+def poisson_ball(n_target, r, R, rng):
+    """Dart-throwing packing of n_target spheres inside a ball of radius R centred at the origin."""
+    def sample(g, m):
+        v = g.normal(size=(m, 3))
+        v /= np.linalg.norm(v, axis=1)[:, None]
+        return v * (R * g.uniform(0.0, 1.0, (m, 1)) ** (1.0 / 3.0))
+    return _dart_throw(sample, n_target, r, rng, max(256, n_target // 4))
 
 
 def c4_batched(n_scenes=64, n_min=2000, n_max=50000, r=2e-3, E=1e8, nu=0.3, density=2500.0, break_strain=2e-3,
@@ -291,9 +310,56 @@ def c4_batched(n_scenes=64, n_min=2000, n_max=50000, r=2e-3, E=1e8, nu=0.3, dens
                      name or f"c4_batched{n_scenes}", offsets=np.array(offsets))
 
 
+def cutoff_for_degree(pts, target, lo, hi, sample=20000, iters=30, seed=0):
+    """Bond cutoff giving a mean neighbour count `target` (bisection on a random sample of the points)."""
+    rng = np.random.default_rng(seed)
+    tree = cKDTree(pts)
+    idx = rng.choice(pts.shape[0], size=min(sample, pts.shape[0]), replace=False)
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        deg = np.mean(tree.query_ball_point(pts[idx], mid, return_length=True) - 1)
+        lo, hi = (mid, hi) if deg < target else (lo, mid)
+    return 0.5 * (lo + hi)
+
+
+def c5_impact(n_slab=1_000_000, n_ball=2000, r=2e-3, footprint=0.5, ball_R=0.05, E=1e9, nu=0.3, density=2500.0,
+              break_strain=1e-3, speed=20.0, degree=12.0, dt=2e-4, steps=300, seed=5, name=None) -> Scene:
+    """Large impact: a Poisson-disk slab of n_slab particles on a footprint x footprint base (thickness set by the
+    packing), bonds within the cutoff that gives `degree` neighbours on average; above it a ball of radius ball_R
+    packed with n_ball particles, bonded by the same rule, unbreakable and 10x stiffer, moving down at `speed`.
+    Two scenes' worth of particles in one scene (slab and ball interact through self contact); ground under the
+    slab."""
+    rng = np.random.default_rng(seed)
+    vol = n_slab * (4.0 / 3.0) * math.pi * r ** 3 / 0.28
+    thick = vol / footprint ** 2
+    slab, ext = poisson_box(n_slab, r, rng, aspect=(footprint / thick, footprint / thick, 1.0))
+    slab = slab - np.array([ext[0] / 2.0, ext[1] / 2.0, -r])
+    ball = poisson_ball(n_ball, r, ball_R, rng)
+    ball = ball + np.array([0.0, 0.0, slab[:, 2].max() + r + ball_R + 2.0 * r])
+    cut_s = cutoff_for_degree(slab, degree, 2.0 * r, 4.0 * r)
+    cut_b = cutoff_for_degree(ball, degree, 2.0 * r, 6.0 * r, sample=ball.shape[0])
+    ps = _pairs_within(slab, cut_s)
+    pb = _pairs_within(ball, cut_b) + slab.shape[0]
+    pos = np.concatenate([slab, ball], 0)
+    n = pos.shape[0]
+    mat = np.zeros(n, np.int32)
+    mat[slab.shape[0]:] = 1
+    pairs = np.concatenate([ps, pb], 0)
+    bond_mat = np.concatenate([np.zeros(len(ps), np.int32), np.ones(len(pb), np.int32)])
+    mats = [Material(E, nu, density, break_strain, 1.0, 2.0 * r), Material(10.0 * E, nu, density, math.inf, 1.0, 2.0 * r)]
+    vel = np.zeros((n, 3))
+    vel[slab.shape[0]:, 2] = -speed
+    config = default_config(dt=dt, k_ground=E * r, k_self=E * r, contact_skin=r, steps=steps)
+    sc = _assemble(pos, np.full(n, r), mat, np.zeros(n, np.uint8), pairs, mats, config, name or "c5_impact",
+                   vel=vel, bond_mat=bond_mat)
+    sc.config["bond_cutoff_slab"] = float(cut_s)
+    sc.config["bond_cutoff_ball"] = float(cut_b)
+    return sc
+
+
 def scene_by_name(name: str) -> Scene:
     table = {
         "c1": c1_cube, "c1b": c1b_cube_contact, "c2": c2_plate, "c2_small": c2_plate_small,
-        "c3": c3_textile, "c4": c4_batched,
+        "c3": c3_textile, "c4": c4_batched, "c5": c5_impact,
     }
     return table[name]()
