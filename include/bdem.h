@@ -51,6 +51,7 @@ typedef enum {
 
 enum { BDEM_FP64 = 0, BDEM_MIXED = 1 };   /* bdem_config.precision */
 enum { BDEM_SPD_EIG = 0 };                /* bdem_config.spd_mode */
+enum { BDEM_OPT_SECOND_ORDER = 0, BDEM_OPT_FIRST_ORDER = 1 };  /* bdem_config.optimizer */
 
 /* Bond material (Sec. 3.2). G = E / (2 (1 + nu)) (isotropic relation; the paper does not define G). */
 typedef struct {
@@ -81,8 +82,17 @@ typedef struct {
   double contact_skin;      /* >= 0; candidate pairs are collected once per step at the initial guess when
                                |p_i - p_j| < r_i + r_j + contact_skin (same scene, not joined by an intact bond) */
   int32_t spd_mode;         /* BDEM_SPD_EIG: per-term eigenvalue clamp */
-  int32_t reserved0;
+  int32_t optimizer;        /* BDEM_OPT_SECOND_ORDER (0): Newton directions from the projected Riemannian Hessian and
+                               PCG (Alg. 2 inside Alg. 3); BDEM_OPT_FIRST_ORDER (1): the direction -grad f with the
+                               same line search and stopping test (Alg. 1), no Hessian and no linear solve */
   void* cuda_stream;        /* cudaStream_t the library launches on (NULL: the legacy default stream) */
+  double friction_slide;    /* >= 0, mu_s of the post-step friction correction (Sec. 5.4, Friction); 0: off */
+  double friction_roll;     /* >= 0, mu_r of the rotation friction; 0: off. After the velocity update each element's
+                               linear and angular velocity is corrected from the contacts active at x_{n+1}:
+                               dv = -min(1, mu_s |F_n| dt / (m |v_t|)) v_t and
+                               dw = -min(1, mu_r |F_n| r^3 dt / (I |w_ij|)) w_ij per contact (I = 2/5 m r^2,
+                               relative velocities of the element pair, the ground at rest), summed, projected on
+                               the element's own velocity direction and clamped so that it only slows down */
 } bdem_config;
 
 /* Per-scene statistics of one bdem_step call (sums over its steps, norms of the last step). */

@@ -46,8 +46,9 @@ def lib():
 class OrcConfig(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("gravity", ctypes.c_double * 3), ("newton_rel_tol", ctypes.c_double),
                 ("newton_max_iter", ctypes.c_int32), ("pcg_max_iter", ctypes.c_int32),
-                ("ls_max_halvings", ctypes.c_int32), ("pad0", ctypes.c_int32), ("ground_z", ctypes.c_double),
-                ("k_ground", ctypes.c_double), ("k_self", ctypes.c_double), ("contact_skin", ctypes.c_double)]
+                ("ls_max_halvings", ctypes.c_int32), ("optimizer", ctypes.c_int32), ("ground_z", ctypes.c_double),
+                ("k_ground", ctypes.c_double), ("k_self", ctypes.c_double), ("contact_skin", ctypes.c_double),
+                ("mu_slide", ctypes.c_double), ("mu_roll", ctypes.c_double)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -225,6 +226,9 @@ class OracleSim:
         C.k_ground = c["k_ground"]
         C.k_self = c["k_self"]
         C.contact_skin = c["contact_skin"]
+        C.optimizer = int(c.get("optimizer", 0))
+        C.mu_slide = c.get("friction_slide", 0.0)
+        C.mu_roll = c.get("friction_roll", 0.0)
         return C
 
     def _build_problem(self):

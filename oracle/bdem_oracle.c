@@ -1109,11 +1109,17 @@ static int newton_scene(const orc_config* C, orc_problem* P, int scene, double* 
     st->g_norm = gn;
     if (gn <= C->newton_rel_tol * st->g0_norm) break;
     if (k >= C->newton_max_iter) { status = 4; break; }
-    double eps_r = fmin(0.5, sqrt(gn));
-    for (int i = 0; i < n6; ++i) rhs[i] = -S.g[i];
-    st->pcg_iters += pcg(&S, rhs, eps_r, C->pcg_max_iter, dx);
-    if (vdot(n6, S.g, dx) >= 0.0)
+    if (C->optimizer == 1) {
+      /* Alg. 1: the descent direction is -grad f; in the reduced coordinates dq = G_l(q)^T y, so y = -g_y gives
+       * dq = -(I - q q^T) grad_q F, the projected gradient of the first-order method */
       for (int i = 0; i < n6; ++i) dx[i] = -S.g[i];
+    } else {
+      double eps_r = fmin(0.5, sqrt(gn));
+      for (int i = 0; i < n6; ++i) rhs[i] = -S.g[i];
+      st->pcg_iters += pcg(&S, rhs, eps_r, C->pcg_max_iter, dx);
+      if (vdot(n6, S.g, dx) >= 0.0)
+        for (int i = 0; i < n6; ++i) dx[i] = -S.g[i];
+    }
     ++k;
     double alpha = 1.0;
     int accepted = 0;
@@ -1135,6 +1141,102 @@ static int newton_scene(const orc_config* C, orc_problem* P, int scene, double* 
   free(dx); free(rhs); free(tp); free(tq);
   sys_free(&S);
   return status;
+}
+
+/* ------------------------------------------------------------------------------------------------ */
+/* Friction (Sec. 5.4, Friction; Alg. 3: project v_{n+1} to the friction cone), an explicit velocity   */
+/* correction after the velocity update, with the readings:                                          */
+/*  - the contacts are those active at x_{n+1}: the ground when g = p_z - z_ground - r < 0 (normal     */
+/*    e_z, |F_n| = k_c |g|), and the step's self-contact candidates that overlap at x_{n+1} (normal    */
+/*    (p_i - p_j)/|p_i - p_j|, |F_n| = k_ec |d - r_i - r_j|);                                           */
+/*  - v_ij = v_i - v_j (v_i for the ground), w_ij = w_i - w_j (w_i) with w the angular velocity in the  */
+/*    world frame, q' = 1/2 (w, 0) (x) q;                                                              */
+/*  - each contact contributes dv = -min(1, mu_s |F_n| dt / (m_i |v_t|)) v_t and                       */
+/*    dw = -min(1, mu_r |F_n| r_i^3 dt / (I_i |w_ij|)) w_ij with I_i = 2/5 m_i r_i^2; the contributions */
+/*    of all contacts add, computed from the velocities before any correction;                        */
+/*  - the sums are projected on the directions of v_i and w_i and clamped to [-|v_i|, 0] and           */
+/*    [-|w_i|, 0] along them (the correction only slows the element, down to rest at most);            */
+/*  - q' changes by 1/2 (dw, 0) (x) q; kinematic particles keep their velocities.                      */
+/* ------------------------------------------------------------------------------------------------ */
+
+static void ang_vel(const double q[4], const double u[4], double w[3]) {
+  double qc[4] = {-q[0], -q[1], -q[2], q[3]}, t[4];
+  orc_qmul(u, qc, t);
+  w[0] = 2.0 * t[0]; w[1] = 2.0 * t[1]; w[2] = 2.0 * t[2];
+}
+
+static void contact_friction(const orc_config* C, const double* p, const double* vv, const double* ww, int i, int j,
+                             const double* radius, double mi, double dv[3], double dw[3]) {
+  /* j < 0: the ground */
+  double n[3], fn, vij[3], wij[3];
+  double ri = radius[i];
+  if (j < 0) {
+    double g = p[3 * i + 2] - C->ground_z - ri;
+    if (!(g < 0.0)) return;
+    n[0] = 0.0; n[1] = 0.0; n[2] = 1.0;
+    fn = C->k_ground * fabs(g);
+    for (int k = 0; k < 3; ++k) { vij[k] = vv[3 * i + k]; wij[k] = ww[3 * i + k]; }
+  } else {
+    double e[3] = {p[3 * i] - p[3 * j], p[3 * i + 1] - p[3 * j + 1], p[3 * i + 2] - p[3 * j + 2]};
+    double d = sqrt(dot3(e, e)), R = ri + radius[j];
+    if (!(d < R)) return;
+    for (int k = 0; k < 3; ++k) n[k] = e[k] / d;
+    fn = C->k_self * fabs(d - R);
+    for (int k = 0; k < 3; ++k) { vij[k] = vv[3 * i + k] - vv[3 * j + k]; wij[k] = ww[3 * i + k] - ww[3 * j + k]; }
+  }
+  double vn = dot3(vij, n), vt[3] = {vij[0] - vn * n[0], vij[1] - vn * n[1], vij[2] - vn * n[2]};
+  double nvt = sqrt(dot3(vt, vt)), nw = sqrt(dot3(wij, wij));
+  if (nvt > 0.0) {
+    double c = C->mu_slide * fn * C->dt / (mi * nvt);
+    if (c > 1.0) c = 1.0;
+    for (int k = 0; k < 3; ++k) dv[k] -= c * vt[k];
+  }
+  if (nw > 0.0) {
+    double I = 0.4 * mi * ri * ri;
+    double c = C->mu_roll * fn * ri * ri * ri * C->dt / (I * nw);
+    if (c > 1.0) c = 1.0;
+    for (int k = 0; k < 3; ++k) dw[k] -= c * wij[k];
+  }
+}
+
+/* clamps the correction d to the direction of x: d <- s x/|x| with s = d.x/|x| limited to [-|x|, 0] */
+static void slow_only(const double x[3], double d[3]) {
+  double nx = sqrt(dot3(x, x));
+  if (!(nx > 0.0)) { d[0] = d[1] = d[2] = 0.0; return; }
+  double s = dot3(d, x) / nx;
+  if (s > 0.0) s = 0.0;
+  if (s < -nx) s = -nx;
+  for (int k = 0; k < 3; ++k) d[k] = s * x[k] / nx;
+}
+
+static void apply_friction(const orc_config* C, orc_problem* P, const double* pred) {
+  int n = P->n;
+  double *vv = malloc(sizeof(double) * 3 * n), *ww = malloc(sizeof(double) * 3 * n);
+  double *dv = calloc(3 * (size_t)n, sizeof(double)), *dw = calloc(3 * (size_t)n, sizeof(double));
+  memcpy(vv, P->v, sizeof(double) * 3 * n);
+  for (int i = 0; i < n; ++i) ang_vel(P->q + 4 * i, P->u + 4 * i, ww + 3 * i);
+  for (int s = 0; s < P->n_scenes; ++s) {
+    int32_t* cand = NULL;
+    int nc = C->k_self > 0.0 ? find_candidates(C, P, s, pred, &cand, 0) : 0;  /* the step's candidates */
+    for (int i = (int)P->scene_start[s]; i < (int)P->scene_start[s + 1]; ++i)
+      if (C->k_ground > 0.0) contact_friction(C, P->p, vv, ww, i, -1, P->radius, P->mass[i], dv + 3 * i, dw + 3 * i);
+    for (int k = 0; k < nc; ++k) {
+      int a = cand[2 * k], b = cand[2 * k + 1];
+      contact_friction(C, P->p, vv, ww, a, b, P->radius, P->mass[a], dv + 3 * a, dw + 3 * a);
+      contact_friction(C, P->p, vv, ww, b, a, P->radius, P->mass[b], dv + 3 * b, dw + 3 * b);
+    }
+    free(cand);
+  }
+  for (int i = 0; i < n; ++i) {
+    if (is_kin(P, i)) continue;
+    slow_only(vv + 3 * i, dv + 3 * i);
+    slow_only(ww + 3 * i, dw + 3 * i);
+    for (int k = 0; k < 3; ++k) P->v[3 * i + k] += dv[3 * i + k];
+    double x[4] = {dw[3 * i], dw[3 * i + 1], dw[3 * i + 2], 0.0}, t[4];
+    orc_qmul(x, P->q + 4 * i, t);
+    for (int k = 0; k < 4; ++k) P->u[4 * i + k] += 0.5 * t[k];
+  }
+  free(vv); free(ww); free(dv); free(dw);
 }
 
 int orc_step(const orc_config* C, orc_problem* P, orc_scene_stats* stats) {
@@ -1160,6 +1262,8 @@ int orc_step(const orc_config* C, orc_problem* P, orc_scene_stats* stats) {
     for (int k = 0; k < 3; ++k) { P->v[3 * i + k] = (xp[3 * i + k] - P->p[3 * i + k]) / dt; P->p[3 * i + k] = xp[3 * i + k]; }
     for (int k = 0; k < 4; ++k) { P->u[4 * i + k] = (xq[4 * i + k] - P->q[4 * i + k]) / dt; P->q[4 * i + k] = xq[4 * i + k]; }
   }
+  /* friction correction of the new velocities (contacts from the step's candidates, found at the prediction) */
+  if (C->mu_slide > 0.0 || C->mu_roll > 0.0) apply_friction(C, P, phat);
   /* bond state update, all bonds at once at the new state: tensile strain fracture, and the stress criterion
    * sigma > sigma_c or tau > tau_c of Sec. 3.2 where the bond's strengths are finite */
   for (int b = 0; b < P->nb; ++b) {

@@ -28,11 +28,13 @@ typedef struct {
   int32_t newton_max_iter;
   int32_t pcg_max_iter;
   int32_t ls_max_halvings;
-  int32_t pad0;
+  int32_t optimizer;       /* 0: second-order manifold optimisation (Alg. 2); 1: first-order (Alg. 1) */
   double ground_z;         /* ground plane z = ground_z */
   double k_ground;         /* 0: no ground */
   double k_self;           /* 0: no self contact */
   double contact_skin;     /* candidate distance margin */
+  double mu_slide;         /* sliding friction coefficient of the post-step friction (0: off) */
+  double mu_roll;          /* rotation friction coefficient (0: off) */
 } orc_config;
 
 /* Particle, bond and scene arrays. Bond rest data is filled by orc_bond_rest(). */

@@ -35,7 +35,8 @@ class bdem_config(ctypes.Structure):
                 ("newton_max_iter", ctypes.c_int32), ("pcg_max_iter", ctypes.c_int32),
                 ("ls_max_halvings", ctypes.c_int32), ("precision", ctypes.c_int32), ("ground_z", ctypes.c_double),
                 ("k_ground", ctypes.c_double), ("k_self", ctypes.c_double), ("contact_skin", ctypes.c_double),
-                ("spd_mode", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
+                ("spd_mode", ctypes.c_int32), ("optimizer", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
+                ("friction_slide", ctypes.c_double), ("friction_roll", ctypes.c_double)]
 
 
 class bdem_step_stats(ctypes.Structure):
@@ -144,7 +145,10 @@ def make_config(cfg: dict, precision=BDEM_FP64, cuda_stream=None) -> bdem_config
     c.k_self = cfg["k_self"]
     c.contact_skin = cfg["contact_skin"]
     c.spd_mode = 0
+    c.optimizer = int(cfg.get("optimizer", 0))
     c.cuda_stream = cuda_stream
+    c.friction_slide = cfg.get("friction_slide", 0.0)
+    c.friction_roll = cfg.get("friction_roll", 0.0)
     return c
 
 

@@ -215,9 +215,13 @@ static bdem_status check_config(const bdem_config* c) {
   if (c->precision != BDEM_FP64 && c->precision != BDEM_MIXED)
     return fail(nullptr, BDEM_E_INVALID, "precision must be BDEM_FP64 or BDEM_MIXED");
   if (c->spd_mode != BDEM_SPD_EIG) return fail(nullptr, BDEM_E_INVALID, "spd_mode must be BDEM_SPD_EIG");
+  if (c->optimizer != BDEM_OPT_SECOND_ORDER && c->optimizer != BDEM_OPT_FIRST_ORDER)
+    return fail(nullptr, BDEM_E_INVALID, "optimizer must be BDEM_OPT_SECOND_ORDER or BDEM_OPT_FIRST_ORDER");
   if (!(c->k_ground >= 0.0) || !(c->k_self >= 0.0) || !(c->contact_skin >= 0.0) || !fin(c->ground_z) ||
       !fin(c->k_ground) || !fin(c->k_self) || !fin(c->contact_skin))
     return fail(nullptr, BDEM_E_INVALID, "contact parameters must be finite and >= 0");
+  if (!(c->friction_slide >= 0.0) || !(c->friction_roll >= 0.0) || !fin(c->friction_slide) || !fin(c->friction_roll))
+    return fail(nullptr, BDEM_E_INVALID, "friction coefficients must be finite and >= 0");
   return BDEM_OK;
 }
 
@@ -510,6 +514,9 @@ extern "C" bdem_status bdem_create(const bdem_config* config, int32_t n_scenes, 
   d.k_ground = c.k_ground;
   d.k_self = c.k_self;
   d.skin = c.contact_skin;
+  d.mu_slide = c.friction_slide;
+  d.first_order = c.optimizer == BDEM_OPT_FIRST_ORDER;
+  d.mu_roll = c.friction_roll;
   double rmax = 0.0;
   for (int64_t i = 0; i < n; ++i) rmax = std::max(rmax, radius[i]);
   d.cell_h = std::max(2.0 * rmax + c.contact_skin, 1e-12);
@@ -858,15 +865,17 @@ static bdem_status do_step(bdem_sim* s, std::vector<SceneCtl>& ctl) {
     }
     if (c.n_active == 0) break;
     if (k > d.newton_max + 1) return fail(s, BDEM_E_CUDA, "Newton loop did not terminate");
-    phase_begin(s, BDEM_PH_HESS);
-    TRY(check_launch(s, launch_bond_hess(d, 0, st)));
-    TRY(check_launch(s, launch_particle_hess(d, 1, 0, st)));
-    phase_end(s);
-    phase_begin(s, BDEM_PH_PCG);
-    TRY(run_pcg(s, d, 1, 1));
-    phase_end(s);
+    if (!d.first_order) {
+      phase_begin(s, BDEM_PH_HESS);
+      TRY(check_launch(s, launch_bond_hess(d, 0, st)));
+      TRY(check_launch(s, launch_particle_hess(d, 1, 0, st)));
+      phase_end(s);
+      phase_begin(s, BDEM_PH_PCG);
+      TRY(run_pcg(s, d, 1, 1));
+      phase_end(s);
+    }
     phase_begin(s, BDEM_PH_LINESEARCH);
-    TRY(check_launch(s, launch_gdx(d, st)));
+    if (!d.first_order) TRY(check_launch(s, launch_gdx(d, st)));
     TRY(check_launch(s, launch_scene_reduce(d, RED_GDX, 0, st)));
     for (int h = 0; h <= d.ls_max + 1; ++h) {
       TRY(check_launch(s, launch_ls_trial(d, st)));
@@ -983,10 +992,12 @@ static bool build_step_graph(bdem_sim* s) {
   G_TRY("begin body capture", cudaStreamBeginCaptureToGraph(s->cap[1], bodyN, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   if (e == cudaSuccess) {
     cudaStream_t st = s->cap[1];
-    body += launch_bond_hess(d, 0, st);
-    body += launch_particle_hess(d, 1, 0, st);
-    body += launch_pcg(d, 1, 1, st, &pe);
-    body += launch_gdx(d, st);
+    if (!d.first_order) {
+      body += launch_bond_hess(d, 0, st);
+      body += launch_particle_hess(d, 1, 0, st);
+      body += launch_pcg(d, 1, 1, st, &pe);
+      body += launch_gdx(d, st);
+    }
     body += launch_scene_reduce(d, RED_GDX, hL, st);
     G_TRY("PCG launch", pe);
     G_TRY("Newton body launches", cudaGetLastError());

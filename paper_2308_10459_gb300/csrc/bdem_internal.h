@@ -77,8 +77,10 @@ struct DevArrays {
   int32_t c_cap;                // capacity of the contact arrays
   int32_t hash_size;            // power of two
   double dt, gx, gy, gz, tol, ground_z, k_ground, k_self, skin, cell_h;
+  double mu_slide, mu_roll;     // friction coefficients of the post-step correction (0: off)
   int32_t newton_max, pcg_max, ls_max;
   int32_t stress_on;            // some bond has a finite tensile or shear strength
+  int32_t first_order, pad3;    // first_order: descent direction -g (Alg. 1) instead of the Newton direction
   // particles
   double4 *xp, *xq, *x0p, *x0q, *vp, *vq, *hp, *hq, *tp, *tq;
   double2* coef;

@@ -674,6 +674,13 @@ __global__ void __launch_bounds__(kTile) k_matvec(DevArrays d, int mask) {
 // p = z + beta p, s = w + beta s (= H p), x += alpha p, r -= alpha s, z = M^-1 r.
 // ================================================================================================
 
+// L2 prefetch of a byte range by the whole block, one 128-byte line per thread and step
+__device__ __forceinline__ void prefetch_l2(const void* base, size_t bytes) {
+  const char* p = static_cast<const char*>(base);
+  for (size_t off = (size_t)threadIdx.x * 128; off < bytes; off += (size_t)blockDim.x * 128)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p + off));
+}
+
 // grid barrier with a bounded wait; the last block to arrive runs `work` (whole block) before releasing the others
 template <typename F>
 __device__ bool grid_barrier(const DevArrays& d, F&& work) {
@@ -723,24 +730,35 @@ __device__ __forceinline__ double scene_partial(const DevArrays& d, int s, int k
 
 // the PCG decision of one scene from its reduced dots (run by a single thread): convergence test, then the
 // Chronopoulos-Gear step lengths; returns whether the scene keeps iterating
-__device__ bool pcg_decide_scene(const DevArrays& d, SceneCtl* c, double gam, double del, double rho, int k_iter) {
-  // every field the decision reads, loaded together from L2 (other blocks wrote them since this SM last cached them)
-  int newton_active = __ldcg(&c->newton_active), pcg_active = __ldcg(&c->pcg_active), it = __ldcg(&c->pcg_iters);
-  double eps_r = __ldcg(&c->eps_r), bnorm = __ldcg(&c->bnorm), rz = __ldcg(&c->rz), alpha = __ldcg(&c->alpha);
-  if (!newton_active) return false;
+// the fields of a scene's control block that the PCG decision reads, loaded together from L2 (other blocks wrote
+// them since this SM last cached them) and issued before the partial dots so that both loads overlap
+struct PcgPrev {
+  int newton_active, pcg_active, it;
+  double eps_r, bnorm, rz, alpha;
+};
+__device__ __forceinline__ PcgPrev load_prev(const SceneCtl* c) {
+  return {__ldcg(&c->newton_active), __ldcg(&c->pcg_active), __ldcg(&c->pcg_iters), __ldcg(&c->eps_r),
+          __ldcg(&c->bnorm), __ldcg(&c->rz), __ldcg(&c->alpha)};
+}
+
+// the PCG decision of one scene from its reduced dots (run by a single thread): convergence test, then the
+// Chronopoulos-Gear step lengths; returns whether the scene keeps iterating
+__device__ bool pcg_decide_scene(const DevArrays& d, SceneCtl* c, PcgPrev pv, double gam, double del, double rho,
+                                 int k_iter) {
+  if (!pv.newton_active) return false;
   if (k_iter == 0) {
-    bnorm = sqrt(rho);
-    it = 0;
-    pcg_active = 1;
-    c->bnorm = bnorm;
+    pv.bnorm = sqrt(rho);
+    pv.it = 0;
+    pv.pcg_active = 1;
+    c->bnorm = pv.bnorm;
     c->pcg_iters = 0;
     c->pcg_active = 1;
   }
-  if (!pcg_active) return false;
-  bool stop = !(sqrt(rho) > eps_r * bnorm) || it >= d.pcg_max;
+  if (!pv.pcg_active) return false;
+  bool stop = !(sqrt(rho) > pv.eps_r * pv.bnorm) || pv.it >= d.pcg_max;
   if (!stop) {
-    double beta = (it == 0) ? 0.0 : gam / rz;
-    double den = (it == 0) ? del : del - beta * gam / alpha;
+    double beta = (pv.it == 0) ? 0.0 : gam / pv.rz;
+    double den = (pv.it == 0) ? del : del - beta * gam / pv.alpha;
     if (!(den > 0.0) || !(gam > 0.0)) {
       stop = true;  // breakdown: no further decrease along this Krylov space
     } else {
@@ -748,7 +766,7 @@ __device__ bool pcg_decide_scene(const DevArrays& d, SceneCtl* c, double gam, do
       c->alpha = gam / den;
       c->rz = gam;
       c->pq = den;
-      c->pcg_iters = it + 1;
+      c->pcg_iters = pv.it + 1;
     }
   }
   if (stop) c->pcg_active = 0;
@@ -760,17 +778,19 @@ constexpr int kBlockScene = 64;  // scenes with more PCG segments than this are 
 // per-scene decision after the fused product, run by the last block to reach the barrier. The partial dots of a
 // scene's segments are summed in a fixed order: by one warp (lanes stride over the segments) for a scene with at
 // most kBlockScene segments, by the whole block (threads stride, then warps in order) for a larger one, so that a
-// large scene costs one round of loads instead of a serial walk over its segments.
-__device__ void pcg_decide(const DevArrays& d, int k_iter) {
+// large scene costs one round of loads instead of a serial walk over its segments. sseg: the scenes' first
+// segments staged in shared memory (NULL: read them from global memory).
+__device__ __noinline__ void pcg_decide(const DevArrays& d, int k_iter, const int* sseg) {
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   __shared__ int s_active[kTile / 32];
   __shared__ double s_acc[3][kTile / 32];
   __shared__ int s_big[kTile], s_nbig;
   if (threadIdx.x == 0) s_nbig = 0;
   __syncthreads();
+  const int* ss = sseg ? sseg : d.scene_seg;
   int active = 0;
   for (int s = warp; s < d.n_scenes; s += nw) {
-    int a = d.scene_seg[s], b = d.scene_seg[s + 1];
+    int a = ss[s], b = ss[s + 1];
     if (b - a > kBlockScene) {
       if (lane == 0) {
         int k = atomicAdd(&s_nbig, 1);  // list order is irrelevant: each scene is reduced on its own
@@ -778,6 +798,8 @@ __device__ void pcg_decide(const DevArrays& d, int k_iter) {
       }
       continue;
     }
+    PcgPrev pv;
+    if (lane == 0) pv = load_prev(d.sc + s);
     double gam = 0.0, del = 0.0, rho = 0.0;
     for (int t = a + lane; t < b; t += 32) {
       gam += __ldcg(d.part_s + kPartials * t);
@@ -787,7 +809,7 @@ __device__ void pcg_decide(const DevArrays& d, int k_iter) {
     gam = warp_sum(gam);
     del = warp_sum(del);
     rho = warp_sum(rho);
-    if (lane == 0 && pcg_decide_scene(d, d.sc + s, gam, del, rho, k_iter)) ++active;
+    if (lane == 0 && pcg_decide_scene(d, d.sc + s, pv, gam, del, rho, k_iter)) ++active;
   }
   if (lane == 0) s_active[warp] = active;
   __syncthreads();
@@ -795,7 +817,9 @@ __device__ void pcg_decide(const DevArrays& d, int k_iter) {
   int big_active = 0;
   for (int k = 0; k < nbig; ++k) {
     int s = s_big[k];
-    int a = d.scene_seg[s], b = d.scene_seg[s + 1];
+    int a = ss[s], b = ss[s + 1];
+    PcgPrev pv;
+    if (threadIdx.x == 0) pv = load_prev(d.sc + s);
     double gam = 0.0, del = 0.0, rho = 0.0;
     for (int t = a + threadIdx.x; t < b; t += blockDim.x) {
       gam += __ldcg(d.part_s + kPartials * t);
@@ -818,7 +842,7 @@ __device__ void pcg_decide(const DevArrays& d, int k_iter) {
         D += s_acc[1][w];
         R += s_acc[2][w];
       }
-      if (pcg_decide_scene(d, d.sc + s, G, D, R, k_iter)) ++big_active;
+      if (pcg_decide_scene(d, d.sc + s, pv, G, D, R, k_iter)) ++big_active;
     }
     __syncthreads();
   }
@@ -855,6 +879,10 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
     s_rows[i - R0] = make_int4(a - E0, d.inc_start[i + 1] - a, na | kin, d.c_start[i]);
   }
   for (int e = E0 + threadIdx.x; e < E1; e += blockDim.x) s_ent[e - E0] = d.inc2[e];
+  __shared__ int s_sseg[kTile + 1];  // first PCG segment of each scene, for the decision (up to kTile scenes)
+  const bool sseg_ok = d.n_scenes <= kTile;
+  if (sseg_ok)
+    for (int x = threadIdx.x; x <= d.n_scenes; x += blockDim.x) s_sseg[x] = d.scene_seg[x];
   __syncthreads();
   // the elementwise phases (init and B) use the equal-rows partition: their cost is per row, while the product's
   // partition balances rows against incidence entries
@@ -949,7 +977,14 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
         d.part_s[kPartials * g + 2] = acc[2];
       }
     }
-    if (!grid_barrier(d, [&] { pcg_decide(d, k_iter); })) return;
+    {  // the update phase's rows into L2 while the grid waits for the slowest product and the decision
+      const size_t u0 = d.useg_row[useg0], nu = d.useg_row[useg1] - u0;
+      T* vecs[6] = {Z, W, P, S, X, R};
+#pragma unroll
+      for (int v = 0; v < 6; ++v) prefetch_l2(vecs[v] + 6 * u0, 6 * sizeof(T) * nu);
+      prefetch_l2(Dinv + kDiagStride * u0, kDiagStride * sizeof(T) * nu);
+    }
+    if (!grid_barrier(d, [&] { pcg_decide(d, k_iter, sseg_ok ? s_sseg : nullptr); })) return;
     if (__ldcg(&d.cnt->n_active) == 0 || __ldcg(&d.cnt->timeout)) break;
     // ---- B: p = z + beta p, s = w + beta s, x += alpha p, r -= alpha s, z = M^-1 r
     for (int g = useg0; g < useg1; ++g) {
@@ -975,6 +1010,10 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
         store6<T>(Z, i, zn);
       }
     }
+    // the next product's own-row data (diagonal blocks, z, r) into L2 while the grid waits
+    prefetch_l2(Dm + kDiagStride * (size_t)R0, kDiagStride * sizeof(T) * (size_t)(R1 - R0));
+    prefetch_l2(Z + 6 * (size_t)R0, 6 * sizeof(T) * (size_t)(R1 - R0));
+    prefetch_l2(R + 6 * (size_t)R0, 6 * sizeof(T) * (size_t)(R1 - R0));
     if (!grid_barrier(d, [] {})) return;
   }
 }
@@ -1021,7 +1060,7 @@ __global__ void k_scene_reduce(DevArrays d, int mode, unsigned long long cond) {
     } else if (mode == RED_GDX) {
       if (!c->newton_active) continue;
       c->gdx = v;
-      c->use_neg_grad = !(v < 0.0);
+      c->use_neg_grad = d.first_order || !(v < 0.0);  // first order (Alg. 1): always -grad f
       c->ls_alpha = 1.0;
       c->ls_state = 0;
       c->pad1 = 0;  // halvings in this line search
@@ -1251,6 +1290,68 @@ __global__ void k_finish(DevArrays d) {
   d.vq[i] = make_double4((q.x - q0.x) * idt, (q.y - q0.y) * idt, (q.z - q0.z) * idt, (q.w - q0.w) * idt);
   d.x0p[i] = p;
   d.x0q[i] = q;
+}
+
+// friction (Sec. 5.4, Friction; Alg. 3): explicit correction of the new velocities from the contacts active at the
+// committed state x_{n+1} (the ground, and the step's self-contact candidates that overlap), Jacobi style: every
+// particle reads the uncorrected velocities and writes its corrected ones to the trial arrays
+__device__ __forceinline__ V3<double> ang_vel(double4 q, double4 u) {  // q' = 1/2 (w, 0) (x) q
+  Q4<double> t = qmul(Q4<double>{u.x, u.y, u.z, u.w}, qconj(to_q(q)));
+  return {2.0 * t.x, 2.0 * t.y, 2.0 * t.z};
+}
+
+__device__ __forceinline__ void friction_term(const DevArrays& d, double fn, V3<double> n, V3<double> vij,
+                                              V3<double> wij, double m, double r, V3<double>& dv, V3<double>& dw) {
+  V3<double> vt = vij - dot(vij, n) * n;
+  double nvt = sqrt(dot(vt, vt)), nw = sqrt(dot(wij, wij));
+  if (nvt > 0.0) dv = dv - fmin(1.0, d.mu_slide * fn * d.dt / (m * nvt)) * vt;
+  if (nw > 0.0) dw = dw - fmin(1.0, d.mu_roll * fn * r * r * r * d.dt / (0.4 * m * r * r * nw)) * wij;
+}
+
+// the correction d along x only, limited to bring x to rest at most
+__device__ __forceinline__ V3<double> slow_only(V3<double> x, V3<double> dd) {
+  double nx = sqrt(dot(x, x));
+  if (!(nx > 0.0)) return {0.0, 0.0, 0.0};
+  double s = fmax(-nx, fmin(0.0, dot(dd, x) / nx));
+  return (s / nx) * x;
+}
+
+__global__ void k_friction(DevArrays d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n || step_aborted(d)) return;
+  double4 v4 = d.vp[i], u4 = d.vq[i];
+  d.tp[i] = v4;
+  d.tq[i] = u4;
+  if (d.kin[i]) return;
+  double4 p = d.x0p[i], q = d.x0q[i];
+  double m = d.hp[i].w, r = p.w;
+  V3<double> vi = to_v(v4), wi = ang_vel(q, u4), dv = {0.0, 0.0, 0.0}, dw = {0.0, 0.0, 0.0};
+  if (d.k_ground > 0.0) {
+    double g = p.z - d.ground_z - r;
+    if (g < 0.0) friction_term(d, d.k_ground * fabs(g), V3<double>{0.0, 0.0, 1.0}, vi, wi, m, r, dv, dw);
+  }
+  if (d.k_self > 0.0)
+    for (int e = d.c_start[i]; e < d.c_start[i + 1]; ++e) {
+      int j = d.c_nbr[e];
+      double4 pj = d.x0p[j];
+      V3<double> ev = to_v(p) - to_v(pj);
+      double dist = sqrt(dot(ev, ev)), R = r + pj.w;
+      if (!(dist < R)) continue;
+      friction_term(d, d.k_self * fabs(dist - R), (1.0 / dist) * ev, vi - to_v(d.vp[j]),
+                    wi - ang_vel(d.x0q[j], d.vq[j]), m, r, dv, dw);
+    }
+  dv = slow_only(vi, dv);
+  dw = slow_only(wi, dw);
+  Q4<double> du = qmul(Q4<double>{dw.x, dw.y, dw.z, 0.0}, to_q(q));
+  d.tp[i] = make_double4(v4.x + dv.x, v4.y + dv.y, v4.z + dv.z, v4.w);
+  d.tq[i] = make_double4(u4.x + 0.5 * du.x, u4.y + 0.5 * du.y, u4.z + 0.5 * du.z, u4.w + 0.5 * du.w);
+}
+
+__global__ void k_friction_commit(DevArrays d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n || step_aborted(d)) return;
+  d.vp[i] = d.tp[i];
+  d.vq[i] = d.tq[i];
 }
 
 __global__ void k_fracture(DevArrays d) {
@@ -1551,6 +1652,11 @@ int launch_ls_commit(const DevArrays& d, cudaStream_t s) {
 int launch_finish(const DevArrays& d, cudaStream_t s) {
   int k = 0;
   if (d.n) { k_finish<<<blocks_for(d.n, 256), 256, 0, s>>>(d); ++k; }
+  if (d.n && (d.mu_slide > 0.0 || d.mu_roll > 0.0)) {
+    k_friction<<<blocks_for(d.n, 128), 128, 0, s>>>(d);
+    k_friction_commit<<<blocks_for(d.n, 256), 256, 0, s>>>(d);
+    k += 2;
+  }
   if (d.nb) { k_fracture<<<blocks_for(d.nb, 256), 256, 0, s>>>(d); ++k; }
   return k;
 }
