@@ -36,6 +36,12 @@ WORKLOAD = ("ceramic plate fracture: HCP disk R=0.284 m, 3 layers, r=1 mm, bonds
             "E=5e9 Pa, nu=0.3, rho=2500, break strain 1e-3, dropped at 3 m/s tilted 10 deg, ground and self "
             "penalty contact k=E*r, dt=5e-4 s, Newton tol 1e-6 relative")
 SAMPLE_R = 0.02  # radius of the bounded CPU sample of the same plate construction
+OTHER_WORKLOADS = {  # extra measurement lines (not the benchmark's workload), selected with --workload
+    "batched": "64 independent Poisson-disk boxes, 2K-50K particles each (log-uniform, seed 4), r=2 mm, bonds within "
+               "1.1*2r, drops 0.1-1 m, E=1e8 Pa, break strain 2e-3, ground and self contact k=E*r, dt=1e-3 s",
+    "impact": "1M-particle Poisson-disk slab (r=2 mm, bond cutoff for mean degree 12, E=1e9 Pa, break strain 1e-3) hit "
+              "by a 2,000-particle unbreakable ball (E=1e10 Pa) at 20 m/s, ground and self contact, dt=2e-4 s",
+}
 
 
 # ------------------------------------------------------------------------------------------------
@@ -286,6 +292,8 @@ def main():
     ap.add_argument("--pcg-blocks", type=int, default=0, help="PCG grid size with --pcg-lanes (0: all resident)")
     ap.add_argument("--pcg-probe", type=int, default=0,
                     help="time N PCG iterations of one solve (eps 0) on the workload's system and exit (profiling)")
+    ap.add_argument("--workload", default="plate", choices=["plate", "batched", "impact"],
+                    help="plate: the benchmark workload; batched / impact: extra measurement lines")
     ap.add_argument("--radius", type=float, default=0.284,
                     help="plate radius; anything but 0.284 m is a smaller profiling case, not the benchmark workload")
     args = ap.parse_args()
@@ -311,7 +319,12 @@ def main():
     torch.cuda.set_device(local)
     bmod.build()
     pkg.load()
-    sc = scenes.c2_plate(R=args.radius)
+    if args.workload == "batched":
+        sc = scenes.c4_batched()
+    elif args.workload == "impact":
+        sc = scenes.c5_impact()
+    else:
+        sc = scenes.c2_plate(R=args.radius)
 
     # ---- FP32-mixed path, inputs resident ----
     sim = pkg.Sim(sc, precision=pkg.BDEM_MIXED)
@@ -344,14 +357,19 @@ def main():
     same_work = all(a[k]["newton_iters"] == b[k]["newton_iters"] and a[k]["pcg_iters"] == b[k]["pcg_iters"]
                     for a, b in zip(run["stats"], rrun["stats"]) for k in range(len(sizes)))
     prof = rrun["prof"]
-    intact = min(int(st[0]["intact_bonds"]) for st in rrun["stats"])
     pcg_launches = max(prof["intervals"]["pcg"], 1)
     pcg_iters_launch = prof["pcg_iters"] / pcg_launches
     pcg_ms_launch = prof["ms"]["pcg"] / pcg_launches
-    act_pcg = sum(int(st[0]["contact_entry_pcg_iters"]) for st in rrun["stats"])
-    bytes_iter = pcg_bytes_per_iter(sc.n, intact, 0, 4)
-    bytes_launch = (bytes_iter * prof["pcg_iters"] + act_pcg * (4 + 4 * 4)) / pcg_launches + \
-        pcg_bytes_per_launch_fixed(sc.n, sc.nb)
+    # per scene and step: its PCG iterations x its bytes per iteration (intact bonds after the step: a lower bound
+    # of the bonds in its systems), plus the active contact entries actually in the systems
+    alg = 0.0
+    for st in rrun["stats"]:
+        for k in range(len(sizes)):
+            alg += int(st[k]["pcg_iters"]) * pcg_bytes_per_iter(int(sizes[k]), int(st[k]["intact_bonds"]), 0, 4)
+            alg += int(st[k]["contact_entry_pcg_iters"]) * (4 + 4 * 4)
+    bytes_launch = alg / pcg_launches + pcg_bytes_per_launch_fixed(sc.n, sc.nb)
+    bytes_iter = pcg_bytes_per_iter(sc.n, sum(int(rrun["stats"][-1][k]["intact_bonds"]) for k in range(len(sizes))),
+                                    0, 4)
     achieved = bytes_launch / (pcg_ms_launch * 1e-3) / 1e9
     peaks, peak_kind = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -397,7 +415,7 @@ def main():
         sim64.close()
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "plate":
         import oracle
         oracle.build()
         rate, secs, npart, its = oracle_sample_rate(1)
@@ -410,7 +428,9 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.radius == 0.284 else f"profiling case R={args.radius} m",
+            "config": {"workload": (OTHER_WORKLOADS[args.workload] if args.workload != "plate" else
+                                    WORKLOAD if args.radius == 0.284 else f"profiling case R={args.radius} m"),
+                       "n_scenes": sc.n_scenes,
                        "precision": "FP32-mixed (f32 Hessian/PCG, f64 gradient/reductions/state)",
                        "n_particles": sc.n, "n_bonds": sc.nb, "replicas": world,
                        "l2": "working set of every timed stage exceeds the 129 MB L2; no flush between steps"},
