@@ -91,11 +91,22 @@ __device__ __forceinline__ Vec6<double> load6_cg<double>(const double* base, int
   return Vec6<double>{{a.x, a.y, b.x, b.y, c.x, c.y}};
 }
 
+// 6-word row stores as three 8-byte (FP32) or 16-byte (FP64) stores: rows start at 24 B / 48 B multiples
 template <typename T>
-__device__ __forceinline__ void store6(T* base, int i, const T (&v)[6]) {
-  T* p = base + 6 * (size_t)i;
-#pragma unroll
-  for (int k = 0; k < 6; ++k) p[k] = v[k];
+__device__ __forceinline__ void store6(T* base, int i, const T (&v)[6]);
+template <>
+__device__ __forceinline__ void store6<float>(float* base, int i, const float (&v)[6]) {
+  float2* p = reinterpret_cast<float2*>(base + 6 * (size_t)i);
+  p[0] = make_float2(v[0], v[1]);
+  p[1] = make_float2(v[2], v[3]);
+  p[2] = make_float2(v[4], v[5]);
+}
+template <>
+__device__ __forceinline__ void store6<double>(double* base, int i, const double (&v)[6]) {
+  double2* p = reinterpret_cast<double2*>(base + 6 * (size_t)i);
+  p[0] = make_double2(v[0], v[1]);
+  p[1] = make_double2(v[2], v[3]);
+  p[2] = make_double2(v[4], v[5]);
 }
 
 template <typename T>
@@ -741,36 +752,105 @@ __device__ __forceinline__ PcgPrev load_prev(const SceneCtl* c) {
           __ldcg(&c->bnorm), __ldcg(&c->rz), __ldcg(&c->alpha)};
 }
 
-// the PCG decision of one scene from its reduced dots (run by a single thread): convergence test, then the
-// Chronopoulos-Gear step lengths; returns whether the scene keeps iterating
-__device__ bool pcg_decide_scene(const DevArrays& d, SceneCtl* c, PcgPrev pv, double gam, double del, double rho,
-                                 int k_iter) {
-  if (!pv.newton_active) return false;
+// the PCG decision of one scene from its reduced dots: convergence test, then the Chronopoulos-Gear step lengths.
+// Updates the scene's solver state in place and returns whether the scene keeps iterating.
+struct PcgState {
+  int newton_active, pcg_active, it;
+  double eps_r, bnorm, rz, alpha, beta, pq;
+};
+__device__ bool pcg_decision(PcgState& s, double gam, double del, double rho, int k_iter, int pcg_max) {
+  if (!s.newton_active) return false;
   if (k_iter == 0) {
-    pv.bnorm = sqrt(rho);
-    pv.it = 0;
-    pv.pcg_active = 1;
-    c->bnorm = pv.bnorm;
-    c->pcg_iters = 0;
-    c->pcg_active = 1;
+    s.bnorm = sqrt(rho);
+    s.it = 0;
+    s.pcg_active = 1;
   }
-  if (!pv.pcg_active) return false;
-  bool stop = !(sqrt(rho) > pv.eps_r * pv.bnorm) || pv.it >= d.pcg_max;
+  if (!s.pcg_active) return false;
+  bool stop = !(sqrt(rho) > s.eps_r * s.bnorm) || s.it >= pcg_max;
   if (!stop) {
-    double beta = (pv.it == 0) ? 0.0 : gam / pv.rz;
-    double den = (pv.it == 0) ? del : del - beta * gam / pv.alpha;
+    double beta = (s.it == 0) ? 0.0 : gam / s.rz;
+    double den = (s.it == 0) ? del : del - beta * gam / s.alpha;
     if (!(den > 0.0) || !(gam > 0.0)) {
       stop = true;  // breakdown: no further decrease along this Krylov space
     } else {
-      c->beta = beta;
-      c->alpha = gam / den;
-      c->rz = gam;
-      c->pq = den;
-      c->pcg_iters = pv.it + 1;
+      s.beta = beta;
+      s.alpha = gam / den;
+      s.rz = gam;
+      s.pq = den;
+      s.it += 1;
     }
   }
-  if (stop) c->pcg_active = 0;
+  if (stop) s.pcg_active = 0;
   return !stop;
+}
+
+__device__ __forceinline__ void store_pcg_state(SceneCtl* c, const PcgState& s) {
+  c->bnorm = s.bnorm;
+  c->pcg_iters = s.it;
+  c->pcg_active = s.pcg_active;
+  c->alpha = s.alpha;
+  c->beta = s.beta;
+  c->rz = s.rz;
+  c->pq = s.pq;
+}
+
+// the decision of one scene whose solver state lives in its control block (run by a single thread)
+__device__ bool pcg_decide_scene(const DevArrays& d, SceneCtl* c, PcgPrev pv, double gam, double del, double rho,
+                                 int k_iter) {
+  PcgState s = {pv.newton_active, pv.pcg_active, pv.it, pv.eps_r, pv.bnorm, pv.rz, pv.alpha, 0.0, 0.0};
+  if (!s.newton_active) return false;
+  double beta0 = __ldcg(&c->beta), pq0 = __ldcg(&c->pq);
+  s.beta = beta0;
+  s.pq = pq0;
+  bool go = pcg_decision(s, gam, del, rho, k_iter, d.pcg_max);
+  store_pcg_state(c, s);
+  return go;
+}
+
+// few scenes: every block sums every scene's partial dots in the same fixed order and takes the same decision
+// with its own copy of the solver state, so the grid needs only a plain barrier (no decision inside it, no
+// control-block reads after it); block 0 keeps the control blocks current for the host
+constexpr int kLocalScenes = 4;
+struct LocalPcg {
+  PcgState st[kLocalScenes];
+  double acc[3][kTile / 32];
+  int n_active;
+};
+
+__device__ void pcg_decide_local(const DevArrays& d, int k_iter, const int* ss, LocalPcg& L) {
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  int active = 0;
+  for (int s = 0; s < d.n_scenes; ++s) {
+    int a = ss[s], b = ss[s + 1];
+    double gam = 0.0, del = 0.0, rho = 0.0;
+    for (int t = a + threadIdx.x; t < b; t += blockDim.x) {
+      gam += __ldcg(d.part_s + kPartials * t);
+      del += __ldcg(d.part_s + kPartials * t + 1);
+      rho += __ldcg(d.part_s + kPartials * t + 2);
+    }
+    gam = warp_sum(gam);
+    del = warp_sum(del);
+    rho = warp_sum(rho);
+    if (lane == 0) {
+      L.acc[0][warp] = gam;
+      L.acc[1][warp] = del;
+      L.acc[2][warp] = rho;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double G = 0.0, D = 0.0, R = 0.0;
+      for (int w = 0; w < nw; ++w) {
+        G += L.acc[0][w];
+        D += L.acc[1][w];
+        R += L.acc[2][w];
+      }
+      if (pcg_decision(L.st[s], G, D, R, k_iter, d.pcg_max)) ++active;
+      if (blockIdx.x == 0) store_pcg_state(d.sc + s, L.st[s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) L.n_active = active;
+  __syncthreads();
 }
 
 constexpr int kBlockScene = 64;  // scenes with more PCG segments than this are reduced by the whole block
@@ -883,6 +963,12 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
   const bool sseg_ok = d.n_scenes <= kTile;
   if (sseg_ok)
     for (int x = threadIdx.x; x <= d.n_scenes; x += blockDim.x) s_sseg[x] = d.scene_seg[x];
+  __shared__ LocalPcg s_loc;
+  const bool local = d.n_scenes <= kLocalScenes;
+  if (local && threadIdx.x < d.n_scenes) {
+    const SceneCtl* c = d.sc + threadIdx.x;
+    s_loc.st[threadIdx.x] = PcgState{c->newton_active, c->newton_active, 0, c->eps_r, 0.0, 0.0, 0.0, 0.0, 0.0};
+  }
   __syncthreads();
   // the elementwise phases (init and B) use the equal-rows partition: their cost is per row, while the product's
   // partition balances rows against incidence entries
@@ -919,7 +1005,8 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
     // ---- A: w = H z, gamma = r.z, delta = w.z, rho = r.r (per segment, deterministic)
     for (int g = seg0; g < seg1; ++g) {
       int sc = d.seg_scene[g];
-      bool act = d.sc[sc].newton_active && (k_iter == 0 || __ldcg(&d.sc[sc].pcg_active));
+      bool act = local ? s_loc.st[sc].pcg_active != 0
+                       : d.sc[sc].newton_active && (k_iter == 0 || __ldcg(&d.sc[sc].pcg_active));
       DotAcc<T> dg, dd, dr;
       if (act) {
         int r0 = d.seg_row[g], r1 = d.seg_row[g + 1];
@@ -984,13 +1071,27 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
       for (int v = 0; v < 6; ++v) prefetch_l2(vecs[v] + 6 * u0, 6 * sizeof(T) * nu);
       prefetch_l2(Dinv + kDiagStride * u0, kDiagStride * sizeof(T) * nu);
     }
-    if (!grid_barrier(d, [&] { pcg_decide(d, k_iter, sseg_ok ? s_sseg : nullptr); })) return;
-    if (__ldcg(&d.cnt->n_active) == 0 || __ldcg(&d.cnt->timeout)) break;
+    if (local) {
+      if (!grid_barrier(d, [] {})) return;
+      pcg_decide_local(d, k_iter, s_sseg, s_loc);
+      if (s_loc.n_active == 0 || __ldcg(&d.cnt->timeout)) break;
+    } else {
+      if (!grid_barrier(d, [&] { pcg_decide(d, k_iter, sseg_ok ? s_sseg : nullptr); })) return;
+      if (__ldcg(&d.cnt->n_active) == 0 || __ldcg(&d.cnt->timeout)) break;
+    }
     // ---- B: p = z + beta p, s = w + beta s, x += alpha p, r -= alpha s, z = M^-1 r
     for (int g = useg0; g < useg1; ++g) {
       int sc = d.useg_scene[g];
-      if (!d.sc[sc].newton_active || !__ldcg(&d.sc[sc].pcg_active)) continue;
-      T al = (T)__ldcg(&d.sc[sc].alpha), be = (T)__ldcg(&d.sc[sc].beta);
+      T al, be;
+      if (local) {
+        if (!s_loc.st[sc].pcg_active) continue;
+        al = (T)s_loc.st[sc].alpha;
+        be = (T)s_loc.st[sc].beta;
+      } else {
+        if (!d.sc[sc].newton_active || !__ldcg(&d.sc[sc].pcg_active)) continue;
+        al = (T)__ldcg(&d.sc[sc].alpha);
+        be = (T)__ldcg(&d.sc[sc].beta);
+      }
       for (int i = d.useg_row[g] + threadIdx.x; i < d.useg_row[g + 1]; i += blockDim.x) {
         Vec6<T> z = load6_cg<T>(Z, i), w = load6_cg<T>(W, i), p = load6_cg<T>(P, i), s = load6_cg<T>(S, i);
         Vec6<T> x = load6_cg<T>(X, i), r = load6_cg<T>(R, i);
