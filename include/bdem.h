@@ -212,6 +212,7 @@ int64_t bdem_launch_count(const bdem_sim* sim);
  * bit-identical runs. */
 bdem_status bdem_set_pcg_shape(bdem_sim* sim, int32_t lanes_per_row, int32_t blocks);
 
+
 /* Times the PCG kernel for `iters` iterations on the system at the current committed state for each candidate shape
  * (lanes 1, 2, 4, 8 x 1..all co-resident blocks per SM), keeps the fastest, and reports it (either pointer may be
  * NULL). Host-blocking. */

@@ -413,7 +413,9 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
 
 // default PCG launch shape: 4 lanes per row, every co-resident block, at least 64 rows per block
 // co-resident PCG blocks as the registers allow (the partition's shared memory is checked in apply_pcg_shape)
-static int pcg_blocks_by_regs(const bdem_sim* s, int lanes) { return pcg_max_blocks(s->d.mixed, lanes, 1024); }
+static int pcg_blocks_by_regs(const bdem_sim* s, int lanes) {
+  return pcg_max_blocks(s->d.mixed, lanes, 1024);
+}
 
 // builds the partition for (lanes, grid) and shrinks the grid until every block is co-resident with the partition's
 // actual shared-memory need (a cooperative launch requires it)

@@ -39,7 +39,7 @@ constexpr int kDiagStride = 24; // words per stored 6x6 symmetric block (21 used
 struct SceneCtl {
   double g0, gnorm, eps_r, bnorm;
   double rz, pq, alpha, beta;
-  double dphi, ls_alpha, gdx, pad0;
+  double dphi, ls_alpha, gdx, pcg_thr2;  // pcg_thr2: (eps_r |b|)^2 of the current solve
   long long act_cur;            // active self-contact matrix entries of the current Newton system
   long long act_pcg;            // sum over this step's solves of act_cur x PCG iterations
   long long intact;             // intact bonds after the step's fracture test

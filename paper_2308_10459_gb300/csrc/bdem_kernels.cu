@@ -745,31 +745,42 @@ __device__ __forceinline__ double scene_partial(const DevArrays& d, int s, int k
 // them since this SM last cached them) and issued before the partial dots so that both loads overlap
 struct PcgPrev {
   int newton_active, pcg_active, it;
-  double eps_r, bnorm, rz, alpha;
+  double eps_r, bnorm, rz, alpha, beta, pq, thr2;
 };
 __device__ __forceinline__ PcgPrev load_prev(const SceneCtl* c) {
   return {__ldcg(&c->newton_active), __ldcg(&c->pcg_active), __ldcg(&c->pcg_iters), __ldcg(&c->eps_r),
-          __ldcg(&c->bnorm), __ldcg(&c->rz), __ldcg(&c->alpha)};
+          __ldcg(&c->bnorm), __ldcg(&c->rz), __ldcg(&c->alpha), __ldcg(&c->beta), __ldcg(&c->pq),
+          __ldcg(&c->pcg_thr2)};
 }
 
 // the PCG decision of one scene from its reduced dots: convergence test, then the Chronopoulos-Gear step lengths.
 // Updates the scene's solver state in place and returns whether the scene keeps iterating.
+// FP64 division and square root are long dependent sequences on this part, so the decision keeps them off its
+// critical path: the stopping test compares squares (|r| <= eps_r |b| as rho <= eps_r^2 |b|^2), and the
+// reciprocals of the previous gamma and alpha (needed for beta and for the denominator) are taken when the state is
+// loaded, while the block still waits for the partial dots; one division (alpha) remains on the path.
 struct PcgState {
   int newton_active, pcg_active, it;
   double eps_r, bnorm, rz, alpha, beta, pq;
+  double thr2, inv_rz, inv_alpha;  // (eps_r |b|)^2; 1 / previous gamma; 1 / previous alpha
 };
+__device__ __forceinline__ void pcg_prepare(PcgState& s) {
+  s.inv_rz = s.it > 0 ? 1.0 / s.rz : 0.0;
+  s.inv_alpha = s.it > 0 ? s.pq * s.inv_rz : 0.0;  // 1 / alpha = den / gamma
+}
 __device__ bool pcg_decision(PcgState& s, double gam, double del, double rho, int k_iter, int pcg_max) {
   if (!s.newton_active) return false;
   if (k_iter == 0) {
+    s.thr2 = s.eps_r * s.eps_r * rho;
     s.bnorm = sqrt(rho);
     s.it = 0;
     s.pcg_active = 1;
   }
   if (!s.pcg_active) return false;
-  bool stop = !(sqrt(rho) > s.eps_r * s.bnorm) || s.it >= pcg_max;
+  bool stop = !(rho > s.thr2) || s.it >= pcg_max;
   if (!stop) {
-    double beta = (s.it == 0) ? 0.0 : gam / s.rz;
-    double den = (s.it == 0) ? del : del - beta * gam / s.alpha;
+    double beta = (s.it == 0) ? 0.0 : gam * s.inv_rz;
+    double den = (s.it == 0) ? del : del - beta * gam * s.inv_alpha;
     if (!(den > 0.0) || !(gam > 0.0)) {
       stop = true;  // breakdown: no further decrease along this Krylov space
     } else {
@@ -786,6 +797,7 @@ __device__ bool pcg_decision(PcgState& s, double gam, double del, double rho, in
 
 __device__ __forceinline__ void store_pcg_state(SceneCtl* c, const PcgState& s) {
   c->bnorm = s.bnorm;
+  c->pcg_thr2 = s.thr2;
   c->pcg_iters = s.it;
   c->pcg_active = s.pcg_active;
   c->alpha = s.alpha;
@@ -797,11 +809,10 @@ __device__ __forceinline__ void store_pcg_state(SceneCtl* c, const PcgState& s) 
 // the decision of one scene whose solver state lives in its control block (run by a single thread)
 __device__ bool pcg_decide_scene(const DevArrays& d, SceneCtl* c, PcgPrev pv, double gam, double del, double rho,
                                  int k_iter) {
-  PcgState s = {pv.newton_active, pv.pcg_active, pv.it, pv.eps_r, pv.bnorm, pv.rz, pv.alpha, 0.0, 0.0};
+  PcgState s = {pv.newton_active, pv.pcg_active, pv.it, pv.eps_r, pv.bnorm, pv.rz, pv.alpha, pv.beta, pv.pq,
+                pv.thr2, 0.0, 0.0};
   if (!s.newton_active) return false;
-  double beta0 = __ldcg(&c->beta), pq0 = __ldcg(&c->pq);
-  s.beta = beta0;
-  s.pq = pq0;
+  pcg_prepare(s);
   bool go = pcg_decision(s, gam, del, rho, k_iter, d.pcg_max);
   store_pcg_state(c, s);
   return go;
@@ -820,6 +831,7 @@ struct LocalPcg {
 __device__ void pcg_decide_local(const DevArrays& d, int k_iter, const int* ss, LocalPcg& L) {
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   int active = 0;
+  if (threadIdx.x < d.n_scenes) pcg_prepare(L.st[threadIdx.x]);  // overlaps the partial loads below
   for (int s = 0; s < d.n_scenes; ++s) {
     int a = ss[s], b = ss[s + 1];
     double gam = 0.0, del = 0.0, rho = 0.0;
@@ -967,7 +979,8 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
   const bool local = d.n_scenes <= kLocalScenes;
   if (local && threadIdx.x < d.n_scenes) {
     const SceneCtl* c = d.sc + threadIdx.x;
-    s_loc.st[threadIdx.x] = PcgState{c->newton_active, c->newton_active, 0, c->eps_r, 0.0, 0.0, 0.0, 0.0, 0.0};
+    s_loc.st[threadIdx.x] = PcgState{c->newton_active, c->newton_active, 0, c->eps_r, 0.0, 0.0, 0.0, 0.0, 0.0,
+                                     0.0, 0.0, 0.0};
   }
   __syncthreads();
   // the elementwise phases (init and B) use the equal-rows partition: their cost is per row, while the product's
