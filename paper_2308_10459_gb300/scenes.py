@@ -288,12 +288,12 @@ def poisson_ball(n_target, r, R, rng):
 
 
 def c4_batched(n_scenes=64, n_min=2000, n_max=50000, r=2e-3, E=1e8, nu=0.3, density=2500.0, break_strain=2e-3,
-               cutoff_factor=1.1, dt=1e-3, steps=200, seed=4, name=None) -> Scene:
+               cutoff_factor=1.1, dt=1e-3, steps=200, seed=4, heights=(0.1, 1.0), name=None) -> Scene:
     """Independent Poisson-disk boxes with log-uniform particle counts and drop heights U[0.1, 1] m; each
     scene has its own ground contact and no contact across scenes."""
     rng = np.random.default_rng(seed)
     counts = np.exp(rng.uniform(math.log(n_min), math.log(n_max), n_scenes)).astype(int)
-    heights = rng.uniform(0.1, 1.0, n_scenes)
+    heights = rng.uniform(heights[0], heights[1], n_scenes)
     pos_all, pairs_all, offsets = [], [], [0]
     for s in range(n_scenes):
         pts, ext = poisson_box(int(counts[s]), r, rng)
