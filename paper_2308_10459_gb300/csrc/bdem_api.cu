@@ -1497,7 +1497,9 @@ extern "C" bdem_status bdem_autotune_pcg(bdem_sim* s, int32_t iters, int32_t* la
   for (int lanes : lanes_c) {
     int mx = pcg_blocks_by_regs(s, lanes);
     for (int per = 1; per <= std::max(1, mx / sms); ++per) {
-      TRY(bdem_set_pcg_shape(s, lanes, per * sms));
+      bdem_status sst = bdem_set_pcg_shape(s, lanes, per * sms);
+      if (sst == BDEM_E_INVALID) continue;  // the block row ranges do not fit this shape's shared memory
+      if (sst != BDEM_OK) return sst;
       DevArrays d = s->d;
       d.pcg_max = iters;
       float t_min = 1e30f;

@@ -1,0 +1,63 @@
+"""Writes newton_spread.json: how far the oracle's own trajectory moves when its Newton tolerance is tightened 100x.
+
+A Newton solve stopped at |g| <= tol |g_0| pins the state down only to the scene's sensitivity to that stopping
+test; two correct solvers that round differently can land that far apart. For each case of the per-configuration
+parity report whose FP64 agreement is limited by it, this runs the oracle (and nothing else) at the case's tolerance
+and at 1/100 of it and records the
+largest position difference (relative to the bounding-box diagonal) and quaternion difference over the steps.
+
+    python tests/golden/make_newton_spread.py
+"""
+import json
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+import oracle  # noqa: E402
+from paper_2308_10459_gb300 import scenes  # noqa: E402
+
+# the cases whose FP64 agreement with the oracle is limited by this spread rather than by rounding (the cube and
+# plate cases agree to 1e-12, far inside the 1e-9 bound; the textile's bound is derived where it is tested, since
+# tightening its tolerance changes its break set)
+CASES = {
+    "c4": (lambda: scenes.c4_batched(n_scenes=3, n_min=150, n_max=400, heights=(0.0002, 0.001)), 25, 1e-6),
+    "c5": (lambda: scenes.c5_impact(n_slab=600, n_ball=80, footprint=0.035, ball_R=0.008), 3, 1e-6),
+}
+
+
+def qerr(a, b):
+    return float(np.minimum(np.abs(a - b).max(1), np.abs(a + b).max(1)).max()) if len(a) else 0.0
+
+
+def spread(make, steps, tol):
+    sc = make()
+    L = float(np.linalg.norm(sc.pos.max(0) - sc.pos.min(0)))
+    runs = []
+    for t in (tol, tol / 100.0):
+        o = oracle.OracleSim(sc, dict(newton_rel_tol=t))
+        states = []
+        for _ in range(steps):
+            o.step(1)
+            states.append(o.state())
+        runs.append(states)
+    ep = max(float(np.abs(a["pos"] - b["pos"]).max()) / L for a, b in zip(*runs))
+    eq = max(qerr(a["quat"], b["quat"]) for a, b in zip(*runs))
+    return ep, eq
+
+
+def main():
+    oracle.build()
+    out = {}
+    for name, (make, steps, tol) in CASES.items():
+        ep, eq = spread(make, steps, tol)
+        out[name] = {"steps": steps, "newton_rel_tol": tol, "pos": ep, "quat": eq}
+        print(name, out[name], flush=True)
+    with open(os.path.join(HERE, "newton_spread.json"), "w") as f:
+        json.dump(out, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()
