@@ -194,6 +194,11 @@ bdem_status bdem_debug_bonds(bdem_sim* sim, int64_t count, const int32_t* ids, d
  * included, evaluated as if intact). */
 bdem_status bdem_debug_bond_stress(bdem_sim* sim, double* out);
 
+/* Runs one device-side wait on a word that nothing writes, with a time limit of limit_ms (0..10000) instead of the
+ * 2 s every wait of the library uses: the wait gives up, sets the device's timeout flag, and the call returns
+ * BDEM_E_TIMEOUT as a step would (the simulation stays usable). For testing the failure path without a GPU fault. */
+bdem_status bdem_debug_wait_timeout(bdem_sim* sim, double limit_ms);
+
 /* y = H x with the system of the last bdem_debug_system call; x, y host [n][6]. */
 bdem_status bdem_debug_matvec(bdem_sim* sim, const double* x, double* y);
 

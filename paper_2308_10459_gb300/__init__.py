@@ -78,6 +78,7 @@ _PROTOS = {
     "bdem_debug_matvec": (ctypes.c_int, [_vp, _dp, _dp]),
     "bdem_debug_bonds": (ctypes.c_int, [_vp, ctypes.c_int64, _ip, _dp]),
     "bdem_debug_bond_stress": (ctypes.c_int, [_vp, _dp]),
+    "bdem_debug_wait_timeout": (ctypes.c_int, [_vp, ctypes.c_double]),
     "bdem_debug_pcg": (ctypes.c_int, [_vp, _dp, ctypes.c_double, ctypes.c_int32, _dp, _ip]),
     "bdem_launch_count": (ctypes.c_int64, [_vp]),
     "bdem_set_step_graph": (ctypes.c_int, [_vp, ctypes.c_int32]),
@@ -268,6 +269,10 @@ class Sim:
         out = np.zeros((max(nb, 1), 2))
         self._check(self.L.bdem_debug_bond_stress(self.h, _ptr(out, _dp)))
         return out[:nb]
+
+    def bdem_debug_wait_timeout(self, limit_ms):
+        """Status of a device wait that must run out after limit_ms (BDEM_E_TIMEOUT expected)."""
+        return int(self.L.bdem_debug_wait_timeout(self.h, float(limit_ms)))
 
     def bdem_debug_matvec(self, x):
         x = _arr(x, np.float64, (self.n, 6))

@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/bdem.h"
 #include "bdem_internal.h"
 
@@ -50,6 +52,7 @@ struct bdem_sim {
   std::vector<Pending> pending;
   cudaEvent_t ev_open = nullptr;
   int ph_open = -1;
+  bool nvtx_open = false;
   // captured step graph: one graph launch per step, the Newton and line-search loops run as conditional while
   // nodes decided on the device
   bool graph_enabled = true;
@@ -75,7 +78,14 @@ static cudaEvent_t ev_get(bdem_sim* s) {
   return e;
 }
 
+// phases of the host-driven step: an NVTX range each (for timeline tools), and CUDA events when timing is on
+static const char* const kPhaseName[BDEM_N_PHASES] = {"predict", "contact", "grad", "hess", "pcg", "linesearch",
+                                                      "finish"};
+
 static void phase_begin(bdem_sim* s, int ph) {
+  if (s->nvtx_open) nvtxRangePop();  // a phase left open by an early loop exit
+  nvtxRangePushA(kPhaseName[ph]);
+  s->nvtx_open = true;
   if (!s->prof_on) return;
   s->ev_open = ev_get(s);
   s->ph_open = ph;
@@ -83,6 +93,10 @@ static void phase_begin(bdem_sim* s, int ph) {
 }
 
 static void phase_end(bdem_sim* s) {
+  if (s->nvtx_open) {
+    nvtxRangePop();
+    s->nvtx_open = false;
+  }
   if (!s->prof_on || s->ph_open < 0) return;
   cudaEvent_t b = ev_get(s);
   cudaEventRecord(b, s->stream);
@@ -245,6 +259,9 @@ static bdem_status alloc_particles(bdem_sim* s) {
   while (hs < 2 * (int)n) hs <<= 1;
   d.hash_size = hs;
   size_t mx = std::max((size_t)hs, n);
+  TRY(dalloc_t(s, &d.pcg_grp, (size_t)kPcgMaxBlocks / kBarrierGroup));
+  TRY(dalloc_t(s, &d.pcg_bpart, (size_t)kPcgMaxBlocks * kPcgScenes * kPartials));
+  TRY(dalloc_t(s, &d.pcg_gpart, (size_t)kPcgMaxBlocks / kBarrierGroup * kPcgScenes * kPartials));
   TRY(dalloc_t(s, &d.c_start, n + 1));
   TRY(dalloc_t(s, &d.cell_key, n));
   TRY(dalloc_t(s, &d.hash_count, (size_t)hs));
@@ -333,6 +350,7 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
   DevArrays& d = s->d;
   int64_t n = s->n;
   if (grid < 1) grid = 1;
+  if (grid > kPcgMaxBlocks) grid = kPcgMaxBlocks;
   if (n > 0 && grid > n) grid = (int)n;
   std::vector<int32_t> seg_row, seg_scene, block_seg(grid + 1, 0), scene_seg(s->n_scenes + 1, 0);
   // block boundaries at equal cumulative work, a row weighing 4 + its bond count (the product's entries)
@@ -351,9 +369,14 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
     for (int64_t i = bounds[b]; i < bounds[b + 1]; ++i) ent += s->deg[i];
     max_ent = std::max(max_ent, ent);
   }
-  if (max_rows * (int64_t)sizeof(int4) + max_ent * (int64_t)sizeof(int2) > (int64_t)200 * 1024)
-    return fail(s, BDEM_E_INVALID, "PCG grid of %d blocks leaves %lld rows in one block; use more blocks", grid,
-                (long long)max_rows);
+  // the rows and entries are staged in shared memory when a block's share fits beside the other blocks of its SM
+  // (the grid's blocks per SM share 227 KB); otherwise they are read from L2 at every product
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t per_sm = std::max(1, (grid + sms - 1) / std::max(sms, 1));
+  const int64_t budget = std::min<int64_t>(200 * 1024, 227 * 1024 / per_sm - 4 * 1024);
+  const int staged = max_rows * (int64_t)sizeof(int4) + max_ent * (int64_t)sizeof(int2) <= budget;
   // cuts block row ranges at scene boundaries
   auto cut = [&](const std::vector<int64_t>& bnd, std::vector<int32_t>& row, std::vector<int32_t>& scn,
                  std::vector<int32_t>& blk) {
@@ -408,13 +431,14 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
   d.pcg_lanes = lanes;
   d.pcg_max_rows = (int32_t)std::max<int64_t>(max_rows, 1);
   d.pcg_max_entries = (int32_t)std::max<int64_t>(max_ent, 1);
+  d.pcg_staged = staged;
   return BDEM_OK;
 }
 
 // default PCG launch shape: 4 lanes per row, every co-resident block, at least 64 rows per block
 // co-resident PCG blocks as the registers allow (the partition's shared memory is checked in apply_pcg_shape)
 static int pcg_blocks_by_regs(const bdem_sim* s, int lanes) {
-  return pcg_max_blocks(s->d.mixed, lanes, 1024);
+  return pcg_max_blocks(s->d.mixed, lanes, 1024, 1);
 }
 
 // builds the partition for (lanes, grid) and shrinks the grid until every block is co-resident with the partition's
@@ -422,7 +446,7 @@ static int pcg_blocks_by_regs(const bdem_sim* s, int lanes) {
 static bdem_status apply_pcg_shape(bdem_sim* s, int lanes, int grid) {
   for (int tries = 0; tries < 16; ++tries) {
     TRY(build_pcg_segments(s, lanes, grid));
-    int mx = pcg_max_blocks(s->d.mixed, lanes, pcg_smem_bytes(s->d));
+    int mx = pcg_max_blocks(s->d.mixed, lanes, pcg_smem_bytes(s->d), s->d.pcg_staged);
     if (mx < 1) return fail(s, BDEM_E_CUDA, "no resident blocks for the PCG kernel");
     if (s->d.pcg_grid <= mx) return BDEM_OK;
     grid = mx;
@@ -517,6 +541,7 @@ extern "C" bdem_status bdem_create(const bdem_config* config, int32_t n_scenes, 
   d.k_self = c.k_self;
   d.skin = c.contact_skin;
   d.mu_slide = c.friction_slide;
+  d.wait_ns = 2000000000ull;  // 2 s
   d.first_order = c.optimizer == BDEM_OPT_FIRST_ORDER;
   d.mu_roll = c.friction_roll;
   double rmax = 0.0;
@@ -794,12 +819,20 @@ extern "C" bdem_status bdem_add_bonds(bdem_sim* s, int64_t n, const int32_t* I, 
 // step
 // ------------------------------------------------------------------------------------------------
 
+// clears the device counters and the PCG barrier's group counters after a step that did not complete (a wait
+// that gave up can leave a group partly counted in)
+static void reset_counters(bdem_sim* s, unsigned sync_gen) {
+  Counters z{};
+  z.sync_gen = sync_gen;
+  cudaMemcpy(s->d.cnt, &z, sizeof z, cudaMemcpyHostToDevice);
+  cudaMemset(s->d.pcg_grp, 0, sizeof(unsigned) * kPcgMaxBlocks / kBarrierGroup);
+}
+
 static bdem_status read_counters(bdem_sim* s, Counters* c) {
   CUDA_TRY(s, cudaMemcpyAsync(c, s->d.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s->stream));
   TRY(sync(s));
   if (c->timeout) {
-    Counters z{};
-    cudaMemcpy(s->d.cnt, &z, sizeof z, cudaMemcpyHostToDevice);
+    reset_counters(s, c->sync_gen);
     return fail(s, BDEM_E_TIMEOUT, "a device-side wait gave up; the step was rolled back");
   }
   return BDEM_OK;
@@ -861,8 +894,7 @@ static bdem_status do_step(bdem_sim* s, std::vector<SceneCtl>& ctl) {
     phase_end(s);
     TRY(read_counters(s, &c));
     if (c.nonfinite) {
-      Counters z{};
-      cudaMemcpy(d.cnt, &z, sizeof z, cudaMemcpyHostToDevice);
+      reset_counters(s, c.sync_gen);
       return fail(s, BDEM_E_NONFINITE, "the Newton residual became non-finite; the step was rolled back");
     }
     if (c.n_active == 0) break;
@@ -1055,9 +1087,7 @@ static bdem_status graph_step(bdem_sim* s, std::vector<SceneCtl>& ctl, bool* red
   s->launches += s->g_pre + (int64_t)std::max(0, c.loops_newton - 1) * s->g_body + (int64_t)c.ls_total * s->g_ls +
                  s->g_post;
   if (c.timeout || c.nonfinite || c.overflow || c.runaway) {
-    Counters z{};
-    z.sync_gen = c.sync_gen;
-    CUDA_TRY(s, cudaMemcpy(d.cnt, &z, sizeof z, cudaMemcpyHostToDevice));
+    reset_counters(s, c.sync_gen);
     if (c.timeout) return fail(s, BDEM_E_TIMEOUT, "a device-side wait gave up; the step was rolled back");
     if (c.nonfinite)
       return fail(s, BDEM_E_NONFINITE, "the Newton residual became non-finite; the step was rolled back");
@@ -1325,6 +1355,16 @@ extern "C" bdem_status bdem_debug_bond_stress(bdem_sim* s, double* out) {
   return sync(s);
 }
 
+extern "C" bdem_status bdem_debug_wait_timeout(bdem_sim* s, double limit_ms) {
+  if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
+  if (!(limit_ms >= 0.0) || !(limit_ms <= 10000.0)) return fail(s, BDEM_E_INVALID, "limit_ms must be in [0, 10000]");
+  DevArrays d = s->d;
+  d.wait_ns = (unsigned long long)(limit_ms * 1e6);
+  TRY(check_launch(s, launch_wait_test(d, s->stream)));
+  Counters c{};
+  return read_counters(s, &c);  // BDEM_E_TIMEOUT once the wait has given up; the counters are reset
+}
+
 extern "C" bdem_status bdem_debug_matvec(bdem_sim* s, const double* x, double* y) {
   if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
   if (!s->system_ready) return fail(s, BDEM_E_INVALID, "call bdem_debug_system first");
@@ -1411,7 +1451,10 @@ extern "C" bdem_status bdem_pcg_static(bdem_sim* s, const double* b_dev, double*
   size_t off_sc = 0;
   size_t off_cnt = off_sc + align256(sizeof(SceneCtl) * (size_t)std::max(s->n_scenes, 1));
   size_t off_part = off_cnt + align256(sizeof(Counters));
-  size_t off_vec = off_part + align256(sizeof(double) * kPartials * (size_t)std::max(d.n_seg, 1));
+  size_t off_grp = off_part + align256(sizeof(double) * kPartials * (size_t)std::max(d.n_seg, 1));
+  size_t off_bpart = off_grp + align256(sizeof(unsigned) * kPcgMaxBlocks / kBarrierGroup);
+  size_t off_gpart = off_bpart + align256(sizeof(double) * kPcgMaxBlocks * kPcgScenes * kPartials);
+  size_t off_vec = off_gpart + align256(sizeof(double) * kPcgMaxBlocks / kBarrierGroup * kPcgScenes * kPartials);
   size_t vec_bytes = align256(w * 6 * std::max<size_t>(n, 1));
   size_t need = off_vec + kVecs * vec_bytes;
   if (need > static_pcg_capacity())
@@ -1428,6 +1471,9 @@ extern "C" bdem_status bdem_pcg_static(bdem_sim* s, const double* b_dev, double*
   d.sc = reinterpret_cast<SceneCtl*>(b8 + off_sc);
   d.cnt = reinterpret_cast<Counters*>(b8 + off_cnt);
   d.part_s = reinterpret_cast<double*>(b8 + off_part);
+  d.pcg_grp = reinterpret_cast<unsigned*>(b8 + off_grp);
+  d.pcg_bpart = reinterpret_cast<double*>(b8 + off_bpart);
+  d.pcg_gpart = reinterpret_cast<double*>(b8 + off_gpart);
   void** vecs[] = {&d.vx, &d.vr, &d.vz, &d.vp_, &d.vq_, &d.vs};
   for (int k = 0; k < kVecs; ++k) *vecs[k] = b8 + off_vec + k * vec_bytes;
   d.pcg_max = max_iter;

@@ -35,6 +35,9 @@ namespace bdem {
 constexpr int kTile = 256;      // rows (particles or bonds) per tile = threads per block of tile kernels
 constexpr int kPartials = 4;    // partial sums per tile
 constexpr int kDiagStride = 24; // words per stored 6x6 symmetric block (21 used, padded for 128-bit loads)
+constexpr int kBarrierGroup = 8;     // blocks per arrival group of the PCG's grid barrier
+constexpr int kPcgScenes = 4;        // up to this many scenes every PCG block takes the decision itself
+constexpr int kPcgMaxBlocks = 2048;  // capacity of the PCG's per-block arrays (grids are at most 8 blocks per SM)
 
 struct SceneCtl {
   double g0, gnorm, eps_r, bnorm;
@@ -68,7 +71,7 @@ struct Counters {               // small device-side summary read by the host af
   int32_t loops_newton;         // gradient reductions in this step (device-driven Newton loop trips + 1)
   int32_t loops_ls;             // trials of the current line search
   int32_t ls_total;             // line-search trials in this step
-  int32_t pad;
+  unsigned int never;           // written by nothing: the word the wait test waits on
 };
 
 struct DevArrays {
@@ -78,6 +81,7 @@ struct DevArrays {
   int32_t hash_size;            // power of two
   double dt, gx, gy, gz, tol, ground_z, k_ground, k_self, skin, cell_h;
   double mu_slide, mu_roll;     // friction coefficients of the post-step correction (0: off)
+  unsigned long long wait_ns;   // time limit of every device-side wait
   int32_t newton_max, pcg_max, ls_max;
   int32_t stress_on;            // some bond has a finite tensile or shear strength
   int32_t first_order, pad3;    // first_order: descent direction -g (Alg. 1) instead of the Newton direction
@@ -113,10 +117,13 @@ struct DevArrays {
   int32_t *btile_start, *btile_scene, *btile_begin;
   double *part_p, *part_b;      // [tiles][kPartials]
   int32_t n_seg, pcg_grid, pcg_lanes, pcg_max_rows;  // pcg_max_rows: most rows of one PCG block
-  int32_t pcg_max_entries, pad2;                     // most incidence entries of one PCG block's rows
+  int32_t pcg_max_entries, pcg_staged;               // most incidence entries of one PCG block's rows; 1: the
+                                                     // block's rows and entries are staged in shared memory
   int32_t *seg_row, *seg_scene, *block_seg, *scene_seg;
   int32_t *useg_row, *useg_scene, *ublock_seg;      // equal-rows partition of the elementwise PCG phases
   double* part_s;               // [n_seg][kPartials]
+  unsigned* pcg_grp;            // [kPcgMaxBlocks / kBarrierGroup] arrival counters of the barrier groups
+  double *pcg_bpart, *pcg_gpart;  // [blocks][kPcgScenes][kPartials], [groups][kPcgScenes][kPartials]
   SceneCtl* sc;
   Counters* cnt;
 };
@@ -138,7 +145,7 @@ enum ReduceMode { RED_GRAD = 0, RED_GDX = 1, RED_LS = 2, RED_FORCE_ACTIVE = 3, R
 int launch_scene_reduce(const DevArrays& d, int mode, unsigned long long cond, cudaStream_t s);
 // PCG: rhs_from_g = 1 uses b = -g; else b is read from vr (already T) and eps from sc.eps_r
 int launch_pcg(const DevArrays& d, int rhs_from_g, int mask_kin, cudaStream_t s, cudaError_t* err);
-int pcg_max_blocks(int mixed, int lanes, size_t smem);
+int pcg_max_blocks(int mixed, int lanes, size_t smem, int staged);
 size_t pcg_smem_bytes(const DevArrays& d);  // shared memory of a PCG block: row descriptors + incidence entries  // co-resident PCG blocks on this device (0: none)
 int launch_gdx(const DevArrays& d, cudaStream_t s);
 int launch_ls_trial(const DevArrays& d, cudaStream_t s);
@@ -161,6 +168,7 @@ int launch_convert_perm(const void* src, int src_double, void* dst, int dst_doub
 size_t static_pcg_capacity();
 cudaError_t static_pcg_address(void** out);
 int launch_static_pcg_init(const DevArrays& d, double eps_r, cudaStream_t s);
+int launch_wait_test(const DevArrays& d, cudaStream_t s);  // a bounded wait that always runs out
 int launch_convert(const void* src, int src_double, void* dst, int dst_double, int64_t count, cudaStream_t s);
 
 }  // namespace bdem

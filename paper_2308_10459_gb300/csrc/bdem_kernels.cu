@@ -692,28 +692,63 @@ __device__ __forceinline__ void prefetch_l2(const void* base, size_t bytes) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p + off));
 }
 
+// the one form of device-side waiting in the library: until *word differs from old (acquire loads), for at most
+// d.wait_ns nanoseconds; on giving up it sets the timeout flag (the host reports BDEM_E_TIMEOUT) and returns false
+__device__ bool bounded_wait_change(const DevArrays& d, const unsigned* word, unsigned old) {
+  unsigned long long t0 = global_ns();
+  while (ld_acquire(word) == old) {
+    __nanosleep(32);
+    if (global_ns() - t0 > d.wait_ns) {
+      atomicExch(&d.cnt->timeout, 1);
+      return false;
+    }
+  }
+  return true;
+}
+
+// a wait on a word that nothing writes, for testing the time limit and the host's handling of it
+__global__ void k_wait_test(DevArrays d) {
+  if (threadIdx.x == 0) bounded_wait_change(d, &d.cnt->never, ld_acquire(&d.cnt->never));
+}
+
+int launch_wait_test(const DevArrays& d, cudaStream_t s) {
+  k_wait_test<<<1, 32, 0, s>>>(d);
+  return 1;
+}
+
 // grid barrier with a bounded wait; the last block to arrive runs `work` (whole block) before releasing the others
+// the per-block partial dots of the few-scene PCG decision, summed per group of blocks in block order (thread 0)
+__device__ void group_partials(const DevArrays& d, int g, int g0, int gn) {
+  for (int s = 0; s < d.n_scenes; ++s)
+    for (int c = 0; c < 3; ++c) {
+      double v = 0.0;
+      for (int b = g0; b < g0 + gn; ++b) v += __ldcg(d.pcg_bpart + (size_t)kPartials * (b * kPcgScenes + s) + c);
+      d.pcg_gpart[(size_t)kPartials * (g * kPcgScenes + s) + c] = v;
+    }
+}
+
+// Arrivals count in two levels: the blocks of each group of kBarrierGroup consecutive blocks on the group's counter,
+// the group's last arrival on the grid's, so that the longest chain of atomics on one word is a group plus the
+// groups instead of the whole grid. With gsum, the group's last arrival first sums the group's per-block partials.
 template <typename F>
-__device__ bool grid_barrier(const DevArrays& d, F&& work) {
+__device__ bool grid_barrier(const DevArrays& d, F&& work, bool gsum = false) {
   __shared__ int s_last, s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned gen = ld_acquire(&d.cnt->sync_gen);
     __threadfence();
-    unsigned arrived = atomicAdd(&d.cnt->sync_count, 1u) + 1u;
-    s_last = (arrived == gridDim.x);
-    s_ok = 1;
-    if (!s_last) {
-      unsigned long long t0 = global_ns();
-      while (ld_acquire(&d.cnt->sync_gen) == gen) {
-        __nanosleep(32);
-        if (global_ns() - t0 > 2000000000ull) {  // 2 s: give up, flag the timeout
-          s_ok = 0;
-          atomicExch(&d.cnt->timeout, 1);
-          break;
-        }
-      }
+    const int g = blockIdx.x / kBarrierGroup, g0 = g * kBarrierGroup;
+    const int gn = min(kBarrierGroup, (int)gridDim.x - g0);
+    const unsigned ngroups = (gridDim.x + kBarrierGroup - 1) / kBarrierGroup;
+    bool last = false;
+    if (atomicAdd(d.pcg_grp + g, 1u) + 1u == (unsigned)gn) {
+      d.pcg_grp[g] = 0u;  // every block of the group has arrived; the next arrivals come after the release
+      if (gsum) group_partials(d, g, g0, gn);
+      __threadfence();
+      last = atomicAdd(&d.cnt->sync_count, 1u) + 1u == ngroups;
     }
+    s_last = last;
+    s_ok = last ? 1 : (bounded_wait_change(d, &d.cnt->sync_gen, gen) ? 1 : 0);
     __threadfence();
   }
   __syncthreads();
@@ -821,24 +856,26 @@ __device__ bool pcg_decide_scene(const DevArrays& d, SceneCtl* c, PcgPrev pv, do
 // few scenes: every block sums every scene's partial dots in the same fixed order and takes the same decision
 // with its own copy of the solver state, so the grid needs only a plain barrier (no decision inside it, no
 // control-block reads after it); block 0 keeps the control blocks current for the host
-constexpr int kLocalScenes = 4;
+constexpr int kLocalScenes = kPcgScenes;
 struct LocalPcg {
   PcgState st[kLocalScenes];
   double acc[3][kTile / 32];
   int n_active;
 };
 
-__device__ void pcg_decide_local(const DevArrays& d, int k_iter, const int* ss, LocalPcg& L) {
+// the partials are one per barrier group and scene (pcg_gpart), summed by the groups' last arrivals
+__device__ void pcg_decide_local(const DevArrays& d, int k_iter, LocalPcg& L) {
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   int active = 0;
+  const int ngroups = (gridDim.x + kBarrierGroup - 1) / kBarrierGroup;
   if (threadIdx.x < d.n_scenes) pcg_prepare(L.st[threadIdx.x]);  // overlaps the partial loads below
   for (int s = 0; s < d.n_scenes; ++s) {
-    int a = ss[s], b = ss[s + 1];
     double gam = 0.0, del = 0.0, rho = 0.0;
-    for (int t = a + threadIdx.x; t < b; t += blockDim.x) {
-      gam += __ldcg(d.part_s + kPartials * t);
-      del += __ldcg(d.part_s + kPartials * t + 1);
-      rho += __ldcg(d.part_s + kPartials * t + 2);
+    for (int t = threadIdx.x; t < ngroups; t += blockDim.x) {
+      const double* p = d.pcg_gpart + (size_t)kPartials * (t * kPcgScenes + s);
+      gam += __ldcg(p);
+      del += __ldcg(p + 1);
+      rho += __ldcg(p + 2);
     }
     gam = warp_sum(gam);
     del = warp_sum(del);
@@ -945,7 +982,10 @@ __device__ __noinline__ void pcg_decide(const DevArrays& d, int k_iter, const in
   }
 }
 
-template <typename T, int G>
+// STAGED: the block's row descriptors and incidence entries are copied to shared memory once per solve; for
+// systems whose block row ranges would not fit (about 25 KB per 1,000 rows of degree 12), they are read from global
+// memory (L2) at every product instead
+template <typename T, int G, bool STAGED>
 __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays d, int rhs_from_g, int mask) {
   T* X = reinterpret_cast<T*>(d.vx);
   T* R = reinterpret_cast<T*>(d.vr);
@@ -964,13 +1004,19 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
   int2* s_ent = reinterpret_cast<int2*>(s_rows + d.pcg_max_rows);
   const int R0 = d.seg_row[seg0], R1 = d.seg_row[seg1];
   const int E0 = d.inc_start[R0], E1 = d.inc_start[R1];
-  for (int i = R0 + threadIdx.x; i < R1; i += blockDim.x) {
+  // row descriptor: first incidence entry (relative to the block's first when staged), bond count, active-contact
+  // count with the kinematic flag in bit 30, first contact entry
+  auto row_desc = [&](int i) {
     int a = d.inc_start[i];
     int na = (d.k_self > 0.0) ? d.c_act[i] : 0;
     int kin = (mask && d.kin[i]) ? (1 << 30) : 0;
-    s_rows[i - R0] = make_int4(a - E0, d.inc_start[i + 1] - a, na | kin, d.c_start[i]);
+    return make_int4(STAGED ? a - E0 : a, d.inc_start[i + 1] - a, na | kin, d.c_start[i]);
+  };
+  if (STAGED) {
+    for (int i = R0 + threadIdx.x; i < R1; i += blockDim.x) s_rows[i - R0] = row_desc(i);
+    for (int e = E0 + threadIdx.x; e < E1; e += blockDim.x) s_ent[e - E0] = d.inc2[e];
   }
-  for (int e = E0 + threadIdx.x; e < E1; e += blockDim.x) s_ent[e - E0] = d.inc2[e];
+  const int2* ent_all = STAGED ? s_ent : d.inc2;
   __shared__ int s_sseg[kTile + 1];  // first PCG segment of each scene, for the decision (up to kTile scenes)
   const bool sseg_ok = d.n_scenes <= kTile;
   if (sseg_ok)
@@ -982,6 +1028,7 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
     s_loc.st[threadIdx.x] = PcgState{c->newton_active, c->newton_active, 0, c->eps_r, 0.0, 0.0, 0.0, 0.0, 0.0,
                                      0.0, 0.0, 0.0};
   }
+  __shared__ double s_cp[kLocalScenes][3];  // few scenes: this block's dots per scene, summed in segment order
   __syncthreads();
   // the elementwise phases (init and B) use the equal-rows partition: their cost is per row, while the product's
   // partition balances rows against incidence entries
@@ -1016,6 +1063,8 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
   const int sub = threadIdx.x % G, grp = threadIdx.x / G, rows_per_pass = blockDim.x / G;
   for (int k_iter = 0;; ++k_iter) {
     // ---- A: w = H z, gamma = r.z, delta = w.z, rho = r.r (per segment, deterministic)
+    if (local && threadIdx.x < kLocalScenes * 3) (&s_cp[0][0])[threadIdx.x] = 0.0;
+    __syncthreads();
     for (int g = seg0; g < seg1; ++g) {
       int sc = d.seg_scene[g];
       bool act = local ? s_loc.st[sc].pcg_active != 0
@@ -1027,14 +1076,14 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
           int i = base + grp;
           bool valid = i < r1;
           T y[6] = {0, 0, 0, 0, 0, 0};
-          int4 rd = valid ? s_rows[i - R0] : make_int4(0, 0, 1 << 30, 0);
+          int4 rd = valid ? (STAGED ? s_rows[i - R0] : row_desc(i)) : make_int4(0, 0, 1 << 30, 0);
           bool live = valid && !(rd.z & (1 << 30));
           if (live) {
             if (sub == 0) {
               Vec6<T> zi = load6_cg<T>(Z, i);
               sym6_mul<T>(Dm + kDiagStride * (size_t)i, zi.v, y);
             }
-            const int2* ent = s_ent + rd.x;
+            const int2* ent = ent_all + rd.x;
             const T* Mall = reinterpret_cast<const T*>(d.bM);
 #pragma unroll 2
             for (int k = sub; k < rd.y; k += G) {
@@ -1072,11 +1121,20 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
       double acc[3] = {dg.value(), dd.value(), dr.value()};
       block_sum<3>(acc);
       if (threadIdx.x == 0) {
-        d.part_s[kPartials * g] = acc[0];
-        d.part_s[kPartials * g + 1] = acc[1];
-        d.part_s[kPartials * g + 2] = acc[2];
+        if (local) {
+          s_cp[sc][0] += acc[0];
+          s_cp[sc][1] += acc[1];
+          s_cp[sc][2] += acc[2];
+        } else {
+          d.part_s[kPartials * g] = acc[0];
+          d.part_s[kPartials * g + 1] = acc[1];
+          d.part_s[kPartials * g + 2] = acc[2];
+        }
       }
     }
+    if (local && threadIdx.x == 0)
+      for (int s = 0; s < d.n_scenes; ++s)
+        for (int c = 0; c < 3; ++c) d.pcg_bpart[(size_t)kPartials * (blockIdx.x * kPcgScenes + s) + c] = s_cp[s][c];
     {  // the update phase's rows into L2 while the grid waits for the slowest product and the decision
       const size_t u0 = d.useg_row[useg0], nu = d.useg_row[useg1] - u0;
       T* vecs[6] = {Z, W, P, S, X, R};
@@ -1085,8 +1143,8 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
       prefetch_l2(Dinv + kDiagStride * u0, kDiagStride * sizeof(T) * nu);
     }
     if (local) {
-      if (!grid_barrier(d, [] {})) return;
-      pcg_decide_local(d, k_iter, s_sseg, s_loc);
+      if (!grid_barrier(d, [] {}, true)) return;
+      pcg_decide_local(d, k_iter, s_loc);
       if (s_loc.n_active == 0 || __ldcg(&d.cnt->timeout)) break;
     } else {
       if (!grid_barrier(d, [&] { pcg_decide(d, k_iter, sseg_ok ? s_sseg : nullptr); })) return;
@@ -1607,6 +1665,7 @@ cudaError_t static_pcg_address(void** out) {
 __global__ void k_static_pcg_init(DevArrays d, double eps_r) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s == 0) *d.cnt = Counters{};
+  for (int g = s; g < kPcgMaxBlocks / kBarrierGroup; g += gridDim.x * blockDim.x) d.pcg_grp[g] = 0u;
   if (s >= d.n_scenes) return;
   SceneCtl c = {};
   c.newton_active = 1;
@@ -1698,25 +1757,32 @@ int launch_scene_reduce(const DevArrays& d, int mode, unsigned long long cond, c
 }
 
 size_t pcg_smem_bytes(const DevArrays& d) {
+  if (!d.pcg_staged) return 0;
   return sizeof(int4) * (size_t)(d.pcg_max_rows > 0 ? d.pcg_max_rows : 1) +
          sizeof(int2) * (size_t)(d.pcg_max_entries > 0 ? d.pcg_max_entries : 1);
 }
 
 template <typename T>
-static const void* pcg_kernel(int lanes) {
+static const void* pcg_kernel(int lanes, int staged) {
+  if (staged) switch (lanes) {
+      case 1: return (const void*)k_pcg<T, 1, true>;
+      case 2: return (const void*)k_pcg<T, 2, true>;
+      case 8: return (const void*)k_pcg<T, 8, true>;
+      default: return (const void*)k_pcg<T, 4, true>;
+    }
   switch (lanes) {
-    case 1: return (const void*)k_pcg<T, 1>;
-    case 2: return (const void*)k_pcg<T, 2>;
-    case 8: return (const void*)k_pcg<T, 8>;
-    default: return (const void*)k_pcg<T, 4>;
+    case 1: return (const void*)k_pcg<T, 1, false>;
+    case 2: return (const void*)k_pcg<T, 2, false>;
+    case 8: return (const void*)k_pcg<T, 8, false>;
+    default: return (const void*)k_pcg<T, 4, false>;
   }
 }
 
-int pcg_max_blocks(int mixed, int lanes, size_t smem) {
+int pcg_max_blocks(int mixed, int lanes, size_t smem, int staged) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const void* k = mixed ? pcg_kernel<float>(lanes) : pcg_kernel<double>(lanes);
+  const void* k = mixed ? pcg_kernel<float>(lanes, staged) : pcg_kernel<double>(lanes, staged);
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kTile, smem) != cudaSuccess) return 0;
   return sms * per;
@@ -1729,7 +1795,7 @@ int launch_pcg(const DevArrays& d, int rhs_from_g, int mask, cudaStream_t s, cud
   }
   DevArrays dd = d;
   void* args[] = {&dd, &rhs_from_g, &mask};
-  const void* k = d.mixed ? pcg_kernel<float>(d.pcg_lanes) : pcg_kernel<double>(d.pcg_lanes);
+  const void* k = d.mixed ? pcg_kernel<float>(d.pcg_lanes, d.pcg_staged) : pcg_kernel<double>(d.pcg_lanes, d.pcg_staged);
   size_t smem = pcg_smem_bytes(d);
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   *err = cudaLaunchCooperativeKernel(k, d.pcg_grid, kTile, args, smem, s);
