@@ -259,9 +259,6 @@ static bdem_status alloc_particles(bdem_sim* s) {
   while (hs < 2 * (int)n) hs <<= 1;
   d.hash_size = hs;
   size_t mx = std::max((size_t)hs, n);
-  TRY(dalloc_t(s, &d.pcg_grp, (size_t)kPcgMaxBlocks / kBarrierGroup));
-  TRY(dalloc_t(s, &d.pcg_bpart, (size_t)kPcgMaxBlocks * kPcgScenes * kPartials));
-  TRY(dalloc_t(s, &d.pcg_gpart, (size_t)kPcgMaxBlocks / kBarrierGroup * kPcgScenes * kPartials));
   TRY(dalloc_t(s, &d.c_start, n + 1));
   TRY(dalloc_t(s, &d.cell_key, n));
   TRY(dalloc_t(s, &d.hash_count, (size_t)hs));
@@ -819,13 +816,12 @@ extern "C" bdem_status bdem_add_bonds(bdem_sim* s, int64_t n, const int32_t* I, 
 // step
 // ------------------------------------------------------------------------------------------------
 
-// clears the device counters and the PCG barrier's group counters after a step that did not complete (a wait
-// that gave up can leave a group partly counted in)
+// clears the device counters after a step that did not complete (a wait that gave up leaves the grid barrier's
+// arrival count behind)
 static void reset_counters(bdem_sim* s, unsigned sync_gen) {
   Counters z{};
   z.sync_gen = sync_gen;
   cudaMemcpy(s->d.cnt, &z, sizeof z, cudaMemcpyHostToDevice);
-  cudaMemset(s->d.pcg_grp, 0, sizeof(unsigned) * kPcgMaxBlocks / kBarrierGroup);
 }
 
 static bdem_status read_counters(bdem_sim* s, Counters* c) {
@@ -1451,10 +1447,7 @@ extern "C" bdem_status bdem_pcg_static(bdem_sim* s, const double* b_dev, double*
   size_t off_sc = 0;
   size_t off_cnt = off_sc + align256(sizeof(SceneCtl) * (size_t)std::max(s->n_scenes, 1));
   size_t off_part = off_cnt + align256(sizeof(Counters));
-  size_t off_grp = off_part + align256(sizeof(double) * kPartials * (size_t)std::max(d.n_seg, 1));
-  size_t off_bpart = off_grp + align256(sizeof(unsigned) * kPcgMaxBlocks / kBarrierGroup);
-  size_t off_gpart = off_bpart + align256(sizeof(double) * kPcgMaxBlocks * kPcgScenes * kPartials);
-  size_t off_vec = off_gpart + align256(sizeof(double) * kPcgMaxBlocks / kBarrierGroup * kPcgScenes * kPartials);
+  size_t off_vec = off_part + align256(sizeof(double) * kPartials * (size_t)std::max(d.n_seg, 1));
   size_t vec_bytes = align256(w * 6 * std::max<size_t>(n, 1));
   size_t need = off_vec + kVecs * vec_bytes;
   if (need > static_pcg_capacity())
@@ -1471,9 +1464,6 @@ extern "C" bdem_status bdem_pcg_static(bdem_sim* s, const double* b_dev, double*
   d.sc = reinterpret_cast<SceneCtl*>(b8 + off_sc);
   d.cnt = reinterpret_cast<Counters*>(b8 + off_cnt);
   d.part_s = reinterpret_cast<double*>(b8 + off_part);
-  d.pcg_grp = reinterpret_cast<unsigned*>(b8 + off_grp);
-  d.pcg_bpart = reinterpret_cast<double*>(b8 + off_bpart);
-  d.pcg_gpart = reinterpret_cast<double*>(b8 + off_gpart);
   void** vecs[] = {&d.vx, &d.vr, &d.vz, &d.vp_, &d.vq_, &d.vs};
   for (int k = 0; k < kVecs; ++k) *vecs[k] = b8 + off_vec + k * vec_bytes;
   d.pcg_max = max_iter;

@@ -35,9 +35,7 @@ namespace bdem {
 constexpr int kTile = 256;      // rows (particles or bonds) per tile = threads per block of tile kernels
 constexpr int kPartials = 4;    // partial sums per tile
 constexpr int kDiagStride = 24; // words per stored 6x6 symmetric block (21 used, padded for 128-bit loads)
-constexpr int kBarrierGroup = 8;     // blocks per arrival group of the PCG's grid barrier
-constexpr int kPcgScenes = 4;        // up to this many scenes every PCG block takes the decision itself
-constexpr int kPcgMaxBlocks = 2048;  // capacity of the PCG's per-block arrays (grids are at most 8 blocks per SM)
+constexpr int kPcgMaxBlocks = 2048;  // largest PCG grid (grids are at most 8 blocks of kTile threads per SM)
 
 struct SceneCtl {
   double g0, gnorm, eps_r, bnorm;
@@ -122,8 +120,6 @@ struct DevArrays {
   int32_t *seg_row, *seg_scene, *block_seg, *scene_seg;
   int32_t *useg_row, *useg_scene, *ublock_seg;      // equal-rows partition of the elementwise PCG phases
   double* part_s;               // [n_seg][kPartials]
-  unsigned* pcg_grp;            // [kPcgMaxBlocks / kBarrierGroup] arrival counters of the barrier groups
-  double *pcg_bpart, *pcg_gpart;  // [blocks][kPcgScenes][kPartials], [groups][kPcgScenes][kPartials]
   SceneCtl* sc;
   Counters* cnt;
 };

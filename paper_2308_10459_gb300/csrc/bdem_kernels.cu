@@ -717,36 +717,14 @@ int launch_wait_test(const DevArrays& d, cudaStream_t s) {
 }
 
 // grid barrier with a bounded wait; the last block to arrive runs `work` (whole block) before releasing the others
-// the per-block partial dots of the few-scene PCG decision, summed per group of blocks in block order (thread 0)
-__device__ void group_partials(const DevArrays& d, int g, int g0, int gn) {
-  for (int s = 0; s < d.n_scenes; ++s)
-    for (int c = 0; c < 3; ++c) {
-      double v = 0.0;
-      for (int b = g0; b < g0 + gn; ++b) v += __ldcg(d.pcg_bpart + (size_t)kPartials * (b * kPcgScenes + s) + c);
-      d.pcg_gpart[(size_t)kPartials * (g * kPcgScenes + s) + c] = v;
-    }
-}
-
-// Arrivals count in two levels: the blocks of each group of kBarrierGroup consecutive blocks on the group's counter,
-// the group's last arrival on the grid's, so that the longest chain of atomics on one word is a group plus the
-// groups instead of the whole grid. With gsum, the group's last arrival first sums the group's per-block partials.
 template <typename F>
-__device__ bool grid_barrier(const DevArrays& d, F&& work, bool gsum = false) {
+__device__ bool grid_barrier(const DevArrays& d, F&& work) {
   __shared__ int s_last, s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned gen = ld_acquire(&d.cnt->sync_gen);
     __threadfence();
-    const int g = blockIdx.x / kBarrierGroup, g0 = g * kBarrierGroup;
-    const int gn = min(kBarrierGroup, (int)gridDim.x - g0);
-    const unsigned ngroups = (gridDim.x + kBarrierGroup - 1) / kBarrierGroup;
-    bool last = false;
-    if (atomicAdd(d.pcg_grp + g, 1u) + 1u == (unsigned)gn) {
-      d.pcg_grp[g] = 0u;  // every block of the group has arrived; the next arrivals come after the release
-      if (gsum) group_partials(d, g, g0, gn);
-      __threadfence();
-      last = atomicAdd(&d.cnt->sync_count, 1u) + 1u == ngroups;
-    }
+    bool last = atomicAdd(&d.cnt->sync_count, 1u) + 1u == gridDim.x;
     s_last = last;
     s_ok = last ? 1 : (bounded_wait_change(d, &d.cnt->sync_gen, gen) ? 1 : 0);
     __threadfence();
@@ -856,26 +834,24 @@ __device__ bool pcg_decide_scene(const DevArrays& d, SceneCtl* c, PcgPrev pv, do
 // few scenes: every block sums every scene's partial dots in the same fixed order and takes the same decision
 // with its own copy of the solver state, so the grid needs only a plain barrier (no decision inside it, no
 // control-block reads after it); block 0 keeps the control blocks current for the host
-constexpr int kLocalScenes = kPcgScenes;
+constexpr int kLocalScenes = 4;
 struct LocalPcg {
   PcgState st[kLocalScenes];
   double acc[3][kTile / 32];
   int n_active;
 };
 
-// the partials are one per barrier group and scene (pcg_gpart), summed by the groups' last arrivals
-__device__ void pcg_decide_local(const DevArrays& d, int k_iter, LocalPcg& L) {
+__device__ void pcg_decide_local(const DevArrays& d, int k_iter, const int* ss, LocalPcg& L) {
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   int active = 0;
-  const int ngroups = (gridDim.x + kBarrierGroup - 1) / kBarrierGroup;
   if (threadIdx.x < d.n_scenes) pcg_prepare(L.st[threadIdx.x]);  // overlaps the partial loads below
   for (int s = 0; s < d.n_scenes; ++s) {
+    int a = ss[s], b = ss[s + 1];
     double gam = 0.0, del = 0.0, rho = 0.0;
-    for (int t = threadIdx.x; t < ngroups; t += blockDim.x) {
-      const double* p = d.pcg_gpart + (size_t)kPartials * (t * kPcgScenes + s);
-      gam += __ldcg(p);
-      del += __ldcg(p + 1);
-      rho += __ldcg(p + 2);
+    for (int t = a + threadIdx.x; t < b; t += blockDim.x) {
+      gam += __ldcg(d.part_s + kPartials * t);
+      del += __ldcg(d.part_s + kPartials * t + 1);
+      rho += __ldcg(d.part_s + kPartials * t + 2);
     }
     gam = warp_sum(gam);
     del = warp_sum(del);
@@ -1028,7 +1004,6 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
     s_loc.st[threadIdx.x] = PcgState{c->newton_active, c->newton_active, 0, c->eps_r, 0.0, 0.0, 0.0, 0.0, 0.0,
                                      0.0, 0.0, 0.0};
   }
-  __shared__ double s_cp[kLocalScenes][3];  // few scenes: this block's dots per scene, summed in segment order
   __syncthreads();
   // the elementwise phases (init and B) use the equal-rows partition: their cost is per row, while the product's
   // partition balances rows against incidence entries
@@ -1063,8 +1038,6 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
   const int sub = threadIdx.x % G, grp = threadIdx.x / G, rows_per_pass = blockDim.x / G;
   for (int k_iter = 0;; ++k_iter) {
     // ---- A: w = H z, gamma = r.z, delta = w.z, rho = r.r (per segment, deterministic)
-    if (local && threadIdx.x < kLocalScenes * 3) (&s_cp[0][0])[threadIdx.x] = 0.0;
-    __syncthreads();
     for (int g = seg0; g < seg1; ++g) {
       int sc = d.seg_scene[g];
       bool act = local ? s_loc.st[sc].pcg_active != 0
@@ -1121,20 +1094,11 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
       double acc[3] = {dg.value(), dd.value(), dr.value()};
       block_sum<3>(acc);
       if (threadIdx.x == 0) {
-        if (local) {
-          s_cp[sc][0] += acc[0];
-          s_cp[sc][1] += acc[1];
-          s_cp[sc][2] += acc[2];
-        } else {
-          d.part_s[kPartials * g] = acc[0];
-          d.part_s[kPartials * g + 1] = acc[1];
-          d.part_s[kPartials * g + 2] = acc[2];
-        }
+        d.part_s[kPartials * g] = acc[0];
+        d.part_s[kPartials * g + 1] = acc[1];
+        d.part_s[kPartials * g + 2] = acc[2];
       }
     }
-    if (local && threadIdx.x == 0)
-      for (int s = 0; s < d.n_scenes; ++s)
-        for (int c = 0; c < 3; ++c) d.pcg_bpart[(size_t)kPartials * (blockIdx.x * kPcgScenes + s) + c] = s_cp[s][c];
     {  // the update phase's rows into L2 while the grid waits for the slowest product and the decision
       const size_t u0 = d.useg_row[useg0], nu = d.useg_row[useg1] - u0;
       T* vecs[6] = {Z, W, P, S, X, R};
@@ -1143,8 +1107,8 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
       prefetch_l2(Dinv + kDiagStride * u0, kDiagStride * sizeof(T) * nu);
     }
     if (local) {
-      if (!grid_barrier(d, [] {}, true)) return;
-      pcg_decide_local(d, k_iter, s_loc);
+      if (!grid_barrier(d, [] {})) return;
+      pcg_decide_local(d, k_iter, s_sseg, s_loc);
       if (s_loc.n_active == 0 || __ldcg(&d.cnt->timeout)) break;
     } else {
       if (!grid_barrier(d, [&] { pcg_decide(d, k_iter, sseg_ok ? s_sseg : nullptr); })) return;
@@ -1665,7 +1629,6 @@ cudaError_t static_pcg_address(void** out) {
 __global__ void k_static_pcg_init(DevArrays d, double eps_r) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s == 0) *d.cnt = Counters{};
-  for (int g = s; g < kPcgMaxBlocks / kBarrierGroup; g += gridDim.x * blockDim.x) d.pcg_grp[g] = 0u;
   if (s >= d.n_scenes) return;
   SceneCtl c = {};
   c.newton_active = 1;
