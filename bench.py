@@ -373,7 +373,8 @@ def main():
     achieved = bytes_launch / (pcg_ms_launch * 1e-3) / 1e9
     peaks, peak_kind = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    trec = traffic_record()
+    # the ncu record is of the plate's PCG: it scales to the plate's launches only
+    trec = traffic_record() if args.workload == "plate" else None
     traffic = None if trec is None else trec["dram_bytes_per_pcg_iter"] * pcg_iters_launch + trec["dram_bytes_once"]
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region ----
