@@ -48,7 +48,8 @@ class OrcConfig(ctypes.Structure):
                 ("newton_max_iter", ctypes.c_int32), ("pcg_max_iter", ctypes.c_int32),
                 ("ls_max_halvings", ctypes.c_int32), ("optimizer", ctypes.c_int32), ("ground_z", ctypes.c_double),
                 ("k_ground", ctypes.c_double), ("k_self", ctypes.c_double), ("contact_skin", ctypes.c_double),
-                ("mu_slide", ctypes.c_double), ("mu_roll", ctypes.c_double)]
+                ("mu_slide", ctypes.c_double), ("mu_roll", ctypes.c_double),
+                ("integrator", ctypes.c_int32), ("pad1", ctypes.c_int32)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -76,11 +77,15 @@ def _setup(L):
     L.orc_bond_rest.argtypes = [P, _dp, _dp, _dp, _dp, _dp]
     L.orc_step.argtypes = [C, P, ctypes.POINTER(OrcStats)]
     L.orc_bond_terms.argtypes = [P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.orc_bond_terms_at.argtypes = [P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_double, _dp, _dp, _dp,
+                                    _dp]
+    L.orc_bond_terms_at.restype = None
     L.orc_bond_energy_parts.argtypes = [P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
     L.orc_bond_stress.argtypes = [P, ctypes.c_int, _dp, _dp, _dp]
     L.orc_bond_stress.restype = None
     L.orc_system.argtypes = [C, P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _ip]
     L.orc_matvec.argtypes = [C, P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.orc_zhat.argtypes = [C, P, ctypes.c_int, _dp, _dp, _dp, _dp]
     L.orc_pcg_solve.argtypes = [C, P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp]
     L.orc_energy_diff.argtypes = [C, P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     L.orc_energy_diff.restype = ctypes.c_double
@@ -229,6 +234,7 @@ class OracleSim:
         C.optimizer = int(c.get("optimizer", 0))
         C.mu_slide = c.get("friction_slide", 0.0)
         C.mu_roll = c.get("friction_roll", 0.0)
+        C.integrator = int(c.get("integrator", 0))
         return C
 
     def _build_problem(self):
@@ -270,6 +276,15 @@ class OracleSim:
         e, g, H, Hs = np.zeros(1), np.zeros(12), np.zeros((12, 12)), np.zeros((12, 12))
         pi, qi, pj, qj = f64(pi), f64(qi), f64(pj), f64(qj)
         lib().orc_bond_terms(ctypes.byref(self.P), int(b), _d(pi), _d(qi), _d(pj), _d(qj), _d(e), _d(g), _d(H), _d(Hs))
+        return e[0], g, H, Hs
+
+    def bond_terms_at(self, b, pvi, qvi, pvj, qvj, qi, qj, w):
+        """Energy at the evaluation point, reduced gradient (12) and unprojected / projected reduced Hessians
+        (12x12) of the bond term x -> V_b(w x + (1 - w) x_n), reduced at the state's quaternions (qi, qj)."""
+        e, g, H, Hs = np.zeros(1), np.zeros(12), np.zeros((12, 12)), np.zeros((12, 12))
+        args = [f64(x) for x in (pvi, qvi, pvj, qvj, qi, qj)]
+        lib().orc_bond_terms_at(ctypes.byref(self.P), int(b), *[_d(x) for x in args], float(w), _d(e), _d(g), _d(H),
+                                _d(Hs))
         return e[0], g, H, Hs
 
     def bond_energy_parts(self, b, pi, qi, pj, qj):
@@ -334,6 +349,14 @@ class OracleSim:
         cnt = lib().orc_contact_candidates(ctypes.byref(self.C), ctypes.byref(self.P), scene, _d(p),
                                            pairs.ctypes.data_as(_ip), cap, 1 if brute else 0)
         return pairs[:min(cnt, cap)].copy()
+
+    def zhat(self, phat, qhat, scene=0):
+        """The variational midpoint target zhat of the scene (Sec. 3.1, App. C) for the inertia targets
+        (phat, qhat); contact candidates found at phat."""
+        zp, zq = np.zeros((self.scene.n, 3)), np.zeros((self.scene.n, 4))
+        phat, qhat = f64(phat), f64(qhat)
+        lib().orc_zhat(ctypes.byref(self.C), ctypes.byref(self.P), scene, _d(phat), _d(qhat), _d(zp), _d(zq))
+        return zp, zq
 
     def predict(self):
         """xhat = x_n + dt v_n and the initial guess (phat, qhat/|qhat|) of Alg. 3."""

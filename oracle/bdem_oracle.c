@@ -523,9 +523,11 @@ static double bond_energy(const orc_problem* P, int b, const double* p, const do
 
 /* V_b(x1) - V_b(x0), with the stretch and bend-twist parts written as exact difference identities
  * (l1 - l0 = (d1 - d0).(d1 + d0)/(l1 + l0); t1 - t0 = R0 (G_l(q_j1 - q_j0) q_i1 + G_l(q_j0)(q_i1 - q_i0)))
- * so that the difference is accurate relative to itself; the shear part is differenced directly. */
+ * so that the difference is accurate relative to itself; the shear part is differenced directly. The differences
+ * x1 - x0 are taken from (dp, dq) when given (x0 and x1 are then rounded midpoints whose own difference would
+ * carry their rounding), else formed from x1 and x0. */
 static double bond_energy_diff(const orc_problem* P, int b, const double* p0, const double* q0, const double* p1,
-                               const double* q1) {
+                               const double* q1, const double* dp, const double* dq) {
   int i = P->bi[b], j = P->bj[b], save = g_order;
   double e0[3], e1[3], l0v, l1v, t0[3], t1[3];
   g_order = 0;
@@ -534,13 +536,16 @@ static double bond_energy_diff(const orc_problem* P, int b, const double* p0, co
   g_order = save;
   double dd[3], ds[3];
   for (int k = 0; k < 3; ++k) {
-    dd[k] = (p1[3 * j + k] - p0[3 * j + k]) - (p1[3 * i + k] - p0[3 * i + k]);
+    dd[k] = dp ? dp[3 * j + k] - dp[3 * i + k] : (p1[3 * j + k] - p0[3 * j + k]) - (p1[3 * i + k] - p0[3 * i + k]);
     ds[k] = (p0[3 * j + k] - p0[3 * i + k]) + (p1[3 * j + k] - p1[3 * i + k]);
   }
   double dl = dot3(dd, ds) / (l0v + l1v);
   double dVs = 0.5 * P->kn[b] * dl * ((l0v - P->l0[b]) + (l1v - P->l0[b]));
   double dqi[4], dqj[4], G1[12], G0[12], dw[3];
-  for (int k = 0; k < 4; ++k) { dqi[k] = q1[4 * i + k] - q0[4 * i + k]; dqj[k] = q1[4 * j + k] - q0[4 * j + k]; }
+  for (int k = 0; k < 4; ++k) {
+    dqi[k] = dq ? dq[4 * i + k] : q1[4 * i + k] - q0[4 * i + k];
+    dqj[k] = dq ? dq[4 * j + k] : q1[4 * j + k] - q0[4 * j + k];
+  }
   orc_Gl(dqj, G1);
   orc_Gl(q0 + 4 * j, G0);
   for (int r = 0; r < 3; ++r) {
@@ -556,20 +561,31 @@ static double bond_energy_diff(const orc_problem* P, int b, const double* p0, co
   return dVs + (e1[1] - e0[1]) + dVbt;
 }
 
-/* pair term derivatives -> reduced gradient g12 and reduced Hessian H12 (unprojected) */
-static void pair_reduce(const jet* V, const double qa[4], const double qb[4], double* g12, double* H12) {
+/* pair term derivatives -> reduced gradient g12 and reduced Hessian H12 (unprojected). The term is evaluated at a
+ * point whose Euclidean coordinates move by w times those of the state (w = 1: the state itself; w = 1/2: the
+ * midpoint with the step's start state), so its Euclidean gradient and Hessian with respect to the state are w and
+ * w^2 times those at the evaluation point; the reduction takes place at the state's quaternions (qa, qb). */
+static void pair_reduce(const jet* V, const double qa[4], const double qb[4], double w, double* g12, double* H12) {
   double ge[14], He[196];
   jet_grad_hess(V, ge, He);
+  for (int k = 0; k < 14; ++k) ge[k] *= w;
+  for (int k = 0; k < 196; ++k) He[k] *= w * w;
   const double* qe[2] = {qa, qb};
   riemann_reduce(2, qe, ge, He, g12, H12);
 }
 
 void orc_bond_terms(const orc_problem* P, int b, const double pi[3], const double qi[4], const double pj[3],
                     const double qj[4], double* energy, double* grad12, double* hess12, double* hess12_spd) {
+  orc_bond_terms_at(P, b, pi, qi, pj, qj, qi, qj, 1.0, energy, grad12, hess12, hess12_spd);
+}
+
+void orc_bond_terms_at(const orc_problem* P, int b, const double pvi[3], const double qvi[4], const double pvj[3],
+                       const double qvj[4], const double qi[4], const double qj[4], double w, double* energy,
+                       double* grad12, double* hess12, double* hess12_spd) {
   g_order = 2;
-  jet V = bond_energy_jet(P, b, pi, qi, pj, qj, NULL, NULL, NULL, NULL);
+  jet V = bond_energy_jet(P, b, pvi, qvi, pvj, qvj, NULL, NULL, NULL, NULL);
   double g12[12], H12[144];
-  pair_reduce(&V, qi, qj, g12, H12);
+  pair_reduce(&V, qi, qj, w, g12, H12);
   if (energy) *energy = V.v;
   if (grad12) memcpy(grad12, g12, sizeof g12);
   if (hess12) memcpy(hess12, H12, sizeof H12);
@@ -602,14 +618,14 @@ static double contact_energy(double k, double R, const double pa[3], const doubl
 }
 
 /* contact energy difference; when active at both states, 1/2 k (d1 - d0)(e1 + e0) with
- * d1 - d0 = (x1 - x0).(x1 + x0)/(d1 + d0), x = p_a - p_b */
+ * d1 - d0 = (x1 - x0).(x1 + x0)/(d1 + d0), x = p_a - p_b; (dpa, dpb), when given, are the endpoint differences */
 static double contact_energy_diff(double k, double R, const double* pa0, const double* pb0, const double* pa1,
-                                  const double* pb1) {
+                                  const double* pb1, const double* dpa, const double* dpb) {
   double x0[3], x1[3], dx[3], sx[3];
   for (int c = 0; c < 3; ++c) {
     x0[c] = pa0[c] - pb0[c];
     x1[c] = pa1[c] - pb1[c];
-    dx[c] = (pa1[c] - pa0[c]) - (pb1[c] - pb0[c]);
+    dx[c] = dpa ? dpa[c] - dpb[c] : (pa1[c] - pa0[c]) - (pb1[c] - pb0[c]);
     sx[c] = x0[c] + x1[c];
   }
   double d0 = sqrt(dot3(x0, x0)), d1 = sqrt(dot3(x1, x1));
@@ -617,52 +633,58 @@ static double contact_energy_diff(double k, double R, const double* pa0, const d
   return contact_energy(k, R, pa1, pb1) - contact_energy(k, R, pa0, pb0);
 }
 
-/* Per-particle term: inertia 1/(2dt^2) (x - xhat)^T M_s (x - xhat), gravity -m g.p and the ground. */
+/* Per-particle term: inertia 1/(2dt^2) (x - xhat)^T M_s (x - xhat) at the state (p, q), gravity -m g.pv and the
+ * ground at the potential's evaluation point pv (the state itself, or the midpoint with the step's start state). */
 static double particle_energy(const orc_config* C, double m, double r, const double p[3], const double q[4],
-                              const double ph[3], const double qh[4]) {
+                              const double pv[3], const double ph[3], const double qh[4]) {
   double dt2 = C->dt * C->dt, cp = m / dt2, cq = 1.6 * m * r * r / dt2, e = 0.0;
   for (int k = 0; k < 3; ++k) e += 0.5 * cp * (p[k] - ph[k]) * (p[k] - ph[k]);
   for (int k = 0; k < 4; ++k) e += 0.5 * cq * (q[k] - qh[k]) * (q[k] - qh[k]);
-  e -= m * dot3(C->gravity, p);
+  e -= m * dot3(C->gravity, pv);
   if (C->k_ground > 0.0) {
-    double gd = p[2] - C->ground_z - r;
+    double gd = pv[2] - C->ground_z - r;
     if (gd < 0.0) e += 0.5 * C->k_ground * gd * gd;
   }
   return e;
 }
 
 /* particle-term difference written with dp = p1 - p0: 1/2 c (|p1 - ph|^2 - |p0 - ph|^2) = c dp.((p0 - ph) + dp/2),
- * the same for q, -m g.dp, and for the ground 1/2 k (g1 - g0)(g1 + g0) when active at both states */
+ * the same for q, -m g.dv, and for the ground 1/2 k (g1 - g0)(g1 + g0) when active at both evaluation points
+ * (v0, v1: the potential's evaluation points, dv = v1 - v0; the state itself, or the midpoints with the step's
+ * start state and dv = dp/2) */
 static double particle_energy_diff(const orc_config* C, double m, double r, const double* p0, const double* q0,
-                                   const double* p1, const double* q1, const double* ph, const double* qh) {
+                                   const double* p1, const double* q1, const double* v0, const double* v1,
+                                   double wv, const double* ph, const double* qh) {
   double dt2 = C->dt * C->dt, cp = m / dt2, cq = 1.6 * m * r * r / dt2, e = 0.0;
   for (int k = 0; k < 3; ++k) {
     double dp = p1[k] - p0[k];
-    e += cp * dp * ((p0[k] - ph[k]) + 0.5 * dp) - m * C->gravity[k] * dp;
+    e += cp * dp * ((p0[k] - ph[k]) + 0.5 * dp) - m * C->gravity[k] * (wv * dp);
   }
   for (int k = 0; k < 4; ++k) {
     double dq = q1[k] - q0[k];
     e += cq * dq * ((q0[k] - qh[k]) + 0.5 * dq);
   }
   if (C->k_ground > 0.0) {
-    double g0 = p0[2] - C->ground_z - r, g1 = p1[2] - C->ground_z - r;
-    if (g0 < 0.0 && g1 < 0.0) e += 0.5 * C->k_ground * (p1[2] - p0[2]) * (g0 + g1);
+    double g0 = v0[2] - C->ground_z - r, g1 = v1[2] - C->ground_z - r;
+    if (g0 < 0.0 && g1 < 0.0) e += 0.5 * C->k_ground * (wv * (p1[2] - p0[2])) * (g0 + g1);
     else e += 0.5 * C->k_ground * ((g1 < 0.0 ? g1 * g1 : 0.0) - (g0 < 0.0 ? g0 * g0 : 0.0));
   }
   return e;
 }
 
-/* reduced gradient (6) and projected reduced Hessian (6x6) of the particle term */
+/* reduced gradient (6) and projected reduced Hessian (6x6) of the particle term; gravity and the ground are
+ * evaluated at pv, whose coordinates move by w times those of the state (see pair_reduce) */
 static void particle_terms(const orc_config* C, double m, double r, const double p[3], const double q[4],
-                           const double ph[3], const double qh[4], double g6[6], double H6[36]) {
+                           const double pv[3], double w, const double ph[3], const double qh[4], double g6[6],
+                           double H6[36]) {
   double dt2 = C->dt * C->dt, cp = m / dt2, cq = 1.6 * m * r * r / dt2;
   double ge[7], He[49];
   memset(He, 0, sizeof He);
-  for (int k = 0; k < 3; ++k) { ge[k] = cp * (p[k] - ph[k]) - m * C->gravity[k]; He[8 * k] = cp; }
+  for (int k = 0; k < 3; ++k) { ge[k] = cp * (p[k] - ph[k]) - w * m * C->gravity[k]; He[8 * k] = cp; }
   for (int k = 0; k < 4; ++k) { ge[3 + k] = cq * (q[k] - qh[k]); He[8 * (3 + k)] = cq; }
   if (C->k_ground > 0.0) {
-    double gd = p[2] - C->ground_z - r;
-    if (gd < 0.0) { ge[2] += C->k_ground * gd; He[8 * 2] += C->k_ground; }
+    double gd = pv[2] - C->ground_z - r;
+    if (gd < 0.0) { ge[2] += w * C->k_ground * gd; He[8 * 2] += w * w * C->k_ground; }
   }
   const double* qe[1] = {q};
   riemann_reduce(1, qe, ge, He, g6, H6);
@@ -826,6 +848,9 @@ typedef struct {
   double* Hb;                  /* [nbond][144] bond blocks */
   double* Hc;                  /* [ncand][144] contact blocks */
   double* D;                   /* [ns][36] assembled diagonal blocks (preconditioner) */
+  int mid;                     /* variational midpoint form: potentials at (x + x_n)/2 */
+  const double *pn, *qn;       /* the step's start state x_n (the problem's state arrays) */
+  double *pm0, *qm0, *pm1, *qm1, *dpm, *dqm;  /* [n][3], [n][4] midpoints and their differences (mid only) */
 } scene_sys;
 
 static void sys_init(scene_sys* S, const orc_config* C, const orc_problem* P, int scene, const double* phat,
@@ -841,10 +866,27 @@ static void sys_init(scene_sys* S, const orc_config* C, const orc_problem* P, in
   S->Hp = malloc(sizeof(double) * 36 * S->ns);
   S->D = malloc(sizeof(double) * 36 * S->ns);
   S->Hb = malloc(sizeof(double) * 144 * (S->nbond + 1));
+  S->mid = C->integrator == 1;
+  S->pn = P->p;
+  S->qn = P->q;
+  if (S->mid) {
+    S->pm0 = calloc(3 * (size_t)P->n, sizeof(double)); S->qm0 = calloc(4 * (size_t)P->n, sizeof(double));
+    S->pm1 = calloc(3 * (size_t)P->n, sizeof(double)); S->qm1 = calloc(4 * (size_t)P->n, sizeof(double));
+    S->dpm = calloc(3 * (size_t)P->n, sizeof(double)); S->dqm = calloc(4 * (size_t)P->n, sizeof(double));
+  }
+}
+
+/* the midpoint (x + x_n)/2 of the scene's particles (Sec. 3.1, Eq. variational optimisation form) */
+static void sys_midpoint(const scene_sys* S, const double* p, const double* q, double* pm, double* qm) {
+  for (int i = S->n0; i < S->n0 + S->ns; ++i) {
+    for (int k = 0; k < 3; ++k) pm[3 * i + k] = 0.5 * (p[3 * i + k] + S->pn[3 * i + k]);
+    for (int k = 0; k < 4; ++k) qm[4 * i + k] = 0.5 * (q[4 * i + k] + S->qn[4 * i + k]);
+  }
 }
 
 static void sys_free(scene_sys* S) {
   free(S->bonds); free(S->g); free(S->Hp); free(S->D); free(S->Hb); free(S->Hc); free(S->cand);
+  free(S->pm0); free(S->qm0); free(S->pm1); free(S->qm1); free(S->dpm); free(S->dqm);
 }
 
 static void sys_set_candidates(scene_sys* S, int scene, const double* p) {
@@ -856,16 +898,22 @@ static void sys_set_candidates(scene_sys* S, int scene, const double* p) {
 
 static int is_kin(const orc_problem* P, int i) { return P->kinematic && P->kinematic[i]; }
 
-/* Phi(x) summed term by term */
+/* Phi(x) summed term by term (potentials at x, or at the midpoint (x + x_n)/2) */
 static double sys_energy(const scene_sys* S, const double* p, const double* q) {
   const orc_problem* P = S->P;
+  const double *pv = p, *qv = q;
+  if (S->mid) {
+    sys_midpoint(S, p, q, S->pm0, S->qm0);
+    pv = S->pm0; qv = S->qm0;
+  }
   double e = 0.0;
   for (int i = S->n0; i < S->n0 + S->ns; ++i)
-    e += particle_energy(S->C, P->mass[i], P->radius[i], p + 3 * i, q + 4 * i, S->phat + 3 * i, S->qhat + 4 * i);
-  for (int k = 0; k < S->nbond; ++k) e += bond_energy(P, S->bonds[k], p, q);
+    e += particle_energy(S->C, P->mass[i], P->radius[i], p + 3 * i, q + 4 * i, pv + 3 * i, S->phat + 3 * i,
+                         S->qhat + 4 * i);
+  for (int k = 0; k < S->nbond; ++k) e += bond_energy(P, S->bonds[k], pv, qv);
   for (int k = 0; k < S->ncand; ++k) {
     int a = S->cand[2 * k], b = S->cand[2 * k + 1];
-    e += contact_energy(S->C->k_self, P->radius[a] + P->radius[b], p + 3 * a, p + 3 * b);
+    e += contact_energy(S->C->k_self, P->radius[a] + P->radius[b], pv + 3 * a, pv + 3 * b);
   }
   return e;
 }
@@ -874,14 +922,28 @@ static double sys_energy(const scene_sys* S, const double* p, const double* q) {
  * differences are summed; near convergence the total is far below the rounding of Phi itself */
 static double sys_energy_diff(const scene_sys* S, const double* p0, const double* q0, const double* p1, const double* q1) {
   const orc_problem* P = S->P;
+  /* evaluation points of the potentials and, at the midpoints, their exact differences (x1 - x0)/2 */
+  const double *v0 = p0, *w0 = q0, *v1 = p1, *w1 = q1, *dv = NULL, *dw = NULL;
+  double wv = 1.0;
+  if (S->mid) {
+    sys_midpoint(S, p0, q0, S->pm0, S->qm0);
+    sys_midpoint(S, p1, q1, S->pm1, S->qm1);
+    for (int i = S->n0; i < S->n0 + S->ns; ++i) {
+      for (int k = 0; k < 3; ++k) S->dpm[3 * i + k] = 0.5 * (p1[3 * i + k] - p0[3 * i + k]);
+      for (int k = 0; k < 4; ++k) S->dqm[4 * i + k] = 0.5 * (q1[4 * i + k] - q0[4 * i + k]);
+    }
+    v0 = S->pm0; w0 = S->qm0; v1 = S->pm1; w1 = S->qm1; dv = S->dpm; dw = S->dqm;
+    wv = 0.5;
+  }
   double e = 0.0;
   for (int i = S->n0; i < S->n0 + S->ns; ++i)
     e += particle_energy_diff(S->C, P->mass[i], P->radius[i], p0 + 3 * i, q0 + 4 * i, p1 + 3 * i, q1 + 4 * i,
-                              S->phat + 3 * i, S->qhat + 4 * i);
-  for (int k = 0; k < S->nbond; ++k) e += bond_energy_diff(P, S->bonds[k], p0, q0, p1, q1);
+                              v0 + 3 * i, v1 + 3 * i, wv, S->phat + 3 * i, S->qhat + 4 * i);
+  for (int k = 0; k < S->nbond; ++k) e += bond_energy_diff(P, S->bonds[k], v0, w0, v1, w1, dv, dw);
   for (int k = 0; k < S->ncand; ++k) {
     int a = S->cand[2 * k], b = S->cand[2 * k + 1];
-    e += contact_energy_diff(S->C->k_self, P->radius[a] + P->radius[b], p0 + 3 * a, p0 + 3 * b, p1 + 3 * a, p1 + 3 * b);
+    e += contact_energy_diff(S->C->k_self, P->radius[a] + P->radius[b], v0 + 3 * a, v0 + 3 * b, v1 + 3 * a,
+                             v1 + 3 * b, dv ? dv + 3 * a : NULL, dv ? dv + 3 * b : NULL);
   }
   return e;
 }
@@ -903,11 +965,19 @@ double orc_energy_diff(const orc_config* C, const orc_problem* P, int scene, con
 static void sys_assemble(scene_sys* S, const double* p, const double* q, int mask_kin) {
   const orc_problem* P = S->P;
   int n0 = S->n0, ns = S->ns;
+  /* potentials at x (w = 1) or at the midpoint (x + x_n)/2 (w = 1/2), reduced at x */
+  const double *pv = p, *qv = q;
+  double w = 1.0;
+  if (S->mid) {
+    sys_midpoint(S, p, q, S->pm0, S->qm0);
+    pv = S->pm0; qv = S->qm0; w = 0.5;
+  }
   memset(S->g, 0, sizeof(double) * 6 * ns);
   memset(S->D, 0, sizeof(double) * 36 * ns);
   for (int i = n0; i < n0 + ns; ++i) {
     double g6[6], H6[36];
-    particle_terms(S->C, P->mass[i], P->radius[i], p + 3 * i, q + 4 * i, S->phat + 3 * i, S->qhat + 4 * i, g6, H6);
+    particle_terms(S->C, P->mass[i], P->radius[i], p + 3 * i, q + 4 * i, pv + 3 * i, w, S->phat + 3 * i,
+                   S->qhat + 4 * i, g6, H6);
     for (int a = 0; a < 6; ++a) S->g[6 * (i - n0) + a] += g6[a];
     memcpy(S->Hp + 36 * (i - n0), H6, sizeof H6);
     for (int a = 0; a < 36; ++a) S->D[36 * (i - n0) + a] += H6[a];
@@ -919,14 +989,15 @@ static void sys_assemble(scene_sys* S, const double* p, const double* q, int mas
       int bd = S->bonds[k];
       a = P->bi[bd]; b = P->bj[bd];
       H12 = S->Hb + 144 * k;
-      orc_bond_terms(P, bd, p + 3 * a, q + 4 * a, p + 3 * b, q + 4 * b, NULL, g12, NULL, H12);
+      orc_bond_terms_at(P, bd, pv + 3 * a, qv + 4 * a, pv + 3 * b, qv + 4 * b, q + 4 * a, q + 4 * b, w, NULL, g12,
+                        NULL, H12);
     } else {
       int c = k - S->nbond;
       a = S->cand[2 * c]; b = S->cand[2 * c + 1];
       H12 = S->Hc + 144 * c;
       g_order = 2;
-      jet V = contact_energy_jet(S->C->k_self, P->radius[a] + P->radius[b], p + 3 * a, p + 3 * b);
-      pair_reduce(&V, q + 4 * a, q + 4 * b, g12, H12);
+      jet V = contact_energy_jet(S->C->k_self, P->radius[a] + P->radius[b], pv + 3 * a, pv + 3 * b);
+      pair_reduce(&V, q + 4 * a, q + 4 * b, w, g12, H12);
       orc_eig_clamp(12, H12);
     }
     int ia = a - n0, ib = b - n0;
@@ -1043,6 +1114,21 @@ static int pcg(const scene_sys* S, const double* b, double eps_r, int max_iter, 
   return it;
 }
 
+static void sys_zhat(const scene_sys* S, const double* phat, const double* qhat, double* zp, double* zq);
+
+int orc_zhat(const orc_config* C, const orc_problem* P, int scene, const double* phat, const double* qhat,
+             double* zp, double* zq) {
+  scene_sys S;
+  sys_init(&S, C, P, scene, phat, qhat);
+  sys_set_candidates(&S, scene, phat);
+  memcpy(zp, phat, sizeof(double) * 3 * P->n);
+  memcpy(zq, qhat, sizeof(double) * 4 * P->n);
+  sys_zhat(&S, phat, qhat, zp, zq);
+  int nc = S.ncand;
+  sys_free(&S);
+  return nc;
+}
+
 int orc_system(const orc_config* C, const orc_problem* P, int scene, const double* p, const double* q,
                const double* phat, const double* qhat, double* phi, double* g, double* diag, double* bondH,
                int32_t* n_candidates) {
@@ -1090,12 +1176,68 @@ int orc_pcg_solve(const orc_config* C, const orc_problem* P, int scene, const do
 /* velocity and are excluded from the solve.                                                          */
 /* ------------------------------------------------------------------------------------------------ */
 
+/* The target of the variational midpoint form (Sec. 3.1; App. C):
+ *   zhat = xhat - 1/2 M_s^{-1} dt^2 grad V((x_{n-1} + x_n)/2),  x_{n-1} = x_n - dt v_n,
+ * with the Euclidean gradient (R^3 x R^4 per particle) of every potential term of the scene at that midpoint: the
+ * intact bonds, gravity, the ground and the step's contact candidates. Kinematic particles keep zhat = xhat. */
+static void sys_zhat(const scene_sys* S, const double* phat, const double* qhat, double* zp, double* zq) {
+  const orc_problem* P = S->P;
+  const orc_config* C = S->C;
+  int n = P->n, n0 = S->n0, ns = S->ns;
+  double *pm = malloc(sizeof(double) * 3 * n), *qm = malloc(sizeof(double) * 4 * n);
+  double* ge = calloc(7 * (size_t)n, sizeof(double));
+  double dt = C->dt;
+  for (int i = n0; i < n0 + ns; ++i) {
+    for (int k = 0; k < 3; ++k) pm[3 * i + k] = P->p[3 * i + k] - 0.5 * dt * P->v[3 * i + k];
+    for (int k = 0; k < 4; ++k) qm[4 * i + k] = P->q[4 * i + k] - 0.5 * dt * P->u[4 * i + k];
+    double m = P->mass[i];
+    for (int k = 0; k < 3; ++k) ge[7 * i + k] = -m * C->gravity[k];
+    if (C->k_ground > 0.0) {
+      double gd = pm[3 * i + 2] - C->ground_z - P->radius[i];
+      if (gd < 0.0) ge[7 * i + 2] += C->k_ground * gd;
+    }
+  }
+  g_order = 2;
+  for (int k = 0; k < S->nbond + S->ncand; ++k) {
+    int a, b;
+    jet V;
+    if (k < S->nbond) {
+      int bd = S->bonds[k];
+      a = P->bi[bd]; b = P->bj[bd];
+      V = bond_energy_jet(P, bd, pm + 3 * a, qm + 4 * a, pm + 3 * b, qm + 4 * b, NULL, NULL, NULL, NULL);
+    } else {
+      int c = k - S->nbond;
+      a = S->cand[2 * c]; b = S->cand[2 * c + 1];
+      V = contact_energy_jet(C->k_self, P->radius[a] + P->radius[b], pm + 3 * a, pm + 3 * b);
+    }
+    double g14[14], H[196];
+    jet_grad_hess(&V, g14, H);
+    for (int c = 0; c < 7; ++c) { ge[7 * a + c] += g14[c]; ge[7 * b + c] += g14[7 + c]; }
+  }
+  for (int i = n0; i < n0 + ns; ++i) {
+    double m = P->mass[i], r = P->radius[i];
+    double cp = m / (dt * dt), cq = 1.6 * m * r * r / (dt * dt);
+    int kin = P->kinematic && P->kinematic[i];
+    for (int k = 0; k < 3; ++k) zp[3 * i + k] = kin ? phat[3 * i + k] : phat[3 * i + k] - 0.5 * ge[7 * i + k] / cp;
+    for (int k = 0; k < 4; ++k) zq[4 * i + k] = kin ? qhat[4 * i + k] : qhat[4 * i + k] - 0.5 * ge[7 * i + 3 + k] / cq;
+  }
+  free(pm); free(qm); free(ge);
+}
+
 static int newton_scene(const orc_config* C, orc_problem* P, int scene, double* xp, double* xq, const double* phat,
                         const double* qhat, orc_scene_stats* st) {
   scene_sys S;
   sys_init(&S, C, P, scene, phat, qhat);
   sys_set_candidates(&S, scene, xp);
   st->n_candidates = S.ncand;
+  double *zp = NULL, *zq = NULL;
+  if (S.mid) {  /* the inertia targets become zhat */
+    zp = malloc(sizeof(double) * 3 * P->n);
+    zq = malloc(sizeof(double) * 4 * P->n);
+    sys_zhat(&S, phat, qhat, zp, zq);
+    S.phat = zp;
+    S.qhat = zq;
+  }
   int n0 = S.n0, ns = S.ns, n6 = 6 * ns, status = 0;
   double *dx = malloc(sizeof(double) * n6), *rhs = malloc(sizeof(double) * n6);
   double *tp = malloc(sizeof(double) * 3 * P->n), *tq = malloc(sizeof(double) * 4 * P->n);
@@ -1138,7 +1280,7 @@ static int newton_scene(const orc_config* C, orc_problem* P, int scene, double* 
   }
   st->newton_iters = k;
   st->status = status;
-  free(dx); free(rhs); free(tp); free(tq);
+  free(dx); free(rhs); free(tp); free(tq); free(zp); free(zq);
   sys_free(&S);
   return status;
 }

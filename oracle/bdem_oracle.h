@@ -35,6 +35,9 @@ typedef struct {
   double contact_skin;     /* candidate distance margin */
   double mu_slide;         /* sliding friction coefficient of the post-step friction (0: off) */
   double mu_roll;          /* rotation friction coefficient (0: off) */
+  int32_t integrator;      /* 0: the implicit-Euler-like form (V at x_{n+1}); 1: the variational midpoint form of
+                              Sec. 3.1 / App. C (V at (x_{n+1} + x_n)/2 and the target zhat) */
+  int32_t pad1;
 } orc_config;
 
 /* Particle, bond and scene arrays. Bond rest data is filled by orc_bond_rest(). */
@@ -86,6 +89,13 @@ int orc_step(const orc_config* C, orc_problem* P, orc_scene_stats* stats);
 void orc_bond_terms(const orc_problem* P, int b, const double pi[3], const double qi[4], const double pj[3],
                     const double qj[4], double* energy, double* grad12, double* hess12, double* hess12_spd);
 
+/* The same for the bond term x -> V_b(w x + (1 - w) x_n) of the variational midpoint form (w = 1/2): the energy
+ * and its Euclidean derivatives are taken at the evaluation point (pv, qv), scaled by w and w^2, and reduced at the
+ * state's quaternions (qi, qj). orc_bond_terms is the case pv = p, qv = q, w = 1. */
+void orc_bond_terms_at(const orc_problem* P, int b, const double pvi[3], const double qvi[4], const double pvj[3],
+                       const double qvj[4], const double qi[4], const double qj[4], double w, double* energy,
+                       double* grad12, double* hess12, double* hess12_spd);
+
 /* Stresses (sigma, tau) of one bond at the state (p[n][3], q[n][4]) for the stress fracture criterion. */
 void orc_bond_stress(const orc_problem* P, int b, const double* p, const double* q, double out[2]);
 
@@ -93,13 +103,23 @@ void orc_bond_stress(const orc_problem* P, int b, const double* p, const double*
 void orc_bond_energy_parts(const orc_problem* P, int b, const double pi[3], const double qi[4],
                            const double pj[3], const double qj[4], double parts[3]);
 
-/* The Newton system of one scene at state (p, q) with inertia targets (phat, qhat) and the contact
+/* With integrator = 1 every potential term below is evaluated at the midpoint ((p, q) + (P->p, P->q))/2 of the
+ * state and the step's start state held in the problem, its Euclidean derivatives scaled by 1/2 (gradient) and
+ * 1/4 (Hessian) and reduced at (p, q); the inertia targets are then zhat.
+ *
+ * The Newton system of one scene at state (p, q) with inertia targets (phat, qhat) and the contact
  * candidates found at (p, q): objective Phi, reduced gradient g[6n_s], assembled projected diagonal
  * blocks diag[n_s][36], per-bond projected 12x12 Hessians bondH[nb][144] (intact bonds of the scene,
  * NULL allowed), and the number of contact candidates. Kinematic particles are not masked here. */
 int orc_system(const orc_config* C, const orc_problem* P, int scene, const double* p, const double* q,
                const double* phat, const double* qhat, double* phi, double* g, double* diag, double* bondH,
                int32_t* n_candidates);
+
+/* The variational midpoint target zhat = xhat - 1/2 M_s^{-1} dt^2 grad V((x_{n-1} + x_n)/2) of one scene (Sec. 3.1,
+ * App. C), x_n the problem's state and x_{n-1} = x_n - dt v_n, contact candidates found at phat; zp [n][3], zq
+ * [n][4] get xhat outside the scene. Returns the number of contact candidates. */
+int orc_zhat(const orc_config* C, const orc_problem* P, int scene, const double* phat, const double* qhat,
+             double* zp, double* zq);
 
 /* y = H x for the projected Hessian of orc_system (same arguments), x and y [6 n_s]. */
 int orc_matvec(const orc_config* C, const orc_problem* P, int scene, const double* p, const double* q,

@@ -6,7 +6,7 @@ parity report whose FP64 agreement is limited by it, this runs the oracle (and n
 and at 1/100 of it and records the
 largest position difference (relative to the bounding-box diagonal) and quaternion difference over the steps.
 
-    python tests/golden/make_newton_spread.py
+    python tests/golden/make_newton_spread.py [case ...]   # all cases, or only the named ones (merged into the file)
 """
 import json
 import os
@@ -25,6 +25,8 @@ from paper_2308_10459_gb300 import scenes  # noqa: E402
 CASES = {
     "c4": (lambda: scenes.c4_batched(n_scenes=3, n_min=150, n_max=400, heights=(0.0002, 0.001)), 25, 1e-6),
     "c5": (lambda: scenes.c5_impact(n_slab=600, n_ball=80, footprint=0.035, ball_R=0.008), 3, 1e-6),
+    # the plate at R = 50 mm (about 6,800 particles) of the PCG launch-shape test: two grids that round differently
+    "plate50": (lambda: scenes.c2_plate_small(R=0.05), 2, 1e-6),
 }
 
 
@@ -48,16 +50,22 @@ def spread(make, steps, tol):
     return ep, eq
 
 
-def main():
+def main(names):
     oracle.build()
+    path = os.path.join(HERE, "newton_spread.json")
     out = {}
+    if names and os.path.exists(path):
+        with open(path) as f:
+            out = json.load(f)
     for name, (make, steps, tol) in CASES.items():
+        if names and name not in names:
+            continue
         ep, eq = spread(make, steps, tol)
         out[name] = {"steps": steps, "newton_rel_tol": tol, "pos": ep, "quat": eq}
         print(name, out[name], flush=True)
-    with open(os.path.join(HERE, "newton_spread.json"), "w") as f:
+    with open(path, "w") as f:
         json.dump(out, f, indent=1)
 
 
 if __name__ == "__main__":
-    main()
+    main(sys.argv[1:])
