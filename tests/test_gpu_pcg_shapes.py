@@ -4,8 +4,14 @@ A block whose rows fit beside the other blocks of its SM keeps its row descripto
 memory; a larger share is read from L2 at every product. On the plate construction at R = 50 mm (about 6,800
 particles) a 2-block grid takes the second form and a 64-block grid the first; both solve the assembled FP64 system
 to the requested residual (checked with an independent product), within a few iterations of each other, and give the
-same trajectory to 1e-9.
+same trajectory up to what the Newton stopping test leaves open: each run stops once |g| <= 1e-6 |g_0| (Sec. 5,
+Alg. 3), which pins this scene's state down only to the distance the oracle's own trajectory moves when that
+tolerance is tightened 100x (tests/golden/newton_spread.json, "plate50"); two runs that round differently can stop
+on either side of the converged state, so they are held to twice that distance.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -46,5 +52,7 @@ def test_staged_and_unstaged_grids_agree():
     scale = np.abs(sols[64]).max()
     assert np.abs(sols[2] - sols[64]).max() <= 1e-3 * scale  # two solves to 1e-6 of an ill-conditioned system
     L = float(np.linalg.norm(sc.pos.max(0) - sc.pos.min(0)))
-    assert np.abs(traj[2]["pos"] - traj[64]["pos"]).max() <= 1e-9 * L
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "newton_spread.json")) as f:
+        spread = json.load(f)["plate50"]
+    assert np.abs(traj[2]["pos"] - traj[64]["pos"]).max() <= 2.0 * max(1e-9, spread["pos"]) * L
     assert np.array_equal(traj[2]["broken"], traj[64]["broken"])
