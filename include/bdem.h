@@ -52,6 +52,7 @@ typedef enum {
 enum { BDEM_FP64 = 0, BDEM_MIXED = 1 };   /* bdem_config.precision */
 enum { BDEM_SPD_EIG = 0 };                /* bdem_config.spd_mode */
 enum { BDEM_OPT_SECOND_ORDER = 0, BDEM_OPT_FIRST_ORDER = 1 };  /* bdem_config.optimizer */
+enum { BDEM_INT_EULER = 0, BDEM_INT_MIDPOINT = 1 };             /* bdem_config.integrator */
 
 /* Bond material (Sec. 3.2). G = E / (2 (1 + nu)) (isotropic relation; the paper does not define G). */
 typedef struct {
@@ -93,6 +94,15 @@ typedef struct {
                                dw = -min(1, mu_r |F_n| r^3 dt / (I |w_ij|)) w_ij per contact (I = 2/5 m r^2,
                                relative velocities of the element pair, the ground at rest), summed, projected on
                                the element's own velocity direction and clamped so that it only slows down */
+  int32_t integrator;       /* BDEM_INT_EULER (0): Phi(x) = 1/(2 dt^2) (x - xhat)^T M_s (x - xhat) + V(x), the
+                               first-order form the paper uses in its experiments (Sec. 3.1, Eq.
+                               implicit_euler_integrator). BDEM_INT_MIDPOINT (1): the variational midpoint form
+                               (Sec. 3.1, App. C): Phi(x) = 1/(2 dt^2) (x - zhat)^T M_s (x - zhat) + V((x + x_n)/2)
+                               with zhat = xhat - 1/2 M_s^{-1} dt^2 grad V((x_{n-1} + x_n)/2), x_{n-1} = x_n - dt v_n;
+                               every potential (bonds, gravity, ground, self contact) at the plain average of the two
+                               states in R^3 x R^4 (quaternions not renormalised); contact candidates and fracture as
+                               for BDEM_INT_EULER */
+  int32_t reserved1;        /* 0 */
 } bdem_config;
 
 /* Per-scene statistics of one bdem_step call (sums over its steps, norms of the last step). */
@@ -184,6 +194,18 @@ const char* bdem_last_error(const bdem_sim* sim);
  * caller's order, bonds in their order of addition. */
 bdem_status bdem_debug_system(bdem_sim* sim, const double* phat, const double* qhat, double* g, double* diag,
                               double* bond_hess, int64_t* n_candidates);
+
+/* The same at the iterate x = (pos [n][3], quat [n][4]) given by the caller (both NULL: the committed state). The
+ * committed state is the step's start state x_n of the variational midpoint form (bdem_config.integrator), whose
+ * potentials are then evaluated at (x + x_n)/2; contact candidates are collected at x. */
+bdem_status bdem_debug_system_at(bdem_sim* sim, const double* pos, const double* quat, const double* phat,
+                                 const double* qhat, double* g, double* diag, double* bond_hess, int64_t* n_candidates);
+
+/* The inertia targets a step from the committed state uses, in the caller's order: xhat = x_n + dt v_n with
+ * BDEM_INT_EULER; with BDEM_INT_MIDPOINT zhat = xhat - 1/2 M_s^{-1} dt^2 grad V((x_{n-1} + x_n)/2) (Sec. 3.1,
+ * App. C; x_{n-1} = x_n - dt v_n; the step's contact candidates, collected at (xhat, qhat/|qhat|)). zp [n][3],
+ * zq [n][4] host. Replaces the system of the last bdem_debug_system call. */
+bdem_status bdem_debug_zhat(bdem_sim* sim, double* zp, double* zq);
 
 /* Per-bond projected reduced Hessians [count][12][12] of the bonds ids[k] (order of addition) from the system of the
  * last bdem_debug_system call (called with bond_hess = NULL to skip the full download). */

@@ -19,6 +19,7 @@ LIB_PATH = _build_mod.LIB
 BDEM_OK, BDEM_E_INVALID, BDEM_E_NOMEM, BDEM_E_CUDA = 0, 1, 2, 3
 BDEM_E_NEWTON_MAXITER, BDEM_E_LINESEARCH, BDEM_E_NONFINITE, BDEM_E_TIMEOUT = 4, 5, 6, 7
 BDEM_FP64, BDEM_MIXED = 0, 1
+BDEM_INT_EULER, BDEM_INT_MIDPOINT = 0, 1
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "NOMEM", 3: "CUDA", 4: "NEWTON_MAXITER", 5: "LINESEARCH", 6: "NONFINITE",
                 7: "TIMEOUT"}
 
@@ -36,7 +37,8 @@ class bdem_config(ctypes.Structure):
                 ("ls_max_halvings", ctypes.c_int32), ("precision", ctypes.c_int32), ("ground_z", ctypes.c_double),
                 ("k_ground", ctypes.c_double), ("k_self", ctypes.c_double), ("contact_skin", ctypes.c_double),
                 ("spd_mode", ctypes.c_int32), ("optimizer", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
-                ("friction_slide", ctypes.c_double), ("friction_roll", ctypes.c_double)]
+                ("friction_slide", ctypes.c_double), ("friction_roll", ctypes.c_double),
+                ("integrator", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
 
 
 class bdem_step_stats(ctypes.Structure):
@@ -75,6 +77,8 @@ _PROTOS = {
     "bdem_destroy": (None, [_vp]),
     "bdem_last_error": (ctypes.c_char_p, [_vp]),
     "bdem_debug_system": (ctypes.c_int, [_vp, _dp, _dp, _dp, _dp, _dp, _lp]),
+    "bdem_debug_system_at": (ctypes.c_int, [_vp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _lp]),
+    "bdem_debug_zhat": (ctypes.c_int, [_vp, _dp, _dp]),
     "bdem_debug_matvec": (ctypes.c_int, [_vp, _dp, _dp]),
     "bdem_debug_bonds": (ctypes.c_int, [_vp, ctypes.c_int64, _ip, _dp]),
     "bdem_debug_bond_stress": (ctypes.c_int, [_vp, _dp]),
@@ -150,6 +154,7 @@ def make_config(cfg: dict, precision=BDEM_FP64, cuda_stream=None) -> bdem_config
     c.cuda_stream = cuda_stream
     c.friction_slide = cfg.get("friction_slide", 0.0)
     c.friction_roll = cfg.get("friction_roll", 0.0)
+    c.integrator = int(cfg.get("integrator", 0))
     return c
 
 
@@ -247,15 +252,30 @@ class Sim:
 
     write_state = bdem_write_state
 
-    def bdem_debug_system(self, phat, qhat, want_bonds=True):
+    def bdem_debug_system(self, phat, qhat, want_bonds=True, pos=None, quat=None):
+        """The Newton system at the committed state, or at the iterate (pos, quat) when given (bdem_debug_system_at)."""
         n, nb, _ = self.sizes()
         phat, qhat = _arr(phat, np.float64, (n, 3)), _arr(qhat, np.float64, (n, 4))
         g, D = np.zeros((n, 6)), np.zeros((n, 6, 6))
         H = np.zeros((max(nb, 1), 12, 12)) if want_bonds else None
         nc = ctypes.c_int64()
-        self._check(self.L.bdem_debug_system(self.h, _ptr(phat, _dp), _ptr(qhat, _dp), _ptr(g, _dp), _ptr(D, _dp),
-                                             _ptr(H, _dp) if want_bonds else None, ctypes.byref(nc)))
+        if pos is None:
+            self._check(self.L.bdem_debug_system(self.h, _ptr(phat, _dp), _ptr(qhat, _dp), _ptr(g, _dp),
+                                                 _ptr(D, _dp), _ptr(H, _dp) if want_bonds else None,
+                                                 ctypes.byref(nc)))
+        else:
+            pos, quat = _arr(pos, np.float64, (n, 3)), _arr(quat, np.float64, (n, 4))
+            self._check(self.L.bdem_debug_system_at(self.h, _ptr(pos, _dp), _ptr(quat, _dp), _ptr(phat, _dp),
+                                                    _ptr(qhat, _dp), _ptr(g, _dp), _ptr(D, _dp),
+                                                    _ptr(H, _dp) if want_bonds else None, ctypes.byref(nc)))
         return dict(g=g, diag=D, bondH=None if H is None else H[:nb], n_candidates=nc.value)
+
+    def bdem_debug_zhat(self):
+        """The inertia targets of a step from the committed state: xhat, or zhat in the midpoint form."""
+        n = self.sizes()[0]
+        zp, zq = np.zeros((n, 3)), np.zeros((n, 4))
+        self._check(self.L.bdem_debug_zhat(self.h, _ptr(zp, _dp), _ptr(zq, _dp)))
+        return zp, zq
 
     def bdem_debug_bonds(self, ids):
         ids = _arr(ids, np.int32)

@@ -231,6 +231,8 @@ static bdem_status check_config(const bdem_config* c) {
   if (c->spd_mode != BDEM_SPD_EIG) return fail(nullptr, BDEM_E_INVALID, "spd_mode must be BDEM_SPD_EIG");
   if (c->optimizer != BDEM_OPT_SECOND_ORDER && c->optimizer != BDEM_OPT_FIRST_ORDER)
     return fail(nullptr, BDEM_E_INVALID, "optimizer must be BDEM_OPT_SECOND_ORDER or BDEM_OPT_FIRST_ORDER");
+  if (c->integrator != BDEM_INT_EULER && c->integrator != BDEM_INT_MIDPOINT)
+    return fail(nullptr, BDEM_E_INVALID, "integrator must be BDEM_INT_EULER or BDEM_INT_MIDPOINT");
   if (!(c->k_ground >= 0.0) || !(c->k_self >= 0.0) || !(c->contact_skin >= 0.0) || !fin(c->ground_z) ||
       !fin(c->k_ground) || !fin(c->k_self) || !fin(c->contact_skin))
     return fail(nullptr, BDEM_E_INVALID, "contact parameters must be finite and >= 0");
@@ -540,6 +542,7 @@ extern "C" bdem_status bdem_create(const bdem_config* config, int32_t n_scenes, 
   d.mu_slide = c.friction_slide;
   d.wait_ns = 2000000000ull;  // 2 s
   d.first_order = c.optimizer == BDEM_OPT_FIRST_ORDER;
+  d.midpoint = c.integrator == BDEM_INT_MIDPOINT;
   d.mu_roll = c.friction_roll;
   double rmax = 0.0;
   for (int64_t i = 0; i < n; ++i) rmax = std::max(rmax, radius[i]);
@@ -880,6 +883,7 @@ static bdem_status do_step(bdem_sim* s, std::vector<SceneCtl>& ctl) {
     CUDA_TRY(s, cudaMemsetAsync(d.c_start, 0, sizeof(int32_t) * (d.n + 1), st));
   }
   TRY(check_launch(s, launch_scene_reduce(d, RED_CAND, 0, st)));
+  TRY(check_launch(s, launch_zhat(d, st)));
   phase_end(s);
   Counters c{};
   for (int k = 0;; ++k) {
@@ -1006,6 +1010,7 @@ static bool build_step_graph(bdem_sim* s) {
       cudaMemsetAsync(d.c_start, 0, sizeof(int32_t) * (d.n + 1), st);
     }
     pre += launch_scene_reduce(d, RED_CAND, 0, st);
+    pre += launch_zhat(d, st);
     pre += launch_bond_grad(d, 0, st);
     pre += launch_particle_grad(d, 1, 0, st);
     pre += launch_scene_reduce(d, RED_GRAD, hN, st);
@@ -1275,8 +1280,15 @@ static bdem_status dbg_reserve(bdem_sim* s, size_t count) {
 
 extern "C" bdem_status bdem_debug_system(bdem_sim* s, const double* phat, const double* qhat, double* g, double* diag,
                                          double* bond_hess, int64_t* n_candidates) {
+  return bdem_debug_system_at(s, nullptr, nullptr, phat, qhat, g, diag, bond_hess, n_candidates);
+}
+
+extern "C" bdem_status bdem_debug_system_at(bdem_sim* s, const double* pos, const double* quat, const double* phat,
+                                            const double* qhat, double* g, double* diag, double* bond_hess,
+                                            int64_t* n_candidates) {
   if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
   if (!phat || !qhat) return fail(s, BDEM_E_INVALID, "phat and qhat are required");
+  if ((pos == nullptr) != (quat == nullptr)) return fail(s, BDEM_E_INVALID, "pos and quat go together");
   DevArrays& d = s->d;
   cudaStream_t st = s->stream;
   size_t n = (size_t)s->n;
@@ -1285,8 +1297,15 @@ extern "C" bdem_status bdem_debug_system(bdem_sim* s, const double* phat, const 
     CUDA_TRY(s, cudaMemcpyAsync(sp, phat, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
     CUDA_TRY(s, cudaMemcpyAsync(sq, qhat, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, st));
     TRY(check_launch(s, launch_set_hat(d, sp, sq, st)));
-    CUDA_TRY(s, cudaMemcpyAsync(d.xp, d.x0p, sizeof(double4) * n, cudaMemcpyDeviceToDevice, st));
-    CUDA_TRY(s, cudaMemcpyAsync(d.xq, d.x0q, sizeof(double4) * n, cudaMemcpyDeviceToDevice, st));
+    if (pos) {
+      double *sx = s->stage + stage_off(n, 2), *sy = s->stage + stage_off(n, 3);
+      CUDA_TRY(s, cudaMemcpyAsync(sx, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+      CUDA_TRY(s, cudaMemcpyAsync(sy, quat, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, st));
+      TRY(check_launch(s, launch_set_iterate(d, sx, sy, st)));
+    } else {
+      CUDA_TRY(s, cudaMemcpyAsync(d.xp, d.x0p, sizeof(double4) * n, cudaMemcpyDeviceToDevice, st));
+      CUDA_TRY(s, cudaMemcpyAsync(d.xq, d.x0q, sizeof(double4) * n, cudaMemcpyDeviceToDevice, st));
+    }
   }
   TRY(check_launch(s, launch_scene_reduce(d, RED_FORCE_ACTIVE, 0, st)));
   if (d.k_self > 0.0 && d.n > 0) TRY(build_contacts(s));
@@ -1321,6 +1340,26 @@ extern "C" bdem_status bdem_debug_system(bdem_sim* s, const double* phat, const 
   TRY(sync(s));
   s->system_ready = true;
   return BDEM_OK;
+}
+
+extern "C" bdem_status bdem_debug_zhat(bdem_sim* s, double* zp, double* zq) {
+  if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
+  if (!zp || !zq) return fail(s, BDEM_E_INVALID, "zp and zq are required");
+  DevArrays& d = s->d;
+  cudaStream_t st = s->stream;
+  size_t n = (size_t)s->n;
+  if (n == 0) return BDEM_OK;
+  TRY(check_launch(s, launch_predict(d, st)));
+  if (d.k_self > 0.0) TRY(build_contacts(s));
+  else CUDA_TRY(s, cudaMemsetAsync(d.c_start, 0, sizeof(int32_t) * (d.n + 1), st));
+  TRY(check_launch(s, launch_zhat(d, st)));
+  // hp, hq (double4) to the caller's order through the staging buffer
+  double *sp = s->stage + stage_off(n, 0), *sq = s->stage + stage_off(n, 1);
+  TRY(check_launch(s, launch_pack_hat(d, sp, sq, st)));
+  CUDA_TRY(s, cudaMemcpyAsync(zp, sp, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(s, cudaMemcpyAsync(zq, sq, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, st));
+  s->system_ready = false;
+  return sync(s);
 }
 
 extern "C" bdem_status bdem_debug_bonds(bdem_sim* s, int64_t count, const int32_t* ids, double* out) {

@@ -133,6 +133,11 @@ struct BondEval {
   V3<double> dhat, cd;  // cd = grad_d c
   double rho_m, c, sigma;
   AngleFn fa;
+  // variational midpoint form only (bond_first_order_mid): the bend-twist chain factors at the reduction
+  // quaternions (ri, rj) of the state, conj(q_j^mid) ri = (ra, sa) and conj(q_i^mid) rj = (rb, sb), and
+  // conj(ri) rj = (sv, ss)
+  V3<double> ra, rb, sv;
+  double sa, sb, ss;
 };
 
 // K r with K = ktw d0 d0^T + kb (I - d0 d0^T) (the bend-twist stiffness in the bond frame, expressed in the frame of
@@ -223,6 +228,51 @@ __device__ __forceinline__ void bond_first_order(const BondParams& b, V3<double>
   E.g[6] = gyj.x; E.g[7] = gyj.y; E.g[8] = gyj.z;
 }
 
+// The bond term x -> V_b((x + x_n)/2) of the variational midpoint form (Sec. 3.1; App. C): the energy and its
+// Euclidean derivatives are taken at the midpoint (pvi, qvi, pvj, qvj), scaled by 1/2 per derivative, and reduced
+// at the state's quaternions (ri, rj), whose retraction moves the midpoint by 1/2 G_l(r)^T y. With
+// J_i = G_l(q_j^mid) G_l(ri)^T = sa I + [ra]x and J_j = -G_l(q_i^mid) G_l(rj)^T = -(sb I + [rb]x) (the bend-twist
+// vector r = vec(conj(q_j) q_i) = G_l(q_j) q_i = -G_l(q_i) q_j is bilinear), the gradient is
+// (1/2 grad_d V, 1/2 (J_i^T kappa + s1 G_l(ri) grad_m c), 1/2 (J_j^T kappa + s1 sigma G_l(rj) grad_m c)).
+__device__ __forceinline__ void bond_first_order_mid(const BondParams& b, V3<double> pvi, Q4<double> qvi,
+                                                     V3<double> pvj, Q4<double> qvj, Q4<double> ri, Q4<double> rj,
+                                                     BondEval& E) {
+  bond_first_order(b, pvi, qvi, pvj, qvj, E);  // every value at the midpoint
+  Q4<double> ta = qmul(qconj(qvj), ri), tb = qmul(qconj(qvi), rj), tv = qmul(qconj(ri), rj);
+  E.ra = qvec(ta);
+  E.sa = ta.w;
+  E.rb = qvec(tb);
+  E.sb = tb.w;
+  E.sv = qvec(tv);
+  E.ss = tv.w;
+  V3<double> ka = E.kappa;
+  V3<double> gyi = E.sa * ka - cross(E.ra, ka);
+  V3<double> gyj = cross(E.rb, ka) - E.sb * ka;
+  double s1 = 0.5 * b.kt * E.fa.f1;
+  V3<double> gd = (b.kn * E.elong) * E.n + s1 * E.cd;
+  gyi = gyi + s1 * gl_mul(ri, E.gm);
+  gyj = gyj + (s1 * E.sigma) * gl_mul(rj, E.gm);
+  E.g[0] = 0.5 * gd.x; E.g[1] = 0.5 * gd.y; E.g[2] = 0.5 * gd.z;
+  E.g[3] = 0.5 * gyi.x; E.g[4] = 0.5 * gyi.y; E.g[5] = 0.5 * gyi.z;
+  E.g[6] = 0.5 * gyj.x; E.g[7] = 0.5 * gyj.y; E.g[8] = 0.5 * gyj.z;
+}
+
+// Euclidean gradient of the bond energy at (pi, qi, pj, qj) in (d = p_j - p_i, q_i, q_j) (11 values): grad_d,
+// G_l(q_j)^T kappa + s1 grad_m c = q_j (x) (kappa, 0) + s1 grad_m c, and -q_i (x) (kappa, 0) + s1 sigma grad_m c
+__device__ __forceinline__ void bond_euclid_grad(const BondParams& b, V3<double> pi, Q4<double> qi, V3<double> pj,
+                                                 Q4<double> qj, double g[11]) {
+  BondEval E;
+  bond_first_order(b, pi, qi, pj, qj, E);
+  double s1 = 0.5 * b.kt * E.fa.f1;
+  V3<double> gd = (b.kn * E.elong) * E.n + s1 * E.cd;
+  Q4<double> kq = {E.kappa.x, E.kappa.y, E.kappa.z, 0.0};
+  Q4<double> ga = qmul(qj, kq), gb = qmul(qi, kq);
+  g[0] = gd.x; g[1] = gd.y; g[2] = gd.z;
+  g[3] = ga.x + s1 * E.gm.x; g[4] = ga.y + s1 * E.gm.y; g[5] = ga.z + s1 * E.gm.z; g[6] = ga.w + s1 * E.gm.w;
+  double s2 = s1 * E.sigma;
+  g[7] = -gb.x + s2 * E.gm.x; g[8] = -gb.y + s2 * E.gm.y; g[9] = -gb.z + s2 * E.gm.z; g[10] = -gb.w + s2 * E.gm.w;
+}
+
 // stresses of the stress fracture criterion (Sec. 3.2, Fracture Criteria) from the implicit potentials:
 // |F_n| = |grad_p V_stretch| = kn |l - l0|; |F_s| = |grad_p V_shear| = |1/2 kt f'(c)| |grad_d c|; the bend-twist
 // moment kappa = K r split into its twist part along the bond axis d0 and its bending part;
@@ -263,14 +313,17 @@ __device__ __forceinline__ void hadd(T* H, int a, int b, T v) {  // H[a][b] += v
   H[sidx<9>(a, b)] += v;
 }
 
-template <typename T>
+// MID: the bond term x -> V_b((x + x_n)/2) of the variational midpoint form; E from bond_first_order_mid, (qi, qj)
+// the state's quaternions at which the reduction takes place. Every second derivative of the energy enters with
+// the factor 1/4, the retraction's second-order (curvature) terms with 1/2.
+template <typename T, bool MID = false>
 __device__ void bond_hessian(const BondParams& b, Q4<double> qi, Q4<double> qj, const BondEval& E, T* H /*45*/) {
 #pragma unroll
   for (int k = 0; k < 45; ++k) H[k] = (T)0;
   // ---- stretch: kn n n^T + kn (l - l0)/l (I - n n^T) on the d block
   {
     T nn[3] = {(T)E.n.x, (T)E.n.y, (T)E.n.z};
-    T kn = (T)b.kn, kp = (T)(b.kn * E.elong / E.l);
+    T kn = (T)(MID ? 0.25 * b.kn : b.kn), kp = (T)(MID ? 0.25 * (b.kn * E.elong / E.l) : b.kn * E.elong / E.l);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -285,14 +338,28 @@ __device__ void bond_hessian(const BondParams& b, Q4<double> qi, Q4<double> qj, 
     T kb = (T)b.kb, kdiff = (T)(b.ktw - b.kb);
     // J_i = s_r I + [r]x, J_j = -s_r I + [r]x ; [r]x = [[0,-rz,ry],[rz,0,-rx],[-ry,rx,0]]
     T Ji[3][3], Jj[3][3], KJi[3][3], KJj[3][3];
-    T rx[3][3] = {{0, -r[2], r[1]}, {r[2], 0, -r[0]}, {-r[1], r[0], 0}};
+    if constexpr (MID) {  // J_i = sa I + [ra]x, J_j = -(sb I + [rb]x)
+      T ra[3] = {(T)E.ra.x, (T)E.ra.y, (T)E.ra.z}, rb[3] = {(T)E.rb.x, (T)E.rb.y, (T)E.rb.z};
+      T sa = (T)E.sa, sb = (T)E.sb;
+      T ax[3][3] = {{0, -ra[2], ra[1]}, {ra[2], 0, -ra[0]}, {-ra[1], ra[0], 0}};
+      T bx[3][3] = {{0, -rb[2], rb[1]}, {rb[2], 0, -rb[0]}, {-rb[1], rb[0], 0}};
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+      for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        Ji[a][c] = rx[a][c] + (a == c ? sr : (T)0);
-        Jj[a][c] = rx[a][c] - (a == c ? sr : (T)0);
-      }
+        for (int c = 0; c < 3; ++c) {
+          Ji[a][c] = ax[a][c] + (a == c ? sa : (T)0);
+          Jj[a][c] = -bx[a][c] - (a == c ? sb : (T)0);
+        }
+    } else {
+      T rx[3][3] = {{0, -r[2], r[1]}, {r[2], 0, -r[0]}, {-r[1], r[0], 0}};
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          Ji[a][c] = rx[a][c] + (a == c ? sr : (T)0);
+          Jj[a][c] = rx[a][c] - (a == c ? sr : (T)0);
+        }
+    }
     // K J: K = kb I + (ktw - kb) d0 d0^T
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -312,15 +379,31 @@ __device__ void bond_hessian(const BondParams& b, Q4<double> qi, Q4<double> qj, 
         T ii = Ji[0][a] * KJi[0][c] + Ji[1][a] * KJi[1][c] + Ji[2][a] * KJi[2][c];
         T jj = Jj[0][a] * KJj[0][c] + Jj[1][a] * KJj[1][c] + Jj[2][a] * KJj[2][c];
         T ij = Ji[0][a] * KJj[0][c] + Ji[1][a] * KJj[1][c] + Ji[2][a] * KJj[2][c];
-        // second-order terms of the retraction: -(kappa.r) I on both diagonal blocks;
-        // r kappa^T + kappa r^T - (kappa.r) I - s_r [kappa]x on the (y_i, y_j) block
-        T dg = (a == c) ? kr : (T)0;
-        ij += r[a] * kap[c] + kap[a] * r[c] - dg - sr * kx[a][c];
-        if (c >= a) {
-          hadd(H, 3 + a, 3 + c, ii - dg);
-          hadd(H, 6 + a, 6 + c, jj - dg);
+        if constexpr (MID) {
+          // 1/4 J^T K J; retraction terms -1/2 (kappa.ra) I and +1/2 (kappa.rb) I on the diagonal blocks; on the
+          // (y_i, y_j) block 1/4 of the bilinear term G_l(ri) Q_r((kappa, 0)) G_l(rj)^T =
+          // -ss [kappa]x - sv kappa^T - kappa sv^T + (sv.kappa) I with conj(ri) rj = (sv, ss)
+          T sv[3] = {(T)E.sv.x, (T)E.sv.y, (T)E.sv.z};
+          T svk = (T)dot(E.sv, E.kappa), ss = (T)E.ss;
+          T da = (a == c) ? (T)(0.5 * dot(E.kappa, E.ra)) : (T)0;
+          T db = (a == c) ? (T)(0.5 * dot(E.kappa, E.rb)) : (T)0;
+          T m = -ss * kx[a][c] - sv[a] * kap[c] - kap[a] * sv[c] + ((a == c) ? svk : (T)0);
+          if (c >= a) {
+            hadd(H, 3 + a, 3 + c, (T)0.25 * ii - da);
+            hadd(H, 6 + a, 6 + c, (T)0.25 * jj + db);
+          }
+          hadd(H, 3 + a, 6 + c, (T)0.25 * (ij + m));
+        } else {
+          // second-order terms of the retraction: -(kappa.r) I on both diagonal blocks;
+          // r kappa^T + kappa r^T - (kappa.r) I - s_r [kappa]x on the (y_i, y_j) block
+          T dg = (a == c) ? kr : (T)0;
+          ij += r[a] * kap[c] + kap[a] * r[c] - dg - sr * kx[a][c];
+          if (c >= a) {
+            hadd(H, 3 + a, 3 + c, ii - dg);
+            hadd(H, 6 + a, 6 + c, jj - dg);
+          }
+          hadd(H, 3 + a, 6 + c, ij);
         }
-        hadd(H, 3 + a, 6 + c, ij);
       }
   }
   // ---- shear: 1/2 kt (f'' grad c grad c^T + f' Hess c)
@@ -453,6 +536,19 @@ __device__ void bond_hessian(const BondParams& b, Q4<double> qi, Q4<double> qj, 
         Hc[6 + a][6 + k] = jj - (a == k ? sg * qgj : (T)0);
         Hc[3 + a][6 + k] = sg * ij;
       }
+    if constexpr (MID) {  // chain factors: 1/2 on the gradient of c, 1/4 on its Hessian, 1/2 on the retraction terms
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        gc[a] *= (T)0.5;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Hc[a][k] *= (T)0.25;
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        Hc[3 + a][3 + a] -= (T)0.25 * qgi;
+        Hc[6 + a][6 + a] -= (T)0.25 * sg * qgj;
+      }
+    }
 #pragma unroll
     for (int a = 0; a < 9; ++a)
 #pragma unroll

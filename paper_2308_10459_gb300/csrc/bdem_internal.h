@@ -82,7 +82,8 @@ struct DevArrays {
   unsigned long long wait_ns;   // time limit of every device-side wait
   int32_t newton_max, pcg_max, ls_max;
   int32_t stress_on;            // some bond has a finite tensile or shear strength
-  int32_t first_order, pad3;    // first_order: descent direction -g (Alg. 1) instead of the Newton direction
+  int32_t first_order;          // descent direction -g (Alg. 1) instead of the Newton direction
+  int32_t midpoint;             // variational midpoint form: potentials at (x + x0)/2, inertia targets zhat
   // particles
   double4 *xp, *xq, *x0p, *x0q, *vp, *vq, *hp, *hq, *tp, *tq;
   double2* coef;
@@ -126,6 +127,11 @@ struct DevArrays {
 
 // ---- launchers (bdem_kernels.cu); each returns the number of kernels launched -----------------------------------
 int launch_predict(const DevArrays& d, cudaStream_t s);
+// variational midpoint form: zhat = xhat - 1/2 M^-1 dt^2 grad V((x_{n-1} + x_n)/2) into hp, hq (after the contact
+// candidates of the step exist); no launch otherwise
+int launch_zhat(const DevArrays& d, cudaStream_t s);
+// the iterate x (xp, xq) from the caller's order (inspection calls)
+int launch_set_iterate(const DevArrays& d, const double* pos3, const double* quat4, cudaStream_t s);
 // stage 0: hash + count, 1: fill, 2: capacity guard of the graph path (records the overflow and empties every
 // candidate list, so that no later kernel reads past the contact arrays)
 int launch_contacts(const DevArrays& d, int stage, cudaStream_t s);
@@ -157,6 +163,7 @@ int launch_pack_state(const DevArrays& d, double* pos3, double* quat4, double* v
 int launch_unpack_state(const DevArrays& d, const double* pos3, const double* quat4, const double* vel3,
                         const double* qvel4, cudaStream_t s);
 int launch_set_hat(const DevArrays& d, const double* phat3, const double* qhat4, cudaStream_t s);
+int launch_pack_hat(const DevArrays& d, double* phat3, double* qhat4, cudaStream_t s);  // hp, hq -> caller order
 int launch_bond_flags(const DevArrays& d, uint8_t* ext, int to_device, cudaStream_t s);
 int launch_convert_perm(const void* src, int src_double, void* dst, int dst_double, const int32_t* perm, int dir,
                         int n, cudaStream_t s);

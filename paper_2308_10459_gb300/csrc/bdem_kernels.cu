@@ -165,6 +165,19 @@ __device__ __forceinline__ bool step_aborted(const DevArrays& d) {
   return c->timeout || c->nonfinite || c->overflow || c->runaway;
 }
 
+// the variational midpoint form (Sec. 3.1; App. C) evaluates every potential at the plain average (x + x_n)/2 of the
+// state and the step's start state in R^3 x R^4 (.w of a position keeps the radius)
+__device__ __forceinline__ double4 mid4(double4 a, double4 b) {
+  return make_double4(0.5 * (a.x + b.x), 0.5 * (a.y + b.y), 0.5 * (a.z + b.z), a.w);
+}
+__device__ __forceinline__ Q4<double> midq(double4 a, double4 b) {
+  return {0.5 * (a.x + b.x), 0.5 * (a.y + b.y), 0.5 * (a.z + b.z), 0.5 * (a.w + b.w)};
+}
+// evaluation point of the potentials for particle i at the iterate arrays x (xp or tp)
+__device__ __forceinline__ double4 pot_p(const DevArrays& d, const double4* x, int i) {
+  return d.midpoint ? mid4(x[i], d.x0p[i]) : x[i];
+}
+
 // xhat = x_n + dt v_n; the initial guess x_0 = (phat, qhat/|qhat|) (Alg. 3; qhat itself stays unnormalised)
 __global__ void k_predict(DevArrays d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -179,6 +192,73 @@ __global__ void k_predict(DevArrays d) {
   d.hq[i] = hq;
   d.xp[i] = make_double4(hp.x, hp.y, hp.z, p.w);
   d.xq[i] = make_double4(hq.x / nq, hq.y / nq, hq.z / nq, hq.w / nq);
+}
+
+// The target of the variational midpoint form (Sec. 3.1; App. C): zhat = xhat - 1/2 M_s^{-1} dt^2 grad V(m) at the
+// midpoint m = (x_{n-1} + x_n)/2 = x_n - dt v_n / 2 (x_{n-1} = x_n - dt v_n), with the Euclidean gradient (R^3 x R^4
+// per particle) of the intact bonds, gravity, the ground and the step's contact candidates. The per-bond gradients
+// (d, q_i, q_j: 11 values, padded to 12) go to the bond-Hessian buffer, unused until the step's first Hessian.
+__global__ void __launch_bounds__(kTile) k_zhat_bonds(DevArrays d) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= d.nb || d.bbroken[b]) return;
+  int2 ij = d.bij[b];
+  double hdt = 0.5 * d.dt;
+  double4 pi = d.x0p[ij.x], pj = d.x0p[ij.y], vi = d.vp[ij.x], vj = d.vp[ij.y];
+  double4 qi = d.x0q[ij.x], qj = d.x0q[ij.y], ui = d.vq[ij.x], uj = d.vq[ij.y];
+  V3<double> mpi = {pi.x - hdt * vi.x, pi.y - hdt * vi.y, pi.z - hdt * vi.z};
+  V3<double> mpj = {pj.x - hdt * vj.x, pj.y - hdt * vj.y, pj.z - hdt * vj.z};
+  Q4<double> mqi = {qi.x - hdt * ui.x, qi.y - hdt * ui.y, qi.z - hdt * ui.z, qi.w - hdt * ui.w};
+  Q4<double> mqj = {qj.x - hdt * uj.x, qj.y - hdt * uj.y, qj.z - hdt * uj.z, qj.w - hdt * uj.w};
+  double g[11];
+  bond_euclid_grad(load_bond(d.brest[b], d.bstiff[b]), mpi, mqi, mpj, mqj, g);
+  double* out = reinterpret_cast<double*>(d.bM) + 12 * (size_t)b;
+#pragma unroll
+  for (int k = 0; k < 11; ++k) out[k] = g[k];
+}
+
+__device__ __forceinline__ double4 zhat_mid_p(const DevArrays& d, int i) {
+  double4 p = d.x0p[i], v = d.vp[i];
+  double hdt = 0.5 * d.dt;
+  return make_double4(p.x - hdt * v.x, p.y - hdt * v.y, p.z - hdt * v.z, p.w);
+}
+
+__global__ void __launch_bounds__(kTile) k_zhat_particles(DevArrays d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n || d.kin[i]) return;  // kinematic particles keep zhat = xhat
+  double4 hp = d.hp[i], hq = d.hq[i];
+  double m = hp.w;
+  double4 pm = zhat_mid_p(d, i);
+  double gp[3] = {-m * d.gx, -m * d.gy, -m * d.gz}, gq[4] = {0.0, 0.0, 0.0, 0.0};
+  if (d.k_ground > 0.0) {
+    double gd = pm.z - d.ground_z - pm.w;
+    if (gd < 0.0) gp[2] += d.k_ground * gd;
+  }
+  const double* gall = reinterpret_cast<const double*>(d.bM);
+  for (int e = d.inc_start[i]; e < d.inc_start[i + 1]; ++e) {
+    int ent = d.inc2[e].x, b = ent >> 1;
+    if (d.bbroken[b]) continue;
+    const double* g = gall + 12 * (size_t)b;
+    double sg = (ent & 1) ? 1.0 : -1.0;  // dV/dp_j = dV/dd, dV/dp_i = -dV/dd
+    const double* gqe = g + ((ent & 1) ? 7 : 3);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gp[k] += sg * g[k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) gq[k] += gqe[k];
+  }
+  if (d.k_self > 0.0)
+    for (int e = d.c_start[i]; e < d.c_start[i + 1]; ++e) {
+      double4 pj = zhat_mid_p(d, d.c_nbr[e]);
+      double ex = pm.x - pj.x, ey = pm.y - pj.y, ez = pm.z - pj.z;
+      double dd = sqrt(ex * ex + ey * ey + ez * ez), R = pm.w + pj.w;
+      if (dd < R) {
+        double f = d.k_self * (dd - R) / dd;
+        gp[0] += f * ex; gp[1] += f * ey; gp[2] += f * ez;
+      }
+    }
+  double2 cf = d.coef[i];
+  d.hp[i] = make_double4(hp.x - 0.5 * gp[0] / cf.x, hp.y - 0.5 * gp[1] / cf.x, hp.z - 0.5 * gp[2] / cf.x, m);
+  d.hq[i] = make_double4(hq.x - 0.5 * gq[0] / cf.y, hq.y - 0.5 * gq[1] / cf.y, hq.z - 0.5 * gq[2] / cf.y,
+                         hq.w - 0.5 * gq[3] / cf.y);
 }
 
 // ================================================================================================
@@ -355,22 +435,30 @@ __global__ void __launch_bounds__(kTile) k_bond_grad(DevArrays d, int all) {
   int2 ij = d.bij[b];
   BondParams bp = load_bond(d.brest[b], d.bstiff[b]);
   BondEval E;
-  bond_first_order(bp, to_v(d.xp[ij.x]), to_q(d.xq[ij.x]), to_v(d.xp[ij.y]), to_q(d.xq[ij.y]), E);
+  if (d.midpoint)
+    bond_first_order_mid(bp, to_v(mid4(d.xp[ij.x], d.x0p[ij.x])), midq(d.xq[ij.x], d.x0q[ij.x]),
+                         to_v(mid4(d.xp[ij.y], d.x0p[ij.y])), midq(d.xq[ij.y], d.x0q[ij.y]), to_q(d.xq[ij.x]),
+                         to_q(d.xq[ij.y]), E);
+  else
+    bond_first_order(bp, to_v(d.xp[ij.x]), to_q(d.xq[ij.x]), to_v(d.xp[ij.y]), to_q(d.xq[ij.y]), E);
 #pragma unroll
   for (int k = 0; k < 9; ++k) g[k] = E.g[k];
 }
 
-// inertia + gravity + ground (particle term) reduced gradient: (c_p (p - phat) - m g + ground, -c_q vec(conj(q) qhat))
+// inertia + gravity + ground (particle term) reduced gradient: (c_p (p - phat) - m g + ground, -c_q vec(conj(q) qhat));
+// in the midpoint form gravity and the ground act at the midpoint with the chain factor 1/2
 __device__ __forceinline__ void particle_term_grad(const DevArrays& d, int i, double g[6]) {
   double4 p = d.xp[i], q = d.xq[i], hp = d.hp[i], hq = d.hq[i];
   double2 cf = d.coef[i];
   double m = hp.w;
-  g[0] = cf.x * (p.x - hp.x) - m * d.gx;
-  g[1] = cf.x * (p.y - hp.y) - m * d.gy;
-  g[2] = cf.x * (p.z - hp.z) - m * d.gz;
+  double w = d.midpoint ? 0.5 : 1.0;
+  double4 pv = d.midpoint ? mid4(p, d.x0p[i]) : p;
+  g[0] = cf.x * (p.x - hp.x) - w * m * d.gx;
+  g[1] = cf.x * (p.y - hp.y) - w * m * d.gy;
+  g[2] = cf.x * (p.z - hp.z) - w * m * d.gz;
   if (d.k_ground > 0.0) {
-    double gd = p.z - d.ground_z - p.w;
-    if (gd < 0.0) g[2] += d.k_ground * gd;
+    double gd = pv.z - d.ground_z - pv.w;
+    if (gd < 0.0) g[2] += w * d.k_ground * gd;
   }
   V3<double> gy = gl_mul(to_q(q), to_q(hq));
   g[3] = -cf.y * gy.x;
@@ -400,14 +488,15 @@ __global__ void __launch_bounds__(kTile) k_particle_grad(DevArrays d, int mask, 
       }
     }
     if (d.k_self > 0.0) {
-      double4 pi = d.xp[i];
+      double4 pi = pot_p(d, d.xp, i);
+      double w = d.midpoint ? 0.5 : 1.0;
       for (int e = d.c_start[i]; e < d.c_start[i + 1]; ++e) {
         int j = d.c_nbr[e];
-        double4 pj = d.xp[j];
+        double4 pj = pot_p(d, d.xp, j);
         double ex = pi.x - pj.x, ey = pi.y - pj.y, ez = pi.z - pj.z;
         double dd = sqrt(ex * ex + ey * ey + ez * ez), R = pi.w + pj.w;
         if (dd < R) {
-          double f = d.k_self * (dd - R) / dd;
+          double f = w * d.k_self * (dd - R) / dd;
           g[0] += f * ex; g[1] += f * ey; g[2] += f * ez;
         }
       }
@@ -427,7 +516,7 @@ __global__ void __launch_bounds__(kTile) k_particle_grad(DevArrays d, int mask, 
 // Hessian
 // ================================================================================================
 
-template <typename T>
+template <typename T, bool MID>
 __global__ void __launch_bounds__(128) k_bond_hess(DevArrays d, int all) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= d.nb) return;
@@ -446,9 +535,13 @@ __global__ void __launch_bounds__(128) k_bond_hess(DevArrays d, int all) {
   BondParams bp = load_bond(d.brest[b], d.bstiff[b]);
   Q4<double> qi = to_q(d.xq[ij.x]), qj = to_q(d.xq[ij.y]);
   BondEval E;
-  bond_first_order(bp, to_v(d.xp[ij.x]), qi, to_v(d.xp[ij.y]), qj, E);
+  if constexpr (MID)
+    bond_first_order_mid(bp, to_v(mid4(d.xp[ij.x], d.x0p[ij.x])), midq(d.xq[ij.x], d.x0q[ij.x]),
+                         to_v(mid4(d.xp[ij.y], d.x0p[ij.y])), midq(d.xq[ij.y], d.x0q[ij.y]), qi, qj, E);
+  else
+    bond_first_order(bp, to_v(d.xp[ij.x]), qi, to_v(d.xp[ij.y]), qj, E);
   T H[45];
-  bond_hessian<T>(bp, qi, qj, E, H);
+  bond_hessian<T, MID>(bp, qi, qj, E, H);
   // orthonormal coordinates u = d / sqrt(2): H_uu = 2 H_dd, H_uy = sqrt(2) H_dy; clamp; back to d
   const T r2 = (T)1.4142135623730951;
 #pragma unroll
@@ -495,7 +588,9 @@ __global__ void __launch_bounds__(kTile) k_particle_hess(DevArrays d, int mask, 
   T D[21];
 #pragma unroll
   for (int k = 0; k < 21; ++k) D[k] = (T)0;
-  double4 p = d.xp[i], q = d.xq[i], hq = d.hq[i];
+  double4 q = d.xq[i], hq = d.hq[i];
+  double4 p = pot_p(d, d.xp, i);  // the potentials' evaluation point
+  double w2 = d.midpoint ? 0.25 : 1.0;
   double2 cf = d.coef[i];
   // particle term: diag(c_p I (+ k_ground e_z e_z^T), max(c_q q.qhat, 0) I), already clamped
   double cy = cf.y * (q.x * hq.x + q.y * hq.y + q.z * hq.z + q.w * hq.w);
@@ -503,7 +598,7 @@ __global__ void __launch_bounds__(kTile) k_particle_hess(DevArrays d, int mask, 
   D[sidx<6>(0, 0)] = (T)cf.x;
   D[sidx<6>(1, 1)] = (T)cf.x;
   D[sidx<6>(2, 2)] = (T)cf.x;
-  if (d.k_ground > 0.0 && p.z - d.ground_z - p.w < 0.0) D[sidx<6>(2, 2)] += (T)d.k_ground;
+  if (d.k_ground > 0.0 && p.z - d.ground_z - p.w < 0.0) D[sidx<6>(2, 2)] += (T)(w2 * d.k_ground);
   D[sidx<6>(3, 3)] = (T)cy;
   D[sidx<6>(4, 4)] = (T)cy;
   D[sidx<6>(5, 5)] = (T)cy;
@@ -535,12 +630,12 @@ __global__ void __launch_bounds__(kTile) k_particle_hess(DevArrays d, int mask, 
     int c0 = d.c_start[i];
     for (int e = c0; e < d.c_start[i + 1]; ++e) {
       int j = d.c_nbr[e];
-      double4 pj = d.xp[j];
+      double4 pj = pot_p(d, d.xp, j);
       double ex = p.x - pj.x, ey = p.y - pj.y, ez = p.z - pj.z;
       double dd = sqrt(ex * ex + ey * ey + ez * ez), R = p.w + pj.w;
       if (dd < R) {  // clamped penalty Hessian k n n^T (the transverse part k (d - R)/d < 0 is removed)
         T n[3] = {(T)(ex / dd), (T)(ey / dd), (T)(ez / dd)};
-        T k = (T)d.k_self;
+        T k = (T)(w2 * d.k_self);
         blk[c0 + nact] = T4<T>{n[0], n[1], n[2], k};
         d.c_anbr[c0 + nact] = j;
         ++nact;
@@ -1315,30 +1410,46 @@ __global__ void k_ls_trial(DevArrays d) {
   d.tq[i] = make_double4(qn.x / nq, qn.y / nq, qn.z / nq, qn.w / nq);
 }
 
-// particle-term difference with dp = p1 - p0: c dp.((p0 - phat) + dp/2) - m g.dp (+ ground), the same for q
+// particle-term difference with dp = p1 - p0: c dp.((p0 - phat) + dp/2) - m g.dp (+ ground), the same for q; in the
+// midpoint form gravity and the ground see the midpoints, whose difference is exactly dp/2
 __device__ __forceinline__ double particle_dphi(const DevArrays& d, int i) {
   double4 p0 = d.xp[i], q0 = d.xq[i], p1 = d.tp[i], q1 = d.tq[i], hp = d.hp[i], hq = d.hq[i];
   double2 cf = d.coef[i];
   double m = hp.w;
   double dpx = p1.x - p0.x, dpy = p1.y - p0.y, dpz = p1.z - p0.z;
   double e = cf.x * (dpx * ((p0.x - hp.x) + 0.5 * dpx) + dpy * ((p0.y - hp.y) + 0.5 * dpy) + dpz * ((p0.z - hp.z) + 0.5 * dpz));
-  e -= m * (d.gx * dpx + d.gy * dpy + d.gz * dpz);
+  double wv = 1.0;
+  if (d.midpoint) {
+    double4 pn = d.x0p[i];
+    wv = 0.5;
+    p0 = mid4(p0, pn);
+    p1 = mid4(p1, pn);
+  }
+  e -= m * (d.gx * (wv * dpx) + d.gy * (wv * dpy) + d.gz * (wv * dpz));
   double dqx = q1.x - q0.x, dqy = q1.y - q0.y, dqz = q1.z - q0.z, dqw = q1.w - q0.w;
   e += cf.y * (dqx * ((q0.x - hq.x) + 0.5 * dqx) + dqy * ((q0.y - hq.y) + 0.5 * dqy) + dqz * ((q0.z - hq.z) + 0.5 * dqz) +
                dqw * ((q0.w - hq.w) + 0.5 * dqw));
   if (d.k_ground > 0.0) {
     double g0 = p0.z - d.ground_z - p0.w, g1 = p1.z - d.ground_z - p0.w;
-    if (g0 < 0.0 && g1 < 0.0) e += 0.5 * d.k_ground * dpz * (g0 + g1);
+    if (g0 < 0.0 && g1 < 0.0) e += 0.5 * d.k_ground * (wv * dpz) * (g0 + g1);
     else e += 0.5 * d.k_ground * ((g1 < 0.0 ? g1 * g1 : 0.0) - (g0 < 0.0 ? g0 * g0 : 0.0));
   }
   return e;
 }
 
-// contact difference; when overlapping at both states 1/2 k (d1 - d0)(e1 + e0), d1 - d0 = (x1 - x0).(x1 + x0)/(d1 + d0)
+// contact difference; when overlapping at both states 1/2 k (d1 - d0)(e1 + e0), d1 - d0 = (x1 - x0).(x1 + x0)/(d1 + d0);
+// in the midpoint form at the midpoints, with the endpoint differences (p1 - p0)/2
 __device__ __forceinline__ double contact_dphi(const DevArrays& d, int i, int j) {
   double4 a0 = d.xp[i], b0 = d.xp[j], a1 = d.tp[i], b1 = d.tp[j];
-  double x0[3] = {a0.x - b0.x, a0.y - b0.y, a0.z - b0.z}, x1[3] = {a1.x - b1.x, a1.y - b1.y, a1.z - b1.z};
   double dx[3] = {(a1.x - a0.x) - (b1.x - b0.x), (a1.y - a0.y) - (b1.y - b0.y), (a1.z - a0.z) - (b1.z - b0.z)};
+  if (d.midpoint) {
+    double4 an = d.x0p[i], bn = d.x0p[j];
+    dx[0] = 0.5 * (a1.x - a0.x) - 0.5 * (b1.x - b0.x);
+    dx[1] = 0.5 * (a1.y - a0.y) - 0.5 * (b1.y - b0.y);
+    dx[2] = 0.5 * (a1.z - a0.z) - 0.5 * (b1.z - b0.z);
+    a0 = mid4(a0, an); a1 = mid4(a1, an); b0 = mid4(b0, bn); b1 = mid4(b1, bn);
+  }
+  double x0[3] = {a0.x - b0.x, a0.y - b0.y, a0.z - b0.z}, x1[3] = {a1.x - b1.x, a1.y - b1.y, a1.z - b1.z};
   double d0 = sqrt(x0[0] * x0[0] + x0[1] * x0[1] + x0[2] * x0[2]);
   double d1 = sqrt(x1[0] * x1[0] + x1[1] * x1[1] + x1[2] * x1[2]);
   double R = a0.w + b0.w, k = d.k_self;
@@ -1380,16 +1491,24 @@ __global__ void __launch_bounds__(kTile) k_ls_energy_bonds(DevArrays d) {
     BondParams bp = load_bond(d.brest[b], d.bstiff[b]);
     double4 pi0 = d.xp[ij.x], pj0 = d.xp[ij.y], pi1 = d.tp[ij.x], pj1 = d.tp[ij.y];
     Q4<double> qi0 = to_q(d.xq[ij.x]), qj0 = to_q(d.xq[ij.y]), qi1 = to_q(d.tq[ij.x]), qj1 = to_q(d.tq[ij.y]);
+    V3<double> ddd = (to_v(pj1) - to_v(pj0)) - (to_v(pi1) - to_v(pi0));
+    Q4<double> dqj = {qj1.x - qj0.x, qj1.y - qj0.y, qj1.z - qj0.z, qj1.w - qj0.w};
+    Q4<double> dqi = {qi1.x - qi0.x, qi1.y - qi0.y, qi1.z - qi0.z, qi1.w - qi0.w};
+    if (d.midpoint) {  // midpoints with the start state; their differences are exactly half the state's
+      double4 ai = d.x0p[ij.x], aj = d.x0p[ij.y], bi = d.x0q[ij.x], bj = d.x0q[ij.y];
+      ddd = 0.5 * (to_v(pj1) - to_v(pj0)) - 0.5 * (to_v(pi1) - to_v(pi0));
+      dqj = {0.5 * (qj1.x - qj0.x), 0.5 * (qj1.y - qj0.y), 0.5 * (qj1.z - qj0.z), 0.5 * (qj1.w - qj0.w)};
+      dqi = {0.5 * (qi1.x - qi0.x), 0.5 * (qi1.y - qi0.y), 0.5 * (qi1.z - qi0.z), 0.5 * (qi1.w - qi0.w)};
+      qi0 = midq(d.xq[ij.x], bi); qj0 = midq(d.xq[ij.y], bj); qi1 = midq(d.tq[ij.x], bi); qj1 = midq(d.tq[ij.y], bj);
+      pi0 = mid4(pi0, ai); pj0 = mid4(pj0, aj); pi1 = mid4(pi1, ai); pj1 = mid4(pj1, aj);
+    }
     // stretch
     V3<double> dd0 = to_v(pj0) - to_v(pi0), dd1 = to_v(pj1) - to_v(pi1);
-    V3<double> ddd = (to_v(pj1) - to_v(pj0)) - (to_v(pi1) - to_v(pi0));
     double l0 = sqrt(dot(dd0, dd0)), l1 = sqrt(dot(dd1, dd1));
     double dl = dot(ddd, dd0 + dd1) / (l0 + l1);
     double e = 0.5 * bp.kn * dl * ((l0 - bp.l0) + (l1 - bp.l0));
     // bend-twist
     V3<double> r0 = qvec(qmul(qconj(qj0), qi0)), r1 = qvec(qmul(qconj(qj1), qi1));
-    Q4<double> dqj = {qj1.x - qj0.x, qj1.y - qj0.y, qj1.z - qj0.z, qj1.w - qj0.w};
-    Q4<double> dqi = {qi1.x - qi0.x, qi1.y - qi0.y, qi1.z - qi0.z, qi1.w - qi0.w};
     V3<double> dr = qvec(qmul(qconj(dqj), qi1)) + qvec(qmul(qconj(qj0), dqi));
     e += 0.5 * dot(dr, kmul(bp, r0 + r1));
     // shear
@@ -1654,6 +1773,17 @@ int launch_predict(const DevArrays& d, cudaStream_t s) {
   return 2;
 }
 
+int launch_zhat(const DevArrays& d, cudaStream_t s) {
+  if (!d.midpoint || d.n == 0) return 0;
+  int k = 0;
+  if (d.nb) {
+    k_zhat_bonds<<<blocks_for(d.nb, kTile), kTile, 0, s>>>(d);
+    ++k;
+  }
+  k_zhat_particles<<<blocks_for(d.n, kTile), kTile, 0, s>>>(d);
+  return k + 1;
+}
+
 int launch_contacts(const DevArrays& d, int stage, cudaStream_t s) {
   if (d.n == 0) return 0;
   if (stage == 0) {
@@ -1702,8 +1832,13 @@ int launch_particle_grad(const DevArrays& d, int mask, int all, cudaStream_t s) 
 
 int launch_bond_hess(const DevArrays& d, int all, cudaStream_t s) {
   if (d.nb == 0) return 0;
-  if (d.mixed) k_bond_hess<float><<<blocks_for(d.nb, 128), 128, 0, s>>>(d, all);
-  else k_bond_hess<double><<<blocks_for(d.nb, 128), 128, 0, s>>>(d, all);
+  if (d.midpoint) {
+    if (d.mixed) k_bond_hess<float, true><<<blocks_for(d.nb, 128), 128, 0, s>>>(d, all);
+    else k_bond_hess<double, true><<<blocks_for(d.nb, 128), 128, 0, s>>>(d, all);
+  } else {
+    if (d.mixed) k_bond_hess<float, false><<<blocks_for(d.nb, 128), 128, 0, s>>>(d, all);
+    else k_bond_hess<double, false><<<blocks_for(d.nb, 128), 128, 0, s>>>(d, all);
+  }
   return 1;
 }
 
@@ -1866,6 +2001,25 @@ __global__ void k_set_hat(DevArrays d, const double* phat3, const double* qhat4)
   d.hq[k] = make_double4(qhat4[4 * u], qhat4[4 * u + 1], qhat4[4 * u + 2], qhat4[4 * u + 3]);
 }
 
+__global__ void k_pack_hat(DevArrays d, double* phat3, double* qhat4) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.n) return;
+  size_t u = (size_t)d.perm[k];
+  double4 p = d.hp[k], q = d.hq[k];
+  phat3[3 * u] = p.x; phat3[3 * u + 1] = p.y; phat3[3 * u + 2] = p.z;
+  qhat4[4 * u] = q.x; qhat4[4 * u + 1] = q.y; qhat4[4 * u + 2] = q.z; qhat4[4 * u + 3] = q.w;
+}
+
+// the iterate (xp, xq) given in the caller's order (inspection calls); the radius in xp.w is kept
+__global__ void k_set_iterate(DevArrays d, const double* pos3, const double* quat4) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.n) return;
+  size_t u = (size_t)d.perm[k];
+  double r = d.x0p[k].w;
+  d.xp[k] = make_double4(pos3[3 * u], pos3[3 * u + 1], pos3[3 * u + 2], r);
+  d.xq[k] = make_double4(quat4[4 * u], quat4[4 * u + 1], quat4[4 * u + 2], quat4[4 * u + 3]);
+}
+
 // bond flags between the caller's bond order (order of addition) and the stored order: ext2int[e] = stored index
 __global__ void k_bond_flags(DevArrays d, uint8_t* ext, int to_device) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1891,6 +2045,18 @@ int launch_unpack_state(const DevArrays& d, const double* pos3, const double* qu
 int launch_set_hat(const DevArrays& d, const double* phat3, const double* qhat4, cudaStream_t s) {
   if (d.n == 0) return 0;
   k_set_hat<<<blocks_for(d.n, 256), 256, 0, s>>>(d, phat3, qhat4);
+  return 1;
+}
+
+int launch_pack_hat(const DevArrays& d, double* phat3, double* qhat4, cudaStream_t s) {
+  if (d.n == 0) return 0;
+  k_pack_hat<<<blocks_for(d.n, 256), 256, 0, s>>>(d, phat3, qhat4);
+  return 1;
+}
+
+int launch_set_iterate(const DevArrays& d, const double* pos3, const double* quat4, cudaStream_t s) {
+  if (d.n == 0) return 0;
+  k_set_iterate<<<blocks_for(d.n, 256), 256, 0, s>>>(d, pos3, quat4);
   return 1;
 }
 

@@ -27,7 +27,16 @@ CASES = {
     "c5": (lambda: scenes.c5_impact(n_slab=600, n_ball=80, footprint=0.035, ball_R=0.008), 3, 1e-6),
     # the plate at R = 50 mm (about 6,800 particles) of the PCG launch-shape test: two grids that round differently
     "plate50": (lambda: scenes.c2_plate_small(R=0.05), 2, 1e-6),
+    # the variational midpoint form: the 4x4x4 cube bouncing off the ground and three Poisson-disk boxes landing
+    "cube_mid": (lambda: scenes.cube_lattice(nx=4, z_bottom=0.01, k_ground=1e6, steps=50, integrator=1), 50, 1e-6),
+    "c4_mid": (lambda: _with(scenes.c4_batched(n_scenes=3, n_min=150, n_max=400, heights=(0.0002, 0.001)),
+                             integrator=1), 25, 1e-6),
 }
+
+
+def _with(sc, **cfg):
+    sc.config = dict(sc.config, **cfg)
+    return sc
 
 
 def qerr(a, b):

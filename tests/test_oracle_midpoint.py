@@ -225,6 +225,36 @@ def test_system_gradient_matches_objective_differences():
         assert abs(dd - (phi1 - phi0)) <= 1e-9 * abs(phi1 - phi0) + 1e-13 * abs(phi0)
 
 
+def test_sphere_bounce_matches_a_scalar_solve_of_the_discrete_equation():
+    """A sphere dropped on the penalty ground: each step's z_{n+1} is the root, found by bracketing, of
+    m (z_{n+1} - 2 z_n + z_{n-1}) / dt^2 + 1/2 V'((z_{n+1} + z_n)/2) + 1/2 V'((z_n + z_{n-1})/2) = 0 with
+    V(z) = m 9.81 z + 1/2 k min(z - r, 0)^2. With the contact stiffness far beyond 1/dt^2 (w dt = 28) the one-sided
+    contact switching inside a step makes the sphere leave faster than it arrived: a property of this form, reproduced
+    here by the scalar solve."""
+    brentq = pytest.importorskip("scipy.optimize").brentq
+    k, dt, z0 = 1e6, 1e-3, 0.01
+    cfg = scenes.default_config(dt=dt, k_ground=k, integrator=1, newton_rel_tol=1e-13)
+    sc = scenes._assemble(np.array([[0.0, 0.0, z0]]), np.full(1, R), np.zeros(1, np.int32), np.zeros(1, np.uint8),
+                          np.zeros((0, 2), np.int64), [scenes.Material(E, NU, RHO)], cfg, "sphere")
+    o = oracle.OracleSim(sc)
+
+    def dV(z):
+        return MASS * 9.81 + (k * (z - R) if z < R else 0.0)
+
+    zprev, z = z0, z0
+    v_in = v_out = 0.0
+    for n in range(45):
+        def f(zn):
+            return MASS * (zn - 2.0 * z + zprev) / dt ** 2 + 0.5 * dV(0.5 * (zn + z)) + 0.5 * dV(0.5 * (z + zprev))
+        zn = brentq(f, z - 0.05, z + 0.05, xtol=1e-16, rtol=1e-15)
+        zprev, z = z, zn
+        o.step(1)
+        assert abs(o.p[0, 2] - z) <= 1e-10 * z0, (n, o.p[0, 2], z)
+        v = (z - zprev) / dt
+        v_in, v_out = min(v_in, v), max(v_out, v)
+    assert v_in < -0.3 and v_out > 2.0 * abs(v_in)
+
+
 def test_midpoint_differs_from_euler_only_through_the_potential():
     """With no potential (free unbonded particles, no gravity, no contact) both forms reduce to x_{n+1} = xhat."""
     pos = np.array([[0.0, 0.0, 0.0], [0.05, 0.0, 0.0]])
