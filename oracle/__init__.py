@@ -49,7 +49,7 @@ class OrcConfig(ctypes.Structure):
                 ("ls_max_halvings", ctypes.c_int32), ("optimizer", ctypes.c_int32), ("ground_z", ctypes.c_double),
                 ("k_ground", ctypes.c_double), ("k_self", ctypes.c_double), ("contact_skin", ctypes.c_double),
                 ("mu_slide", ctypes.c_double), ("mu_roll", ctypes.c_double),
-                ("integrator", ctypes.c_int32), ("pad1", ctypes.c_int32)]
+                ("integrator", ctypes.c_int32), ("preconditioner", ctypes.c_int32)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -63,7 +63,7 @@ class OrcProblem(ctypes.Structure):
                 ("scene_start", _lp), ("p", _dp), ("q", _dp), ("v", _dp), ("u", _dp), ("radius", _dp), ("mass", _dp),
                 ("kinematic", _up), ("bi", _ip), ("bj", _ip), ("l0", _dp), ("d0", _dp), ("R0", _dp), ("kn", _dp),
                 ("kt", _dp), ("kbt", _dp), ("shear_scale", _dp), ("break_strain", _dp), ("broken", _up),
-                ("tensile_strength", _dp), ("shear_strength", _dp)]
+                ("tensile_strength", _dp), ("shear_strength", _dp), ("morton", _ip)]
 
 
 class OrcStats(ctypes.Structure):
@@ -86,6 +86,10 @@ def _setup(L):
     L.orc_system.argtypes = [C, P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _ip]
     L.orc_matvec.argtypes = [C, P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
     L.orc_zhat.argtypes = [C, P, ctypes.c_int, _dp, _dp, _dp, _dp]
+    L.orc_morton_order.argtypes = [_lp, ctypes.c_int, _dp, _ip]
+    L.orc_morton_order.restype = None
+    L.orc_amg_apply.argtypes = [C, P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.orc_amg_level1_apply.argtypes = [C, P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
     L.orc_pcg_solve.argtypes = [C, P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp]
     L.orc_energy_diff.argtypes = [C, P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     L.orc_energy_diff.restype = ctypes.c_double
@@ -235,6 +239,7 @@ class OracleSim:
         C.mu_slide = c.get("friction_slide", 0.0)
         C.mu_roll = c.get("friction_roll", 0.0)
         C.integrator = int(c.get("integrator", 0))
+        C.preconditioner = int(c.get("preconditioner", 0))
         return C
 
     def _build_problem(self):
@@ -249,6 +254,13 @@ class OracleSim:
         P.shear_scale, P.break_strain = _d(self.shs), _d(self.brk)
         P.broken = self.broken.ctypes.data_as(_up)
         P.tensile_strength, P.shear_strength = _d(self.sig_c), _d(self.tau_c)
+        # Z-order of the initial positions (the AMG's aggregation order)
+        self.morton = np.zeros(max(self.scene.n, 1), np.int32)
+        if self.scene.n:
+            pos0 = f64(self.scene.pos)
+            lib().orc_morton_order(self.starts.ctypes.data_as(_lp), int(self.scene.n_scenes), _d(pos0),
+                                   self.morton.ctypes.data_as(_ip))
+        P.morton = self.morton.ctypes.data_as(_ip)
         self.P = P
 
     def step(self, n_steps=1):
@@ -349,6 +361,24 @@ class OracleSim:
         cnt = lib().orc_contact_candidates(ctypes.byref(self.C), ctypes.byref(self.P), scene, _d(p),
                                            pairs.ctypes.data_as(_ip), cap, 1 if brute else 0)
         return pairs[:min(cnt, cap)].copy()
+
+    def amg_apply(self, p, q, phat, qhat, r, scene=0):
+        """z = M^-1 r of the scene's AMG preconditioner at (p, q); returns (z [ns,6], number of levels)."""
+        a, b = self._scene_range(scene)
+        z = np.zeros((b - a, 6))
+        args = [f64(x) for x in (p, q, phat, qhat, r)]
+        nl = lib().orc_amg_apply(ctypes.byref(self.C), ctypes.byref(self.P), scene, *[_d(x) for x in args], _d(z))
+        return z, nl
+
+    def amg_level1_apply(self, p, q, phat, qhat, e, scene=0):
+        """y = A_1 e with the AMG's level-1 (Galerkin) operator; e [n_agg,6] in Z-order of the aggregates."""
+        e = f64(e)
+        y = np.zeros_like(e)
+        args = [f64(x) for x in (p, q, phat, qhat)]
+        m = lib().orc_amg_level1_apply(ctypes.byref(self.C), ctypes.byref(self.P), scene, *[_d(x) for x in args],
+                                       _d(e), _d(y))
+        assert m == e.shape[0], (m, e.shape)
+        return y
 
     def zhat(self, phat, qhat, scene=0):
         """The variational midpoint target zhat of the scene (Sec. 3.1, App. C) for the inertia targets

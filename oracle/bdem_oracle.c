@@ -851,6 +851,7 @@ typedef struct {
   int mid;                     /* variational midpoint form: potentials at (x + x_n)/2 */
   const double *pn, *qn;       /* the step's start state x_n (the problem's state arrays) */
   double *pm0, *qm0, *pm1, *qm1, *dpm, *dqm;  /* [n][3], [n][4] midpoints and their differences (mid only) */
+  const double *cur_p, *cur_q; /* the state of the last sys_assemble (the AMG's rigid modes are taken there) */
 } scene_sys;
 
 static void sys_init(scene_sys* S, const orc_config* C, const orc_problem* P, int scene, const double* phat,
@@ -965,6 +966,8 @@ double orc_energy_diff(const orc_config* C, const orc_problem* P, int scene, con
 static void sys_assemble(scene_sys* S, const double* p, const double* q, int mask_kin) {
   const orc_problem* P = S->P;
   int n0 = S->n0, ns = S->ns;
+  S->cur_p = p;
+  S->cur_q = q;
   /* potentials at x (w = 1) or at the midpoint (x + x_n)/2 (w = 1/2), reduced at x */
   const double *pv = p, *qv = q;
   double w = 1.0;
@@ -1085,7 +1088,329 @@ static double vdot(int n, const double* a, const double* b) {
 }
 
 /* Preconditioned conjugate gradient on H x = b from x = 0, stopping when |r| <= eps_r |b| (Sec. 5.3) */
+
+/* ------------------------------------------------------------------------------------------------ */
+/* Algebraic multigrid preconditioner (Sec. 5.3 names an AMG preconditioner for the PCG and nothing    */
+/* more). Reading, an aggregation AMG built for this method's block structure:                       */
+/*  - level 0: the scene's particles in the Z-order (Morton order) of their initial positions, as      */
+/*    defined by orc_morton_order; level l+1: consecutive groups of 8 level-l nodes; coarsest level: a  */
+/*    level of at most 8 nodes, solved exactly (dense Cholesky);                                      */
+/*  - the coarse space of an aggregate is its infinitesimal rigid motions (t, w): a level-0 node i in  */
+/*    aggregate I moves by dp_i = t + w x (p_i - c_I) and turns by y_i = 1/2 R(q_i)^T w (dq = q (x)     */
+/*    (y, 0) for the world rotation dq = 1/2 (w, 0) (x) q); a level-l node k (l >= 1) by t_k =          */
+/*    t + w x (c_k - c_I), w_k = w; c = centroid (mean of the members' positions or centroids);        */
+/*  - A_0 = the assembled system without the off-diagonal blocks of the contact terms (each dropped   */
+/*    block leaves its PSD diagonal part, so A_0 stays SPD), kinematic rows and columns replaced by    */
+/*    identity; A_{l+1} = P_l^T A_l P_l (Galerkin);                                                     */
+/*  - symmetric V(1,1) cycle: x = w D^-1 r; x += P A_c^-1-cycle P^T (r - A x); x += w D^-1 (r - A x)    */
+/*    with D the block diagonal of A_l and w = 0.6.                                                     */
+/* ------------------------------------------------------------------------------------------------ */
+
+#define AMG_AGG 8
+#define AMG_OMEGA 0.6
+
+typedef struct { int r, c; double v[36]; } blk_entry;
+typedef struct {
+  int n;              /* nodes */
+  int nnz;            /* block entries, sorted by (r, c), unique */
+  int* rs;            /* [n+1] row starts */
+  blk_entry* e;
+  double* Dinv;       /* [n][36] inverse of the diagonal block */
+  double* P;          /* [n][36] prolongation block of each node into its aggregate (none on the coarsest) */
+  double* cen;        /* [n][3] centroid */
+  double *r, *x, *t;  /* [6n] work vectors */
+} amg_level;
+typedef struct {
+  int nl;
+  amg_level L[16];
+  double* chol;       /* coarsest level: dense Cholesky factor, (6 n_L)^2 */
+  int mask0;          /* level 0 nodes that are kinematic get zeroed by the caller */
+} amg_hier;
+
+static int cmp_blk(const void* a, const void* b) {
+  const blk_entry *x = a, *y = b;
+  if (x->r != y->r) return x->r < y->r ? -1 : 1;
+  if (x->c != y->c) return x->c < y->c ? -1 : 1;
+  return 0;
+}
+
+/* sorts the entries and sums duplicates in their order of appearance (qsort on (r, c, position)) */
+typedef struct { blk_entry e; int pos; } blk_tmp;
+static int cmp_blk_tmp(const void* a, const void* b) {
+  const blk_tmp *x = a, *y = b;
+  int c = cmp_blk(&x->e, &y->e);
+  if (c) return c;
+  return x->pos < y->pos ? -1 : (x->pos > y->pos);
+}
+static void amg_finish_level(amg_level* L, blk_entry* raw, int nraw) {
+  blk_tmp* t = malloc(sizeof(blk_tmp) * (nraw + 1));
+  for (int k = 0; k < nraw; ++k) { t[k].e = raw[k]; t[k].pos = k; }
+  qsort(t, nraw, sizeof(blk_tmp), cmp_blk_tmp);
+  L->e = malloc(sizeof(blk_entry) * (nraw + 1));
+  int m = 0;
+  for (int k = 0; k < nraw; ++k) {
+    if (m > 0 && L->e[m - 1].r == t[k].e.r && L->e[m - 1].c == t[k].e.c) {
+      for (int a = 0; a < 36; ++a) L->e[m - 1].v[a] += t[k].e.v[a];
+    } else {
+      L->e[m++] = t[k].e;
+    }
+  }
+  free(t);
+  L->nnz = m;
+  L->rs = calloc(L->n + 1, sizeof(int));
+  for (int k = 0; k < m; ++k) L->rs[L->e[k].r + 1]++;
+  for (int i = 0; i < L->n; ++i) L->rs[i + 1] += L->rs[i];
+  L->r = calloc(6 * (size_t)L->n, sizeof(double));
+  L->x = calloc(6 * (size_t)L->n, sizeof(double));
+  L->t = calloc(6 * (size_t)L->n, sizeof(double));
+}
+
+static void inv6(const double* A, double* Ai) {  /* inverse of an SPD 6x6 block by solving A X = I */
+  for (int c = 0; c < 6; ++c) {
+    double e[6] = {0, 0, 0, 0, 0, 0}, z[6];
+    e[c] = 1.0;
+    precond_apply(A, e, z);
+    for (int r = 0; r < 6; ++r) Ai[6 * r + c] = z[r];
+  }
+}
+
+static void rot_of(const double q[4], double R[9]) {  /* R(q) for a unit quaternion {x, y, z, w} */
+  double x = q[0], y = q[1], z = q[2], w = q[3];
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - z * w);     R[2] = 2 * (x * z + y * w);
+  R[3] = 2 * (x * y + z * w);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - x * w);
+  R[6] = 2 * (x * z - y * w);     R[7] = 2 * (y * z + x * w);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* the rigid-motion block of a node at position c_k in an aggregate with centroid c_I: [[I, -[c_k - c_I]x], [0, B]] */
+static void rigid_block(const double* ck, const double* cI, const double* B3, double* P) {
+  double d[3] = {ck[0] - cI[0], ck[1] - cI[1], ck[2] - cI[2]};
+  memset(P, 0, sizeof(double) * 36);
+  for (int a = 0; a < 3; ++a) P[6 * a + a] = 1.0;
+  /* -[d]x: rows of (w x d) = -d x w */
+  P[6 * 0 + 4] = d[2];  P[6 * 0 + 5] = -d[1];
+  P[6 * 1 + 3] = -d[2]; P[6 * 1 + 5] = d[0];
+  P[6 * 2 + 3] = d[1];  P[6 * 2 + 4] = -d[0];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) P[6 * (3 + a) + 3 + b] = B3[3 * a + b];
+}
+
+static void amg_free(amg_hier* H) {
+  for (int l = 0; l < H->nl; ++l) {
+    amg_level* L = &H->L[l];
+    free(L->rs); free(L->e); free(L->Dinv); free(L->P); free(L->cen); free(L->r); free(L->x); free(L->t);
+  }
+  free(H->chol);
+}
+
+static void amg_cholesky(int n, double* A) {  /* in place, lower triangle */
+  for (int j = 0; j < n; ++j) {
+    double s = A[n * j + j];
+    for (int k = 0; k < j; ++k) s -= A[n * j + k] * A[n * j + k];
+    A[n * j + j] = sqrt(s > 0.0 ? s : 1e-300);
+    for (int i = j + 1; i < n; ++i) {
+      double t = A[n * i + j];
+      for (int k = 0; k < j; ++k) t -= A[n * i + k] * A[n * j + k];
+      A[n * i + j] = t / A[n * j + j];
+    }
+  }
+}
+
+/* builds the hierarchy of one scene from its assembled system (sys_assemble with the kinematic mask) */
+static void amg_build(const scene_sys* S, const double* p, const double* q, amg_hier* H) {
+  const orc_problem* P = S->P;
+  int n0 = S->n0, ns = S->ns;
+  memset(H, 0, sizeof *H);
+  /* level 0: node k = particle morton[n0 + k]; pos[] local node index of each particle */
+  int* node_of = malloc(sizeof(int) * (ns + 1));
+  for (int k = 0; k < ns; ++k) node_of[P->morton[n0 + k] - n0] = k;
+  amg_level* L0 = &H->L[0];
+  L0->n = ns;
+  int nraw = 0, cap = ns + 2 * S->nbond + 1;
+  blk_entry* raw = malloc(sizeof(blk_entry) * cap);
+  for (int k = 0; k < ns; ++k) {
+    int i = P->morton[n0 + k];
+    raw[nraw].r = raw[nraw].c = k;
+    memcpy(raw[nraw].v, S->D + 36 * (i - n0), sizeof(double) * 36);
+    ++nraw;
+  }
+  for (int k = 0; k < S->nbond; ++k) {
+    int a = P->bi[S->bonds[k]], b = P->bj[S->bonds[k]];
+    if (is_kin(P, a) || is_kin(P, b)) continue;
+    const double* H12 = S->Hb + 144 * k;
+    int na = node_of[a - n0], nb = node_of[b - n0];
+    raw[nraw].r = na; raw[nraw].c = nb;
+    for (int r = 0; r < 6; ++r)
+      for (int c = 0; c < 6; ++c) raw[nraw].v[6 * r + c] = H12[12 * r + 6 + c];
+    ++nraw;
+    raw[nraw].r = nb; raw[nraw].c = na;
+    for (int r = 0; r < 6; ++r)
+      for (int c = 0; c < 6; ++c) raw[nraw].v[6 * r + c] = H12[12 * (6 + r) + c];
+    ++nraw;
+  }
+  amg_finish_level(L0, raw, nraw);
+  free(raw);
+  L0->cen = malloc(sizeof(double) * 3 * (ns + 1));
+  for (int k = 0; k < ns; ++k) memcpy(L0->cen + 3 * k, p + 3 * P->morton[n0 + k], sizeof(double) * 3);
+  int l = 0;
+  for (;;) {
+    amg_level* L = &H->L[l];
+    L->Dinv = malloc(sizeof(double) * 36 * (L->n + 1));
+    for (int i = 0; i < L->n; ++i)
+      for (int k = L->rs[i]; k < L->rs[i + 1]; ++k)
+        if (L->e[k].c == i) inv6(L->e[k].v, L->Dinv + 36 * i);
+    if (L->n <= AMG_AGG || l == 15) break;
+    /* aggregates of consecutive groups of AMG_AGG nodes: centroids, prolongation blocks, Galerkin product */
+    amg_level* C = &H->L[l + 1];
+    C->n = (L->n + AMG_AGG - 1) / AMG_AGG;
+    C->cen = calloc(3 * (size_t)C->n + 3, sizeof(double));
+    for (int I = 0; I < C->n; ++I) {
+      int a = I * AMG_AGG, b = a + AMG_AGG < L->n ? a + AMG_AGG : L->n;
+      for (int k = a; k < b; ++k)
+        for (int c = 0; c < 3; ++c) C->cen[3 * I + c] += L->cen[3 * k + c];
+      for (int c = 0; c < 3; ++c) C->cen[3 * I + c] /= (double)(b - a);
+    }
+    L->P = malloc(sizeof(double) * 36 * (L->n + 1));
+    for (int k = 0; k < L->n; ++k) {
+      double B3[9];
+      if (l == 0) {
+        double R[9];
+        rot_of(q + 4 * P->morton[n0 + k], R);
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) B3[3 * a + b] = 0.5 * R[3 * b + a];  /* 1/2 R^T */
+      } else {
+        for (int a = 0; a < 9; ++a) B3[a] = (a % 4 == 0) ? 1.0 : 0.0;
+      }
+      rigid_block(L->cen + 3 * k, C->cen + 3 * (k / AMG_AGG), B3, L->P + 36 * k);
+    }
+    blk_entry* craw = malloc(sizeof(blk_entry) * (L->nnz + 1));
+    for (int k = 0; k < L->nnz; ++k) {
+      const blk_entry* e = &L->e[k];
+      double T[36], Pt[36];
+      craw[k].r = e->r / AMG_AGG;
+      craw[k].c = e->c / AMG_AGG;
+      matmul(6, 6, 6, e->v, L->P + 36 * e->c, T);        /* A_rc P_c */
+      transpose(6, 6, L->P + 36 * e->r, Pt);
+      matmul(6, 6, 6, Pt, T, craw[k].v);                  /* P_r^T A_rc P_c */
+    }
+    amg_finish_level(C, craw, L->nnz);
+    free(craw);
+    ++l;
+  }
+  H->nl = l + 1;
+  /* coarsest: dense Cholesky */
+  amg_level* Lc = &H->L[l];
+  int m = 6 * Lc->n;
+  H->chol = calloc((size_t)m * m + 1, sizeof(double));
+  for (int k = 0; k < Lc->nnz; ++k)
+    for (int a = 0; a < 6; ++a)
+      for (int b = 0; b < 6; ++b) H->chol[(size_t)m * (6 * Lc->e[k].r + a) + 6 * Lc->e[k].c + b] = Lc->e[k].v[6 * a + b];
+  amg_cholesky(m, H->chol);
+  free(node_of);
+}
+
+static void amg_spmv_res(const amg_level* L, const double* x, const double* r, double* t) {  /* t = r - A x */
+  for (int i = 0; i < L->n; ++i) {
+    double s[6];
+    for (int a = 0; a < 6; ++a) s[a] = r[6 * i + a];
+    for (int k = L->rs[i]; k < L->rs[i + 1]; ++k) {
+      const blk_entry* e = &L->e[k];
+      for (int a = 0; a < 6; ++a)
+        for (int b = 0; b < 6; ++b) s[a] -= e->v[6 * a + b] * x[6 * e->c + b];
+    }
+    for (int a = 0; a < 6; ++a) t[6 * i + a] = s[a];
+  }
+}
+
+static void amg_cycle(amg_hier* H, int l, const double* r, double* x) {
+  amg_level* L = &H->L[l];
+  int n6 = 6 * L->n;
+  if (l == H->nl - 1) {  /* exact solve with the Cholesky factor */
+    double* w = malloc(sizeof(double) * (n6 + 1));
+    for (int i = 0; i < n6; ++i) {
+      double s = r[i];
+      for (int k = 0; k < i; ++k) s -= H->chol[(size_t)n6 * i + k] * w[k];
+      w[i] = s / H->chol[(size_t)n6 * i + i];
+    }
+    for (int i = n6 - 1; i >= 0; --i) {
+      double s = w[i];
+      for (int k = i + 1; k < n6; ++k) s -= H->chol[(size_t)n6 * k + i] * x[k];
+      x[i] = s / H->chol[(size_t)n6 * i + i];
+    }
+    free(w);
+    return;
+  }
+  amg_level* C = &H->L[l + 1];
+  /* pre-smoothing from zero */
+  for (int i = 0; i < L->n; ++i) {
+    double z[6];
+    matmul(6, 6, 1, L->Dinv + 36 * i, r + 6 * i, z);
+    for (int a = 0; a < 6; ++a) x[6 * i + a] = AMG_OMEGA * z[a];
+  }
+  /* restriction of the residual, coarse correction, prolongation */
+  amg_spmv_res(L, x, r, L->t);
+  memset(C->r, 0, sizeof(double) * 6 * C->n);
+  for (int k = 0; k < L->n; ++k) {
+    double Pt[36], v[6];
+    transpose(6, 6, L->P + 36 * k, Pt);
+    matmul(6, 6, 1, Pt, L->t + 6 * k, v);
+    for (int a = 0; a < 6; ++a) C->r[6 * (k / AMG_AGG) + a] += v[a];
+  }
+  double* e = malloc(sizeof(double) * (6 * C->n + 1));
+  double* rc = malloc(sizeof(double) * (6 * C->n + 1));
+  memcpy(rc, C->r, sizeof(double) * 6 * C->n);
+  amg_cycle(H, l + 1, rc, e);
+  for (int k = 0; k < L->n; ++k) {
+    double v[6];
+    matmul(6, 6, 1, L->P + 36 * k, e + 6 * (k / AMG_AGG), v);
+    for (int a = 0; a < 6; ++a) x[6 * k + a] += v[a];
+  }
+  free(e); free(rc);
+  /* post-smoothing */
+  amg_spmv_res(L, x, r, L->t);
+  for (int i = 0; i < L->n; ++i) {
+    double z[6];
+    matmul(6, 6, 1, L->Dinv + 36 * i, L->t + 6 * i, z);
+    for (int a = 0; a < 6; ++a) x[6 * i + a] += AMG_OMEGA * z[a];
+  }
+}
+
+/* z = M^-1 r for the scene's vectors in particle order (kinematic entries of z zeroed) */
+static void amg_apply(const scene_sys* S, amg_hier* H, const double* r, double* z) {
+  const orc_problem* P = S->P;
+  int n0 = S->n0, ns = S->ns;
+  double *rn = calloc(6 * (size_t)ns + 1, sizeof(double)), *xn = calloc(6 * (size_t)ns + 1, sizeof(double));
+  for (int k = 0; k < ns; ++k) {
+    int i = P->morton[n0 + k];
+    for (int a = 0; a < 6; ++a) rn[6 * k + a] = is_kin(P, i) ? 0.0 : r[6 * (i - n0) + a];
+  }
+  amg_cycle(H, 0, rn, xn);
+  for (int k = 0; k < ns; ++k) {
+    int i = P->morton[n0 + k];
+    for (int a = 0; a < 6; ++a) z[6 * (i - n0) + a] = is_kin(P, i) ? 0.0 : xn[6 * k + a];
+  }
+  free(rn); free(xn);
+}
+
+/* z = M^-1 r: block Jacobi (the assembled diagonal blocks), or the AMG cycle when H is given */
+static void prec(const scene_sys* S, amg_hier* H, const double* r, double* z) {
+  if (H) { amg_apply(S, H, r, z); return; }
+  for (int i = 0; i < S->ns; ++i) precond_apply(S->D + 36 * i, r + 6 * i, z + 6 * i);
+}
+
+static int pcg_with(const scene_sys* S, amg_hier* H, const double* b, double eps_r, int max_iter, double* x);
+
 static int pcg(const scene_sys* S, const double* b, double eps_r, int max_iter, double* x) {
+  if (S->C->preconditioner == 1 && S->P->morton) {
+    amg_hier H;
+    amg_build(S, S->cur_p, S->cur_q, &H);
+    int it = pcg_with(S, &H, b, eps_r, max_iter, x);
+    amg_free(&H);
+    return it;
+  }
+  return pcg_with(S, NULL, b, eps_r, max_iter, x);
+}
+
+static int pcg_with(const scene_sys* S, amg_hier* H, const double* b, double eps_r, int max_iter, double* x) {
   int n = 6 * S->ns;
   double *r = malloc(sizeof(double) * n), *z = malloc(sizeof(double) * n), *pv = malloc(sizeof(double) * n),
          *qv = malloc(sizeof(double) * n);
@@ -1093,7 +1418,7 @@ static int pcg(const scene_sys* S, const double* b, double eps_r, int max_iter, 
   double bn = sqrt(vdot(n, b, b)), rz;
   int it = 0;
   if (sqrt(vdot(n, r, r)) > eps_r * bn) {
-    for (int i = 0; i < S->ns; ++i) precond_apply(S->D + 36 * i, r + 6 * i, z + 6 * i);
+    prec(S, H, r, z);
     for (int i = 0; i < n; ++i) pv[i] = z[i];
     rz = vdot(n, r, z);
     while (it < max_iter) {
@@ -1104,7 +1429,7 @@ static int pcg(const scene_sys* S, const double* b, double eps_r, int max_iter, 
       double alpha = rz / pq;
       for (int i = 0; i < n; ++i) { x[i] += alpha * pv[i]; r[i] -= alpha * qv[i]; }
       if (sqrt(vdot(n, r, r)) <= eps_r * bn) break;
-      for (int i = 0; i < S->ns; ++i) precond_apply(S->D + 36 * i, r + 6 * i, z + 6 * i);
+      prec(S, H, r, z);
       double rz1 = vdot(n, r, z), beta = rz1 / rz;
       rz = rz1;
       for (int i = 0; i < n; ++i) pv[i] = z[i] + beta * pv[i];
@@ -1154,6 +1479,89 @@ int orc_matvec(const orc_config* C, const orc_problem* P, int scene, const doubl
   sys_matvec(&S, x, y, 0);
   sys_free(&S);
   return 0;
+}
+
+static uint64_t spread_bits3(uint64_t x) {  /* bit k of x moves to bit 3k (21 bits) */
+  uint64_t out = 0;
+  for (int k = 0; k < 21; ++k) out |= ((x >> k) & 1ull) << (3 * k);
+  return out;
+}
+
+typedef struct { uint64_t code; int32_t id; } morton_key;
+static int cmp_morton(const void* a, const void* b) {
+  const morton_key *x = a, *y = b;
+  if (x->code != y->code) return x->code < y->code ? -1 : 1;
+  return x->id < y->id ? -1 : (x->id > y->id);
+}
+
+void orc_morton_order(const int64_t* scene_start, int n_scenes, const double* pos, int32_t* out) {
+  for (int s = 0; s < n_scenes; ++s) {
+    int64_t a = scene_start[s], b = scene_start[s + 1];
+    if (b <= a) continue;
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t i = a; i < b; ++i)
+      for (int k = 0; k < 3; ++k) {
+        if (pos[3 * i + k] < lo[k]) lo[k] = pos[3 * i + k];
+        if (pos[3 * i + k] > hi[k]) hi[k] = pos[3 * i + k];
+      }
+    double ext = 1e-300;
+    for (int k = 0; k < 3; ++k) if (hi[k] - lo[k] > ext) ext = hi[k] - lo[k];
+    double scale = 2097151.0 / ext;
+    morton_key* keys = malloc(sizeof(morton_key) * (size_t)(b - a));
+    for (int64_t i = a; i < b; ++i) {
+      uint64_t c = 0;
+      for (int k = 0; k < 3; ++k) {
+        double v = (pos[3 * i + k] - lo[k]) * scale;
+        if (v < 0.0) v = 0.0;
+        if (v > 2097151.0) v = 2097151.0;
+        c |= spread_bits3((uint64_t)v) << k;
+      }
+      keys[i - a].code = c;
+      keys[i - a].id = (int32_t)i;
+    }
+    qsort(keys, (size_t)(b - a), sizeof(morton_key), cmp_morton);
+    for (int64_t i = a; i < b; ++i) out[i] = keys[i - a].id;
+    free(keys);
+  }
+}
+
+int orc_amg_apply(const orc_config* C, const orc_problem* P, int scene, const double* p, const double* q,
+                  const double* phat, const double* qhat, const double* r, double* z) {
+  if (!P->morton) return -1;
+  scene_sys S;
+  sys_init(&S, C, P, scene, phat, qhat);
+  sys_set_candidates(&S, scene, p);
+  sys_assemble(&S, p, q, 1);
+  amg_hier H;
+  amg_build(&S, p, q, &H);
+  amg_apply(&S, &H, r, z);
+  int nl = H.nl;
+  amg_free(&H);
+  sys_free(&S);
+  return nl;
+}
+
+int orc_amg_level1_apply(const orc_config* C, const orc_problem* P, int scene, const double* p, const double* q,
+                         const double* phat, const double* qhat, const double* e, double* y) {
+  if (!P->morton) return -1;
+  scene_sys S;
+  sys_init(&S, C, P, scene, phat, qhat);
+  sys_set_candidates(&S, scene, p);
+  sys_assemble(&S, p, q, 1);
+  amg_hier H;
+  amg_build(&S, p, q, &H);
+  int m = -1;
+  if (H.nl > 1) {
+    amg_level* L1 = &H.L[1];
+    m = L1->n;
+    memset(y, 0, sizeof(double) * 6 * m);
+    for (int k = 0; k < L1->nnz; ++k)
+      for (int a = 0; a < 6; ++a)
+        for (int b = 0; b < 6; ++b) y[6 * L1->e[k].r + a] += L1->e[k].v[6 * a + b] * e[6 * L1->e[k].c + b];
+  }
+  amg_free(&H);
+  sys_free(&S);
+  return m;
 }
 
 int orc_pcg_solve(const orc_config* C, const orc_problem* P, int scene, const double* p, const double* q,

@@ -37,7 +37,7 @@ typedef struct {
   double mu_roll;          /* rotation friction coefficient (0: off) */
   int32_t integrator;      /* 0: the implicit-Euler-like form (V at x_{n+1}); 1: the variational midpoint form of
                               Sec. 3.1 / App. C (V at (x_{n+1} + x_n)/2 and the target zhat) */
-  int32_t pad1;
+  int32_t preconditioner;  /* 0: block Jacobi; 1: the aggregation AMG cycle (Sec. 5.3; needs P->morton) */
 } orc_config;
 
 /* Particle, bond and scene arrays. Bond rest data is filled by orc_bond_rest(). */
@@ -64,6 +64,8 @@ typedef struct {
   uint8_t* broken;              /* [nb] */
   const double* tensile_strength; /* [nb] sigma_c of the stress criterion (+inf: off), or NULL */
   const double* shear_strength;   /* [nb] tau_c of the stress criterion (+inf: off), or NULL */
+  const int32_t* morton;          /* [n] the particles of each scene in the Z-order of their initial positions
+                                     (orc_morton_order), or NULL (no AMG) */
 } orc_problem;
 
 typedef struct {
@@ -80,6 +82,20 @@ typedef struct {
 /* Sec. 3.2: per-bond rest data from the current state and per-bond material constants. */
 int orc_bond_rest(orc_problem* P, const double* E, const double* nu, const double* bend_twist_scale,
                   const double* shear_scale, const double* break_strain);
+
+/* The Z-order (Morton order) of each scene's particles: positions quantised to 21 bits per axis over the scene's
+ * bounding box (largest extent), bits interleaved x, y, z from the lowest, particles sorted by code, ties by
+ * index; out[scene_start[s] + k] = index of the k-th particle of scene s. */
+void orc_morton_order(const int64_t* scene_start, int n_scenes, const double* pos, int32_t* out);
+
+/* z = M^-1 r of the AMG preconditioner of one scene's system at (p, q) (arguments as orc_system; r, z [6 n_s]). */
+int orc_amg_apply(const orc_config* C, const orc_problem* P, int scene, const double* p, const double* q,
+                  const double* phat, const double* qhat, const double* r, double* z);
+
+/* The AMG's level-1 operator A_1 = P_0^T A_0 P_0 applied to a coarse vector e [n_agg][6] (aggregates in Z-order):
+ * y = A_1 e. Returns n_agg. */
+int orc_amg_level1_apply(const orc_config* C, const orc_problem* P, int scene, const double* p, const double* q,
+                         const double* phat, const double* qhat, const double* e, double* y);
 
 /* One time step of Alg. 3 for every scene. stats: [n_scenes]. Returns the worst status. */
 int orc_step(const orc_config* C, orc_problem* P, orc_scene_stats* stats);
