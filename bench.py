@@ -294,6 +294,8 @@ def main():
                     help="time N PCG iterations of one solve (eps 0) on the workload's system and exit (profiling)")
     ap.add_argument("--workload", default="plate", choices=["plate", "batched", "impact"],
                     help="plate: the benchmark workload; batched / impact: extra measurement lines")
+    ap.add_argument("--precond", default="block-jacobi", choices=["block-jacobi", "amg"],
+                    help="PCG preconditioner: block Jacobi (the benchmark path) or the aggregation AMG (comparison)")
     ap.add_argument("--radius", type=float, default=0.284,
                     help="plate radius; anything but 0.284 m is a smaller profiling case, not the benchmark workload")
     args = ap.parse_args()
@@ -326,12 +328,16 @@ def main():
     else:
         sc = scenes.c2_plate(R=args.radius)
 
+    amg = args.precond == "amg"
+    pcfg = dict(preconditioner=pkg.BDEM_PRECOND_AMG if amg else pkg.BDEM_PRECOND_BLOCK_JACOBI)
     # ---- FP32-mixed path, inputs resident ----
-    sim = pkg.Sim(sc, precision=pkg.BDEM_MIXED)
+    sim = pkg.Sim(sc, precision=pkg.BDEM_MIXED, config=pcfg)
     if args.pcg_probe:
         return pcg_probe(args, sc, sim, pkg, torch)
     sim.step(args.warmup)
-    if args.pcg_lanes:
+    if amg:
+        shape = None  # the AMG-preconditioned solve runs as host-driven kernels, not the persistent PCG
+    elif args.pcg_lanes:
         sim.set_pcg_shape(args.pcg_lanes, args.pcg_blocks)
         shape = {"lanes_per_row": args.pcg_lanes, "blocks": args.pcg_blocks, "autotuned": False}
     else:
@@ -405,7 +411,7 @@ def main():
     # ---- FP64 GPU path on the same workload ----
     fp64 = None
     if args.fp64_steps > 0:
-        sim64 = pkg.Sim(sc, precision=pkg.BDEM_FP64)
+        sim64 = pkg.Sim(sc, precision=pkg.BDEM_FP64, config=pcfg)
         sim64.step(args.warmup)
         r64 = timed_steps(sim64, args.fp64_steps, world, torch, sizes, profile=False)
         t64, u64 = reduce_timing(r64["elapsed"], r64["units"], world)
@@ -434,6 +440,7 @@ def main():
                        "n_scenes": sc.n_scenes,
                        "precision": "FP32-mixed (f32 Hessian/PCG, f64 gradient/reductions/state)",
                        "n_particles": sc.n, "n_bonds": sc.nb, "replicas": world,
+                       "preconditioner": args.precond,
                        "l2": "working set of every timed stage exceeds the 129 MB L2; no flush between steps"},
             "sim_steps_per_s": args.steps * world / t_max,
             "newton_iters_per_step": run["newton"] / args.steps,
@@ -442,7 +449,7 @@ def main():
             "host_loop_pass": {"ms_per_step": 1e3 * rrun["elapsed"] / args.steps, "same_work": same_work,
                                "phase_ms_per_step": {k: v / max(prof["steps"], 1) for k, v in prof["ms"].items()}},
             "pcg_shape": shape,
-            "roofline": {"bound": "hbm", "kernel": "k_pcg (persistent PCG)", "achieved": achieved, "peak": peak,
+            "roofline": None if amg else {"bound": "hbm", "kernel": "k_pcg (persistent PCG)", "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "algorithmic_bytes_per_launch": bytes_launch,
                          "algorithmic_bytes_per_pcg_iter_without_contacts": bytes_iter,

@@ -53,6 +53,7 @@ enum { BDEM_FP64 = 0, BDEM_MIXED = 1 };   /* bdem_config.precision */
 enum { BDEM_SPD_EIG = 0 };                /* bdem_config.spd_mode */
 enum { BDEM_OPT_SECOND_ORDER = 0, BDEM_OPT_FIRST_ORDER = 1 };  /* bdem_config.optimizer */
 enum { BDEM_INT_EULER = 0, BDEM_INT_MIDPOINT = 1 };             /* bdem_config.integrator */
+enum { BDEM_PRECOND_BLOCK_JACOBI = 0, BDEM_PRECOND_AMG = 1 };   /* bdem_config.preconditioner */
 
 /* Bond material (Sec. 3.2). G = E / (2 (1 + nu)) (isotropic relation; the paper does not define G). */
 typedef struct {
@@ -102,7 +103,14 @@ typedef struct {
                                every potential (bonds, gravity, ground, self contact) at the plain average of the two
                                states in R^3 x R^4 (quaternions not renormalised); contact candidates and fracture as
                                for BDEM_INT_EULER */
-  int32_t reserved1;        /* 0 */
+  int32_t preconditioner;   /* BDEM_PRECOND_BLOCK_JACOBI (0): block-Jacobi PCG in one persistent kernel (and the step
+                               graph). BDEM_PRECOND_AMG (1): the algebraic multigrid preconditioner Sec. 5.3 names,
+                               read as an aggregation AMG: Z-order aggregates of 8 (levels until a scene has at most
+                               8 nodes, at least one), rigid-motion coarse spaces (t, w) per aggregate, Galerkin
+                               coarse operators of the assembled diagonal and bond blocks (contact off-diagonal
+                               blocks left out), a symmetric V(1,1) cycle with block-Jacobi smoothing damped by 0.6,
+                               exact solves of each scene's coarsest level; the textbook PCG around it runs from the
+                               host-driven step loop (no step graph) */
 } bdem_config;
 
 /* Per-scene statistics of one bdem_step call (sums over its steps, norms of the last step). */

@@ -1093,8 +1093,8 @@ static double vdot(int n, const double* a, const double* b) {
 /* Algebraic multigrid preconditioner (Sec. 5.3 names an AMG preconditioner for the PCG and nothing    */
 /* more). Reading, an aggregation AMG built for this method's block structure:                       */
 /*  - level 0: the scene's particles in the Z-order (Morton order) of their initial positions, as      */
-/*    defined by orc_morton_order; level l+1: consecutive groups of 8 level-l nodes; coarsest level: a  */
-/*    level of at most 8 nodes, solved exactly (dense Cholesky);                                      */
+/*    defined by orc_morton_order; level l+1: consecutive groups of 8 level-l nodes; coarsest level: the */
+/*    first level above 0 with at most 8 nodes, solved exactly (dense Cholesky);                       */
 /*  - the coarse space of an aggregate is its infinitesimal rigid motions (t, w): a level-0 node i in  */
 /*    aggregate I moves by dp_i = t + w x (p_i - c_I) and turns by y_i = 1/2 R(q_i)^T w (dq = q (x)     */
 /*    (y, 0) for the world rotation dq = 1/2 (w, 0) (x) q); a level-l node k (l >= 1) by t_k =          */
@@ -1258,7 +1258,7 @@ static void amg_build(const scene_sys* S, const double* p, const double* q, amg_
     for (int i = 0; i < L->n; ++i)
       for (int k = L->rs[i]; k < L->rs[i + 1]; ++k)
         if (L->e[k].c == i) inv6(L->e[k].v, L->Dinv + 36 * i);
-    if (L->n <= AMG_AGG || l == 15) break;
+    if ((L->n <= AMG_AGG && l > 0) || l == 15) break;  /* at least one coarse level */
     /* aggregates of consecutive groups of AMG_AGG nodes: centroids, prolongation blocks, Galerkin product */
     amg_level* C = &H->L[l + 1];
     C->n = (L->n + AMG_AGG - 1) / AMG_AGG;

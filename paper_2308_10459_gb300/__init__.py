@@ -20,6 +20,7 @@ BDEM_OK, BDEM_E_INVALID, BDEM_E_NOMEM, BDEM_E_CUDA = 0, 1, 2, 3
 BDEM_E_NEWTON_MAXITER, BDEM_E_LINESEARCH, BDEM_E_NONFINITE, BDEM_E_TIMEOUT = 4, 5, 6, 7
 BDEM_FP64, BDEM_MIXED = 0, 1
 BDEM_INT_EULER, BDEM_INT_MIDPOINT = 0, 1
+BDEM_PRECOND_BLOCK_JACOBI, BDEM_PRECOND_AMG = 0, 1
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "NOMEM", 3: "CUDA", 4: "NEWTON_MAXITER", 5: "LINESEARCH", 6: "NONFINITE",
                 7: "TIMEOUT"}
 
@@ -38,7 +39,7 @@ class bdem_config(ctypes.Structure):
                 ("k_ground", ctypes.c_double), ("k_self", ctypes.c_double), ("contact_skin", ctypes.c_double),
                 ("spd_mode", ctypes.c_int32), ("optimizer", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
                 ("friction_slide", ctypes.c_double), ("friction_roll", ctypes.c_double),
-                ("integrator", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+                ("integrator", ctypes.c_int32), ("preconditioner", ctypes.c_int32)]
 
 
 class bdem_step_stats(ctypes.Structure):
@@ -155,6 +156,7 @@ def make_config(cfg: dict, precision=BDEM_FP64, cuda_stream=None) -> bdem_config
     c.friction_slide = cfg.get("friction_slide", 0.0)
     c.friction_roll = cfg.get("friction_roll", 0.0)
     c.integrator = int(cfg.get("integrator", 0))
+    c.preconditioner = int(cfg.get("preconditioner", 0))
     return c
 
 

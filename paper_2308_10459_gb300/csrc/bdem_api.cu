@@ -65,6 +65,10 @@ struct bdem_sim {
   cudaStream_t cap[3] = {nullptr, nullptr, nullptr};
   int g_pre = 0, g_body = 0, g_ls = 0, g_post = 0;  // kernels per graph segment
   int64_t graph_steps = 0;
+  // aggregation AMG preconditioner (bdem_config.preconditioner)
+  AmgDev amg{};
+  int64_t amg_nb = -1;                // bond count the AMG patterns were built for (-1: not built)
+  std::vector<void*> amg_allocs;
 };
 
 static cudaEvent_t ev_get(bdem_sim* s) {
@@ -233,6 +237,8 @@ static bdem_status check_config(const bdem_config* c) {
     return fail(nullptr, BDEM_E_INVALID, "optimizer must be BDEM_OPT_SECOND_ORDER or BDEM_OPT_FIRST_ORDER");
   if (c->integrator != BDEM_INT_EULER && c->integrator != BDEM_INT_MIDPOINT)
     return fail(nullptr, BDEM_E_INVALID, "integrator must be BDEM_INT_EULER or BDEM_INT_MIDPOINT");
+  if (c->preconditioner != BDEM_PRECOND_BLOCK_JACOBI && c->preconditioner != BDEM_PRECOND_AMG)
+    return fail(nullptr, BDEM_E_INVALID, "preconditioner must be BDEM_PRECOND_BLOCK_JACOBI or BDEM_PRECOND_AMG");
   if (!(c->k_ground >= 0.0) || !(c->k_self >= 0.0) || !(c->contact_skin >= 0.0) || !fin(c->ground_z) ||
       !fin(c->k_ground) || !fin(c->k_self) || !fin(c->contact_skin))
     return fail(nullptr, BDEM_E_INVALID, "contact parameters must be finite and >= 0");
@@ -543,6 +549,8 @@ extern "C" bdem_status bdem_create(const bdem_config* config, int32_t n_scenes, 
   d.wait_ns = 2000000000ull;  // 2 s
   d.first_order = c.optimizer == BDEM_OPT_FIRST_ORDER;
   d.midpoint = c.integrator == BDEM_INT_MIDPOINT;
+  s->amg.on = c.preconditioner == BDEM_PRECOND_AMG;
+  s->amg.omega = 0.6;
   d.mu_roll = c.friction_roll;
   double rmax = 0.0;
   for (int64_t i = 0; i < n; ++i) rmax = std::max(rmax, radius[i]);
@@ -869,6 +877,187 @@ static bdem_status run_pcg(bdem_sim* s, const DevArrays& d, int rhs_from_g, int 
   return check_launch(s, 0);
 }
 
+// ---- aggregation AMG (Sec. 5.3): static patterns from the bond list --------------------------------------------
+
+static void amg_release(bdem_sim* s) {
+  for (void* p : s->amg_allocs) dfree(s, p);
+  s->amg_allocs.clear();
+  double om = s->amg.omega;
+  int on = s->amg.on;
+  s->amg = AmgDev{};
+  s->amg.omega = om;
+  s->amg.on = on;
+  s->amg_nb = -1;
+}
+
+template <typename P>
+static bdem_status amg_upload(bdem_sim* s, P** dst, const std::vector<P>& src) {
+  TRY(dalloc_t(s, dst, std::max<size_t>(src.size(), 1)));
+  s->amg_allocs.push_back(*dst);
+  if (!src.empty()) CUDA_TRY(s, cudaMemcpy(*dst, src.data(), sizeof(P) * src.size(), cudaMemcpyHostToDevice));
+  return BDEM_OK;
+}
+
+static bdem_status amg_zeros(bdem_sim* s, void** dst, size_t bytes) {
+  TRY(dalloc(s, dst, bytes));
+  s->amg_allocs.push_back(*dst);
+  return BDEM_OK;
+}
+
+// Level 0: the particles in internal (Z-) order, each scene contiguous. A scene gets level 1 always and level l + 1
+// while it has more than kAmgAgg nodes on level l; its nodes on a level are consecutive. Entries of A_1: the diagonal
+// of every node and, per bond, (agg i, agg j) with the code b << 1 and (agg j, agg i) with b << 1 | 1; entries of
+// A_{l+1}: the parents of each level-l entry. Sorted by (row, column, source), so every coarse entry sums its sources
+// in one fixed order.
+static bdem_status build_amg(bdem_sim* s) {
+  amg_release(s);
+  AmgDev& a = s->amg;
+  const int S = s->n_scenes;
+  const size_t wsz = wsize(s);
+  std::vector<std::vector<int64_t>> cnt(1, std::vector<int64_t>(S)), off(1, std::vector<int64_t>(S + 1));
+  for (int sc = 0; sc < S; ++sc) {
+    cnt[0][sc] = s->offsets[sc + 1] - s->offsets[sc];
+    off[0][sc] = s->offsets[sc];
+  }
+  off[0][S] = s->n;
+  std::vector<int64_t> nl_nodes(1, s->n);
+  for (int l = 0; l + 1 < kAmgMaxLevels; ++l) {
+    std::vector<int64_t> c(S, 0), o(S + 1, 0);
+    bool any = false;
+    for (int sc = 0; sc < S; ++sc) {
+      bool next = l == 0 ? cnt[0][sc] > 0 : cnt[l][sc] > kAmgAgg;
+      c[sc] = next ? (cnt[l][sc] + kAmgAgg - 1) / kAmgAgg : 0;
+      any = any || next;
+    }
+    if (!any) break;
+    for (int sc = 0; sc < S; ++sc) o[sc + 1] = o[sc] + c[sc];
+    cnt.push_back(c);
+    off.push_back(o);
+    nl_nodes.push_back(o[S]);
+  }
+  a.nl = (int)cnt.size();
+  if (a.nl < 2) return BDEM_OK;
+  // per level: children ranges and parents
+  std::vector<std::vector<int32_t>> parent(a.nl), cbeg(a.nl), cend(a.nl);
+  for (int l = 0; l < a.nl; ++l) parent[l].assign(std::max<int64_t>(nl_nodes[l], 1), -1);
+  for (int l = 1; l < a.nl; ++l) {
+    cbeg[l].assign(std::max<int64_t>(nl_nodes[l], 1), 0);
+    cend[l].assign(std::max<int64_t>(nl_nodes[l], 1), 0);
+    for (int sc = 0; sc < S; ++sc)
+      for (int64_t k = 0; k < cnt[l][sc]; ++k) {
+        int64_t I = off[l][sc] + k;
+        int64_t c0 = off[l - 1][sc] + kAmgAgg * k, c1 = std::min(c0 + kAmgAgg, off[l - 1][sc] + cnt[l - 1][sc]);
+        cbeg[l][I] = (int32_t)c0;
+        cend[l][I] = (int32_t)c1;
+        for (int64_t ch = c0; ch < c1; ++ch) parent[l - 1][ch] = (int32_t)I;
+      }
+  }
+  // patterns
+  struct Ent { int32_t r, c, src; };
+  std::vector<Ent> raw;
+  raw.reserve(nl_nodes[1] + 2 * s->bi.size());
+  for (int64_t I = 0; I < nl_nodes[1]; ++I) raw.push_back({(int32_t)I, (int32_t)I, -1});
+  for (size_t b = 0; b < s->bi.size(); ++b) {
+    int32_t I = parent[0][s->bi[b]], J = parent[0][s->bj[b]];
+    raw.push_back({I, J, (int32_t)(b << 1)});
+    raw.push_back({J, I, (int32_t)(b << 1 | 1)});
+  }
+  std::vector<int32_t> prev_row, prev_col;  // entries of the level below (l >= 2 sources)
+  for (int l = 1; l < a.nl; ++l) {
+    if (l >= 2) {
+      raw.clear();
+      for (size_t e = 0; e < prev_row.size(); ++e) {
+        int32_t I = parent[l - 1][prev_row[e]], J = parent[l - 1][prev_col[e]];
+        if (I >= 0 && J >= 0) raw.push_back({I, J, (int32_t)e});
+      }
+    }
+    std::sort(raw.begin(), raw.end(), [](const Ent& x, const Ent& y) {
+      return x.r != y.r ? x.r < y.r : (x.c != y.c ? x.c < y.c : x.src < y.src);
+    });
+    std::vector<int32_t> rs(nl_nodes[l] + 1, 0), col, erow, gs(1, 0), gsrc, diag(std::max<int64_t>(nl_nodes[l], 1), -1);
+    for (size_t k = 0; k < raw.size(); ++k) {
+      bool fresh = k == 0 || raw[k].r != raw[k - 1].r || raw[k].c != raw[k - 1].c;
+      if (fresh) {
+        if (k) gs.push_back((int32_t)gsrc.size());
+        col.push_back(raw[k].c);
+        erow.push_back(raw[k].r);
+        rs[raw[k].r + 1] += 1;
+        if (raw[k].r == raw[k].c) diag[raw[k].r] = (int32_t)col.size() - 1;
+      }
+      if (raw[k].src >= 0) gsrc.push_back(raw[k].src);
+    }
+    gs.push_back((int32_t)gsrc.size());
+    for (int64_t I = 0; I < nl_nodes[l]; ++I) rs[I + 1] += rs[I];
+    AmgLevel& L = a.L[l];
+    L.n = (int32_t)nl_nodes[l];
+    L.nnz = (int32_t)col.size();
+    TRY(amg_upload(s, &L.cbeg, cbeg[l]));
+    TRY(amg_upload(s, &L.cend, cend[l]));
+    TRY(amg_upload(s, &L.parent, parent[l]));
+    TRY(amg_upload(s, &L.rs, rs));
+    TRY(amg_upload(s, &L.col, col));
+    TRY(amg_upload(s, &L.erow, erow));
+    TRY(amg_upload(s, &L.diag, diag));
+    TRY(amg_upload(s, &L.gs, gs));
+    TRY(amg_upload(s, &L.gsrc, gsrc));
+    TRY(amg_zeros(s, &L.val, 36 * wsz * std::max<size_t>(col.size(), 1)));
+    TRY(amg_zeros(s, &L.dinv, 36 * wsz * std::max<int64_t>(L.n, 1)));
+    void* cen = nullptr;
+    TRY(amg_zeros(s, &cen, 3 * sizeof(double) * std::max<int64_t>(L.n, 1)));
+    L.cen = reinterpret_cast<double*>(cen);
+    TRY(amg_zeros(s, &L.r, 6 * wsz * std::max<int64_t>(L.n, 1)));
+    TRY(amg_zeros(s, &L.x, 6 * wsz * std::max<int64_t>(L.n, 1)));
+    TRY(amg_zeros(s, &L.t, 6 * wsz * std::max<int64_t>(L.n, 1)));
+    prev_row = erow;
+    prev_col = col;
+  }
+  a.L[0].n = s->n;
+  TRY(amg_upload(s, &a.L[0].parent, parent[0]));
+  TRY(amg_zeros(s, &a.L[0].t, 6 * wsz * std::max<int32_t>(s->n, 1)));
+  std::vector<int32_t> lev(S, 0), o(S, 0), m(S, 0);
+  for (int sc = 0; sc < S; ++sc)
+    for (int l = 1; l < a.nl; ++l)
+      if (cnt[l][sc] > 0) {
+        lev[sc] = l;
+        o[sc] = (int32_t)off[l][sc];
+        m[sc] = (int32_t)cnt[l][sc];
+      }
+  TRY(amg_upload(s, &a.sc_level, lev));
+  TRY(amg_upload(s, &a.sc_off, o));
+  TRY(amg_upload(s, &a.sc_m, m));
+  void* ch = nullptr;
+  TRY(amg_zeros(s, &ch, sizeof(double) * kAmgDense * kAmgDense * std::max(S, 1)));
+  a.chol = reinterpret_cast<double*>(ch);
+  s->amg_nb = s->nb;
+  return BDEM_OK;
+}
+
+// PCG with the AMG cycle as preconditioner on the assembled Newton system (host-driven: one residual read per
+// iteration). from_g: b = -g; else b is read from vr (inspection calls). The solution is left in vx.
+static bdem_status run_amg_pcg(bdem_sim* s, const DevArrays& d, int from_g) {
+  if (s->amg_nb != s->nb) TRY(build_amg(s));
+  AmgDev& a = s->amg;
+  cudaStream_t st = s->stream;
+  if (a.nl < 2 || d.n == 0) return BDEM_OK;
+  TRY(check_launch(s, launch_amg_setup(d, a, s->n_scenes, st)));
+  TRY(check_launch(s, launch_amg_pcg_stage(d, from_g ? 0 : 6, st)));
+  TRY(check_launch(s, launch_amg_cycle(d, a, s->n_scenes, st)));
+  TRY(check_launch(s, launch_amg_pcg_stage(d, 1, st)));
+  for (int it = 0; it <= d.pcg_max; ++it) {
+    CUDA_TRY(s, cudaMemsetAsync(&d.cnt->n_active, 0, sizeof(int32_t), st));
+    TRY(check_launch(s, launch_matvec(d, 1, st)));
+    TRY(check_launch(s, launch_amg_pcg_stage(d, 2, st)));
+    TRY(check_launch(s, launch_amg_pcg_stage(d, 3, st)));
+    int32_t act = 0;
+    CUDA_TRY(s, cudaMemcpyAsync(&act, &d.cnt->n_active, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    TRY(sync(s));
+    if (act == 0) break;
+    TRY(check_launch(s, launch_amg_cycle(d, a, s->n_scenes, st)));
+    TRY(check_launch(s, launch_amg_pcg_stage(d, 4, st)));
+  }
+  return BDEM_OK;
+}
+
 // one time step; on success ctl holds the per-scene control blocks of the step
 static bdem_status do_step(bdem_sim* s, std::vector<SceneCtl>& ctl) {
   DevArrays& d = s->d;
@@ -905,7 +1094,8 @@ static bdem_status do_step(bdem_sim* s, std::vector<SceneCtl>& ctl) {
       TRY(check_launch(s, launch_particle_hess(d, 1, 0, st)));
       phase_end(s);
       phase_begin(s, BDEM_PH_PCG);
-      TRY(run_pcg(s, d, 1, 1));
+      if (s->amg.on) TRY(run_amg_pcg(s, d, 1));
+      else TRY(run_pcg(s, d, 1, 1));
       phase_end(s);
     }
     phase_begin(s, BDEM_PH_LINESEARCH);
@@ -1102,6 +1292,7 @@ static bdem_status graph_step(bdem_sim* s, std::vector<SceneCtl>& ctl, bool* red
 
 static bool graph_usable(bdem_sim* s) {
   if (!s->graph_enabled || s->graph_failed || s->prof_on || s->d.n == 0 || !s->contacts_sized) return false;
+  if (s->amg.on) return false;  // the AMG-preconditioned solve runs from the host-driven loop
   if (s->graph_exec && memcmp(&s->graph_d, &s->d, sizeof(DevArrays)) == 0) return true;
   if (build_step_graph(s)) return true;
   s->graph_failed = true;
@@ -1440,7 +1631,8 @@ extern "C" bdem_status bdem_debug_pcg(bdem_sim* s, const double* b, double eps_r
   TRY(dbg_reserve(s, 12 * n));
   CUDA_TRY(s, cudaMemcpyAsync(s->dbg_buf, b, sizeof(double) * 6 * n, cudaMemcpyHostToDevice, st));
   TRY(check_launch(s, launch_convert_perm(s->dbg_buf, 1, d.vr, !d.mixed, d.perm, 0, (int)n, st)));
-  TRY(run_pcg(s, d, 0, 1));
+  if (s->amg.on) TRY(run_amg_pcg(s, d, 0));
+  else TRY(run_pcg(s, d, 0, 1));
   Counters c{};
   TRY(read_counters(s, &c));
   TRY(check_launch(s, launch_convert_perm(d.vx, !d.mixed, s->dbg_buf + 6 * n, 1, d.perm, 1, (int)n, st)));

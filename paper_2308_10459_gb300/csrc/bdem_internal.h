@@ -125,6 +125,35 @@ struct DevArrays {
   Counters* cnt;
 };
 
+// ---- aggregation AMG preconditioner (Sec. 5.3) --------------------------------------------------------------------
+// Level 0: the particles (internal order = Z-order of the initial positions inside each scene); level l+1: groups of
+// kAmgAgg consecutive level-l nodes of one scene, built while the scene has more than kAmgAgg nodes (at least one
+// coarse level); coarse spaces of rigid motions (t, w) per node; A_1 = Galerkin product of the assembled diagonal
+// blocks and bond blocks (contact off-diagonal blocks left out), A_{l+1} = P^T A_l P; the coarsest level of each
+// scene (<= kAmgAgg nodes) is solved by a dense Cholesky factor. Patterns and Galerkin source lists are built on the
+// host from the bond list; values are recomputed on the device at every Newton iteration.
+constexpr int kAmgMaxLevels = 12;
+constexpr int kAmgAgg = 8;
+constexpr int kAmgDense = 6 * kAmgAgg;  // largest coarsest system per scene
+struct AmgLevel {
+  int32_t n, nnz;
+  int32_t *cbeg, *cend;  // [n] children [cbeg, cend) of each node (level l-1 nodes; on level 1 internal particles)
+  int32_t* parent;  // [n] node of level l+1 holding this node; -1 on the scene's coarsest level
+  int32_t *rs, *col, *erow, *diag;  // block CSR of A_l: row starts [n+1], columns and rows [nnz], diagonal entry [n]
+  int32_t *gs, *gsrc;  // Galerkin sources per entry: level 1 bond codes (b << 1 | o, o = 1: the transposed block),
+                       // level l >= 2 entries of level l-1
+  void *val, *dinv;    // [nnz][36], [n][36] T
+  double* cen;         // [n][3] centroids
+  void *r, *x, *t;     // [n][6] T cycle vectors
+};
+struct AmgDev {
+  int32_t nl, on;              // number of levels (level 0 included); the preconditioner is in use
+  double omega;                // damping of the block-Jacobi smoothing
+  AmgLevel L[kAmgMaxLevels];   // L[0]: only parent (= level-1 node of each particle) and t are used
+  int32_t *sc_level, *sc_off, *sc_m;  // per scene: coarsest level, its first node there, its node count
+  double* chol;                // [S][kAmgDense^2] dense Cholesky factors of the coarsest operators
+};
+
 // ---- launchers (bdem_kernels.cu); each returns the number of kernels launched -----------------------------------
 int launch_predict(const DevArrays& d, cudaStream_t s);
 // variational midpoint form: zhat = xhat - 1/2 M^-1 dt^2 grad V((x_{n-1} + x_n)/2) into hp, hq (after the contact
@@ -173,5 +202,13 @@ cudaError_t static_pcg_address(void** out);
 int launch_static_pcg_init(const DevArrays& d, double eps_r, cudaStream_t s);
 int launch_wait_test(const DevArrays& d, cudaStream_t s);  // a bounded wait that always runs out
 int launch_convert(const void* src, int src_double, void* dst, int dst_double, int64_t count, cudaStream_t s);
+// AMG: coarse operators of the current Newton system (centroids, Galerkin products, block inverses, coarsest
+// factors); one V(1,1) cycle z = M^-1 r (r = PCG residual vr, z = vz); PCG steps with the cycle as preconditioner
+int launch_amg_setup(const DevArrays& d, const AmgDev& a, int n_scenes, cudaStream_t s);
+int launch_amg_cycle(const DevArrays& d, const AmgDev& a, int n_scenes, cudaStream_t s);
+// AMG-preconditioned PCG pieces (per-scene state in SceneCtl): stage 0 r = b = -g (masked), x = 0, |b|^2 -> thr2;
+// 1 gamma = r.z, p = z; 2 alpha from p.q (q = H p); 3 x += alpha p, r -= alpha q, stop test (counts active scenes into
+// cnt->n_active); 4 beta from the new r.z, p = z + beta p
+int launch_amg_pcg_stage(const DevArrays& d, int stage, cudaStream_t s);
 
 }  // namespace bdem

@@ -2091,4 +2091,668 @@ int launch_convert(const void* src, int sd, void* dst, int dd, int64_t count, cu
   return 1;
 }
 
+// ================================================================================================
+// aggregation AMG preconditioner (Sec. 5.3): coarse operators and the V(1,1) cycle
+// ================================================================================================
+
+// R(q) of a unit quaternion (x, y, z, w), row major
+__device__ __forceinline__ void amg_rot(double4 q, double R[9]) {
+  double x = q.x, y = q.y, z = q.z, w = q.w;
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - z * w);     R[2] = 2 * (x * z + y * w);
+  R[3] = 2 * (x * y + z * w);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - x * w);
+  R[6] = 2 * (x * z - y * w);     R[7] = 2 * (y * z + x * w);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+// the rigid-motion block of a node at offset dv from its aggregate's centroid: [[I, -[dv]x], [0, B]]; B = 1/2 R(q)^T
+// on level 0 (a world rotation w turns the particle by y = 1/2 R(q)^T w), identity above
+__device__ __forceinline__ void amg_pblock(const double dv[3], const double* B3, double P[36]) {
+#pragma unroll
+  for (int k = 0; k < 36; ++k) P[k] = 0.0;
+  P[0] = P[7] = P[14] = 1.0;
+  P[4] = dv[2];  P[5] = -dv[1];
+  P[9] = -dv[2]; P[11] = dv[0];
+  P[15] = dv[1]; P[16] = -dv[0];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) P[6 * (3 + a) + 3 + b] = B3 ? B3[3 * a + b] : (a == b ? 1.0 : 0.0);
+}
+
+__device__ __forceinline__ void amg_p0(const DevArrays& d, const AmgDev& a, int i, double P[36]) {
+  int I = a.L[0].parent[i];
+  double4 p = d.xp[i];
+  const double* c = a.L[1].cen + 3 * (size_t)I;
+  double dv[3] = {p.x - c[0], p.y - c[1], p.z - c[2]};
+  double R[9], B[9];
+  amg_rot(d.xq[i], R);
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c2 = 0; c2 < 3; ++c2) B[3 * r + c2] = 0.5 * R[3 * c2 + r];
+  amg_pblock(dv, B, P);
+}
+
+__device__ __forceinline__ void amg_pl(const AmgDev& a, int l, int k, double P[36]) {  // node k of level l >= 1
+  int I = a.L[l].parent[k];
+  const double *ck = a.L[l].cen + 3 * (size_t)k, *cI = a.L[l + 1].cen + 3 * (size_t)I;
+  double dv[3] = {ck[0] - cI[0], ck[1] - cI[1], ck[2] - cI[2]};
+  amg_pblock(dv, nullptr, P);
+}
+
+// acc += P_r^T A P_c (all 6x6, A row major)
+__device__ __forceinline__ void amg_triple(const double Pr[36], const double A[36], const double Pc[36], double acc[36]) {
+  double T[36];
+#pragma unroll
+  for (int r = 0; r < 6; ++r)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) s += A[6 * r + k] * Pc[6 * k + c];
+      T[6 * r + c] = s;
+    }
+#pragma unroll
+  for (int r = 0; r < 6; ++r)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) s += Pr[6 * k + r] * T[6 * k + c];
+      acc[6 * r + c] += s;
+    }
+}
+
+__global__ void k_amg_cent(DevArrays d, AmgDev a, int l) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const AmgLevel& L = a.L[l];
+  if (I >= L.n) return;
+  int c0 = L.cbeg[I], c1 = L.cend[I];
+  double s[3] = {0.0, 0.0, 0.0};
+  for (int k = c0; k < c1; ++k) {
+    if (l == 1) {
+      double4 p = d.xp[k];
+      s[0] += p.x; s[1] += p.y; s[2] += p.z;
+    } else {
+      const double* c = a.L[l - 1].cen + 3 * (size_t)k;
+      s[0] += c[0]; s[1] += c[1]; s[2] += c[2];
+    }
+  }
+  double inv = 1.0 / (double)(c1 - c0);
+  double* o = L.cen + 3 * (size_t)I;
+  o[0] = s[0] * inv; o[1] = s[1] * inv; o[2] = s[2] * inv;
+}
+
+// the (i, j) block of bond b in (dp_i, y_i) x (dp_j, y_j) from its factored storage: [[-Ah, -Cs], [Bs^T, F]]
+template <typename T>
+__device__ __forceinline__ void amg_bond_block(const DevArrays& d, int b, double H[36]) {
+  const T* M = reinterpret_cast<const T*>(d.bM) + 36 * (size_t)b;
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      H[6 * r + c] = -(double)M[sidx<3>(r, c)];
+      H[6 * r + 3 + c] = -(double)M[15 + 3 * r + c];
+      H[6 * (3 + r) + c] = (double)M[6 + 3 * c + r];
+      H[6 * (3 + r) + 3 + c] = (double)M[24 + 3 * r + c];
+    }
+}
+
+template <typename T>
+__global__ void k_amg_gal1(DevArrays d, AmgDev a) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const AmgLevel& L = a.L[1];
+  if (e >= L.nnz) return;
+  int I = L.erow[e], J = L.col[e];
+  double acc[36];
+#pragma unroll
+  for (int k = 0; k < 36; ++k) acc[k] = 0.0;
+  double Pr[36], Pc[36], H[36];
+  if (I == J) {  // the assembled diagonal blocks of the aggregate's particles
+    for (int i = L.cbeg[I]; i < L.cend[I]; ++i) {
+      const T* Dp = reinterpret_cast<const T*>(d.D) + kDiagStride * (size_t)i;
+#pragma unroll
+      for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) H[6 * r + c] = (double)Dp[sidx<6>(r, c)];
+      amg_p0(d, a, i, Pr);
+      amg_triple(Pr, H, Pr, acc);
+    }
+  }
+  for (int k = L.gs[e]; k < L.gs[e + 1]; ++k) {
+    int code = L.gsrc[k], b = code >> 1;
+    if (d.bbroken[b]) continue;
+    int2 ij = d.bij[b];
+    if (d.kin[ij.x] || d.kin[ij.y]) continue;  // the kinematic rows and columns of the system are identity
+    amg_bond_block<T>(d, b, H);
+    if (code & 1) {  // P_j^T H_ij^T P_i
+      double Ht[36];
+#pragma unroll
+      for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) Ht[6 * r + c] = H[6 * c + r];
+      amg_p0(d, a, ij.y, Pr);
+      amg_p0(d, a, ij.x, Pc);
+      amg_triple(Pr, Ht, Pc, acc);
+    } else {
+      amg_p0(d, a, ij.x, Pr);
+      amg_p0(d, a, ij.y, Pc);
+      amg_triple(Pr, H, Pc, acc);
+    }
+  }
+  T* o = reinterpret_cast<T*>(L.val) + 36 * (size_t)e;
+#pragma unroll
+  for (int k = 0; k < 36; ++k) o[k] = (T)acc[k];
+}
+
+template <typename T>
+__global__ void k_amg_gal(AmgDev a, int l) {  // level l >= 2 from level l - 1
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const AmgLevel& L = a.L[l];
+  const AmgLevel& F = a.L[l - 1];
+  if (e >= L.nnz) return;
+  double acc[36];
+#pragma unroll
+  for (int k = 0; k < 36; ++k) acc[k] = 0.0;
+  double Pr[36], Pc[36], A[36];
+  for (int k = L.gs[e]; k < L.gs[e + 1]; ++k) {
+    int f = L.gsrc[k];
+    const T* v = reinterpret_cast<const T*>(F.val) + 36 * (size_t)f;
+#pragma unroll
+    for (int t = 0; t < 36; ++t) A[t] = (double)v[t];
+    amg_pl(a, l - 1, F.erow[f], Pr);
+    amg_pl(a, l - 1, F.col[f], Pc);
+    amg_triple(Pr, A, Pc, acc);
+  }
+  T* o = reinterpret_cast<T*>(L.val) + 36 * (size_t)e;
+#pragma unroll
+  for (int k = 0; k < 36; ++k) o[k] = (T)acc[k];
+}
+
+// inverse of an SPD 6x6 block (FP64 Cholesky; a non-positive pivot falls back to the inverse diagonal)
+__device__ __forceinline__ void amg_inv6(const double A[36], double X[36]) {
+  double Lc[36];
+#pragma unroll
+  for (int k = 0; k < 36; ++k) Lc[k] = 0.0;
+  bool ok = true;
+  for (int j = 0; j < 6 && ok; ++j) {
+    double s = A[7 * j];
+    for (int k = 0; k < j; ++k) s -= Lc[6 * j + k] * Lc[6 * j + k];
+    if (!(s > 0.0)) { ok = false; break; }
+    Lc[7 * j] = sqrt(s);
+    for (int i = j + 1; i < 6; ++i) {
+      double t = A[6 * i + j];
+      for (int k = 0; k < j; ++k) t -= Lc[6 * i + k] * Lc[6 * j + k];
+      Lc[6 * i + j] = t / Lc[7 * j];
+    }
+  }
+  for (int c = 0; c < 6; ++c) {
+    double w[6], z[6];
+    if (!ok) {
+      for (int r = 0; r < 6; ++r) X[6 * r + c] = (r == c && A[7 * r] > 0.0) ? 1.0 / A[7 * r] : (r == c ? 1.0 : 0.0);
+      continue;
+    }
+    for (int i = 0; i < 6; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) s -= Lc[6 * i + k] * w[k];
+      w[i] = s / Lc[7 * i];
+    }
+    for (int i = 5; i >= 0; --i) {
+      double s = w[i];
+      for (int k = i + 1; k < 6; ++k) s -= Lc[6 * k + i] * z[k];
+      z[i] = s / Lc[7 * i];
+    }
+    for (int r = 0; r < 6; ++r) X[6 * r + c] = z[r];
+  }
+}
+
+template <typename T>
+__global__ void k_amg_dinv(AmgDev a, int l) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const AmgLevel& L = a.L[l];
+  if (I >= L.n) return;
+  double A[36], X[36];
+  if (L.diag[I] >= 0) {
+    const T* v = reinterpret_cast<const T*>(L.val) + 36 * (size_t)L.diag[I];
+#pragma unroll
+    for (int k = 0; k < 36; ++k) A[k] = (double)v[k];
+  } else {  // not reached: every node carries its diagonal entry
+#pragma unroll
+    for (int k = 0; k < 36; ++k) A[k] = (k % 7 == 0) ? 1.0 : 0.0;
+  }
+  amg_inv6(A, X);
+  T* o = reinterpret_cast<T*>(L.dinv) + 36 * (size_t)I;
+#pragma unroll
+  for (int k = 0; k < 36; ++k) o[k] = (T)X[k];
+}
+
+// one block per scene: the dense operator of the scene's coarsest level and its Cholesky factor (FP64)
+template <typename T>
+__global__ void k_amg_cfactor(AmgDev a) {
+  int s = blockIdx.x;
+  int l = a.sc_level[s], o = a.sc_off[s], m = a.sc_m[s];
+  if (l <= 0 || m <= 0 || m > kAmgAgg) return;
+  int n = 6 * m;
+  __shared__ double A[kAmgDense * kAmgDense];
+  for (int k = threadIdx.x; k < n * n; k += blockDim.x) A[k] = 0.0;
+  __syncthreads();
+  const AmgLevel& L = a.L[l];
+  for (int I = o + (int)threadIdx.x; I < o + m; I += blockDim.x)
+    for (int e = L.rs[I]; e < L.rs[I + 1]; ++e) {
+      if (L.col[e] < o || L.col[e] >= o + m) continue;  // not reached: entries stay inside their scene
+      const T* v = reinterpret_cast<const T*>(L.val) + 36 * (size_t)e;
+      int r0 = 6 * (I - o), c0 = 6 * (L.col[e] - o);
+      for (int r = 0; r < 6; ++r)
+        for (int c = 0; c < 6; ++c) A[n * (r0 + r) + c0 + c] += (double)v[6 * r + c];
+    }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {  // right-looking Cholesky, rows below the pivot in parallel
+    if (threadIdx.x == 0) {
+      double dj = A[n * j + j];
+      A[n * j + j] = sqrt(dj > 0.0 ? dj : 1e-300);
+    }
+    __syncthreads();
+    double piv = A[n * j + j];
+    for (int i = j + 1 + (int)threadIdx.x; i < n; i += blockDim.x) A[n * i + j] /= piv;
+    __syncthreads();
+    for (int i = j + 1 + (int)threadIdx.x; i < n; i += blockDim.x) {
+      double lij = A[n * i + j];
+      for (int k = j + 1; k <= i; ++k) A[n * i + k] -= lij * A[n * k + j];
+    }
+    __syncthreads();
+  }
+  double* out = a.chol + (size_t)kAmgDense * kAmgDense * s;
+  for (int k = threadIdx.x; k < n * n; k += blockDim.x) out[k] = A[k];
+}
+
+// ---- the cycle --------------------------------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ void amg_mat6(const T* M, const double (&x)[6], double (&y)[6]) {
+#pragma unroll
+  for (int r = 0; r < 6; ++r) {
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s += (double)M[6 * r + c] * x[c];
+    y[r] = s;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void amg_load(const void* base, int i, double (&v)[6]) {
+  const T* p = reinterpret_cast<const T*>(base) + 6 * (size_t)i;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) v[k] = (double)p[k];
+}
+template <typename T>
+__device__ __forceinline__ void amg_store(void* base, int i, const double (&v)[6]) {
+  T* p = reinterpret_cast<T*>(base) + 6 * (size_t)i;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) p[k] = (T)v[k];
+}
+
+// level 0, mode 0: x = w Dinv r (pre-smoothing); mode 1: x += w Dinv t (post-smoothing); x is the PCG's z
+template <typename T>
+__global__ void k_amg_smooth0(DevArrays d, AmgDev a, int mode) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  Vec6<T> r = load6<T>(reinterpret_cast<const T*>(mode ? a.L[0].t : d.vr), i);
+  T y[6];
+  sym6_mul<T>(reinterpret_cast<const T*>(d.Dinv) + kDiagStride * (size_t)i, r.v, y);
+  T out[6];
+  if (mode) {
+    Vec6<T> x = load6<T>(reinterpret_cast<const T*>(d.vz), i);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) out[k] = x.v[k] + (T)a.omega * y[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) out[k] = (T)a.omega * y[k];
+  }
+  if (mode && d.kin[i])
+#pragma unroll
+    for (int k = 0; k < 6; ++k) out[k] = (T)0;
+  store6<T>(reinterpret_cast<T*>(d.vz), i, out);
+}
+
+// level 0: t = r - A_0 x, A_0 = diagonal blocks + bond blocks (kinematic rows: t = r - x; x vanishes on them)
+template <typename T>
+__global__ void k_amg_resid0(DevArrays d, AmgDev a) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  const T* X = reinterpret_cast<const T*>(d.vz);
+  Vec6<T> r = load6<T>(reinterpret_cast<const T*>(d.vr), i);
+  Vec6<T> xi = load6<T>(X, i);
+  T y[6] = {0, 0, 0, 0, 0, 0};
+  if (d.kin[i]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) y[k] = xi.v[k];
+  } else {
+    sym6_mul<T>(reinterpret_cast<const T*>(d.D) + kDiagStride * (size_t)i, xi.v, y);
+    int nbond = d.inc_start[i + 1] - d.inc_start[i];
+    for (int k = 0; k < nbond; ++k) row_entry<T, false>(d, i, k, nbond, X, y);
+  }
+  T t[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) t[k] = r.v[k] - y[k];
+  store6<T>(reinterpret_cast<T*>(a.L[0].t), i, t);
+}
+
+// restriction from level l to l + 1: r_{l+1}[I] = sum over the children k of P_k^T t_l[k]
+// (P^T (v_p, v_y) = (v_p, dv x v_p + B^T v_y))
+template <typename T>
+__global__ void k_amg_restrict(DevArrays d, AmgDev a, int l) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const AmgLevel& C = a.L[l + 1];
+  if (I >= C.n) return;
+  const double* cI = C.cen + 3 * (size_t)I;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int k = C.cbeg[I]; k < C.cend[I]; ++k) {
+    double v[6];
+    amg_load<T>(a.L[l].t, k, v);
+    double ck[3];
+    if (l == 0) {
+      double4 p = d.xp[k];
+      ck[0] = p.x; ck[1] = p.y; ck[2] = p.z;
+      double R[9];
+      amg_rot(d.xq[k], R);  // B^T v_y = 1/2 R v_y
+      double w0 = 0.5 * (R[0] * v[3] + R[1] * v[4] + R[2] * v[5]);
+      double w1 = 0.5 * (R[3] * v[3] + R[4] * v[4] + R[5] * v[5]);
+      double w2 = 0.5 * (R[6] * v[3] + R[7] * v[4] + R[8] * v[5]);
+      v[3] = w0; v[4] = w1; v[5] = w2;
+    } else {
+      const double* c = a.L[l].cen + 3 * (size_t)k;
+      ck[0] = c[0]; ck[1] = c[1]; ck[2] = c[2];
+    }
+    double dv[3] = {ck[0] - cI[0], ck[1] - cI[1], ck[2] - cI[2]};
+    acc[0] += v[0]; acc[1] += v[1]; acc[2] += v[2];
+    acc[3] += dv[1] * v[2] - dv[2] * v[1] + v[3];
+    acc[4] += dv[2] * v[0] - dv[0] * v[2] + v[4];
+    acc[5] += dv[0] * v[1] - dv[1] * v[0] + v[5];
+  }
+  amg_store<T>(C.r, I, acc);
+}
+
+// level l >= 1, non-coarsest nodes: mode 0 x = w Dinv r; mode 1 t = r - A x; mode 2 x += w Dinv t
+template <typename T>
+__global__ void k_amg_level(AmgDev a, int l, int mode) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const AmgLevel& L = a.L[l];
+  if (I >= L.n || L.parent[I] < 0) return;
+  double r[6], y[6];
+  if (mode == 1) {
+    amg_load<T>(L.r, I, r);
+    for (int e = L.rs[I]; e < L.rs[I + 1]; ++e) {
+      double x[6];
+      amg_load<T>(L.x, L.col[e], x);
+      amg_mat6<T>(reinterpret_cast<const T*>(L.val) + 36 * (size_t)e, x, y);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) r[k] -= y[k];
+    }
+    amg_store<T>(L.t, I, r);
+    return;
+  }
+  amg_load<T>(mode ? L.t : L.r, I, r);
+  amg_mat6<T>(reinterpret_cast<const T*>(L.dinv) + 36 * (size_t)I, r, y);
+  if (mode) {
+    double x[6];
+    amg_load<T>(L.x, I, x);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) y[k] = x[k] + a.omega * y[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) y[k] = a.omega * y[k];
+  }
+  amg_store<T>(L.x, I, y);
+}
+
+// one block per scene: x = A^-1 r on the scene's coarsest level with its Cholesky factor
+template <typename T>
+__global__ void k_amg_csolve(AmgDev a) {
+  int s = blockIdx.x;
+  int l = a.sc_level[s], o = a.sc_off[s], m = a.sc_m[s];
+  if (l <= 0 || m <= 0 || m > kAmgAgg || threadIdx.x != 0) return;
+  int n = 6 * m;
+  const double* Lc = a.chol + (size_t)kAmgDense * kAmgDense * s;
+  const AmgLevel& L = a.L[l];
+  double w[kAmgDense], z[kAmgDense];
+  const T* R = reinterpret_cast<const T*>(L.r) + 6 * (size_t)o;
+  for (int i = 0; i < n; ++i) {
+    double v = (double)R[i];
+    for (int k = 0; k < i; ++k) v -= Lc[n * i + k] * w[k];
+    w[i] = v / Lc[n * i + i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double v = w[i];
+    for (int k = i + 1; k < n; ++k) v -= Lc[n * k + i] * z[k];
+    z[i] = v / Lc[n * i + i];
+  }
+  T* X = reinterpret_cast<T*>(L.x) + 6 * (size_t)o;
+  for (int i = 0; i < n; ++i) X[i] = (T)z[i];
+}
+
+// prolongation from level l + 1 to l (nodes whose scene has level l + 1): x_l[k] += P_k e[parent(k)]
+// (P (t, w) = (t + w x dv, B w)); on level 0 the result goes to the PCG's z, kinematic rows kept at zero
+template <typename T>
+__global__ void k_amg_prolong(DevArrays d, AmgDev a, int l) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  int n = l == 0 ? d.n : a.L[l].n;
+  if (k >= n) return;
+  int I = a.L[l].parent[k];
+  if (I < 0) return;
+  double e[6], x[6];
+  amg_load<T>(a.L[l + 1].x, I, e);
+  const double* cI = a.L[l + 1].cen + 3 * (size_t)I;
+  double ck[3], wv[3] = {e[3], e[4], e[5]};
+  void* X = l == 0 ? d.vz : a.L[l].x;
+  amg_load<T>(X, k, x);
+  if (l == 0) {
+    double4 p = d.xp[k];
+    ck[0] = p.x; ck[1] = p.y; ck[2] = p.z;
+    double R[9];
+    amg_rot(d.xq[k], R);  // B w = 1/2 R^T w
+    wv[0] = 0.5 * (R[0] * e[3] + R[3] * e[4] + R[6] * e[5]);
+    wv[1] = 0.5 * (R[1] * e[3] + R[4] * e[4] + R[7] * e[5]);
+    wv[2] = 0.5 * (R[2] * e[3] + R[5] * e[4] + R[8] * e[5]);
+  } else {
+    const double* c = a.L[l].cen + 3 * (size_t)k;
+    ck[0] = c[0]; ck[1] = c[1]; ck[2] = c[2];
+  }
+  double dv[3] = {ck[0] - cI[0], ck[1] - cI[1], ck[2] - cI[2]};
+  x[0] += e[0] + e[4] * dv[2] - e[5] * dv[1];
+  x[1] += e[1] + e[5] * dv[0] - e[3] * dv[2];
+  x[2] += e[2] + e[3] * dv[1] - e[4] * dv[0];
+  x[3] += wv[0]; x[4] += wv[1]; x[5] += wv[2];
+  if (l == 0 && d.kin[k])
+#pragma unroll
+    for (int t = 0; t < 6; ++t) x[t] = 0.0;
+  amg_store<T>(X, k, x);
+}
+
+static inline int amg_blocks(int64_t n) { return (int)((n + 127) / 128); }
+
+template <typename T>
+static int amg_setup_t(const DevArrays& d, const AmgDev& a, int n_scenes, cudaStream_t s) {
+  int k = 0;
+  for (int l = 1; l < a.nl; ++l) {
+    if (a.L[l].n == 0) continue;
+    k_amg_cent<<<amg_blocks(a.L[l].n), 128, 0, s>>>(d, a, l);
+    ++k;
+  }
+  for (int l = 1; l < a.nl; ++l) {
+    if (a.L[l].nnz == 0) continue;
+    if (l == 1) k_amg_gal1<T><<<amg_blocks(a.L[1].nnz), 128, 0, s>>>(d, a);
+    else k_amg_gal<T><<<amg_blocks(a.L[l].nnz), 128, 0, s>>>(a, l);
+    k_amg_dinv<T><<<amg_blocks(a.L[l].n), 128, 0, s>>>(a, l);
+    k += 2;
+  }
+  if (n_scenes > 0) {
+    k_amg_cfactor<T><<<n_scenes, 64, 0, s>>>(a);
+    ++k;
+  }
+  return k;
+}
+
+int launch_amg_setup(const DevArrays& d, const AmgDev& a, int n_scenes, cudaStream_t s) {
+  if (d.n == 0 || a.nl < 2) return 0;
+  return d.mixed ? amg_setup_t<float>(d, a, n_scenes, s) : amg_setup_t<double>(d, a, n_scenes, s);
+}
+
+template <typename T>
+static int amg_cycle_t(const DevArrays& d, const AmgDev& a, int n_scenes, cudaStream_t s) {
+  int k = 0, top = a.nl - 1;
+  k_amg_smooth0<T><<<amg_blocks(d.n), 128, 0, s>>>(d, a, 0);
+  k_amg_resid0<T><<<amg_blocks(d.n), 128, 0, s>>>(d, a);
+  k_amg_restrict<T><<<amg_blocks(a.L[1].n), 128, 0, s>>>(d, a, 0);
+  k += 3;
+  for (int l = 1; l < top; ++l) {
+    if (a.L[l + 1].n == 0) break;
+    k_amg_level<T><<<amg_blocks(a.L[l].n), 128, 0, s>>>(a, l, 0);
+    k_amg_level<T><<<amg_blocks(a.L[l].n), 128, 0, s>>>(a, l, 1);
+    k_amg_restrict<T><<<amg_blocks(a.L[l + 1].n), 128, 0, s>>>(d, a, l);
+    k += 3;
+  }
+  k_amg_csolve<T><<<n_scenes, 32, 0, s>>>(a);
+  ++k;
+  for (int l = top - 1; l >= 1; --l) {
+    if (a.L[l + 1].n == 0) continue;
+    k_amg_prolong<T><<<amg_blocks(a.L[l].n), 128, 0, s>>>(d, a, l);
+    k_amg_level<T><<<amg_blocks(a.L[l].n), 128, 0, s>>>(a, l, 1);
+    k_amg_level<T><<<amg_blocks(a.L[l].n), 128, 0, s>>>(a, l, 2);
+    k += 3;
+  }
+  k_amg_prolong<T><<<amg_blocks(d.n), 128, 0, s>>>(d, a, 0);
+  k_amg_resid0<T><<<amg_blocks(d.n), 128, 0, s>>>(d, a);
+  k_amg_smooth0<T><<<amg_blocks(d.n), 128, 0, s>>>(d, a, 1);
+  return k + 3;
+}
+
+int launch_amg_cycle(const DevArrays& d, const AmgDev& a, int n_scenes, cudaStream_t s) {
+  if (d.n == 0 || a.nl < 2) return 0;
+  return d.mixed ? amg_cycle_t<float>(d, a, n_scenes, s) : amg_cycle_t<double>(d, a, n_scenes, s);
+}
+
+// ---- PCG with the cycle as preconditioner (textbook form, per-scene state in SceneCtl) ---------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(kTile) k_apcg_vec(DevArrays d, int stage) {
+  int t = blockIdx.x;
+  int i = d.ptile_start[t] + threadIdx.x;
+  int s = d.ptile_scene[t];
+  double acc[1] = {0.0};
+  if (i < d.ptile_start[t + 1]) {
+    SceneCtl& c = d.sc[s];
+    T* X = reinterpret_cast<T*>(d.vx);
+    T* R = reinterpret_cast<T*>(d.vr);
+    T* Z = reinterpret_cast<T*>(d.vz);
+    T* P = reinterpret_cast<T*>(d.vp_);
+    T* Q = reinterpret_cast<T*>(d.vq_);
+    if (stage == 0 || stage == 6) {  // r = b (-g, or the given vr) with kinematic rows zero, x = 0, acc = |b|^2
+      T r[6], x[6] = {0, 0, 0, 0, 0, 0};
+      const double* g = d.g + 6 * (size_t)i;
+      Vec6<T> rv = load6<T>(R, i);
+      bool on = c.newton_active && !d.kin[i];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        double b = on ? (stage == 0 ? -g[k] : (double)rv.v[k]) : 0.0;
+        r[k] = (T)b;
+        acc[0] += (double)r[k] * (double)r[k];
+      }
+      store6<T>(X, i, x);
+      store6<T>(R, i, r);
+    } else if (stage == 1 || stage == 4) {  // acc = r.z
+      DotAcc<T> dot;
+      Vec6<T> r = load6<T>(R, i), z = load6<T>(Z, i);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) dot.add(r.v[k], z.v[k]);
+      acc[0] = dot.value();
+    } else if (stage == 2) {  // acc = p.q
+      DotAcc<T> dot;
+      Vec6<T> p = load6<T>(P, i), q = load6<T>(Q, i);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) dot.add(p.v[k], q.v[k]);
+      acc[0] = dot.value();
+    } else if (stage == 3) {  // x += alpha p, r -= alpha q, acc = |r|^2
+      Vec6<T> r = load6<T>(R, i);
+      if (c.pcg_active) {
+        Vec6<T> x = load6<T>(X, i), p = load6<T>(P, i), q = load6<T>(Q, i);
+        T al = (T)c.alpha;
+        T xo[6], ro[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          xo[k] = x.v[k] + al * p.v[k];
+          ro[k] = r.v[k] - al * q.v[k];
+          r.v[k] = ro[k];
+        }
+        store6<T>(X, i, xo);
+        store6<T>(R, i, ro);
+      }
+      DotAcc<T> dot;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) dot.add(r.v[k], r.v[k]);
+      acc[0] = dot.value();
+    } else if (stage == 5) {  // p = z + beta p (beta = 0 on the first step)
+      if (c.pcg_active) {
+        Vec6<T> z = load6<T>(Z, i), p = load6<T>(P, i);
+        T be = (T)c.beta;
+        T po[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) po[k] = z.v[k] + be * p.v[k];
+        store6<T>(P, i, po);
+      }
+    }
+  }
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) d.part_p[kPartials * t] = acc[0];
+}
+
+// per scene: the tile partials of the last k_apcg_vec in a fixed order, then the stage's scalar update
+__global__ void k_apcg_scene(DevArrays d, int stage) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.n_scenes) return;
+  SceneCtl& c = d.sc[s];
+  double v = 0.0;
+  for (int t = d.ptile_begin[s]; t < d.ptile_begin[s + 1]; ++t) v += d.part_p[kPartials * t];
+  if (stage == 0 || stage == 6) {
+    c.pcg_iters = 0;
+    c.pcg_thr2 = c.eps_r * c.eps_r * v;
+    c.bnorm = sqrt(v);
+    c.pcg_active = c.newton_active && v > c.pcg_thr2;
+    c.beta = 0.0;
+  } else if (stage == 1) {
+    c.rz = v;
+  } else if (stage == 2) {
+    if (c.pcg_active) {
+      if (!(v > 0.0) || !(c.rz > 0.0)) c.pcg_active = 0;  // breakdown
+      else c.alpha = c.rz / v;
+    }
+  } else if (stage == 3) {
+    if (c.pcg_active) {
+      c.pcg_iters += 1;
+      if (!(v > c.pcg_thr2) || c.pcg_iters >= d.pcg_max) c.pcg_active = 0;
+    }
+    if (c.pcg_active) atomicAdd(&d.cnt->n_active, 1);
+  } else if (stage == 4) {
+    if (c.pcg_active) {
+      c.beta = v / c.rz;
+      c.rz = v;
+    }
+  }
+}
+
+int launch_amg_pcg_stage(const DevArrays& d, int stage, cudaStream_t s) {
+  if (d.n == 0) return 0;
+  int k = 0;
+  if (stage != 5) {
+    if (d.mixed) k_apcg_vec<float><<<d.n_ptiles, kTile, 0, s>>>(d, stage);
+    else k_apcg_vec<double><<<d.n_ptiles, kTile, 0, s>>>(d, stage);
+    k_apcg_scene<<<(d.n_scenes + 127) / 128, 128, 0, s>>>(d, stage);
+    k = 2;
+  }
+  if (stage == 1 || stage == 4 || stage == 5) {  // then p = z + beta p
+    if (d.mixed) k_apcg_vec<float><<<d.n_ptiles, kTile, 0, s>>>(d, 5);
+    else k_apcg_vec<double><<<d.n_ptiles, kTile, 0, s>>>(d, 5);
+    ++k;
+  }
+  return k;
+}
+
 }  // namespace bdem
