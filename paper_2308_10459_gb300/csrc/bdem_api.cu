@@ -69,6 +69,11 @@ struct bdem_sim {
   AmgDev amg{};
   int64_t amg_nb = -1;                // bond count the AMG patterns were built for (-1: not built)
   std::vector<void*> amg_allocs;
+  cudaStream_t amg_cap = nullptr;     // capture stream of the AMG-PCG iteration graph
+  cudaGraphExec_t amg_exec = nullptr; // one PCG iteration (product, update, stop test, cycle, direction)
+  DevArrays amg_gd{};                 // the arrays and hierarchy the iteration graph was captured with
+  AmgDev amg_ga{};
+  int amg_gk = 0;                     // kernels per iteration graph
 };
 
 static cudaEvent_t ev_get(bdem_sim* s) {
@@ -1013,6 +1018,7 @@ static bdem_status build_amg(bdem_sim* s) {
   }
   a.L[0].n = s->n;
   TRY(amg_upload(s, &a.L[0].parent, parent[0]));
+  TRY(amg_zeros(s, &a.p0, 12 * wsz * std::max<int32_t>(s->n, 1)));
   TRY(amg_zeros(s, &a.L[0].t, 6 * wsz * std::max<int32_t>(s->n, 1)));
   std::vector<int32_t> lev(S, 0), o(S, 0), m(S, 0);
   for (int sc = 0; sc < S; ++sc)
@@ -1043,17 +1049,49 @@ static bdem_status run_amg_pcg(bdem_sim* s, const DevArrays& d, int from_g) {
   TRY(check_launch(s, launch_amg_pcg_stage(d, from_g ? 0 : 6, st)));
   TRY(check_launch(s, launch_amg_cycle(d, a, s->n_scenes, st)));
   TRY(check_launch(s, launch_amg_pcg_stage(d, 1, st)));
+  // one iteration as one graph launch (captured once per set of arrays): q = H p and alpha, the update and stop
+  // test, then the cycle and the new direction (which change nothing for scenes that have stopped)
+  bool use_graph = true;
+  if (!s->amg_exec || memcmp(&s->amg_gd, &d, sizeof(DevArrays)) != 0 || memcmp(&s->amg_ga, &a, sizeof(AmgDev)) != 0) {
+    if (s->amg_exec) cudaGraphExecDestroy(s->amg_exec);
+    s->amg_exec = nullptr;
+    if (!s->amg_cap && cudaStreamCreateWithFlags(&s->amg_cap, cudaStreamNonBlocking) != cudaSuccess) s->amg_cap = nullptr;
+    cudaGraph_t g = nullptr;
+    int k = 0;
+    if (s->amg_cap && cudaStreamBeginCapture(s->amg_cap, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+      cudaMemsetAsync(&d.cnt->n_active, 0, sizeof(int32_t), s->amg_cap);
+      k += launch_amg_pcg_stage(d, 2, s->amg_cap);
+      k += launch_amg_pcg_stage(d, 3, s->amg_cap);
+      k += launch_amg_cycle(d, a, s->n_scenes, s->amg_cap);
+      k += launch_amg_pcg_stage(d, 4, s->amg_cap);
+      cudaError_t e1 = cudaStreamEndCapture(s->amg_cap, &g);
+      if (e1 == cudaSuccess && g && cudaGraphInstantiate(&s->amg_exec, g, 0) == cudaSuccess) {
+        s->amg_gd = d;
+        s->amg_ga = a;
+        s->amg_gk = k;
+      } else {
+        s->amg_exec = nullptr;
+      }
+      if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();
+    use_graph = s->amg_exec != nullptr;
+  }
   for (int it = 0; it <= d.pcg_max; ++it) {
-    CUDA_TRY(s, cudaMemsetAsync(&d.cnt->n_active, 0, sizeof(int32_t), st));
-    TRY(check_launch(s, launch_matvec(d, 1, st)));
-    TRY(check_launch(s, launch_amg_pcg_stage(d, 2, st)));
-    TRY(check_launch(s, launch_amg_pcg_stage(d, 3, st)));
+    if (use_graph) {
+      CUDA_TRY(s, cudaGraphLaunch(s->amg_exec, st));
+      s->launches += s->amg_gk;
+    } else {
+      CUDA_TRY(s, cudaMemsetAsync(&d.cnt->n_active, 0, sizeof(int32_t), st));
+      TRY(check_launch(s, launch_amg_pcg_stage(d, 2, st)));  // q = H p, then alpha
+      TRY(check_launch(s, launch_amg_pcg_stage(d, 3, st)));
+      TRY(check_launch(s, launch_amg_cycle(d, a, s->n_scenes, st)));
+      TRY(check_launch(s, launch_amg_pcg_stage(d, 4, st)));
+    }
     int32_t act = 0;
     CUDA_TRY(s, cudaMemcpyAsync(&act, &d.cnt->n_active, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     TRY(sync(s));
     if (act == 0) break;
-    TRY(check_launch(s, launch_amg_cycle(d, a, s->n_scenes, st)));
-    TRY(check_launch(s, launch_amg_pcg_stage(d, 4, st)));
   }
   return BDEM_OK;
 }
@@ -1443,6 +1481,8 @@ extern "C" void bdem_destroy(bdem_sim* s) {
   cudaStreamSynchronize(s->stream);
   phase_collect(s);
   destroy_step_graph(s);
+  if (s->amg_exec) cudaGraphExecDestroy(s->amg_exec);
+  if (s->amg_cap) cudaStreamDestroy(s->amg_cap);
   for (cudaStream_t c : s->cap)
     if (c) cudaStreamDestroy(c);
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);

@@ -151,6 +151,7 @@ struct AmgDev {
   double omega;                // damping of the block-Jacobi smoothing
   AmgLevel L[kAmgMaxLevels];   // L[0]: only parent (= level-1 node of each particle) and t are used
   int32_t *sc_level, *sc_off, *sc_m;  // per scene: coarsest level, its first node there, its node count
+  void* p0;                    // [N][12] T per particle: offset from its aggregate's centroid (3), 1/2 R(q)^T (9)
   double* chol;                // [S][kAmgDense^2] dense Cholesky factors of the coarsest operators
 };
 
@@ -207,7 +208,7 @@ int launch_convert(const void* src, int src_double, void* dst, int dst_double, i
 int launch_amg_setup(const DevArrays& d, const AmgDev& a, int n_scenes, cudaStream_t s);
 int launch_amg_cycle(const DevArrays& d, const AmgDev& a, int n_scenes, cudaStream_t s);
 // AMG-preconditioned PCG pieces (per-scene state in SceneCtl): stage 0 r = b = -g (masked), x = 0, |b|^2 -> thr2;
-// 1 gamma = r.z, p = z; 2 alpha from p.q (q = H p); 3 x += alpha p, r -= alpha q, stop test (counts active scenes into
+// 1 gamma = r.z, p = z; 2 q = H p and alpha from p.q; 3 x += alpha p, r -= alpha q, stop test (counts active scenes into
 // cnt->n_active); 4 beta from the new r.z, p = z + beta p
 int launch_amg_pcg_stage(const DevArrays& d, int stage, cudaStream_t s);
 

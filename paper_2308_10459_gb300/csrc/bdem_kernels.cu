@@ -2184,16 +2184,81 @@ __global__ void k_amg_cent(DevArrays d, AmgDev a, int l) {
 
 // the (i, j) block of bond b in (dp_i, y_i) x (dp_j, y_j) from its factored storage: [[-Ah, -Cs], [Bs^T, F]]
 template <typename T>
-__device__ __forceinline__ void amg_bond_block(const DevArrays& d, int b, double H[36]) {
+__device__ __forceinline__ void amg_bond_block(const DevArrays& d, int b, T H[36]) {
   const T* M = reinterpret_cast<const T*>(d.bM) + 36 * (size_t)b;
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      H[6 * r + c] = -(double)M[sidx<3>(r, c)];
-      H[6 * r + 3 + c] = -(double)M[15 + 3 * r + c];
-      H[6 * (3 + r) + c] = (double)M[6 + 3 * c + r];
-      H[6 * (3 + r) + 3 + c] = (double)M[24 + 3 * r + c];
+      H[6 * r + c] = -M[sidx<3>(r, c)];
+      H[6 * r + 3 + c] = -M[15 + 3 * r + c];
+      H[6 * (3 + r) + c] = M[6 + 3 * c + r];
+      H[6 * (3 + r) + 3 + c] = M[24 + 3 * r + c];
+    }
+}
+
+// per particle, once per Newton iteration: offset from the aggregate's centroid and 1/2 R(q)^T
+template <typename T>
+__global__ void k_amg_p0(DevArrays d, AmgDev a) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  int I = a.L[0].parent[i];
+  double4 p = d.xp[i];
+  const double* c = a.L[1].cen + 3 * (size_t)I;
+  double R[9];
+  amg_rot(d.xq[i], R);
+  T* o = reinterpret_cast<T*>(a.p0) + 12 * (size_t)i;
+  o[0] = (T)(p.x - c[0]); o[1] = (T)(p.y - c[1]); o[2] = (T)(p.z - c[2]);
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) o[3 + 3 * r + k] = (T)(0.5 * R[3 * k + r]);  // 1/2 R^T
+}
+
+// the block [[I, -[dv]x], [0, B]] from the stored (dv, B) of a particle (or B = I)
+template <typename T>
+__device__ __forceinline__ void amg_pblock_t(T dx, T dy, T dz, const T* B3, T P[36]) {
+#pragma unroll
+  for (int k = 0; k < 36; ++k) P[k] = (T)0;
+  P[0] = P[7] = P[14] = (T)1;
+  P[4] = dz;  P[5] = -dy;
+  P[9] = -dz; P[11] = dx;
+  P[15] = dy; P[16] = -dx;
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) P[6 * (3 + r) + 3 + c] = B3 ? B3[3 * r + c] : (r == c ? (T)1 : (T)0);
+}
+template <typename T>
+__device__ __forceinline__ void amg_p0_load(const AmgDev& a, int i, T P[36]) {
+  const T* o = reinterpret_cast<const T*>(a.p0) + 12 * (size_t)i;
+  T B[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) B[k] = o[3 + k];
+  amg_pblock_t<T>(o[0], o[1], o[2], B, P);
+}
+
+// acc += P_r^T A P_c in the path's precision
+template <typename T>
+__device__ __forceinline__ void amg_triple_t(const T Pr[36], const T A[36], const T Pc[36], T acc[36]) {
+  T W[36];
+#pragma unroll
+  for (int r = 0; r < 6; ++r)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      T s = 0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) s += A[6 * r + k] * Pc[6 * k + c];
+      W[6 * r + c] = s;
+    }
+#pragma unroll
+  for (int r = 0; r < 6; ++r)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      T s = 0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) s += Pr[6 * k + r] * W[6 * k + c];
+      acc[6 * r + c] += s;
     }
 }
 
@@ -2203,19 +2268,19 @@ __global__ void k_amg_gal1(DevArrays d, AmgDev a) {
   const AmgLevel& L = a.L[1];
   if (e >= L.nnz) return;
   int I = L.erow[e], J = L.col[e];
-  double acc[36];
+  T acc[36];
 #pragma unroll
-  for (int k = 0; k < 36; ++k) acc[k] = 0.0;
-  double Pr[36], Pc[36], H[36];
+  for (int k = 0; k < 36; ++k) acc[k] = (T)0;
+  T Pr[36], Pc[36], H[36];
   if (I == J) {  // the assembled diagonal blocks of the aggregate's particles
     for (int i = L.cbeg[I]; i < L.cend[I]; ++i) {
       const T* Dp = reinterpret_cast<const T*>(d.D) + kDiagStride * (size_t)i;
 #pragma unroll
       for (int r = 0; r < 6; ++r)
 #pragma unroll
-        for (int c = 0; c < 6; ++c) H[6 * r + c] = (double)Dp[sidx<6>(r, c)];
-      amg_p0(d, a, i, Pr);
-      amg_triple(Pr, H, Pr, acc);
+        for (int c = 0; c < 6; ++c) H[6 * r + c] = Dp[sidx<6>(r, c)];
+      amg_p0_load<T>(a, i, Pr);
+      amg_triple_t<T>(Pr, H, Pr, acc);
     }
   }
   for (int k = L.gs[e]; k < L.gs[e + 1]; ++k) {
@@ -2225,23 +2290,23 @@ __global__ void k_amg_gal1(DevArrays d, AmgDev a) {
     if (d.kin[ij.x] || d.kin[ij.y]) continue;  // the kinematic rows and columns of the system are identity
     amg_bond_block<T>(d, b, H);
     if (code & 1) {  // P_j^T H_ij^T P_i
-      double Ht[36];
+      T Ht[36];
 #pragma unroll
       for (int r = 0; r < 6; ++r)
 #pragma unroll
         for (int c = 0; c < 6; ++c) Ht[6 * r + c] = H[6 * c + r];
-      amg_p0(d, a, ij.y, Pr);
-      amg_p0(d, a, ij.x, Pc);
-      amg_triple(Pr, Ht, Pc, acc);
+      amg_p0_load<T>(a, ij.y, Pr);
+      amg_p0_load<T>(a, ij.x, Pc);
+      amg_triple_t<T>(Pr, Ht, Pc, acc);
     } else {
-      amg_p0(d, a, ij.x, Pr);
-      amg_p0(d, a, ij.y, Pc);
-      amg_triple(Pr, H, Pc, acc);
+      amg_p0_load<T>(a, ij.x, Pr);
+      amg_p0_load<T>(a, ij.y, Pc);
+      amg_triple_t<T>(Pr, H, Pc, acc);
     }
   }
   T* o = reinterpret_cast<T*>(L.val) + 36 * (size_t)e;
 #pragma unroll
-  for (int k = 0; k < 36; ++k) o[k] = (T)acc[k];
+  for (int k = 0; k < 36; ++k) o[k] = acc[k];
 }
 
 template <typename T>
@@ -2250,22 +2315,25 @@ __global__ void k_amg_gal(AmgDev a, int l) {  // level l >= 2 from level l - 1
   const AmgLevel& L = a.L[l];
   const AmgLevel& F = a.L[l - 1];
   if (e >= L.nnz) return;
-  double acc[36];
+  T acc[36];
 #pragma unroll
-  for (int k = 0; k < 36; ++k) acc[k] = 0.0;
-  double Pr[36], Pc[36], A[36];
+  for (int k = 0; k < 36; ++k) acc[k] = (T)0;
+  T Pr[36], Pc[36], A[36];
   for (int k = L.gs[e]; k < L.gs[e + 1]; ++k) {
     int f = L.gsrc[k];
     const T* v = reinterpret_cast<const T*>(F.val) + 36 * (size_t)f;
 #pragma unroll
-    for (int t = 0; t < 36; ++t) A[t] = (double)v[t];
-    amg_pl(a, l - 1, F.erow[f], Pr);
-    amg_pl(a, l - 1, F.col[f], Pc);
-    amg_triple(Pr, A, Pc, acc);
+    for (int t = 0; t < 36; ++t) A[t] = v[t];
+    int r = F.erow[f], c = F.col[f];
+    const double *cr = F.cen + 3 * (size_t)r, *cc = F.cen + 3 * (size_t)c;
+    const double *Cr = L.cen + 3 * (size_t)F.parent[r], *Cc = L.cen + 3 * (size_t)F.parent[c];
+    amg_pblock_t<T>((T)(cr[0] - Cr[0]), (T)(cr[1] - Cr[1]), (T)(cr[2] - Cr[2]), nullptr, Pr);
+    amg_pblock_t<T>((T)(cc[0] - Cc[0]), (T)(cc[1] - Cc[1]), (T)(cc[2] - Cc[2]), nullptr, Pc);
+    amg_triple_t<T>(Pr, A, Pc, acc);
   }
   T* o = reinterpret_cast<T*>(L.val) + 36 * (size_t)e;
 #pragma unroll
-  for (int k = 0; k < 36; ++k) o[k] = (T)acc[k];
+  for (int k = 0; k < 36; ++k) o[k] = acc[k];
 }
 
 // inverse of an SPD 6x6 block (FP64 Cholesky; a non-positive pivot falls back to the inverse diagonal)
@@ -2567,7 +2635,82 @@ __global__ void k_amg_prolong(DevArrays d, AmgDev a, int l) {
   amg_store<T>(X, k, x);
 }
 
+// fine-level products with G lanes per row (the lanes split the row's entries, the diagonal block goes to lane 0):
+// mode 0: q = H p (the PCG's product: bonds and active contacts, kinematic rows zero); mode 1: t = r - A_0 x
+// (the cycle's residual: bonds only; kinematic rows t = r - x, x vanishes on them)
+template <typename T, int G>
+__global__ void __launch_bounds__(256) k_amg_fine(DevArrays d, AmgDev a, int mode) {
+  int i = blockIdx.x * (256 / G) + threadIdx.x / G;
+  int sub = threadIdx.x % G;
+  bool valid = i < d.n;
+  const T* X = reinterpret_cast<const T*>(mode ? d.vz : d.vp_);
+  T y[6] = {0, 0, 0, 0, 0, 0};
+  bool kin = valid && d.kin[i];
+  if (valid && !kin) {
+    if (sub == 0) {
+      Vec6<T> xi = load6<T>(X, i);
+      sym6_mul<T>(reinterpret_cast<const T*>(d.D) + kDiagStride * (size_t)i, xi.v, y);
+    }
+    int nbond = d.inc_start[i + 1] - d.inc_start[i];
+    int nent = nbond + ((mode == 0 && d.k_self > 0.0) ? d.c_act[i] : 0);
+    for (int k = sub; k < nent; k += G) row_entry<T, false>(d, i, k, nbond, X, y);
+  }
+#pragma unroll
+  for (int o = G / 2; o >= 1; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) y[k] += __shfl_down_sync(0xffffffffu, y[k], o, G);
+  if (!valid || sub != 0) return;
+  if (mode == 0) {
+    if (kin)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) y[k] = (T)0;
+    store6<T>(reinterpret_cast<T*>(d.vq_), i, y);
+  } else {
+    Vec6<T> r = load6<T>(reinterpret_cast<const T*>(d.vr), i);
+    T t[6];
+    if (kin) {
+      Vec6<T> xi = load6<T>(X, i);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) t[k] = r.v[k] - xi.v[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) t[k] = r.v[k] - y[k];
+    }
+    store6<T>(reinterpret_cast<T*>(a.L[0].t), i, t);
+  }
+}
+
+// coarse-level residual t = r - A x with 8 lanes per row (non-coarsest rows)
+template <typename T>
+__global__ void __launch_bounds__(256) k_amg_cresid(AmgDev a, int l) {
+  constexpr int G = 8;
+  int I = blockIdx.x * (256 / G) + threadIdx.x / G;
+  int sub = threadIdx.x % G;
+  const AmgLevel& L = a.L[l];
+  bool valid = I < L.n && L.parent[I] >= 0;
+  double y[6] = {0, 0, 0, 0, 0, 0};
+  if (valid)
+    for (int e = L.rs[I] + sub; e < L.rs[I + 1]; e += G) {
+      double x[6], z[6];
+      amg_load<T>(L.x, L.col[e], x);
+      amg_mat6<T>(reinterpret_cast<const T*>(L.val) + 36 * (size_t)e, x, z);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) y[k] += z[k];
+    }
+#pragma unroll
+  for (int o = G / 2; o >= 1; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) y[k] += __shfl_down_sync(0xffffffffu, y[k], o, G);
+  if (!valid || sub != 0) return;
+  double r[6];
+  amg_load<T>(L.r, I, r);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) r[k] -= y[k];
+  amg_store<T>(L.t, I, r);
+}
+
 static inline int amg_blocks(int64_t n) { return (int)((n + 127) / 128); }
+static inline int amg_lane_blocks(int64_t n, int g) { return (int)((n * g + 255) / 256); }
 
 template <typename T>
 static int amg_setup_t(const DevArrays& d, const AmgDev& a, int n_scenes, cudaStream_t s) {
@@ -2577,6 +2720,8 @@ static int amg_setup_t(const DevArrays& d, const AmgDev& a, int n_scenes, cudaSt
     k_amg_cent<<<amg_blocks(a.L[l].n), 128, 0, s>>>(d, a, l);
     ++k;
   }
+  k_amg_p0<T><<<amg_blocks(d.n), 128, 0, s>>>(d, a);
+  ++k;
   for (int l = 1; l < a.nl; ++l) {
     if (a.L[l].nnz == 0) continue;
     if (l == 1) k_amg_gal1<T><<<amg_blocks(a.L[1].nnz), 128, 0, s>>>(d, a);
@@ -2600,13 +2745,13 @@ template <typename T>
 static int amg_cycle_t(const DevArrays& d, const AmgDev& a, int n_scenes, cudaStream_t s) {
   int k = 0, top = a.nl - 1;
   k_amg_smooth0<T><<<amg_blocks(d.n), 128, 0, s>>>(d, a, 0);
-  k_amg_resid0<T><<<amg_blocks(d.n), 128, 0, s>>>(d, a);
+  k_amg_fine<T, 4><<<amg_lane_blocks(d.n, 4), 256, 0, s>>>(d, a, 1);
   k_amg_restrict<T><<<amg_blocks(a.L[1].n), 128, 0, s>>>(d, a, 0);
   k += 3;
   for (int l = 1; l < top; ++l) {
     if (a.L[l + 1].n == 0) break;
     k_amg_level<T><<<amg_blocks(a.L[l].n), 128, 0, s>>>(a, l, 0);
-    k_amg_level<T><<<amg_blocks(a.L[l].n), 128, 0, s>>>(a, l, 1);
+    k_amg_cresid<T><<<amg_lane_blocks(a.L[l].n, 8), 256, 0, s>>>(a, l);
     k_amg_restrict<T><<<amg_blocks(a.L[l + 1].n), 128, 0, s>>>(d, a, l);
     k += 3;
   }
@@ -2615,12 +2760,12 @@ static int amg_cycle_t(const DevArrays& d, const AmgDev& a, int n_scenes, cudaSt
   for (int l = top - 1; l >= 1; --l) {
     if (a.L[l + 1].n == 0) continue;
     k_amg_prolong<T><<<amg_blocks(a.L[l].n), 128, 0, s>>>(d, a, l);
-    k_amg_level<T><<<amg_blocks(a.L[l].n), 128, 0, s>>>(a, l, 1);
+    k_amg_cresid<T><<<amg_lane_blocks(a.L[l].n, 8), 256, 0, s>>>(a, l);
     k_amg_level<T><<<amg_blocks(a.L[l].n), 128, 0, s>>>(a, l, 2);
     k += 3;
   }
   k_amg_prolong<T><<<amg_blocks(d.n), 128, 0, s>>>(d, a, 0);
-  k_amg_resid0<T><<<amg_blocks(d.n), 128, 0, s>>>(d, a);
+  k_amg_fine<T, 4><<<amg_lane_blocks(d.n, 4), 256, 0, s>>>(d, a, 1);
   k_amg_smooth0<T><<<amg_blocks(d.n), 128, 0, s>>>(d, a, 1);
   return k + 3;
 }
@@ -2704,13 +2849,16 @@ __global__ void __launch_bounds__(kTile) k_apcg_vec(DevArrays d, int stage) {
   if (threadIdx.x == 0) d.part_p[kPartials * t] = acc[0];
 }
 
-// per scene: the tile partials of the last k_apcg_vec in a fixed order, then the stage's scalar update
+// per scene (one warp): the tile partials of the last k_apcg_vec (lane-strided sums and a fixed shuffle tree, so
+// the order is fixed), then the stage's scalar update
 __global__ void k_apcg_scene(DevArrays d, int stage) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (s >= d.n_scenes) return;
   SceneCtl& c = d.sc[s];
   double v = 0.0;
-  for (int t = d.ptile_begin[s]; t < d.ptile_begin[s + 1]; ++t) v += d.part_p[kPartials * t];
+  for (int t = d.ptile_begin[s] + lane; t < d.ptile_begin[s + 1]; t += 32) v += d.part_p[kPartials * t];
+  v = warp_sum(v);
+  if (lane != 0) return;
   if (stage == 0 || stage == 6) {
     c.pcg_iters = 0;
     c.pcg_thr2 = c.eps_r * c.eps_r * v;
@@ -2741,10 +2889,16 @@ __global__ void k_apcg_scene(DevArrays d, int stage) {
 int launch_amg_pcg_stage(const DevArrays& d, int stage, cudaStream_t s) {
   if (d.n == 0) return 0;
   int k = 0;
+  if (stage == 2) {  // q = H p first
+    AmgDev none{};
+    if (d.mixed) k_amg_fine<float, 4><<<amg_lane_blocks(d.n, 4), 256, 0, s>>>(d, none, 0);
+    else k_amg_fine<double, 4><<<amg_lane_blocks(d.n, 4), 256, 0, s>>>(d, none, 0);
+    ++k;
+  }
   if (stage != 5) {
     if (d.mixed) k_apcg_vec<float><<<d.n_ptiles, kTile, 0, s>>>(d, stage);
     else k_apcg_vec<double><<<d.n_ptiles, kTile, 0, s>>>(d, stage);
-    k_apcg_scene<<<(d.n_scenes + 127) / 128, 128, 0, s>>>(d, stage);
+    k_apcg_scene<<<(d.n_scenes + 3) / 4, 128, 0, s>>>(d, stage);
     k = 2;
   }
   if (stage == 1 || stage == 4 || stage == 5) {  // then p = z + beta p
