@@ -1046,9 +1046,9 @@ static bdem_status run_amg_pcg(bdem_sim* s, const DevArrays& d, int from_g) {
   cudaStream_t st = s->stream;
   if (a.nl < 2 || d.n == 0) return BDEM_OK;
   TRY(check_launch(s, launch_amg_setup(d, a, s->n_scenes, st)));
-  TRY(check_launch(s, launch_amg_pcg_stage(d, from_g ? 0 : 6, st)));
+  TRY(check_launch(s, launch_amg_pcg_stage(d, a, from_g ? 0 : 6, st)));
   TRY(check_launch(s, launch_amg_cycle(d, a, s->n_scenes, st)));
-  TRY(check_launch(s, launch_amg_pcg_stage(d, 1, st)));
+  TRY(check_launch(s, launch_amg_pcg_stage(d, a, 1, st)));
   // one iteration as one graph launch (captured once per set of arrays): q = H p and alpha, the update and stop
   // test, then the cycle and the new direction (which change nothing for scenes that have stopped)
   bool use_graph = true;
@@ -1060,10 +1060,10 @@ static bdem_status run_amg_pcg(bdem_sim* s, const DevArrays& d, int from_g) {
     int k = 0;
     if (s->amg_cap && cudaStreamBeginCapture(s->amg_cap, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
       cudaMemsetAsync(&d.cnt->n_active, 0, sizeof(int32_t), s->amg_cap);
-      k += launch_amg_pcg_stage(d, 2, s->amg_cap);
-      k += launch_amg_pcg_stage(d, 3, s->amg_cap);
+      k += launch_amg_pcg_stage(d, a, 2, s->amg_cap);
+      k += launch_amg_pcg_stage(d, a, 3, s->amg_cap);
       k += launch_amg_cycle(d, a, s->n_scenes, s->amg_cap);
-      k += launch_amg_pcg_stage(d, 4, s->amg_cap);
+      k += launch_amg_pcg_stage(d, a, 4, s->amg_cap);
       cudaError_t e1 = cudaStreamEndCapture(s->amg_cap, &g);
       if (e1 == cudaSuccess && g && cudaGraphInstantiate(&s->amg_exec, g, 0) == cudaSuccess) {
         s->amg_gd = d;
@@ -1083,10 +1083,10 @@ static bdem_status run_amg_pcg(bdem_sim* s, const DevArrays& d, int from_g) {
       s->launches += s->amg_gk;
     } else {
       CUDA_TRY(s, cudaMemsetAsync(&d.cnt->n_active, 0, sizeof(int32_t), st));
-      TRY(check_launch(s, launch_amg_pcg_stage(d, 2, st)));  // q = H p, then alpha
-      TRY(check_launch(s, launch_amg_pcg_stage(d, 3, st)));
+      TRY(check_launch(s, launch_amg_pcg_stage(d, a, 2, st)));  // q = H p, then alpha
+      TRY(check_launch(s, launch_amg_pcg_stage(d, a, 3, st)));
       TRY(check_launch(s, launch_amg_cycle(d, a, s->n_scenes, st)));
-      TRY(check_launch(s, launch_amg_pcg_stage(d, 4, st)));
+      TRY(check_launch(s, launch_amg_pcg_stage(d, a, 4, st)));
     }
     int32_t act = 0;
     CUDA_TRY(s, cudaMemcpyAsync(&act, &d.cnt->n_active, sizeof(int32_t), cudaMemcpyDeviceToHost, st));

@@ -204,12 +204,14 @@ int launch_static_pcg_init(const DevArrays& d, double eps_r, cudaStream_t s);
 int launch_wait_test(const DevArrays& d, cudaStream_t s);  // a bounded wait that always runs out
 int launch_convert(const void* src, int src_double, void* dst, int dst_double, int64_t count, cudaStream_t s);
 // AMG: coarse operators of the current Newton system (centroids, Galerkin products, block inverses, coarsest
-// factors); one V(1,1) cycle z = M^-1 r (r = PCG residual vr, z = vz); PCG steps with the cycle as preconditioner
+// factors); one V(1,1) cycle z = M^-1 r (r = PCG residual vr, z = vz; its level-0 smoothing steps belong to the PCG
+// stages around it: the stages that produce r pre-smooth, the stages that read z post-smooth); PCG steps with the
+// cycle as preconditioner
 int launch_amg_setup(const DevArrays& d, const AmgDev& a, int n_scenes, cudaStream_t s);
 int launch_amg_cycle(const DevArrays& d, const AmgDev& a, int n_scenes, cudaStream_t s);
 // AMG-preconditioned PCG pieces (per-scene state in SceneCtl): stage 0 r = b = -g (masked), x = 0, |b|^2 -> thr2;
 // 1 gamma = r.z, p = z; 2 q = H p and alpha from p.q; 3 x += alpha p, r -= alpha q, stop test (counts active scenes into
 // cnt->n_active); 4 beta from the new r.z, p = z + beta p
-int launch_amg_pcg_stage(const DevArrays& d, int stage, cudaStream_t s);
+int launch_amg_pcg_stage(const DevArrays& d, const AmgDev& a, int stage, cudaStream_t s);
 
 }  // namespace bdem

@@ -2435,7 +2435,9 @@ __global__ void k_amg_cfactor(AmgDev a) {
 // ---- the cycle --------------------------------------------------------------------------------------------------
 
 template <typename T>
-__device__ __forceinline__ void amg_mat6(const T* M, const double (&x)[6], double (&y)[6]) {
+__device__ __forceinline__ void amg_mat6(const T* Mg, const double (&x)[6], double (&y)[6]) {
+  T M[36];
+  load_words<36>(Mg, M);  // 16-byte loads: the blocks start at multiples of 144 (FP32) or 288 (FP64) bytes
 #pragma unroll
   for (int r = 0; r < 6; ++r) {
     double s = 0.0;
@@ -2456,52 +2458,6 @@ __device__ __forceinline__ void amg_store(void* base, int i, const double (&v)[6
   T* p = reinterpret_cast<T*>(base) + 6 * (size_t)i;
 #pragma unroll
   for (int k = 0; k < 6; ++k) p[k] = (T)v[k];
-}
-
-// level 0, mode 0: x = w Dinv r (pre-smoothing); mode 1: x += w Dinv t (post-smoothing); x is the PCG's z
-template <typename T>
-__global__ void k_amg_smooth0(DevArrays d, AmgDev a, int mode) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d.n) return;
-  Vec6<T> r = load6<T>(reinterpret_cast<const T*>(mode ? a.L[0].t : d.vr), i);
-  T y[6];
-  sym6_mul<T>(reinterpret_cast<const T*>(d.Dinv) + kDiagStride * (size_t)i, r.v, y);
-  T out[6];
-  if (mode) {
-    Vec6<T> x = load6<T>(reinterpret_cast<const T*>(d.vz), i);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) out[k] = x.v[k] + (T)a.omega * y[k];
-  } else {
-#pragma unroll
-    for (int k = 0; k < 6; ++k) out[k] = (T)a.omega * y[k];
-  }
-  if (mode && d.kin[i])
-#pragma unroll
-    for (int k = 0; k < 6; ++k) out[k] = (T)0;
-  store6<T>(reinterpret_cast<T*>(d.vz), i, out);
-}
-
-// level 0: t = r - A_0 x, A_0 = diagonal blocks + bond blocks (kinematic rows: t = r - x; x vanishes on them)
-template <typename T>
-__global__ void k_amg_resid0(DevArrays d, AmgDev a) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d.n) return;
-  const T* X = reinterpret_cast<const T*>(d.vz);
-  Vec6<T> r = load6<T>(reinterpret_cast<const T*>(d.vr), i);
-  Vec6<T> xi = load6<T>(X, i);
-  T y[6] = {0, 0, 0, 0, 0, 0};
-  if (d.kin[i]) {
-#pragma unroll
-    for (int k = 0; k < 6; ++k) y[k] = xi.v[k];
-  } else {
-    sym6_mul<T>(reinterpret_cast<const T*>(d.D) + kDiagStride * (size_t)i, xi.v, y);
-    int nbond = d.inc_start[i + 1] - d.inc_start[i];
-    for (int k = 0; k < nbond; ++k) row_entry<T, false>(d, i, k, nbond, X, y);
-  }
-  T t[6];
-#pragma unroll
-  for (int k = 0; k < 6; ++k) t[k] = r.v[k] - y[k];
-  store6<T>(reinterpret_cast<T*>(a.L[0].t), i, t);
 }
 
 // restriction from level l to l + 1: r_{l+1}[I] = sum over the children k of P_k^T t_l[k]
@@ -2536,10 +2492,21 @@ __global__ void k_amg_restrict(DevArrays d, AmgDev a, int l) {
     acc[4] += dv[2] * v[0] - dv[0] * v[2] + v[4];
     acc[5] += dv[0] * v[1] - dv[1] * v[0] + v[5];
   }
+  double racc[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) racc[k] = (double)(T)acc[k];  // the stored residual, as the smoother reads it
   amg_store<T>(C.r, I, acc);
+  if (C.parent[I] >= 0) {  // pre-smoothing of the coarse node: x = w Dinv r
+    double y[6];
+    amg_mat6<T>(reinterpret_cast<const T*>(C.dinv) + 36 * (size_t)I, racc, y);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) y[k] *= a.omega;
+    amg_store<T>(C.x, I, y);
+  }
 }
 
-// level l >= 1, non-coarsest nodes: mode 0 x = w Dinv r; mode 1 t = r - A x; mode 2 x += w Dinv t
+// level l >= 1, non-coarsest nodes: mode 0 x = w Dinv r; mode 1 t = r - A x; mode 2 x += w Dinv t (the cycle uses
+// mode 2; the pre-smoothing is part of the restriction and the residual has its own multi-lane kernel)
 template <typename T>
 __global__ void k_amg_level(AmgDev a, int l, int mode) {
   int I = blockIdx.x * blockDim.x + threadIdx.x;
@@ -2572,29 +2539,36 @@ __global__ void k_amg_level(AmgDev a, int l, int mode) {
   amg_store<T>(L.x, I, y);
 }
 
-// one block per scene: x = A^-1 r on the scene's coarsest level with its Cholesky factor
+// one block of 64 threads per scene: x = A^-1 r on the scene's coarsest level with its Cholesky factor (the
+// factor in shared memory; column-oriented substitutions, one row per thread)
 template <typename T>
 __global__ void k_amg_csolve(AmgDev a) {
   int s = blockIdx.x;
   int l = a.sc_level[s], o = a.sc_off[s], m = a.sc_m[s];
-  if (l <= 0 || m <= 0 || m > kAmgAgg || threadIdx.x != 0) return;
-  int n = 6 * m;
+  if (l <= 0 || m <= 0 || m > kAmgAgg) return;
+  int n = 6 * m, t = threadIdx.x;
+  __shared__ double Ls[kAmgDense * kAmgDense];
+  __shared__ double w[kAmgDense];
   const double* Lc = a.chol + (size_t)kAmgDense * kAmgDense * s;
+  for (int k = t; k < n * n; k += blockDim.x) Ls[k] = Lc[k];
   const AmgLevel& L = a.L[l];
-  double w[kAmgDense], z[kAmgDense];
   const T* R = reinterpret_cast<const T*>(L.r) + 6 * (size_t)o;
-  for (int i = 0; i < n; ++i) {
-    double v = (double)R[i];
-    for (int k = 0; k < i; ++k) v -= Lc[n * i + k] * w[k];
-    w[i] = v / Lc[n * i + i];
+  if (t < n) w[t] = (double)R[t];
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {  // forward: L w = r
+    if (t == 0) w[j] /= Ls[n * j + j];
+    __syncthreads();
+    if (t > j && t < n) w[t] -= Ls[n * t + j] * w[j];
+    __syncthreads();
   }
-  for (int i = n - 1; i >= 0; --i) {
-    double v = w[i];
-    for (int k = i + 1; k < n; ++k) v -= Lc[n * k + i] * z[k];
-    z[i] = v / Lc[n * i + i];
+  for (int j = n - 1; j >= 0; --j) {  // backward: L^T z = w
+    if (t == 0) w[j] /= Ls[n * j + j];
+    __syncthreads();
+    if (t < j) w[t] -= Ls[n * j + t] * w[j];
+    __syncthreads();
   }
   T* X = reinterpret_cast<T*>(L.x) + 6 * (size_t)o;
-  for (int i = 0; i < n; ++i) X[i] = (T)z[i];
+  if (t < n) X[t] = (T)w[t];
 }
 
 // prolongation from level l + 1 to l (nodes whose scene has level l + 1): x_l[k] += P_k e[parent(k)]
@@ -2743,19 +2717,18 @@ int launch_amg_setup(const DevArrays& d, const AmgDev& a, int n_scenes, cudaStre
 
 template <typename T>
 static int amg_cycle_t(const DevArrays& d, const AmgDev& a, int n_scenes, cudaStream_t s) {
+  // the level-0 pre-smoothing (z = w Dinv r) was written by the PCG stage that produced r
   int k = 0, top = a.nl - 1;
-  k_amg_smooth0<T><<<amg_blocks(d.n), 128, 0, s>>>(d, a, 0);
   k_amg_fine<T, 4><<<amg_lane_blocks(d.n, 4), 256, 0, s>>>(d, a, 1);
   k_amg_restrict<T><<<amg_blocks(a.L[1].n), 128, 0, s>>>(d, a, 0);
-  k += 3;
+  k += 2;
   for (int l = 1; l < top; ++l) {
     if (a.L[l + 1].n == 0) break;
-    k_amg_level<T><<<amg_blocks(a.L[l].n), 128, 0, s>>>(a, l, 0);
     k_amg_cresid<T><<<amg_lane_blocks(a.L[l].n, 8), 256, 0, s>>>(a, l);
     k_amg_restrict<T><<<amg_blocks(a.L[l + 1].n), 128, 0, s>>>(d, a, l);
-    k += 3;
+    k += 2;
   }
-  k_amg_csolve<T><<<n_scenes, 32, 0, s>>>(a);
+  k_amg_csolve<T><<<n_scenes, 64, 0, s>>>(a);
   ++k;
   for (int l = top - 1; l >= 1; --l) {
     if (a.L[l + 1].n == 0) continue;
@@ -2766,8 +2739,7 @@ static int amg_cycle_t(const DevArrays& d, const AmgDev& a, int n_scenes, cudaSt
   }
   k_amg_prolong<T><<<amg_blocks(d.n), 128, 0, s>>>(d, a, 0);
   k_amg_fine<T, 4><<<amg_lane_blocks(d.n, 4), 256, 0, s>>>(d, a, 1);
-  k_amg_smooth0<T><<<amg_blocks(d.n), 128, 0, s>>>(d, a, 1);
-  return k + 3;
+  return k + 2;  // the post-smoothing is finished by the PCG stage that reads z
 }
 
 int launch_amg_cycle(const DevArrays& d, const AmgDev& a, int n_scenes, cudaStream_t s) {
@@ -2777,8 +2749,19 @@ int launch_amg_cycle(const DevArrays& d, const AmgDev& a, int n_scenes, cudaStre
 
 // ---- PCG with the cycle as preconditioner (textbook form, per-scene state in SceneCtl) ---------------------------
 
+// w Dinv v (the cycle's level-0 smoothing step) for particle i
 template <typename T>
-__global__ void __launch_bounds__(kTile) k_apcg_vec(DevArrays d, int stage) {
+__device__ __forceinline__ void amg_smooth_row(const DevArrays& d, double omega, int i, const T (&v)[6], T (&y)[6]) {
+  sym6_mul<T>(reinterpret_cast<const T*>(d.Dinv) + kDiagStride * (size_t)i, v, y);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) y[k] = (T)omega * y[k];
+}
+
+// The level-0 smoothing steps of the cycle are done here: the stages that produce a new residual r (0, 6, 3) also
+// write the pre-smoothed z = w Dinv r, and the stages that read the cycle's result (1, 4) first finish it with the
+// post-smoothing z += w Dinv t (t = the cycle's last level-0 residual).
+template <typename T>
+__global__ void __launch_bounds__(kTile) k_apcg_vec(DevArrays d, AmgDev a, int stage) {
   int t = blockIdx.x;
   int i = d.ptile_start[t] + threadIdx.x;
   int s = d.ptile_scene[t];
@@ -2803,11 +2786,21 @@ __global__ void __launch_bounds__(kTile) k_apcg_vec(DevArrays d, int stage) {
       }
       store6<T>(X, i, x);
       store6<T>(R, i, r);
-    } else if (stage == 1 || stage == 4) {  // acc = r.z
+      T z[6];
+      amg_smooth_row<T>(d, a.omega, i, r, z);
+      store6<T>(Z, i, z);
+    } else if (stage == 1 || stage == 4) {  // z += w Dinv t (kinematic rows zero), acc = r.z
       DotAcc<T> dot;
-      Vec6<T> r = load6<T>(R, i), z = load6<T>(Z, i);
+      Vec6<T> r = load6<T>(R, i), z = load6<T>(Z, i), t = load6<T>(reinterpret_cast<const T*>(a.L[0].t), i);
+      T y[6];
+      amg_smooth_row<T>(d, a.omega, i, t.v, y);
+      bool kin = d.kin[i];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) dot.add(r.v[k], z.v[k]);
+      for (int k = 0; k < 6; ++k) {
+        z.v[k] = kin ? (T)0 : z.v[k] + y[k];
+        dot.add(r.v[k], z.v[k]);
+      }
+      store6<T>(Z, i, z.v);
       acc[0] = dot.value();
     } else if (stage == 2) {  // acc = p.q
       DotAcc<T> dot;
@@ -2834,6 +2827,9 @@ __global__ void __launch_bounds__(kTile) k_apcg_vec(DevArrays d, int stage) {
 #pragma unroll
       for (int k = 0; k < 6; ++k) dot.add(r.v[k], r.v[k]);
       acc[0] = dot.value();
+      T z[6];
+      amg_smooth_row<T>(d, a.omega, i, r.v, z);
+      store6<T>(Z, i, z);
     } else if (stage == 5) {  // p = z + beta p (beta = 0 on the first step)
       if (c.pcg_active) {
         Vec6<T> z = load6<T>(Z, i), p = load6<T>(P, i);
@@ -2886,24 +2882,23 @@ __global__ void k_apcg_scene(DevArrays d, int stage) {
   }
 }
 
-int launch_amg_pcg_stage(const DevArrays& d, int stage, cudaStream_t s) {
+int launch_amg_pcg_stage(const DevArrays& d, const AmgDev& a, int stage, cudaStream_t s) {
   if (d.n == 0) return 0;
   int k = 0;
   if (stage == 2) {  // q = H p first
-    AmgDev none{};
-    if (d.mixed) k_amg_fine<float, 4><<<amg_lane_blocks(d.n, 4), 256, 0, s>>>(d, none, 0);
-    else k_amg_fine<double, 4><<<amg_lane_blocks(d.n, 4), 256, 0, s>>>(d, none, 0);
+    if (d.mixed) k_amg_fine<float, 4><<<amg_lane_blocks(d.n, 4), 256, 0, s>>>(d, a, 0);
+    else k_amg_fine<double, 4><<<amg_lane_blocks(d.n, 4), 256, 0, s>>>(d, a, 0);
     ++k;
   }
   if (stage != 5) {
-    if (d.mixed) k_apcg_vec<float><<<d.n_ptiles, kTile, 0, s>>>(d, stage);
-    else k_apcg_vec<double><<<d.n_ptiles, kTile, 0, s>>>(d, stage);
+    if (d.mixed) k_apcg_vec<float><<<d.n_ptiles, kTile, 0, s>>>(d, a, stage);
+    else k_apcg_vec<double><<<d.n_ptiles, kTile, 0, s>>>(d, a, stage);
     k_apcg_scene<<<(d.n_scenes + 3) / 4, 128, 0, s>>>(d, stage);
-    k = 2;
+    k += 2;
   }
   if (stage == 1 || stage == 4 || stage == 5) {  // then p = z + beta p
-    if (d.mixed) k_apcg_vec<float><<<d.n_ptiles, kTile, 0, s>>>(d, 5);
-    else k_apcg_vec<double><<<d.n_ptiles, kTile, 0, s>>>(d, 5);
+    if (d.mixed) k_apcg_vec<float><<<d.n_ptiles, kTile, 0, s>>>(d, a, 5);
+    else k_apcg_vec<double><<<d.n_ptiles, kTile, 0, s>>>(d, a, 5);
     ++k;
   }
   return k;
