@@ -2103,6 +2103,65 @@ __device__ __forceinline__ void amg_rot(double4 q, double R[9]) {
   R[6] = 2 * (x * z - y * w);     R[7] = 2 * (y * z + x * w);     R[8] = 1 - 2 * (x * x + y * y);
 }
 
+// the rigid-motion block of a node at offset dv from its aggregate's centroid: [[I, -[dv]x], [0, B]]; B = 1/2 R(q)^T
+// on level 0 (a world rotation w turns the particle by y = 1/2 R(q)^T w), identity above
+__device__ __forceinline__ void amg_pblock(const double dv[3], const double* B3, double P[36]) {
+#pragma unroll
+  for (int k = 0; k < 36; ++k) P[k] = 0.0;
+  P[0] = P[7] = P[14] = 1.0;
+  P[4] = dv[2];  P[5] = -dv[1];
+  P[9] = -dv[2]; P[11] = dv[0];
+  P[15] = dv[1]; P[16] = -dv[0];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) P[6 * (3 + a) + 3 + b] = B3 ? B3[3 * a + b] : (a == b ? 1.0 : 0.0);
+}
+
+__device__ __forceinline__ void amg_p0(const DevArrays& d, const AmgDev& a, int i, double P[36]) {
+  int I = a.L[0].parent[i];
+  double4 p = d.xp[i];
+  const double* c = a.L[1].cen + 3 * (size_t)I;
+  double dv[3] = {p.x - c[0], p.y - c[1], p.z - c[2]};
+  double R[9], B[9];
+  amg_rot(d.xq[i], R);
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c2 = 0; c2 < 3; ++c2) B[3 * r + c2] = 0.5 * R[3 * c2 + r];
+  amg_pblock(dv, B, P);
+}
+
+__device__ __forceinline__ void amg_pl(const AmgDev& a, int l, int k, double P[36]) {  // node k of level l >= 1
+  int I = a.L[l].parent[k];
+  const double *ck = a.L[l].cen + 3 * (size_t)k, *cI = a.L[l + 1].cen + 3 * (size_t)I;
+  double dv[3] = {ck[0] - cI[0], ck[1] - cI[1], ck[2] - cI[2]};
+  amg_pblock(dv, nullptr, P);
+}
+
+// acc += P_r^T A P_c (all 6x6, A row major)
+__device__ __forceinline__ void amg_triple(const double Pr[36], const double A[36], const double Pc[36], double acc[36]) {
+  double T[36];
+#pragma unroll
+  for (int r = 0; r < 6; ++r)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) s += A[6 * r + k] * Pc[6 * k + c];
+      T[6 * r + c] = s;
+    }
+#pragma unroll
+  for (int r = 0; r < 6; ++r)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) s += Pr[6 * k + r] * T[6 * k + c];
+      acc[6 * r + c] += s;
+    }
+}
+
 __global__ void k_amg_cent(DevArrays d, AmgDev a, int l) {
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   const AmgLevel& L = a.L[l];
@@ -2401,6 +2460,155 @@ __device__ __forceinline__ void amg_store(void* base, int i, const double (&v)[6
   for (int k = 0; k < 6; ++k) p[k] = (T)v[k];
 }
 
+// restriction from level l to l + 1: r_{l+1}[I] = sum over the children k of P_k^T t_l[k]
+// (P^T (v_p, v_y) = (v_p, dv x v_p + B^T v_y))
+template <typename T>
+__global__ void k_amg_restrict(DevArrays d, AmgDev a, int l) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const AmgLevel& C = a.L[l + 1];
+  if (I >= C.n) return;
+  const double* cI = C.cen + 3 * (size_t)I;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int k = C.cbeg[I]; k < C.cend[I]; ++k) {
+    double v[6];
+    amg_load<T>(a.L[l].t, k, v);
+    double ck[3];
+    if (l == 0) {
+      double4 p = d.xp[k];
+      ck[0] = p.x; ck[1] = p.y; ck[2] = p.z;
+      double R[9];
+      amg_rot(d.xq[k], R);  // B^T v_y = 1/2 R v_y
+      double w0 = 0.5 * (R[0] * v[3] + R[1] * v[4] + R[2] * v[5]);
+      double w1 = 0.5 * (R[3] * v[3] + R[4] * v[4] + R[5] * v[5]);
+      double w2 = 0.5 * (R[6] * v[3] + R[7] * v[4] + R[8] * v[5]);
+      v[3] = w0; v[4] = w1; v[5] = w2;
+    } else {
+      const double* c = a.L[l].cen + 3 * (size_t)k;
+      ck[0] = c[0]; ck[1] = c[1]; ck[2] = c[2];
+    }
+    double dv[3] = {ck[0] - cI[0], ck[1] - cI[1], ck[2] - cI[2]};
+    acc[0] += v[0]; acc[1] += v[1]; acc[2] += v[2];
+    acc[3] += dv[1] * v[2] - dv[2] * v[1] + v[3];
+    acc[4] += dv[2] * v[0] - dv[0] * v[2] + v[4];
+    acc[5] += dv[0] * v[1] - dv[1] * v[0] + v[5];
+  }
+  double racc[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) racc[k] = (double)(T)acc[k];  // the stored residual, as the smoother reads it
+  amg_store<T>(C.r, I, acc);
+  if (C.parent[I] >= 0) {  // pre-smoothing of the coarse node: x = w Dinv r
+    double y[6];
+    amg_mat6<T>(reinterpret_cast<const T*>(C.dinv) + 36 * (size_t)I, racc, y);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) y[k] *= a.omega;
+    amg_store<T>(C.x, I, y);
+  }
+}
+
+// level l >= 1, non-coarsest nodes: mode 0 x = w Dinv r; mode 1 t = r - A x; mode 2 x += w Dinv t (the cycle uses
+// mode 2; the pre-smoothing is part of the restriction and the residual has its own multi-lane kernel)
+template <typename T>
+__global__ void k_amg_level(AmgDev a, int l, int mode) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const AmgLevel& L = a.L[l];
+  if (I >= L.n || L.parent[I] < 0) return;
+  double r[6], y[6];
+  if (mode == 1) {
+    amg_load<T>(L.r, I, r);
+    for (int e = L.rs[I]; e < L.rs[I + 1]; ++e) {
+      double x[6];
+      amg_load<T>(L.x, L.col[e], x);
+      amg_mat6<T>(reinterpret_cast<const T*>(L.val) + 36 * (size_t)e, x, y);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) r[k] -= y[k];
+    }
+    amg_store<T>(L.t, I, r);
+    return;
+  }
+  amg_load<T>(mode ? L.t : L.r, I, r);
+  amg_mat6<T>(reinterpret_cast<const T*>(L.dinv) + 36 * (size_t)I, r, y);
+  if (mode) {
+    double x[6];
+    amg_load<T>(L.x, I, x);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) y[k] = x[k] + a.omega * y[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) y[k] = a.omega * y[k];
+  }
+  amg_store<T>(L.x, I, y);
+}
+
+// one block of 64 threads per scene: x = A^-1 r on the scene's coarsest level with its Cholesky factor (the
+// factor in shared memory; column-oriented substitutions, one row per thread)
+template <typename T>
+__global__ void k_amg_csolve(AmgDev a) {
+  int s = blockIdx.x;
+  int l = a.sc_level[s], o = a.sc_off[s], m = a.sc_m[s];
+  if (l <= 0 || m <= 0 || m > kAmgAgg) return;
+  int n = 6 * m, t = threadIdx.x;
+  __shared__ double Ls[kAmgDense * kAmgDense];
+  __shared__ double w[kAmgDense];
+  const double* Lc = a.chol + (size_t)kAmgDense * kAmgDense * s;
+  for (int k = t; k < n * n; k += blockDim.x) Ls[k] = Lc[k];
+  const AmgLevel& L = a.L[l];
+  const T* R = reinterpret_cast<const T*>(L.r) + 6 * (size_t)o;
+  if (t < n) w[t] = (double)R[t];
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {  // forward: L w = r
+    if (t == 0) w[j] /= Ls[n * j + j];
+    __syncthreads();
+    if (t > j && t < n) w[t] -= Ls[n * t + j] * w[j];
+    __syncthreads();
+  }
+  for (int j = n - 1; j >= 0; --j) {  // backward: L^T z = w
+    if (t == 0) w[j] /= Ls[n * j + j];
+    __syncthreads();
+    if (t < j) w[t] -= Ls[n * j + t] * w[j];
+    __syncthreads();
+  }
+  T* X = reinterpret_cast<T*>(L.x) + 6 * (size_t)o;
+  if (t < n) X[t] = (T)w[t];
+}
+
+// prolongation from level l + 1 to l (nodes whose scene has level l + 1): x_l[k] += P_k e[parent(k)]
+// (P (t, w) = (t + w x dv, B w)); on level 0 the result goes to the PCG's z, kinematic rows kept at zero
+template <typename T>
+__global__ void k_amg_prolong(DevArrays d, AmgDev a, int l) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  int n = l == 0 ? d.n : a.L[l].n;
+  if (k >= n) return;
+  int I = a.L[l].parent[k];
+  if (I < 0) return;
+  double e[6], x[6];
+  amg_load<T>(a.L[l + 1].x, I, e);
+  const double* cI = a.L[l + 1].cen + 3 * (size_t)I;
+  double ck[3], wv[3] = {e[3], e[4], e[5]};
+  void* X = l == 0 ? d.vz : a.L[l].x;
+  amg_load<T>(X, k, x);
+  if (l == 0) {
+    double4 p = d.xp[k];
+    ck[0] = p.x; ck[1] = p.y; ck[2] = p.z;
+    double R[9];
+    amg_rot(d.xq[k], R);  // B w = 1/2 R^T w
+    wv[0] = 0.5 * (R[0] * e[3] + R[3] * e[4] + R[6] * e[5]);
+    wv[1] = 0.5 * (R[1] * e[3] + R[4] * e[4] + R[7] * e[5]);
+    wv[2] = 0.5 * (R[2] * e[3] + R[5] * e[4] + R[8] * e[5]);
+  } else {
+    const double* c = a.L[l].cen + 3 * (size_t)k;
+    ck[0] = c[0]; ck[1] = c[1]; ck[2] = c[2];
+  }
+  double dv[3] = {ck[0] - cI[0], ck[1] - cI[1], ck[2] - cI[2]};
+  x[0] += e[0] + e[4] * dv[2] - e[5] * dv[1];
+  x[1] += e[1] + e[5] * dv[0] - e[3] * dv[2];
+  x[2] += e[2] + e[3] * dv[1] - e[4] * dv[0];
+  x[3] += wv[0]; x[4] += wv[1]; x[5] += wv[2];
+  if (l == 0 && d.kin[k])
+#pragma unroll
+    for (int t = 0; t < 6; ++t) x[t] = 0.0;
+  amg_store<T>(X, k, x);
+}
+
 // fine-level products with G lanes per row (the lanes split the row's entries, the diagonal block goes to lane 0):
 // mode 0: q = H p (the PCG's product: bonds and active contacts, kinematic rows zero); mode 1: t = r - A_0 x
 // (the cycle's residual: bonds only; kinematic rows t = r - x, x vanishes on them)
@@ -2446,219 +2654,40 @@ __global__ void __launch_bounds__(256) k_amg_fine(DevArrays d, AmgDev a, int mod
   }
 }
 
-
-// ---- fused cycle kernels: one kernel per level on the way down and one on the way up -----------------------------
-
-// P_c^T t of a child: (t_p, dv x t_p + B^T t_y)
-__device__ __forceinline__ void amg_restrict_one(const double dv[3], const double* B3, const double t[6], double o[6]) {
-  double wy[3] = {t[3], t[4], t[5]};
-  if (B3) {
-#pragma unroll
-    for (int r = 0; r < 3; ++r) wy[r] = B3[r] * t[3] + B3[3 + r] * t[4] + B3[6 + r] * t[5];  // B^T t_y
-  }
-  o[0] = t[0]; o[1] = t[1]; o[2] = t[2];
-  o[3] = dv[1] * t[2] - dv[2] * t[1] + wy[0];
-  o[4] = dv[2] * t[0] - dv[0] * t[2] + wy[1];
-  o[5] = dv[0] * t[1] - dv[1] * t[0] + wy[2];
-}
-// P_c e: (t + w x dv, B w)
-__device__ __forceinline__ void amg_prolong_one(const double dv[3], const double* B3, const double e[6], double o[6]) {
-  o[0] = e[0] + e[4] * dv[2] - e[5] * dv[1];
-  o[1] = e[1] + e[5] * dv[0] - e[3] * dv[2];
-  o[2] = e[2] + e[3] * dv[1] - e[4] * dv[0];
-  if (B3) {
-#pragma unroll
-    for (int r = 0; r < 3; ++r) o[3 + r] = B3[3 * r] * e[3] + B3[3 * r + 1] * e[4] + B3[3 * r + 2] * e[5];
-  } else {
-    o[3] = e[3]; o[4] = e[4]; o[5] = e[5];
-  }
-}
-// the (dv, B) of child c of level l (level 0: the stored particle blocks; above: centroid offsets, B = I)
+// coarse-level residual t = r - A x with 8 lanes per row (non-coarsest rows), in the path's precision (the coarse
+// operators are stored in it; FP64 arithmetic here would make the mixed path's coarse levels FP64-bound)
 template <typename T>
-__device__ __forceinline__ bool amg_child(const AmgDev& a, int l, int c, int I, double dv[3], double B[9]) {
-  if (l == 0) {
-    const T* o = reinterpret_cast<const T*>(a.p0) + 12 * (size_t)c;
-    dv[0] = (double)o[0]; dv[1] = (double)o[1]; dv[2] = (double)o[2];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) B[k] = (double)o[3 + k];
-    return true;
-  }
-  const double *cc = a.L[l].cen + 3 * (size_t)c, *cI = a.L[l + 1].cen + 3 * (size_t)I;
-  dv[0] = cc[0] - cI[0]; dv[1] = cc[1] - cI[1]; dv[2] = cc[2] - cI[2];
-  return false;
-}
-
-// down-sweep from level l to l + 1, one warp per node I of level l + 1 (8 children x 4 lanes): the children's
-// residuals t = r - A x (level 0: the fine operator A_0; above: the coarse CSR), the restriction r_{l+1}[I] =
-// sum_c P_c^T t_c, and the pre-smoothing x_{l+1}[I] = w Dinv r_{l+1}[I] when I is not its scene's coarsest node
-template <typename T>
-__global__ void __launch_bounds__(256) k_amg_down(DevArrays d, AmgDev a, int l) {
-  int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31, slot = lane >> 2, sub = lane & 3;
-  const AmgLevel& C = a.L[l + 1];
-  if (I >= C.n) return;  // whole warps
-  int c = C.cbeg[I] + slot;
-  bool has = c < C.cend[I];
-  double t[6] = {0, 0, 0, 0, 0, 0};
-  if (l == 0) {
-    T y[6] = {0, 0, 0, 0, 0, 0};
-    const T* X = reinterpret_cast<const T*>(d.vz);
-    bool kin = has && d.kin[c];
-    if (has && !kin) {
-      if (sub == 0) {
-        Vec6<T> xi = load6<T>(X, c);
-        sym6_mul<T>(reinterpret_cast<const T*>(d.D) + kDiagStride * (size_t)c, xi.v, y);
-      }
-      int nbond = d.inc_start[c + 1] - d.inc_start[c];
-      for (int k = sub; k < nbond; k += 4) row_entry<T, false>(d, c, k, nbond, X, y);
-    }
-#pragma unroll
-    for (int k = 0; k < 6; ++k) t[k] = (double)y[k];
-    if (kin && sub == 0) {  // kinematic rows: t = r - x
-      Vec6<T> xi = load6<T>(X, c);
-#pragma unroll
-      for (int k = 0; k < 6; ++k) t[k] = (double)xi.v[k];
-    }
-  } else {
-    const AmgLevel& L = a.L[l];
-    if (has)
-      for (int e = L.rs[c] + sub; e < L.rs[c + 1]; e += 4) {
-        double x[6], z[6];
-        amg_load<T>(L.x, L.col[e], x);
-        amg_mat6<T>(reinterpret_cast<const T*>(L.val) + 36 * (size_t)e, x, z);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) t[k] += z[k];
-      }
-  }
-#pragma unroll
-  for (int o = 2; o >= 1; o >>= 1)
-#pragma unroll
-    for (int k = 0; k < 6; ++k) t[k] += __shfl_down_sync(0xffffffffu, t[k], o, 4);
-  double rc[6] = {0, 0, 0, 0, 0, 0};
-  if (has && sub == 0) {
-    double r[6], tt[6], dv[3], B[9];
-    if (l == 0) {  // the fine residual in the path's precision, as the fine kernels form it
-      Vec6<T> rv = load6<T>(reinterpret_cast<const T*>(d.vr), c);
-#pragma unroll
-      for (int k = 0; k < 6; ++k) tt[k] = (double)(T)(rv.v[k] - (T)t[k]);
-    } else {
-      amg_load<T>(a.L[l].r, c, r);
-#pragma unroll
-      for (int k = 0; k < 6; ++k) tt[k] = (double)(T)(r[k] - t[k]);
-    }
-    bool b0 = amg_child<T>(a, l, c, I, dv, B);
-    amg_restrict_one(dv, b0 ? B : nullptr, tt, rc);
-  }
-#pragma unroll
-  for (int o = 4; o <= 16; o <<= 1)
-#pragma unroll
-    for (int k = 0; k < 6; ++k) rc[k] += __shfl_xor_sync(0xffffffffu, rc[k], o);
-  if (lane != 0) return;
-  double racc[6];
-#pragma unroll
-  for (int k = 0; k < 6; ++k) racc[k] = (double)(T)rc[k];
-  amg_store<T>(C.r, I, rc);
-  if (C.parent[I] >= 0) {
-    double y[6];
-    amg_mat6<T>(reinterpret_cast<const T*>(C.dinv) + 36 * (size_t)I, racc, y);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) y[k] *= a.omega;
-    amg_store<T>(C.x, I, y);
-  }
-}
-
-// prolongation of a final coarse value e of node I (level l + 1) into its children on level l (level 0: the
-// PCG's z, kinematic rows kept at zero); lane k of the caller handles child cbeg + k
-template <typename T>
-__device__ __forceinline__ void amg_prolong_into(const DevArrays& d, const AmgDev& a, int l, int I, int k,
-                                                 const double e[6]) {
-  const AmgLevel& C = a.L[l + 1];
-  int c = C.cbeg[I] + k;
-  if (c >= C.cend[I]) return;
-  double dv[3], B[9], v[6], x[6];
-  bool b0 = amg_child<T>(a, l, c, I, dv, B);
-  amg_prolong_one(dv, b0 ? B : nullptr, e, v);
-  void* X = l == 0 ? d.vz : a.L[l].x;
-  amg_load<T>(X, c, x);
-#pragma unroll
-  for (int t = 0; t < 6; ++t) x[t] += v[t];
-  if (l == 0 && d.kin[c])
-#pragma unroll
-    for (int t = 0; t < 6; ++t) x[t] = 0.0;
-  amg_store<T>(X, c, x);
-}
-
-// up-sweep on level l >= 1 (non-coarsest nodes, 8 lanes per node): t = r - A x with x already holding the
-// prolongation from above, the post-smoothed value x + w Dinv t (kept in the node's t slot, so that neighbours
-// still read the x the residual needs), and its prolongation into the node's children on level l - 1
-template <typename T>
-__global__ void __launch_bounds__(256) k_amg_up(DevArrays d, AmgDev a, int l) {
+__global__ void __launch_bounds__(256) k_amg_cresid(AmgDev a, int l) {
   constexpr int G = 8;
   int I = blockIdx.x * (256 / G) + threadIdx.x / G;
   int sub = threadIdx.x % G;
   const AmgLevel& L = a.L[l];
   bool valid = I < L.n && L.parent[I] >= 0;
-  double y[6] = {0, 0, 0, 0, 0, 0};
+  T y[6] = {0, 0, 0, 0, 0, 0};
+  const T* X = reinterpret_cast<const T*>(L.x);
   if (valid)
     for (int e = L.rs[I] + sub; e < L.rs[I + 1]; e += G) {
-      double x[6], z[6];
-      amg_load<T>(L.x, L.col[e], x);
-      amg_mat6<T>(reinterpret_cast<const T*>(L.val) + 36 * (size_t)e, x, z);
+      Vec6<T> x = load6<T>(X, L.col[e]);
+      T M[36];
+      load_words<36>(reinterpret_cast<const T*>(L.val) + 36 * (size_t)e, M);
 #pragma unroll
-      for (int k = 0; k < 6; ++k) y[k] += z[k];
+      for (int r = 0; r < 6; ++r) {
+        T s = y[r];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) s += M[6 * r + c] * x.v[c];
+        y[r] = s;
+      }
     }
 #pragma unroll
   for (int o = G / 2; o >= 1; o >>= 1)
 #pragma unroll
-    for (int k = 0; k < 6; ++k) y[k] += __shfl_xor_sync(0xffffffffu, y[k], o, G);
-  if (!valid) return;
-  double r[6], x[6], tt[6], z[6], e[6];
-  amg_load<T>(L.r, I, r);
-  amg_load<T>(L.x, I, x);
+    for (int k = 0; k < 6; ++k) y[k] += __shfl_down_sync(0xffffffffu, y[k], o, G);
+  if (!valid || sub != 0) return;
+  Vec6<T> r = load6<T>(reinterpret_cast<const T*>(L.r), I);
+  T t[6];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) tt[k] = (double)(T)(r[k] - y[k]);
-  amg_mat6<T>(reinterpret_cast<const T*>(L.dinv) + 36 * (size_t)I, tt, z);
-#pragma unroll
-  for (int k = 0; k < 6; ++k) e[k] = (double)(T)(x[k] + a.omega * z[k]);
-  amg_prolong_into<T>(d, a, l - 1, I, sub, e);
-}
-
-// one block of 64 threads per scene: x = A^-1 r on the scene's coarsest level (Cholesky factor in shared memory,
-// row-parallel substitutions), then its prolongation into the children one level down
-template <typename T>
-__global__ void k_amg_csolve_prolong(DevArrays d, AmgDev a) {
-  int s = blockIdx.x;
-  int l = a.sc_level[s], o = a.sc_off[s], m = a.sc_m[s];
-  if (l <= 0 || m <= 0 || m > kAmgAgg) return;
-  int n = 6 * m, t = threadIdx.x;
-  __shared__ double Ls[kAmgDense * kAmgDense];
-  __shared__ double w[kAmgDense];
-  const double* Lc = a.chol + (size_t)kAmgDense * kAmgDense * s;
-  for (int k = t; k < n * n; k += blockDim.x) Ls[k] = Lc[k];
-  const AmgLevel& L = a.L[l];
-  const T* R = reinterpret_cast<const T*>(L.r) + 6 * (size_t)o;
-  if (t < n) w[t] = (double)R[t];
-  __syncthreads();
-  for (int j = 0; j < n; ++j) {
-    if (t == 0) w[j] /= Ls[n * j + j];
-    __syncthreads();
-    if (t > j && t < n) w[t] -= Ls[n * t + j] * w[j];
-    __syncthreads();
-  }
-  for (int j = n - 1; j >= 0; --j) {
-    if (t == 0) w[j] /= Ls[n * j + j];
-    __syncthreads();
-    if (t < j) w[t] -= Ls[n * j + t] * w[j];
-    __syncthreads();
-  }
-  // thread t: node t / 8 of the scene's coarsest level, child t % 8
-  int nd = t / kAmgAgg;
-  if (nd < m) {
-    double e[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) e[k] = (double)(T)w[6 * nd + k];
-    amg_prolong_into<T>(d, a, l - 1, o + nd, t % kAmgAgg, e);
-  }
+  for (int k = 0; k < 6; ++k) t[k] = r.v[k] - y[k];
+  store6<T>(reinterpret_cast<T*>(L.t), I, t);
 }
 
 static inline int amg_blocks(int64_t n) { return (int)((n + 127) / 128); }
@@ -2697,20 +2726,27 @@ template <typename T>
 static int amg_cycle_t(const DevArrays& d, const AmgDev& a, int n_scenes, cudaStream_t s) {
   // the level-0 pre-smoothing (z = w Dinv r) was written by the PCG stage that produced r
   int k = 0, top = a.nl - 1;
-  for (int l = 0; l < top; ++l) {  // residual, restriction and coarse pre-smoothing, one level per kernel
-    if (a.L[l + 1].n == 0) break;
-    k_amg_down<T><<<(int)(((int64_t)a.L[l + 1].n * 32 + 255) / 256), 256, 0, s>>>(d, a, l);
-    ++k;
-  }
-  k_amg_csolve_prolong<T><<<n_scenes, 64, 0, s>>>(d, a);
-  ++k;
-  for (int l = top - 1; l >= 1; --l) {  // residual, post-smoothing and prolongation, one level per kernel
-    if (a.L[l].n == 0) continue;
-    k_amg_up<T><<<amg_lane_blocks(a.L[l].n, 8), 256, 0, s>>>(d, a, l);
-    ++k;
-  }
   k_amg_fine<T, 4><<<amg_lane_blocks(d.n, 4), 256, 0, s>>>(d, a, 1);
-  return k + 1;  // the post-smoothing is finished by the PCG stage that reads z
+  k_amg_restrict<T><<<amg_blocks(a.L[1].n), 128, 0, s>>>(d, a, 0);
+  k += 2;
+  for (int l = 1; l < top; ++l) {
+    if (a.L[l + 1].n == 0) break;
+    k_amg_cresid<T><<<amg_lane_blocks(a.L[l].n, 8), 256, 0, s>>>(a, l);
+    k_amg_restrict<T><<<amg_blocks(a.L[l + 1].n), 128, 0, s>>>(d, a, l);
+    k += 2;
+  }
+  k_amg_csolve<T><<<n_scenes, 64, 0, s>>>(a);
+  ++k;
+  for (int l = top - 1; l >= 1; --l) {
+    if (a.L[l + 1].n == 0) continue;
+    k_amg_prolong<T><<<amg_blocks(a.L[l].n), 128, 0, s>>>(d, a, l);
+    k_amg_cresid<T><<<amg_lane_blocks(a.L[l].n, 8), 256, 0, s>>>(a, l);
+    k_amg_level<T><<<amg_blocks(a.L[l].n), 128, 0, s>>>(a, l, 2);
+    k += 3;
+  }
+  k_amg_prolong<T><<<amg_blocks(d.n), 128, 0, s>>>(d, a, 0);
+  k_amg_fine<T, 4><<<amg_lane_blocks(d.n, 4), 256, 0, s>>>(d, a, 1);
+  return k + 2;  // the post-smoothing is finished by the PCG stage that reads z
 }
 
 int launch_amg_cycle(const DevArrays& d, const AmgDev& a, int n_scenes, cudaStream_t s) {
