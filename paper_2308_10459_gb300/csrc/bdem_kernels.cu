@@ -2461,47 +2461,53 @@ __device__ __forceinline__ void amg_store(void* base, int i, const double (&v)[6
 }
 
 // restriction from level l to l + 1: r_{l+1}[I] = sum over the children k of P_k^T t_l[k]
-// (P^T (v_p, v_y) = (v_p, dv x v_p + B^T v_y))
+// (P^T (v_p, v_y) = (v_p, dv x v_p + B^T v_y)), one lane per child (8 per coarse node), in the path's precision;
+// then the coarse node's pre-smoothing x = w Dinv r when it is not its scene's coarsest node
 template <typename T>
-__global__ void k_amg_restrict(DevArrays d, AmgDev a, int l) {
-  int I = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_amg_restrict(DevArrays d, AmgDev a, int l) {
+  constexpr int G = kAmgAgg;
+  int I = blockIdx.x * (256 / G) + threadIdx.x / G, sub = threadIdx.x % G;
   const AmgLevel& C = a.L[l + 1];
-  if (I >= C.n) return;
-  const double* cI = C.cen + 3 * (size_t)I;
-  double acc[6] = {0, 0, 0, 0, 0, 0};
-  for (int k = C.cbeg[I]; k < C.cend[I]; ++k) {
-    double v[6];
-    amg_load<T>(a.L[l].t, k, v);
-    double ck[3];
-    if (l == 0) {
-      double4 p = d.xp[k];
-      ck[0] = p.x; ck[1] = p.y; ck[2] = p.z;
-      double R[9];
-      amg_rot(d.xq[k], R);  // B^T v_y = 1/2 R v_y
-      double w0 = 0.5 * (R[0] * v[3] + R[1] * v[4] + R[2] * v[5]);
-      double w1 = 0.5 * (R[3] * v[3] + R[4] * v[4] + R[5] * v[5]);
-      double w2 = 0.5 * (R[6] * v[3] + R[7] * v[4] + R[8] * v[5]);
-      v[3] = w0; v[4] = w1; v[5] = w2;
-    } else {
-      const double* c = a.L[l].cen + 3 * (size_t)k;
-      ck[0] = c[0]; ck[1] = c[1]; ck[2] = c[2];
+  bool valid = I < C.n;
+  T acc[6] = {0, 0, 0, 0, 0, 0};
+  if (valid) {
+    int k = C.cbeg[I] + sub;
+    if (k < C.cend[I]) {
+      Vec6<T> v = load6<T>(reinterpret_cast<const T*>(a.L[l].t), k);
+      T dv[3], w[3];
+      if (l == 0) {  // the particle's stored offset and B = 1/2 R(q)^T: B^T v_y
+        const T* o = reinterpret_cast<const T*>(a.p0) + 12 * (size_t)k;
+        dv[0] = o[0]; dv[1] = o[1]; dv[2] = o[2];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) w[r] = o[3 + r] * v.v[3] + o[6 + r] * v.v[4] + o[9 + r] * v.v[5];
+      } else {
+        const double *ck = a.L[l].cen + 3 * (size_t)k, *cI = C.cen + 3 * (size_t)I;
+        dv[0] = (T)(ck[0] - cI[0]); dv[1] = (T)(ck[1] - cI[1]); dv[2] = (T)(ck[2] - cI[2]);
+        w[0] = v.v[3]; w[1] = v.v[4]; w[2] = v.v[5];
+      }
+      acc[0] = v.v[0]; acc[1] = v.v[1]; acc[2] = v.v[2];
+      acc[3] = dv[1] * v.v[2] - dv[2] * v.v[1] + w[0];
+      acc[4] = dv[2] * v.v[0] - dv[0] * v.v[2] + w[1];
+      acc[5] = dv[0] * v.v[1] - dv[1] * v.v[0] + w[2];
     }
-    double dv[3] = {ck[0] - cI[0], ck[1] - cI[1], ck[2] - cI[2]};
-    acc[0] += v[0]; acc[1] += v[1]; acc[2] += v[2];
-    acc[3] += dv[1] * v[2] - dv[2] * v[1] + v[3];
-    acc[4] += dv[2] * v[0] - dv[0] * v[2] + v[4];
-    acc[5] += dv[0] * v[1] - dv[1] * v[0] + v[5];
   }
-  double racc[6];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) racc[k] = (double)(T)acc[k];  // the stored residual, as the smoother reads it
-  amg_store<T>(C.r, I, acc);
-  if (C.parent[I] >= 0) {  // pre-smoothing of the coarse node: x = w Dinv r
-    double y[6];
-    amg_mat6<T>(reinterpret_cast<const T*>(C.dinv) + 36 * (size_t)I, racc, y);
+  for (int o = G / 2; o >= 1; o >>= 1)
 #pragma unroll
-    for (int k = 0; k < 6; ++k) y[k] *= a.omega;
-    amg_store<T>(C.x, I, y);
+    for (int k = 0; k < 6; ++k) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o, G);
+  if (!valid || sub != 0) return;
+  store6<T>(reinterpret_cast<T*>(C.r), I, acc);
+  if (C.parent[I] >= 0) {
+    T M[36], y[6];
+    load_words<36>(reinterpret_cast<const T*>(C.dinv) + 36 * (size_t)I, M);
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+      T sum = 0;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) sum += M[6 * r + c] * acc[c];
+      y[r] = (T)a.omega * sum;
+    }
+    store6<T>(reinterpret_cast<T*>(C.x), I, y);
   }
 }
 
@@ -2539,8 +2545,8 @@ __global__ void k_amg_level(AmgDev a, int l, int mode) {
   amg_store<T>(L.x, I, y);
 }
 
-// one block of 64 threads per scene: x = A^-1 r on the scene's coarsest level with its Cholesky factor (the
-// factor in shared memory; column-oriented substitutions, one row per thread)
+// one warp per scene: x = A^-1 r on the scene's coarsest level with its Cholesky factor (in shared memory); lane t
+// owns rows t and t + 32, the substitutions broadcast each solved entry with a shuffle
 template <typename T>
 __global__ void k_amg_csolve(AmgDev a) {
   int s = blockIdx.x;
@@ -2548,27 +2554,27 @@ __global__ void k_amg_csolve(AmgDev a) {
   if (l <= 0 || m <= 0 || m > kAmgAgg) return;
   int n = 6 * m, t = threadIdx.x;
   __shared__ double Ls[kAmgDense * kAmgDense];
-  __shared__ double w[kAmgDense];
   const double* Lc = a.chol + (size_t)kAmgDense * kAmgDense * s;
-  for (int k = t; k < n * n; k += blockDim.x) Ls[k] = Lc[k];
+  for (int k = t; k < n * n; k += 32) Ls[k] = Lc[k];
   const AmgLevel& L = a.L[l];
   const T* R = reinterpret_cast<const T*>(L.r) + 6 * (size_t)o;
-  if (t < n) w[t] = (double)R[t];
-  __syncthreads();
+  double w0 = t < n ? (double)R[t] : 0.0, w1 = t + 32 < n ? (double)R[t + 32] : 0.0;
+  __syncwarp();
   for (int j = 0; j < n; ++j) {  // forward: L w = r
-    if (t == 0) w[j] /= Ls[n * j + j];
-    __syncthreads();
-    if (t > j && t < n) w[t] -= Ls[n * t + j] * w[j];
-    __syncthreads();
+    double wj = __shfl_sync(0xffffffffu, j < 32 ? w0 : w1, j & 31) / Ls[n * j + j];
+    if (t == (j & 31)) { if (j < 32) w0 = wj; else w1 = wj; }
+    if (t > j && t < n) w0 -= Ls[n * t + j] * wj;
+    if (t + 32 > j && t + 32 < n) w1 -= Ls[n * (t + 32) + j] * wj;
   }
   for (int j = n - 1; j >= 0; --j) {  // backward: L^T z = w
-    if (t == 0) w[j] /= Ls[n * j + j];
-    __syncthreads();
-    if (t < j) w[t] -= Ls[n * j + t] * w[j];
-    __syncthreads();
+    double wj = __shfl_sync(0xffffffffu, j < 32 ? w0 : w1, j & 31) / Ls[n * j + j];
+    if (t == (j & 31)) { if (j < 32) w0 = wj; else w1 = wj; }
+    if (t < j) w0 -= Ls[n * j + t] * wj;
+    if (t + 32 < j) w1 -= Ls[n * j + t + 32] * wj;
   }
   T* X = reinterpret_cast<T*>(L.x) + 6 * (size_t)o;
-  if (t < n) X[t] = (T)w[t];
+  if (t < n) X[t] = (T)w0;
+  if (t + 32 < n) X[t + 32] = (T)w1;
 }
 
 // prolongation from level l + 1 to l (nodes whose scene has level l + 1): x_l[k] += P_k e[parent(k)]
@@ -2580,33 +2586,29 @@ __global__ void k_amg_prolong(DevArrays d, AmgDev a, int l) {
   if (k >= n) return;
   int I = a.L[l].parent[k];
   if (I < 0) return;
-  double e[6], x[6];
-  amg_load<T>(a.L[l + 1].x, I, e);
-  const double* cI = a.L[l + 1].cen + 3 * (size_t)I;
-  double ck[3], wv[3] = {e[3], e[4], e[5]};
+  Vec6<T> e = load6<T>(reinterpret_cast<const T*>(a.L[l + 1].x), I);
   void* X = l == 0 ? d.vz : a.L[l].x;
-  amg_load<T>(X, k, x);
-  if (l == 0) {
-    double4 p = d.xp[k];
-    ck[0] = p.x; ck[1] = p.y; ck[2] = p.z;
-    double R[9];
-    amg_rot(d.xq[k], R);  // B w = 1/2 R^T w
-    wv[0] = 0.5 * (R[0] * e[3] + R[3] * e[4] + R[6] * e[5]);
-    wv[1] = 0.5 * (R[1] * e[3] + R[4] * e[4] + R[7] * e[5]);
-    wv[2] = 0.5 * (R[2] * e[3] + R[5] * e[4] + R[8] * e[5]);
+  Vec6<T> x = load6<T>(reinterpret_cast<const T*>(X), k);
+  T dv[3], wv[3];
+  if (l == 0) {  // stored offset and B = 1/2 R(q)^T: B w
+    const T* o = reinterpret_cast<const T*>(a.p0) + 12 * (size_t)k;
+    dv[0] = o[0]; dv[1] = o[1]; dv[2] = o[2];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) wv[r] = o[3 + 3 * r] * e.v[3] + o[4 + 3 * r] * e.v[4] + o[5 + 3 * r] * e.v[5];
   } else {
-    const double* c = a.L[l].cen + 3 * (size_t)k;
-    ck[0] = c[0]; ck[1] = c[1]; ck[2] = c[2];
+    const double *ck = a.L[l].cen + 3 * (size_t)k, *cI = a.L[l + 1].cen + 3 * (size_t)I;
+    dv[0] = (T)(ck[0] - cI[0]); dv[1] = (T)(ck[1] - cI[1]); dv[2] = (T)(ck[2] - cI[2]);
+    wv[0] = e.v[3]; wv[1] = e.v[4]; wv[2] = e.v[5];
   }
-  double dv[3] = {ck[0] - cI[0], ck[1] - cI[1], ck[2] - cI[2]};
-  x[0] += e[0] + e[4] * dv[2] - e[5] * dv[1];
-  x[1] += e[1] + e[5] * dv[0] - e[3] * dv[2];
-  x[2] += e[2] + e[3] * dv[1] - e[4] * dv[0];
-  x[3] += wv[0]; x[4] += wv[1]; x[5] += wv[2];
+  T o6[6];
+  o6[0] = x.v[0] + e.v[0] + e.v[4] * dv[2] - e.v[5] * dv[1];
+  o6[1] = x.v[1] + e.v[1] + e.v[5] * dv[0] - e.v[3] * dv[2];
+  o6[2] = x.v[2] + e.v[2] + e.v[3] * dv[1] - e.v[4] * dv[0];
+  o6[3] = x.v[3] + wv[0]; o6[4] = x.v[4] + wv[1]; o6[5] = x.v[5] + wv[2];
   if (l == 0 && d.kin[k])
 #pragma unroll
-    for (int t = 0; t < 6; ++t) x[t] = 0.0;
-  amg_store<T>(X, k, x);
+    for (int t = 0; t < 6; ++t) o6[t] = (T)0;
+  store6<T>(reinterpret_cast<T*>(X), k, o6);
 }
 
 // fine-level products with G lanes per row (the lanes split the row's entries, the diagonal block goes to lane 0):
@@ -2727,15 +2729,15 @@ static int amg_cycle_t(const DevArrays& d, const AmgDev& a, int n_scenes, cudaSt
   // the level-0 pre-smoothing (z = w Dinv r) was written by the PCG stage that produced r
   int k = 0, top = a.nl - 1;
   k_amg_fine<T, 4><<<amg_lane_blocks(d.n, 4), 256, 0, s>>>(d, a, 1);
-  k_amg_restrict<T><<<amg_blocks(a.L[1].n), 128, 0, s>>>(d, a, 0);
+  k_amg_restrict<T><<<amg_lane_blocks(a.L[1].n, kAmgAgg), 256, 0, s>>>(d, a, 0);
   k += 2;
   for (int l = 1; l < top; ++l) {
     if (a.L[l + 1].n == 0) break;
     k_amg_cresid<T><<<amg_lane_blocks(a.L[l].n, 8), 256, 0, s>>>(a, l);
-    k_amg_restrict<T><<<amg_blocks(a.L[l + 1].n), 128, 0, s>>>(d, a, l);
+    k_amg_restrict<T><<<amg_lane_blocks(a.L[l + 1].n, kAmgAgg), 256, 0, s>>>(d, a, l);
     k += 2;
   }
-  k_amg_csolve<T><<<n_scenes, 64, 0, s>>>(a);
+  k_amg_csolve<T><<<n_scenes, 32, 0, s>>>(a);
   ++k;
   for (int l = top - 1; l >= 1; --l) {
     if (a.L[l + 1].n == 0) continue;
