@@ -2429,7 +2429,8 @@ __global__ void k_amg_cfactor(AmgDev a) {
     __syncthreads();
   }
   double* out = a.chol + (size_t)kAmgDense * kAmgDense * s;
-  for (int k = threadIdx.x; k < n * n; k += blockDim.x) out[k] = A[k];
+  for (int k = threadIdx.x; k < n * n; k += blockDim.x)  // the diagonal stored as its reciprocal
+    out[k] = (k % (n + 1) == 0) ? 1.0 / A[k] : A[k];
 }
 
 // ---- the cycle --------------------------------------------------------------------------------------------------
@@ -2545,8 +2546,8 @@ __global__ void k_amg_level(AmgDev a, int l, int mode) {
   amg_store<T>(L.x, I, y);
 }
 
-// one warp per scene: x = A^-1 r on the scene's coarsest level with its Cholesky factor (in shared memory); lane t
-// owns rows t and t + 32, the substitutions broadcast each solved entry with a shuffle
+// one warp per scene: x = A^-1 r on the scene's coarsest level with its Cholesky factor (in shared memory, diagonal
+// as reciprocals); lane t owns rows t and t + 32, the substitutions broadcast each solved entry with a shuffle
 template <typename T>
 __global__ void k_amg_csolve(AmgDev a) {
   int s = blockIdx.x;
@@ -2561,13 +2562,13 @@ __global__ void k_amg_csolve(AmgDev a) {
   double w0 = t < n ? (double)R[t] : 0.0, w1 = t + 32 < n ? (double)R[t + 32] : 0.0;
   __syncwarp();
   for (int j = 0; j < n; ++j) {  // forward: L w = r
-    double wj = __shfl_sync(0xffffffffu, j < 32 ? w0 : w1, j & 31) / Ls[n * j + j];
+    double wj = __shfl_sync(0xffffffffu, j < 32 ? w0 : w1, j & 31) * Ls[n * j + j];
     if (t == (j & 31)) { if (j < 32) w0 = wj; else w1 = wj; }
     if (t > j && t < n) w0 -= Ls[n * t + j] * wj;
     if (t + 32 > j && t + 32 < n) w1 -= Ls[n * (t + 32) + j] * wj;
   }
   for (int j = n - 1; j >= 0; --j) {  // backward: L^T z = w
-    double wj = __shfl_sync(0xffffffffu, j < 32 ? w0 : w1, j & 31) / Ls[n * j + j];
+    double wj = __shfl_sync(0xffffffffu, j < 32 ? w0 : w1, j & 31) * Ls[n * j + j];
     if (t == (j & 31)) { if (j < 32) w0 = wj; else w1 = wj; }
     if (t < j) w0 -= Ls[n * j + t] * wj;
     if (t + 32 < j) w1 -= Ls[n * j + t + 32] * wj;
