@@ -184,3 +184,23 @@ def test_amg_with_the_midpoint_form_reaches_the_same_state():
     # the diagonal (measured between the two preconditioners); a different cycle would not change the converged state
     assert np.abs(runs[0]["pos"] - runs[1]["pos"]).max() <= 5e-6 * L
     assert np.abs(runs[0]["quat"] - runs[1]["quat"]).max() <= 5e-6
+
+
+def test_cycle_is_a_contraction_of_the_error():
+    """Without self contact the cycle's operator A_0 is the whole system H. One symmetric V(1,1) cycle with damped
+    block-Jacobi smoothing and Galerkin coarse levels propagates the error by E = I - M^-1 H with E A-self-adjoint and
+    positive semi-definite, so every eigenvalue of M^-1 H lies in (0, 1]: a smoother that diverged (damping too
+    large) or a coarse correction that was not an A-orthogonal projection would put eigenvalues outside."""
+    sc = scenes.cube_lattice(nx=4, spacing=0.0098, r=0.005, k_ground=1e6, z_bottom=0.0045, preconditioner=1)
+    o = oracle.OracleSim(sc)
+    p, q, phat, qhat = deformed(sc, 8)
+    n6 = 6 * sc.n
+    M, H = np.zeros((n6, n6)), np.zeros((n6, n6))
+    for c in range(n6):
+        e = np.zeros(n6)
+        e[c] = 1.0
+        M[:, c] = o.amg_apply(p, q, phat, qhat, e.reshape(-1, 6))[0].ravel()
+        H[:, c] = o.matvec(p, q, phat, qhat, e.reshape(-1, 6)).ravel()
+    lam = np.linalg.eigvals(M @ H).real
+    assert lam.min() > 0.0
+    assert lam.max() <= 1.0 + 1e-8, lam.max()
