@@ -9,7 +9,10 @@
 //   k_particle_hess      diagonal blocks + block-Jacobi inverses                                (Sec. 5.3)
 //   k_pcg                persistent cooperative PCG, per-scene FP64 dot products              (Sec. 5.3)
 //   k_ls_*               exp-map retraction, term-wise energy difference, accept / halve  (Eq. manifold-update-1/2)
-//   k_finish / k_fracture velocity update, tensile-strain bond breaking                      (Alg. 3)
+//   k_finish / k_fracture velocity update, tensile-strain (and stress) bond breaking     (Alg. 3, Sec. 3.2)
+//   k_friction           post-step friction correction of the new velocities                  (Sec. 5.4)
+//   k_zhat_*             target zhat of the variational midpoint form                    (Sec. 3.1, App. C)
+//   k_amg_*, k_apcg_*    aggregation AMG coarse operators, V(1,1) cycle, AMG-preconditioned PCG stages (Sec. 5.3)
 // Every reduction is deterministic: per-tile partial sums (fixed order) reduced per scene in tile order.
 #include <math.h>
 
