@@ -1,4 +1,5 @@
-"""The multi-process (replicas) reduction of bench.py on CPU: two gloo ranks, each timing its own replica.
+"""bench.py on CPU: the multi-process (replicas) reduction with two gloo ranks, each timing its own replica, and the
+reference arm's JSON line.
 
 With N GPUs every rank advances an independent replica of the workload; the job's time is the slowest rank's
 and its work is the sum over ranks. This checks that reduction with a real two-rank process group.
@@ -46,3 +47,23 @@ def test_single_process_reduction_is_identity():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.reduce_timing(1.5, 7, 1) == (1.5, 7)
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` runs the oracle sample on the host (no GPU) and prints one JSON line with the
+    contract's keys, its own cpu_baseline and an e2e object without transfers."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
