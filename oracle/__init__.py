@@ -95,6 +95,8 @@ def _setup(L):
     L.orc_energy_diff.restype = ctypes.c_double
     L.orc_retract.argtypes = [_dp, _dp, _dp, ctypes.c_double, _dp, _dp]
     L.orc_retract.restype = None
+    L.orc_precond_apply.argtypes = [_dp, _dp, _dp]
+    L.orc_precond_apply.restype = ctypes.c_int
     L.orc_eig_clamp.argtypes = [ctypes.c_int, _dp]
     L.orc_eig_clamp.restype = None
     L.orc_eig_sym.argtypes = [ctypes.c_int, _dp, _dp, _dp]
@@ -156,6 +158,16 @@ def retract(p, q, step6, alpha=1.0):
     p, q, s = f64(p), f64(q), f64(step6)
     lib().orc_retract(_d(p), _d(q), _d(s), float(alpha), _d(po), _d(qo))
     return po, qo
+
+
+def precond_apply(D, r):
+    """Block-Jacobi preconditioner of Sec. 5.3 on one 6x6 block: (z = D^-1 r, 1) by Cholesky, or the fallback
+    (r_a / D_aa, 0) for a block that is not positive definite."""
+    D = f64(D, (6, 6)).copy()
+    r = f64(r, (6,)).copy()
+    z = np.zeros(6)
+    ok = lib().orc_precond_apply(_d(D), _d(r), _d(z))
+    return z, int(ok)
 
 
 def eig_clamp(A):

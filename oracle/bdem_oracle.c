@@ -1049,7 +1049,7 @@ static void sys_matvec(const scene_sys* S, const double* x, double* y, int mask_
 
 /* block-Jacobi preconditioner: z_i = D_i^{-1} r_i by Cholesky; a block that is not positive definite
  * falls back to the inverse of its diagonal (entries <= 0 leave r unchanged) */
-static void precond_apply(const double* D, const double* r, double* z) {
+static int precond_apply(const double* D, const double* r, double* z) {
   double L[36];
   memset(L, 0, sizeof L);
   int ok = 1;
@@ -1066,7 +1066,7 @@ static void precond_apply(const double* D, const double* r, double* z) {
   }
   if (!ok) {
     for (int a = 0; a < 6; ++a) z[a] = D[7 * a] > 0.0 ? r[a] / D[7 * a] : r[a];
-    return;
+    return 0;
   }
   double w[6];
   for (int i = 0; i < 6; ++i) {
@@ -1079,7 +1079,10 @@ static void precond_apply(const double* D, const double* r, double* z) {
     for (int k = i + 1; k < 6; ++k) s -= L[6 * k + i] * z[k];
     z[i] = s / L[7 * i];
   }
+  return 1;
 }
+
+int orc_precond_apply(const double D[36], const double r[6], double z[6]) { return precond_apply(D, r, z); }
 
 static double vdot(int n, const double* a, const double* b) {
   double s = 0.0;

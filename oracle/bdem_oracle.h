@@ -156,6 +156,11 @@ double orc_energy_diff(const orc_config* C, const orc_problem* P, int scene, con
 void orc_retract(const double p[3], const double q[4], const double step6[6], double alpha, double p_out[3],
                  double q_out[4]);
 
+/* Block-Jacobi preconditioner of Sec. 5.3 applied to one 6x6 block: z = D^-1 r by a Cholesky factorisation of D
+ * (row-major 6x6, symmetric); a block that is not positive definite falls back to z_a = r_a / D_aa (r_a unchanged
+ * where D_aa <= 0). Returns 1 when the Cholesky path was taken, 0 for the fallback. */
+int orc_precond_apply(const double D[36], const double r[6], double z[6]);
+
 /* Symmetric eigen-clamp by cyclic Jacobi (eigenvalues < 0 set to 0); A is n x n row-major, in place. */
 void orc_eig_clamp(int n, double* A);
 void orc_eig_sym(int n, const double* A, double* evals, double* evecs);

@@ -260,24 +260,51 @@ def test_ground_contact_rest_state():
 
 
 def test_kinematic_particles_and_strain_fracture():
-    """Kinematic particles follow their velocity exactly; a bond breaks at the first converged step whose
-    tensile strain exceeds the limit (all bonds tested at once after the solve)."""
-    l0, v, dt = 0.01, 0.5, 1e-3
+    """Kinematic particles follow their velocity exactly; a bond breaks at the first converged step whose tensile
+    strain (|p_j - p_i| - l0)/l0 strictly exceeds its limit, every intact bond tested at once on the step's converged
+    state (Alg. 3, bond update). The two end particles of a 3-particle chain move apart at v each, so by symmetry
+    each bond's strain is v dt n / l0 = 0.05 n at step n: with limit 0.27 both bonds break together at n = 6
+    (0.30 > 0.27 while 0.25 at n = 5 is below), and not one step earlier or later."""
+    l0, v, dt, lim = 0.01, 0.5, 1e-3, 0.27
     pos = np.array([[0.0, 0.0, 0.0], [l0, 0.0, 0.0], [2 * l0, 0.0, 0.0]])
-    cfg = scenes.default_config(dt=dt, gravity=(0.0, 0.0, 0.0))
+    cfg = scenes.default_config(dt=dt, gravity=(0.0, 0.0, 0.0), newton_rel_tol=1e-10)
     sc = scenes._assemble(pos, np.full(3, 0.005), np.zeros(3, np.int32), np.array([1, 0, 1], np.uint8),
-                          np.array([[0, 1], [1, 2]]), [scenes.Material(1e7, 0.3, 2500.0, 0.25)], cfg, "pull")
+                          np.array([[0, 1], [1, 2]]), [scenes.Material(1e7, 0.3, 2500.0, lim)], cfg, "pull")
     sc.vel[0, 0], sc.vel[2, 0] = -v, v
     o = oracle.OracleSim(sc)
     broke_at = None
-    for n in range(1, 8):
+    for n in range(1, 9):
+        was = o.broken.copy()
         st = o.step(1)[0][0]
         assert np.isclose(o.p[0, 0], -v * dt * n, rtol=0, atol=1e-15) and np.isclose(o.p[2, 0], 2 * l0 + v * dt * n, atol=1e-15)
+        strain = np.array([(np.linalg.norm(o.p[o.bj[b]] - o.p[o.bi[b]]) - l0) / l0 for b in range(2)])
+        if not was.any():
+            assert np.allclose(strain, v * dt * n / l0, rtol=0, atol=1e-9)  # the closed form before the break
+            # broken exactly where the converged state's strain is above the limit, nowhere else
+            assert np.array_equal(o.broken.astype(bool), strain > lim)
+            assert st["bonds_broken"] == int((strain > lim).sum())
         if st["bonds_broken"] and broke_at is None:
             broke_at = n
-            strain = (o.p[2, 0] - o.p[0, 0] - 2 * l0) / (2 * l0)
-            assert strain > 0.25 / 2  # both bonds share the stretch
-    assert broke_at is not None and o.broken.sum() >= 1
+    assert broke_at == 6 and o.broken.sum() == 2
+
+
+def test_fracture_tests_each_bond_against_its_own_limit():
+    """Bonds of different limits in the same stretched chain: only the weaker one breaks, at the first step its
+    strain is above its own limit; the stronger one, at the same strain, stays intact."""
+    l0, v, dt = 0.01, 0.5, 1e-3
+    pos = np.array([[0.0, 0.0, 0.0], [l0, 0.0, 0.0], [2 * l0, 0.0, 0.0]])
+    cfg = scenes.default_config(dt=dt, gravity=(0.0, 0.0, 0.0), newton_rel_tol=1e-10)
+    mats = [scenes.Material(1e7, 0.3, 2500.0, 0.17), scenes.Material(1e7, 0.3, 2500.0, 0.5)]
+    sc = scenes._assemble(pos, np.full(3, 0.005), np.zeros(3, np.int32), np.array([1, 0, 1], np.uint8),
+                          np.array([[0, 1], [1, 2]]), mats, cfg, "pull2", bond_mat=np.array([0, 1], np.int32))
+    sc.vel[0, 0], sc.vel[2, 0] = -v, v
+    o = oracle.OracleSim(sc)
+    for n in range(1, 5):
+        st = o.step(1)[0][0]
+        if n < 4:  # strains 0.05 n <= 0.15 < 0.17
+            assert st["bonds_broken"] == 0 and not o.broken.any()
+    # n = 4: both strains 0.20 (the middle particle is still centred before the test): only bond 0 is above its limit
+    assert o.broken.tolist() == [1, 0]
 
 
 def test_literal_shear_gradient_noise_floor():
