@@ -71,7 +71,8 @@ typedef struct {
 typedef struct {
   double dt;                /* time step > 0 */
   double gravity[3];        /* V_g = -m g.p */
-  double newton_rel_tol;    /* a scene converges when |g_k|_2 <= tol |g_0|_2 (g_0 at the initial guess) */
+  double newton_rel_tol;    /* a scene converges when |g_k|_2 <= tol |g_0|_2 (g_0 at the initial guess) or when
+                               |g_k|_2 <= newton_abs_tol */
   int32_t newton_max_iter;  /* >= 1 */
   int32_t pcg_max_iter;     /* >= 1 */
   int32_t ls_max_halvings;  /* >= 0; the line search tries alpha = 1, 1/2, ..., 2^-ls_max_halvings */
@@ -111,6 +112,16 @@ typedef struct {
                                blocks left out), a symmetric V(1,1) cycle with block-Jacobi smoothing damped by 0.6,
                                exact solves of each scene's coarsest level; the textbook PCG around it runs from the
                                host-driven step loop (no step graph) */
+  double newton_abs_tol;    /* >= 0; a scene also converges when |g_k|_2 <= newton_abs_tol, the absolute test
+                               |grad f| < eps of Alg. 3 (0: off, only the relative test) */
+  int32_t pcg_refine;       /* >= 0 (at most 16): rounds of FP64-residual refinement of each Newton solve in
+                               BDEM_MIXED with block-Jacobi PCG (0: off; ignored in BDEM_FP64 and with the AMG). After
+                               the FP32 PCG stops, the correction is accumulated in FP64, the true residual
+                               r = b - H dx is formed with FP64 arithmetic on the stored blocks, and while
+                               |r| > eps_r |b| the FP32 PCG is run again on H d = r (relative target
+                               eps_r |b| / |r|), at most pcg_refine times, stopping early when |r| grows; the
+                               line search takes the FP64 direction */
+  int32_t reserved0;        /* set to 0 */
 } bdem_config;
 
 /* Per-scene statistics of one bdem_step call (sums over its steps, norms of the last step). */
@@ -127,6 +138,10 @@ typedef struct {
   double g_norm;            /* |g| at exit of the last step */
   int64_t contact_entry_pcg_iters; /* sum over linear solves of (active self-contact matrix entries x PCG iterations) */
   int64_t intact_bonds;     /* intact bonds of the scene after the last step */
+  double lin_rel_residual;  /* |b - H dx| / |b| of the last linear solve of the last step, evaluated in FP64 when
+                               pcg_refine > 0 in BDEM_MIXED (-1: not evaluated) */
+  int32_t refine_rounds;    /* FP64-residual refinement rounds (extra PCG launches) summed over the call's steps */
+  int32_t reserved1;
 } bdem_step_stats;
 
 /* Creates a simulation of n particles split into n_scenes independent scenes: scene s owns particles
@@ -229,11 +244,15 @@ bdem_status bdem_debug_bond_stress(bdem_sim* sim, double* out);
  * BDEM_E_TIMEOUT as a step would (the simulation stays usable). For testing the failure path without a GPU fault. */
 bdem_status bdem_debug_wait_timeout(bdem_sim* sim, double limit_ms);
 
-/* y = H x with the system of the last bdem_debug_system call; x, y host [n][6]. */
+/* y = H x with the system of the last bdem_debug_system call; x, y host [n][6]. The product is formed in FP64
+ * arithmetic on the stored blocks (FP32 words in BDEM_MIXED), so it is the exact product of the stored matrix up to
+ * the rounding of the FP64 sums. */
 bdem_status bdem_debug_matvec(bdem_sim* sim, const double* x, double* y);
 
 /* PCG (Sec. 5.3) on H dx = b with the system of the last bdem_debug_system call (kinematic rows removed), from
- * dx = 0 until |r| <= eps_r |b| or max_iter iterations. b, dx host [n][6]; iters[n_scenes] or NULL. */
+ * dx = 0 until |r| <= eps_r |b| or max_iter iterations. b, dx host [n][6]; iters[n_scenes] or NULL. With
+ * pcg_refine > 0 in BDEM_MIXED the solve is refined as a Newton solve is (the FP64 residual b - H dx of the
+ * accumulated FP64 solution must meet eps_r |b|; iters counts the iterations of every round). */
 bdem_status bdem_debug_pcg(bdem_sim* sim, const double* b, double eps_r, int32_t max_iter, double* dx,
                            int32_t* iters);
 
@@ -257,18 +276,21 @@ bdem_status bdem_autotune_pcg(bdem_sim* sim, int32_t iters, int32_t* lanes_per_r
  * The paper has no counterpart: this entry point exists for callers that cannot allocate device memory, for
  * example code running under an external memory pool that forbids extra cudaMalloc calls, or a host thread that
  * must not trigger allocation while other work is being captured or scheduled.
- * It runs the same PCG solve as bdem_debug_pcg (Sec. 5.3 block-Jacobi PCG, kinematic rows removed) on the system
- * assembled by the last bdem_debug_system call, but keeps all of its scratch (per-scene control blocks, barrier
+ * It runs the block-Jacobi PCG solve (kinematic rows removed) on the system assembled by the last bdem_debug_system
+ * call, whatever bdem_config.preconditioner and pcg_refine say: this is bdem_debug_pcg's solve when the
+ * preconditioner is block Jacobi and pcg_refine is 0 (no FP64-residual refinement). It keeps all of its scratch
+ * (per-scene control blocks, barrier
  * counters, partial sums, PCG vectors) in one static device array of 24 MiB inside the library, so the call itself
  * allocates nothing (no cudaMalloc, cudaFree or allocating library routine). That caps the system at about 87,000
  * particles in BDEM_FP64 and 174,000 in BDEM_MIXED; larger systems get BDEM_E_INVALID with the byte counts.
  *   b_dev, x_dev: caller-owned DEVICE arrays [n][6] of double (right-hand side in, solution out).
  *   iters: NULL or host int32_t[n_scenes] receiving the iterations per scene.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that device current
- * and caches it, so make that first call before any stream capture. Every GPU that loads the library holds the
- * array until the process exits. All calls share the array and each call overwrites it, clearing what must start
- * at zero; calls whose work overlaps on the GPU (other host threads, other streams, other sims) race on it and
- * must be serialised by the caller. Host-blocking: returns after the solve has completed. */
+ * and caches it (the cache is safe to fill from several host threads), so make that first call before any stream
+ * capture. Every GPU that loads the library holds the array until the process exits. All calls share the array and
+ * each call overwrites it, clearing what must start at zero; calls whose work overlaps on the GPU (other host
+ * threads, other streams, other sims) race on it and must be serialised by the caller. Host-blocking: returns after
+ * the solve has completed. */
 bdem_status bdem_pcg_static(bdem_sim* sim, const double* b_dev, double* x_dev, double eps_r, int32_t max_iter,
                             int32_t* iters);
 

@@ -49,7 +49,8 @@ class OrcConfig(ctypes.Structure):
                 ("ls_max_halvings", ctypes.c_int32), ("optimizer", ctypes.c_int32), ("ground_z", ctypes.c_double),
                 ("k_ground", ctypes.c_double), ("k_self", ctypes.c_double), ("contact_skin", ctypes.c_double),
                 ("mu_slide", ctypes.c_double), ("mu_roll", ctypes.c_double),
-                ("integrator", ctypes.c_int32), ("preconditioner", ctypes.c_int32)]
+                ("integrator", ctypes.c_int32), ("preconditioner", ctypes.c_int32),
+                ("newton_abs_tol", ctypes.c_double)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -252,6 +253,7 @@ class OracleSim:
         C.mu_roll = c.get("friction_roll", 0.0)
         C.integrator = int(c.get("integrator", 0))
         C.preconditioner = int(c.get("preconditioner", 0))
+        C.newton_abs_tol = float(c.get("newton_abs_tol", 0.0))
         return C
 
     def _build_problem(self):

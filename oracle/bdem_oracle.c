@@ -1580,11 +1580,12 @@ int orc_pcg_solve(const orc_config* C, const orc_problem* P, int scene, const do
 
 /* ------------------------------------------------------------------------------------------------ */
 /* Alg. 3: one time step.                                                                           */
-/* Readings: Newton stops when |g_k| <= tol |g_0| (g_0 at the initial guess); eps_r uses the absolute */
-/* |g_k|; the line search halves alpha from 1 until Phi(x') - Phi(x) <= 0 (at most ls_max_halvings   */
-/* halvings), and a direction with g.dx >= 0 is replaced by -g; after convergence a bond breaks when */
-/* its tensile strain (|p_j - p_i| - l0)/l0 exceeds its limit; kinematic particles move with their   */
-/* velocity and are excluded from the solve.                                                          */
+/* Readings: Newton stops when |g_k| <= tol |g_0| (g_0 at the initial guess), or, when an absolute   */
+/* tolerance is set, when |g_k| <= newton_abs_tol (Alg. 3's own test |grad f| < eps); eps_r uses the  */
+/* absolute |g_k|; the line search halves alpha from 1 until Phi(x') - Phi(x) <= 0 (at most           */
+/* ls_max_halvings halvings), and a direction with g.dx >= 0 is replaced by -g; after convergence a   */
+/* bond breaks when its tensile strain (|p_j - p_i| - l0)/l0 exceeds its limit; kinematic particles    */
+/* move with their velocity and are excluded from the solve.                                          */
 /* ------------------------------------------------------------------------------------------------ */
 
 /* The target of the variational midpoint form (Sec. 3.1; App. C):
@@ -1660,7 +1661,7 @@ static int newton_scene(const orc_config* C, orc_problem* P, int scene, double* 
     double gn = sqrt(vdot(n6, S.g, S.g));
     if (k == 0) st->g0_norm = gn;
     st->g_norm = gn;
-    if (gn <= C->newton_rel_tol * st->g0_norm) break;
+    if (gn <= C->newton_rel_tol * st->g0_norm || gn <= C->newton_abs_tol) break;
     if (k >= C->newton_max_iter) { status = 4; break; }
     if (C->optimizer == 1) {
       /* Alg. 1: the descent direction is -grad f; in the reduced coordinates dq = G_l(q)^T y, so y = -g_y gives

@@ -38,6 +38,7 @@ typedef struct {
   int32_t integrator;      /* 0: the implicit-Euler-like form (V at x_{n+1}); 1: the variational midpoint form of
                               Sec. 3.1 / App. C (V at (x_{n+1} + x_n)/2 and the target zhat) */
   int32_t preconditioner;  /* 0: block Jacobi; 1: the aggregation AMG cycle (Sec. 5.3; needs P->morton) */
+  double newton_abs_tol;   /* also stop when |g_k| <= newton_abs_tol: Alg. 3's absolute test |grad f| < eps (0: off) */
 } orc_config;
 
 /* Particle, bond and scene arrays. Bond rest data is filled by orc_bond_rest(). */

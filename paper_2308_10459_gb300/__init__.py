@@ -39,7 +39,8 @@ class bdem_config(ctypes.Structure):
                 ("k_ground", ctypes.c_double), ("k_self", ctypes.c_double), ("contact_skin", ctypes.c_double),
                 ("spd_mode", ctypes.c_int32), ("optimizer", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
                 ("friction_slide", ctypes.c_double), ("friction_roll", ctypes.c_double),
-                ("integrator", ctypes.c_int32), ("preconditioner", ctypes.c_int32)]
+                ("integrator", ctypes.c_int32), ("preconditioner", ctypes.c_int32),
+                ("newton_abs_tol", ctypes.c_double), ("pcg_refine", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
 
 class bdem_step_stats(ctypes.Structure):
@@ -47,7 +48,8 @@ class bdem_step_stats(ctypes.Structure):
                 ("ls_halvings", ctypes.c_int32), ("bonds_broken", ctypes.c_int32),
                 ("contact_candidates", ctypes.c_int32), ("status", ctypes.c_int32), ("reserved0", ctypes.c_int32),
                 ("g0_norm", ctypes.c_double), ("g_norm", ctypes.c_double),
-                ("contact_entry_pcg_iters", ctypes.c_int64), ("intact_bonds", ctypes.c_int64)]
+                ("contact_entry_pcg_iters", ctypes.c_int64), ("intact_bonds", ctypes.c_int64),
+                ("lin_rel_residual", ctypes.c_double), ("refine_rounds", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
 
 
 PHASES = ["predict", "contact", "grad", "hess", "pcg", "linesearch", "finish"]
@@ -157,6 +159,9 @@ def make_config(cfg: dict, precision=BDEM_FP64, cuda_stream=None) -> bdem_config
     c.friction_roll = cfg.get("friction_roll", 0.0)
     c.integrator = int(cfg.get("integrator", 0))
     c.preconditioner = int(cfg.get("preconditioner", 0))
+    c.newton_abs_tol = float(cfg.get("newton_abs_tol", 0.0))
+    c.pcg_refine = int(cfg.get("pcg_refine", 0))
+    c.reserved0 = 0
     return c
 
 

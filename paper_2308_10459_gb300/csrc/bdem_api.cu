@@ -63,7 +63,7 @@ struct bdem_sim {
   cudaGraphExec_t graph_exec = nullptr;
   DevArrays graph_d{};                // the arrays the graph was captured with (kernel arguments are by value)
   cudaStream_t cap[3] = {nullptr, nullptr, nullptr};
-  int g_pre = 0, g_body = 0, g_ls = 0, g_post = 0;  // kernels per graph segment
+  int g_pre = 0, g_body = 0, g_ls = 0, g_post = 0, g_ref = 0;  // kernels per graph segment
   int64_t graph_steps = 0;
   // aggregation AMG preconditioner (bdem_config.preconditioner)
   AmgDev amg{};
@@ -233,6 +233,9 @@ static bdem_status check_config(const bdem_config* c) {
     if (!fin(c->gravity[k])) return fail(nullptr, BDEM_E_INVALID, "gravity must be finite");
   if (!(c->newton_rel_tol >= 0.0) || !fin(c->newton_rel_tol))
     return fail(nullptr, BDEM_E_INVALID, "newton_rel_tol must be finite and >= 0");
+  if (!(c->newton_abs_tol >= 0.0) || !fin(c->newton_abs_tol))
+    return fail(nullptr, BDEM_E_INVALID, "newton_abs_tol must be finite and >= 0");
+  if (c->pcg_refine < 0 || c->pcg_refine > 16) return fail(nullptr, BDEM_E_INVALID, "pcg_refine must be in [0, 16]");
   if (c->newton_max_iter < 1 || c->pcg_max_iter < 1 || c->ls_max_halvings < 0 || c->ls_max_halvings > 1000)
     return fail(nullptr, BDEM_E_INVALID, "iteration caps must be newton >= 1, pcg >= 1, 0 <= line search <= 1000");
   if (c->precision != BDEM_FP64 && c->precision != BDEM_MIXED)
@@ -268,6 +271,7 @@ static bdem_status alloc_particles(bdem_sim* s) {
   TRY(dalloc(s, &d.Dinv, w * kDiagStride * n));
   void** pv[] = {&d.vx, &d.vr, &d.vz, &d.vp_, &d.vq_, &d.vs};
   for (void** p : pv) TRY(dalloc(s, p, w * 6 * n));
+  if (d.refine) TRY(dalloc_t(s, &d.x64, 6 * n));
   int hs = 1024;
   while (hs < 2 * (int)n) hs <<= 1;
   d.hash_size = hs;
@@ -546,6 +550,7 @@ extern "C" bdem_status bdem_create(const bdem_config* config, int32_t n_scenes, 
   d.gy = c.gravity[1];
   d.gz = c.gravity[2];
   d.tol = c.newton_rel_tol;
+  d.tol_abs = c.newton_abs_tol;
   d.ground_z = c.ground_z;
   d.k_ground = c.k_ground;
   d.k_self = c.k_self;
@@ -555,6 +560,8 @@ extern "C" bdem_status bdem_create(const bdem_config* config, int32_t n_scenes, 
   d.first_order = c.optimizer == BDEM_OPT_FIRST_ORDER;
   d.midpoint = c.integrator == BDEM_INT_MIDPOINT;
   s->amg.on = c.preconditioner == BDEM_PRECOND_AMG;
+  // FP64-residual refinement: the mixed path's second-order solves with the block-Jacobi PCG
+  d.refine = (d.mixed && !d.first_order && !s->amg.on) ? c.pcg_refine : 0;
   s->amg.omega = 0.6;
   d.mu_roll = c.friction_roll;
   double rmax = 0.0;
@@ -882,6 +889,25 @@ static bdem_status run_pcg(bdem_sim* s, const DevArrays& d, int rhs_from_g, int 
   return check_launch(s, 0);
 }
 
+// FP64-residual refinement of the Newton solve just computed by run_pcg (mixed path): accumulate the solution in
+// FP64, form the true residual, and re-solve for the scenes whose residual is still above the target (host-driven:
+// one counter read per round)
+static bdem_status run_refine(bdem_sim* s, const DevArrays& d) {
+  if (!d.refine) return BDEM_OK;
+  cudaStream_t st = s->stream;
+  TRY(check_launch(s, launch_refine(d, 1, st)));
+  TRY(check_launch(s, launch_scene_reduce(d, RED_REFINE0, 0, st)));
+  Counters c{};
+  TRY(read_counters(s, &c));
+  for (int r = 0; r < d.refine && c.n_active > 0; ++r) {
+    TRY(run_pcg(s, d, 0, 1));
+    TRY(check_launch(s, launch_refine(d, 0, st)));
+    TRY(check_launch(s, launch_scene_reduce(d, RED_REFINE, 0, st)));
+    TRY(read_counters(s, &c));
+  }
+  return BDEM_OK;
+}
+
 // ---- aggregation AMG (Sec. 5.3): static patterns from the bond list --------------------------------------------
 
 static void amg_release(bdem_sim* s) {
@@ -1132,8 +1158,12 @@ static bdem_status do_step(bdem_sim* s, std::vector<SceneCtl>& ctl) {
       TRY(check_launch(s, launch_particle_hess(d, 1, 0, st)));
       phase_end(s);
       phase_begin(s, BDEM_PH_PCG);
-      if (s->amg.on) TRY(run_amg_pcg(s, d, 1));
-      else TRY(run_pcg(s, d, 1, 1));
+      if (s->amg.on) {
+        TRY(run_amg_pcg(s, d, 1));
+      } else {
+        TRY(run_pcg(s, d, 1, 1));
+        TRY(run_refine(s, d));
+      }
       phase_end(s);
     }
     phase_begin(s, BDEM_PH_LINESEARCH);
@@ -1211,10 +1241,10 @@ static bool build_step_graph(bdem_sim* s) {
       s->graph_err = "cudaStreamCreateWithFlags failed";
       return false;
     }
-  cudaGraph_t G = nullptr, bodyN = nullptr, bodyL = nullptr;
-  cudaGraphConditionalHandle hN = 0, hL = 0;
-  cudaError_t e = cudaSuccess, pe = cudaSuccess;
-  int pre = 0, body = 0, ls = 0, post = 0;
+  cudaGraph_t G = nullptr, bodyN = nullptr, bodyL = nullptr, bodyR = nullptr;
+  cudaGraphConditionalHandle hN = 0, hL = 0, hR = 0;
+  cudaError_t e = cudaSuccess, pe = cudaSuccess, pe2 = cudaSuccess;
+  int pre = 0, body = 0, ls = 0, post = 0, ref = 0;
   const char* where = "";
 #define G_TRY(what, call)        \
   do {                           \
@@ -1251,6 +1281,7 @@ static bool build_step_graph(bdem_sim* s) {
     if (e == cudaSuccess && e2 != cudaSuccess) { e = e2; where = "end capture"; }
   }
   G_TRY("line-search handle", cudaGraphConditionalHandleCreate(&hL, bodyN, 0, 0));
+  if (d.refine) G_TRY("refinement handle", cudaGraphConditionalHandleCreate(&hR, bodyN, 0, 0));
   // Newton body
   G_TRY("begin body capture", cudaStreamBeginCaptureToGraph(s->cap[1], bodyN, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   if (e == cudaSuccess) {
@@ -1259,6 +1290,13 @@ static bool build_step_graph(bdem_sim* s) {
       body += launch_bond_hess(d, 0, st);
       body += launch_particle_hess(d, 1, 0, st);
       body += launch_pcg(d, 1, 1, st, &pe);
+      if (d.refine) {  // WHILE(a scene's true residual is above its target) { PCG on the residual, refine }
+        body += launch_refine(d, 1, st);
+        body += launch_scene_reduce(d, RED_REFINE0, hR, st);
+        G_TRY("PCG launch", pe);
+        G_TRY("refinement launches", cudaGetLastError());
+        G_TRY("refinement while node", capture_while(st, hR, &bodyR));
+      }
       body += launch_gdx(d, st);
     }
     body += launch_scene_reduce(d, RED_GDX, hL, st);
@@ -1286,6 +1324,22 @@ static bool build_step_graph(bdem_sim* s) {
     cudaError_t e2 = cudaStreamEndCapture(st, &out);
     if (e == cudaSuccess && e2 != cudaSuccess) { e = e2; where = "end line-search capture"; }
   }
+  // refinement body
+  if (d.refine && !d.first_order) {
+    G_TRY("begin refinement capture",
+          cudaStreamBeginCaptureToGraph(s->cap[2], bodyR, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    if (e == cudaSuccess) {
+      cudaStream_t st = s->cap[2];
+      ref += launch_pcg(d, 0, 1, st, &pe2);
+      ref += launch_refine(d, 0, st);
+      ref += launch_scene_reduce(d, RED_REFINE, hR, st);
+      G_TRY("refinement PCG launch", pe2);
+      G_TRY("refinement launches", cudaGetLastError());
+      cudaGraph_t out = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(st, &out);
+      if (e == cudaSuccess && e2 != cudaSuccess) { e = e2; where = "end refinement capture"; }
+    }
+  }
   G_TRY("cudaGraphInstantiate", cudaGraphInstantiate(&s->graph_exec, G, 0));
 #undef G_TRY
   s->graph = G;
@@ -1300,6 +1354,7 @@ static bool build_step_graph(bdem_sim* s) {
   s->g_body = body;
   s->g_ls = ls;
   s->g_post = post;
+  s->g_ref = ref;
   return true;
 }
 
@@ -1314,7 +1369,7 @@ static bdem_status graph_step(bdem_sim* s, std::vector<SceneCtl>& ctl, bool* red
   CUDA_TRY(s, cudaMemcpyAsync(ctl.data(), d.sc, sizeof(SceneCtl) * s->n_scenes, cudaMemcpyDeviceToHost, s->stream));
   TRY(sync(s));
   s->launches += s->g_pre + (int64_t)std::max(0, c.loops_newton - 1) * s->g_body + (int64_t)c.ls_total * s->g_ls +
-                 s->g_post;
+                 (int64_t)c.loops_refine * s->g_ref + s->g_post;
   if (c.timeout || c.nonfinite || c.overflow || c.runaway) {
     reset_counters(s, c.sync_gen);
     if (c.timeout) return fail(s, BDEM_E_TIMEOUT, "a device-side wait gave up; the step was rolled back");
@@ -1371,6 +1426,8 @@ extern "C" bdem_status bdem_step(bdem_sim* s, int32_t n_steps, bdem_step_stats* 
       o.g_norm = c.gnorm;
       o.contact_entry_pcg_iters += c.act_pcg;
       o.intact_bonds = c.intact;
+      o.lin_rel_residual = c.lin_res;
+      o.refine_rounds += c.refine_total;
     }
   }
   if (worst == BDEM_E_NEWTON_MAXITER) fail(s, BDEM_E_NEWTON_MAXITER, "a scene reached newton_max_iter");
@@ -1639,12 +1696,15 @@ extern "C" bdem_status bdem_debug_matvec(bdem_sim* s, const double* x, double* y
   if (!n) return BDEM_OK;
   DevArrays& d = s->d;
   cudaStream_t st = s->stream;
-  TRY(dbg_reserve(s, 12 * n));
-  CUDA_TRY(s, cudaMemcpyAsync(s->dbg_buf, x, sizeof(double) * 6 * n, cudaMemcpyHostToDevice, st));
-  TRY(check_launch(s, launch_convert_perm(s->dbg_buf, 1, d.vp_, !d.mixed, d.perm, 0, (int)n, st)));
-  TRY(check_launch(s, launch_matvec(d, 0, st)));
-  TRY(check_launch(s, launch_convert_perm(d.vq_, !d.mixed, s->dbg_buf + 6 * n, 1, d.perm, 1, (int)n, st)));
-  CUDA_TRY(s, cudaMemcpyAsync(y, s->dbg_buf + 6 * n, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, st));
+  TRY(dbg_reserve(s, 18 * n));
+  double* xc = s->dbg_buf;           // caller order
+  double* xi = s->dbg_buf + 6 * n;   // internal order
+  double* yi = s->dbg_buf + 12 * n;
+  CUDA_TRY(s, cudaMemcpyAsync(xc, x, sizeof(double) * 6 * n, cudaMemcpyHostToDevice, st));
+  TRY(check_launch(s, launch_convert_perm(xc, 1, xi, 1, d.perm, 0, (int)n, st)));
+  TRY(check_launch(s, launch_matvec64(d, xi, yi, 0, st)));
+  TRY(check_launch(s, launch_convert_perm(yi, 1, xc, 1, d.perm, 1, (int)n, st)));
+  CUDA_TRY(s, cudaMemcpyAsync(y, xc, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, st));
   return sync(s);
 }
 
@@ -1665,22 +1725,34 @@ extern "C" bdem_status bdem_debug_pcg(bdem_sim* s, const double* b, double eps_r
   TRY(sync(s));
   for (auto& c : ctl) {
     c.newton_active = 1;
+    c.pcg_skip = 0;
     c.eps_r = eps_r;
   }
   CUDA_TRY(s, cudaMemcpy(d.sc, ctl.data(), sizeof(SceneCtl) * s->n_scenes, cudaMemcpyHostToDevice));
-  TRY(dbg_reserve(s, 12 * n));
+  TRY(dbg_reserve(s, 18 * n));
   CUDA_TRY(s, cudaMemcpyAsync(s->dbg_buf, b, sizeof(double) * 6 * n, cudaMemcpyHostToDevice, st));
   TRY(check_launch(s, launch_convert_perm(s->dbg_buf, 1, d.vr, !d.mixed, d.perm, 0, (int)n, st)));
-  if (s->amg.on) TRY(run_amg_pcg(s, d, 0));
-  else TRY(run_pcg(s, d, 0, 1));
+  if (s->amg.on) {
+    TRY(run_amg_pcg(s, d, 0));
+  } else {
+    TRY(run_pcg(s, d, 0, 1));
+    if (d.refine) {  // the refinement's residual takes the caller's FP64 right-hand side
+      d.b64 = s->dbg_buf + 12 * n;
+      TRY(check_launch(s, launch_convert_perm(s->dbg_buf, 1, d.b64, 1, d.perm, 0, (int)n, st)));
+      TRY(run_refine(s, d));
+    }
+  }
   Counters c{};
   TRY(read_counters(s, &c));
-  TRY(check_launch(s, launch_convert_perm(d.vx, !d.mixed, s->dbg_buf + 6 * n, 1, d.perm, 1, (int)n, st)));
+  if (d.refine && !s->amg.on)
+    TRY(check_launch(s, launch_convert_perm(d.x64, 1, s->dbg_buf + 6 * n, 1, d.perm, 1, (int)n, st)));
+  else
+    TRY(check_launch(s, launch_convert_perm(d.vx, !d.mixed, s->dbg_buf + 6 * n, 1, d.perm, 1, (int)n, st)));
   CUDA_TRY(s, cudaMemcpyAsync(dx, s->dbg_buf + 6 * n, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(s, cudaMemcpyAsync(ctl.data(), d.sc, sizeof(SceneCtl) * s->n_scenes, cudaMemcpyDeviceToHost, st));
   TRY(sync(s));
   if (iters)
-    for (int sc = 0; sc < s->n_scenes; ++sc) iters[sc] = ctl[sc].pcg_iters;
+    for (int sc = 0; sc < s->n_scenes; ++sc) iters[sc] = (d.refine && !s->amg.on) ? ctl[sc].pcg_acc : ctl[sc].pcg_iters;
   // restore the unmasked diagonal blocks of the inspected system
   TRY(check_launch(s, launch_particle_hess(s->d, 0, 1, st)));
   return sync(s);
@@ -1813,7 +1885,7 @@ extern "C" bdem_status bdem_autotune_pcg(bdem_sim* s, int32_t iters, int32_t* la
       for (int rep = 0; rep < 2; ++rep) {
         std::vector<SceneCtl> ctl(s->n_scenes);
         CUDA_TRY(s, cudaMemcpy(ctl.data(), d.sc, sizeof(SceneCtl) * s->n_scenes, cudaMemcpyDeviceToHost));
-        for (auto& c : ctl) { c.newton_active = 1; c.eps_r = 0.0; }
+        for (auto& c : ctl) { c.newton_active = 1; c.pcg_skip = 0; c.eps_r = 0.0; }
         CUDA_TRY(s, cudaMemcpy(d.sc, ctl.data(), sizeof(SceneCtl) * s->n_scenes, cudaMemcpyHostToDevice));
         cudaEventRecord(a, s->stream);
         TRY(run_pcg(s, d, 1, 1));

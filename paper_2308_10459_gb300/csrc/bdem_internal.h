@@ -55,6 +55,14 @@ struct SceneCtl {
   int32_t bonds_broken;
   int32_t pad1;                 // halvings in the current line search
   int32_t pad2;                 // contact candidates of the step
+  // FP64-residual refinement of the mixed-precision Newton solve (DevArrays::refine > 0)
+  double eps_out, b_out;        // the solve's relative target eps_r and |b| (the first PCG launch's)
+  double res64;                 // |b - H dx| of the accumulated FP64 solution after the last round
+  double lin_res;               // |b - H dx| / |b| of the last completed solve (-1: not evaluated)
+  int32_t pcg_skip;             // 1: the scene takes no part in the current PCG launch (its solve is complete)
+  int32_t refine_round;         // refinement rounds of the current solve
+  int32_t pcg_acc;              // PCG iterations of the current solve over its rounds
+  int32_t refine_total;         // refinement rounds in this step
 };
 
 struct Counters {               // small device-side summary read by the host after reductions
@@ -70,6 +78,8 @@ struct Counters {               // small device-side summary read by the host af
   int32_t loops_ls;             // trials of the current line search
   int32_t ls_total;             // line-search trials in this step
   unsigned int never;           // written by nothing: the word the wait test waits on
+  int32_t loops_refine;         // refinement rounds in this step (graph path: trips of the refinement loop)
+  int32_t pad_c;
 };
 
 struct DevArrays {
@@ -78,12 +88,16 @@ struct DevArrays {
   int32_t c_cap;                // capacity of the contact arrays
   int32_t hash_size;            // power of two
   double dt, gx, gy, gz, tol, ground_z, k_ground, k_self, skin, cell_h;
+  double tol_abs;               // absolute Newton tolerance (0: off)
   double mu_slide, mu_roll;     // friction coefficients of the post-step correction (0: off)
   unsigned long long wait_ns;   // time limit of every device-side wait
   int32_t newton_max, pcg_max, ls_max;
   int32_t stress_on;            // some bond has a finite tensile or shear strength
   int32_t first_order;          // descent direction -g (Alg. 1) instead of the Newton direction
   int32_t midpoint;             // variational midpoint form: potentials at (x + x0)/2, inertia targets zhat
+  int32_t refine;               // rounds of FP64-residual refinement per Newton solve (0: off; mixed + block Jacobi)
+  double* x64;                  // [N][6] FP64 accumulated solution of the refined solve (refine > 0)
+  double* b64;                  // [N][6] FP64 right-hand side of an inspection solve (NULL: b = -g)
   // particles
   double4 *xp, *xq, *x0p, *x0q, *vp, *vq, *hp, *hq, *tp, *tq;
   double2* coef;
@@ -171,7 +185,8 @@ int launch_particle_grad(const DevArrays& d, int mask_kin, int all_scenes, cudaS
 int launch_bond_hess(const DevArrays& d, int all_scenes, cudaStream_t s);
 int launch_particle_hess(const DevArrays& d, int mask_kin, int all_scenes, cudaStream_t s);
 // reduction modes of the per-scene reduce kernel
-enum ReduceMode { RED_GRAD = 0, RED_GDX = 1, RED_LS = 2, RED_FORCE_ACTIVE = 3, RED_CAND = 4 };
+enum ReduceMode { RED_GRAD = 0, RED_GDX = 1, RED_LS = 2, RED_FORCE_ACTIVE = 3, RED_CAND = 4, RED_REFINE0 = 5,
+                  RED_REFINE = 6 };
 // cond: 0, or the conditional handle of the device-driven loop that this reduction controls in the step graph
 // (RED_GRAD: the Newton loop, RED_GDX and RED_LS: the line-search loop)
 int launch_scene_reduce(const DevArrays& d, int mode, unsigned long long cond, cudaStream_t s);
@@ -185,6 +200,12 @@ int launch_ls_energy(const DevArrays& d, cudaStream_t s);
 int launch_ls_commit(const DevArrays& d, cudaStream_t s);
 int launch_finish(const DevArrays& d, cudaStream_t s);
 int launch_matvec(const DevArrays& d, int mask_kin, cudaStream_t s);  // vq_ = H vp_
+// y64 = H x64 in FP64 arithmetic on the stored blocks (both [N][6] double, internal order)
+int launch_matvec64(const DevArrays& d, const double* x64, double* y64, int mask_kin, cudaStream_t s);
+// FP64-residual refinement: first = 1 sets x64 = x (the PCG solution), else x64 += x, for the scenes of the last PCG
+// launch; then r = b - H x64 in FP64 (b = -g, or b64 when set), r rounded into vr for the next PCG launch, and the
+// per-tile |r|^2 partials (reduced by RED_REFINE0 / RED_REFINE)
+int launch_refine(const DevArrays& d, int first, cudaStream_t s);
 int launch_unpack_bond_hess(const DevArrays& d, double* out, const int32_t* ids, int count, cudaStream_t s);
 int launch_unpack_diag(const DevArrays& d, double* out /*device [n][36]*/, cudaStream_t s);
 int launch_bond_stress(const DevArrays& d, double* out /*device [nb][2], caller bond order*/, cudaStream_t s);

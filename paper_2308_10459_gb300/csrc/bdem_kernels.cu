@@ -16,6 +16,8 @@
 // Every reduction is deterministic: per-tile partial sums (fixed order) reduced per scene in tile order.
 #include <math.h>
 
+#include <atomic>
+
 #include "bdem_device.cuh"
 #include "bdem_internal.h"
 
@@ -154,10 +156,12 @@ __global__ void k_step_init(DevArrays d) {
     d.cnt->loops_newton = 0;
     d.cnt->loops_ls = 0;
     d.cnt->ls_total = 0;
+    d.cnt->loops_refine = 0;
   }
   if (s >= d.n_scenes) return;
   SceneCtl c = {};
   c.newton_active = 1;
+  c.lin_res = -1.0;
   d.sc[s] = c;
 }
 
@@ -698,34 +702,43 @@ __device__ __forceinline__ void load_words(const double* src, double (&dst)[NW])
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void sym6_mul(const T* Pg, const T (&x)[6], T (&y)[6]) {
-  T P[kDiagStride];
-  load_words<kDiagStride>(Pg, P);
+// a stored symmetric 6x6 block (words of type TS) times x, in arithmetic of type TA
+template <typename TS, typename TA>
+__device__ __forceinline__ void sym6_mul_as(const TS* Pg, const TA (&x)[6], TA (&y)[6]) {
+  TS Ps[kDiagStride];
+  load_words<kDiagStride>(Pg, Ps);
 #pragma unroll
   for (int a = 0; a < 6; ++a) {
-    T s = 0;
+    TA s = 0;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) s += P[sidx<6>(a, c)] * x[c];
+    for (int c = 0; c < 6; ++c) s += (TA)Ps[sidx<6>(a, c)] * x[c];
     y[a] = s;
   }
 }
-
-// one off-diagonal bond block times the other endpoint's vector, added to y
 template <typename T>
-__device__ __forceinline__ void bond_block_mul(const T* Mg, int side, const Vec6<T>& xo, T (&y)[6]) {
-  T M[36];
-  load_words<36>(Mg, M);
-  T a0 = xo.v[0], a1 = xo.v[1], a2 = xo.v[2], b0 = xo.v[3], b1 = xo.v[4], b2 = xo.v[5];
-  T Ah[6];
+__device__ __forceinline__ void sym6_mul(const T* Pg, const T (&x)[6], T (&y)[6]) {
+  sym6_mul_as<T, T>(Pg, x, y);
+}
+
+// one off-diagonal bond block (stored words of type TS) times the other endpoint's vector, added to y (arithmetic
+// of type TA)
+template <typename TS, typename TA>
+__device__ __forceinline__ void bond_block_mul_as(const TS* Mg, int side, const Vec6<TA>& xo, TA (&y)[6]) {
+  TS Ms[36];
+  load_words<36>(Mg, Ms);
+  TA M[36];
+#pragma unroll
+  for (int k = 0; k < 36; ++k) M[k] = (TA)Ms[k];
+  TA a0 = xo.v[0], a1 = xo.v[1], a2 = xo.v[2], b0 = xo.v[3], b1 = xo.v[4], b2 = xo.v[5];
+  TA Ah[6];
 #pragma unroll
   for (int k = 0; k < 6; ++k) Ah[k] = M[k];
   y[0] -= Ah[0] * a0 + Ah[1] * a1 + Ah[2] * a2;
   y[1] -= Ah[1] * a0 + Ah[3] * a1 + Ah[4] * a2;
   y[2] -= Ah[2] * a0 + Ah[4] * a1 + Ah[5] * a2;
-  const T* Bs = M + 6;
-  const T* Cs = M + 15;
-  const T* F = M + 24;
+  const TA* Bs = M + 6;
+  const TA* Cs = M + 15;
+  const TA* F = M + 24;
   if (!side) {  // the row is i (= bi): H_ij = [[-Ah, -Cs], [Bs^T, F]]
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
@@ -739,6 +752,10 @@ __device__ __forceinline__ void bond_block_mul(const T* Mg, int side, const Vec6
       y[3 + r] += -(Cs[r] * a0 + Cs[3 + r] * a1 + Cs[6 + r] * a2) + F[r] * b0 + F[3 + r] * b1 + F[6 + r] * b2;
     }
   }
+}
+template <typename T>
+__device__ __forceinline__ void bond_block_mul(const T* Mg, int side, const Vec6<T>& xo, T (&y)[6]) {
+  bond_block_mul_as<T, T>(Mg, side, xo, y);
 }
 
 // entry k of row i (bonds first, then active contacts), added to y
@@ -776,6 +793,10 @@ __global__ void __launch_bounds__(kTile) k_matvec(DevArrays d, int mask) {
 }
 
 // ================================================================================================
+// a scene takes part in a PCG launch while its Newton loop runs and its current solve is not complete (the
+// FP64-residual refinement re-solves only the scenes whose true residual is still above the target)
+__device__ __forceinline__ bool pcg_on(const SceneCtl& c) { return c.newton_active && !c.pcg_skip; }
+
 // persistent PCG (Sec. 5.3) in the Chronopoulos-Gear arrangement: per iteration one product w = H z fused with the
 // three dot products (r.z, w.z, r.r) and one grid-wide reduction, then one vector update. In exact arithmetic it
 // produces the iterates of the textbook PCG (x0 = 0, block-Jacobi preconditioner, stop at |r| <= eps_r |b| or the
@@ -859,7 +880,8 @@ struct PcgPrev {
   double eps_r, bnorm, rz, alpha, beta, pq, thr2;
 };
 __device__ __forceinline__ PcgPrev load_prev(const SceneCtl* c) {
-  return {__ldcg(&c->newton_active), __ldcg(&c->pcg_active), __ldcg(&c->pcg_iters), __ldcg(&c->eps_r),
+  return {__ldcg(&c->newton_active) && !__ldcg(&c->pcg_skip), __ldcg(&c->pcg_active), __ldcg(&c->pcg_iters),
+          __ldcg(&c->eps_r),
           __ldcg(&c->bnorm), __ldcg(&c->rz), __ldcg(&c->alpha), __ldcg(&c->beta), __ldcg(&c->pq),
           __ldcg(&c->pcg_thr2)};
 }
@@ -1099,8 +1121,8 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
   const bool local = d.n_scenes <= kLocalScenes;
   if (local && threadIdx.x < d.n_scenes) {
     const SceneCtl* c = d.sc + threadIdx.x;
-    s_loc.st[threadIdx.x] = PcgState{c->newton_active, c->newton_active, 0, c->eps_r, 0.0, 0.0, 0.0, 0.0, 0.0,
-                                     0.0, 0.0, 0.0};
+    int on = pcg_on(*c);
+    s_loc.st[threadIdx.x] = PcgState{on, on, 0, c->eps_r, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   }
   __syncthreads();
   // the elementwise phases (init and B) use the equal-rows partition: their cost is per row, while the product's
@@ -1109,7 +1131,7 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
   // ---- init: x = p = s = 0, r = b, z = M^-1 r
   for (int g = useg0; g < useg1; ++g) {
     int sc = d.useg_scene[g];
-    if (!d.sc[sc].newton_active) continue;
+    if (!pcg_on(d.sc[sc])) continue;
     for (int i = d.useg_row[g] + threadIdx.x; i < d.useg_row[g + 1]; i += blockDim.x) {
       T r[6], z[6];
       if (rhs_from_g) {
@@ -1139,7 +1161,7 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
     for (int g = seg0; g < seg1; ++g) {
       int sc = d.seg_scene[g];
       bool act = local ? s_loc.st[sc].pcg_active != 0
-                       : d.sc[sc].newton_active && (k_iter == 0 || __ldcg(&d.sc[sc].pcg_active));
+                       : pcg_on(d.sc[sc]) && (k_iter == 0 || __ldcg(&d.sc[sc].pcg_active));
       DotAcc<T> dg, dd, dr;
       if (act) {
         int r0 = d.seg_row[g], r1 = d.seg_row[g + 1];
@@ -1221,7 +1243,7 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
         al = (T)s_loc.st[sc].alpha;
         be = (T)s_loc.st[sc].beta;
       } else {
-        if (!d.sc[sc].newton_active || !__ldcg(&d.sc[sc].pcg_active)) continue;
+        if (!pcg_on(d.sc[sc]) || !__ldcg(&d.sc[sc].pcg_active)) continue;
         al = (T)__ldcg(&d.sc[sc].alpha);
         be = (T)__ldcg(&d.sc[sc].beta);
       }
@@ -1282,13 +1304,14 @@ __global__ void k_scene_reduce(DevArrays d, int mode, unsigned long long cond) {
       double gn = sqrt(v);
       if (c->newton_iters == 0) c->g0 = gn;  // first residual of the step
       c->gnorm = gn;
-      if (gn <= d.tol * c->g0) {
+      if (gn <= d.tol * c->g0 || gn <= d.tol_abs) {
         c->newton_active = 0;
       } else if (c->newton_iters >= d.newton_max) {
         c->newton_active = 0;
         c->status = 4;
       } else {
         c->eps_r = fmin(0.5, sqrt(gn));
+        c->pcg_skip = 0;
         ++cnt;
       }
     } else if (mode == RED_GDX) {
@@ -1299,8 +1322,9 @@ __global__ void k_scene_reduce(DevArrays d, int mode, unsigned long long cond) {
       c->ls_state = 0;
       c->pad1 = 0;  // halvings in this line search
       c->newton_iters += 1;
-      c->pcg_total += c->pcg_iters;
-      c->act_pcg += c->act_cur * (long long)c->pcg_iters;
+      int its = d.refine ? c->pcg_acc : c->pcg_iters;  // every round of a refined solve
+      c->pcg_total += its;
+      c->act_pcg += c->act_cur * (long long)its;
       ++cnt;
     } else if (mode == RED_LS) {
       if (!c->newton_active || c->ls_state != 0) continue;
@@ -1319,8 +1343,36 @@ __global__ void k_scene_reduce(DevArrays d, int mode, unsigned long long cond) {
           ++cnt;
         }
       }
+    } else if (mode == RED_REFINE0 || mode == RED_REFINE) {
+      // after a PCG launch: v = |b - H x64|^2 of the accumulated FP64 solution. The solve is complete when the true
+      // residual meets the Newton solve's target eps_r |b|, after d.refine rounds, when a round did not reduce the
+      // residual, or when the solve has used pcg_max iterations; otherwise the next round solves H d = r with the
+      // relative target eps_r |b| / |r|, which reaches the solve's target where the FP32 recurrence is exact
+      if (!pcg_on(*c)) continue;
+      double res = sqrt(v);
+      if (mode == RED_REFINE0) {
+        c->eps_out = c->eps_r;
+        c->b_out = c->bnorm;
+        c->pcg_acc = c->pcg_iters;
+        c->refine_round = 0;
+      } else {
+        c->pcg_acc += c->pcg_iters;
+      }
+      double tgt = c->eps_out * c->b_out;
+      bool worse = mode == RED_REFINE && !(res < c->res64);
+      c->lin_res = c->b_out > 0.0 ? res / c->b_out : 0.0;
+      c->res64 = res;
+      if (!(res > tgt) || c->refine_round >= d.refine || worse || c->pcg_acc >= d.pcg_max || !isfinite(res)) {
+        c->pcg_skip = 1;
+      } else {
+        c->refine_round += 1;
+        c->refine_total += 1;
+        c->eps_r = tgt / res;
+        ++cnt;
+      }
     } else if (mode == RED_FORCE_ACTIVE) {
       c->newton_active = 1;
+      c->pcg_skip = 0;
       ++cnt;
     } else if (mode == RED_CAND) {
       int a = d.ptile_start[d.ptile_begin[s]], b = d.ptile_start[d.ptile_begin[s + 1]];
@@ -1345,11 +1397,96 @@ __global__ void k_scene_reduce(DevArrays d, int mode, unsigned long long cond) {
         int trials = ++d.cnt->loops_ls;
         d.cnt->ls_total += 1;
         if (trials >= d.ls_max + 2) go = 0;
+      } else if (mode == RED_REFINE) {
+        d.cnt->loops_refine += 1;
       }
       if (step_aborted(d)) go = 0;
       cudaGraphSetConditional((cudaGraphConditionalHandle)cond, go);
     }
   }
+}
+
+// ================================================================================================
+// FP64 products and the FP64-residual refinement of the mixed-precision Newton solve
+// ================================================================================================
+
+// row i of y = H x in FP64 arithmetic on the stored blocks of type T (x [N][6] FP64, internal order). The products of
+// FP32 words in FP64 are exact, so the only rounding is that of the FP64 sums: this is the true product of the
+// matrix the PCG iterates with.
+template <typename T>
+__device__ __forceinline__ void row_product64(const DevArrays& d, int i, const double* x, double (&y)[6]) {
+  Vec6<double> xi = load6<double>(x, i);
+  sym6_mul_as<T, double>(reinterpret_cast<const T*>(d.D) + kDiagStride * (size_t)i, xi.v, y);
+  const int a = d.inc_start[i], nbond = d.inc_start[i + 1] - a;
+  const T* Mall = reinterpret_cast<const T*>(d.bM);
+  for (int k = 0; k < nbond; ++k) {
+    int2 e = d.inc2[a + k];
+    Vec6<double> xo = load6<double>(x, e.y);
+    bond_block_mul_as<T, double>(Mall + 36 * (size_t)(e.x >> 1), e.x & 1, xo, y);
+  }
+  if (d.k_self > 0.0) {
+    const int na = d.c_act[i];
+    for (int k = 0; k < na; ++k) {
+      int e = d.c_start[i] + k;
+      T4<T> c = reinterpret_cast<const T4<T>*>(d.c_blk)[e];
+      Vec6<double> xo = load6<double>(x, d.c_anbr[e]);
+      double cx = (double)c.x, cy = (double)c.y, cz = (double)c.z;
+      double t = (double)c.w * (cx * xo.v[0] + cy * xo.v[1] + cz * xo.v[2]);
+      y[0] -= t * cx;
+      y[1] -= t * cy;
+      y[2] -= t * cz;
+    }
+  }
+}
+
+// y = H x in FP64 (inspection product; mask: kinematic rows give 0)
+template <typename T>
+__global__ void __launch_bounds__(kTile) k_matvec64(DevArrays d, const double* x, double* y, int mask) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  if (!(mask && d.kin[i])) row_product64<T>(d, i, x, v);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) y[6 * (size_t)i + k] = v[k];
+}
+
+// x64 = x (first) or x64 += x for the rows of the scenes that solved in the last PCG launch
+template <typename T>
+__global__ void k_refine_acc(DevArrays d, int first) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n || !pcg_on(d.sc[d.pscene[i]])) return;
+  Vec6<T> x = load6<T>(reinterpret_cast<const T*>(d.vx), i);
+  double* o = d.x64 + 6 * (size_t)i;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) o[k] = (first ? 0.0 : o[k]) + (double)x.v[k];
+}
+
+// r = b - H x64 in FP64 for the rows of the scenes that solved in the last PCG launch (b = -g, or b64 for an
+// inspection solve; kinematic rows 0), r rounded into vr as the next launch's right-hand side, per-tile |r|^2
+template <typename T>
+__global__ void __launch_bounds__(kTile) k_refine_res(DevArrays d) {
+  int t = blockIdx.x;
+  int i = d.ptile_start[t] + threadIdx.x;
+  double acc[1] = {0.0};
+  if (i < d.ptile_start[t + 1] && pcg_on(d.sc[d.ptile_scene[t]])) {
+    double r[6] = {0, 0, 0, 0, 0, 0};
+    if (!d.kin[i]) {
+      double y[6];
+      row_product64<T>(d, i, d.x64, y);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        double b = d.b64 ? d.b64[6 * (size_t)i + k] : -d.g[6 * (size_t)i + k];
+        r[k] = b - y[k];
+        acc[0] += r[k] * r[k];
+      }
+    }
+    T rt[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) rt[k] = (T)r[k];
+    store6<T>(reinterpret_cast<T*>(d.vr), i, rt);
+  }
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) d.part_p[kPartials * t] = acc[0];
 }
 
 // partial g . dx for the descent check
@@ -1361,9 +1498,15 @@ __global__ void __launch_bounds__(kTile) k_gdx(DevArrays d) {
   double acc[1] = {0.0};
   if (i < d.ptile_start[t + 1] && d.sc[s].newton_active) {
     const double* g = d.g + 6 * (size_t)i;
-    Vec6<T> x = load6<T>(reinterpret_cast<const T*>(d.vx), i);
+    if (d.refine) {
+      const double* x = d.x64 + 6 * (size_t)i;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) acc[0] += g[k] * (double)x.v[k];
+      for (int k = 0; k < 6; ++k) acc[0] += g[k] * x[k];
+    } else {
+      Vec6<T> x = load6<T>(reinterpret_cast<const T*>(d.vx), i);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc[0] += g[k] * (double)x.v[k];
+    }
   }
   block_sum<1>(acc);
   if (threadIdx.x == 0) d.part_p[kPartials * t] = acc[0];
@@ -1390,6 +1533,9 @@ __global__ void k_ls_trial(DevArrays d) {
     const double* g = d.g + 6 * (size_t)i;
 #pragma unroll
     for (int k = 0; k < 6; ++k) st[k] = -g[k];
+  } else if (d.refine) {  // the refined FP64 solution
+#pragma unroll
+    for (int k = 0; k < 6; ++k) st[k] = d.x64[6 * (size_t)i + k];
   } else {
     Vec6<T> x = load6<T>(reinterpret_cast<const T*>(d.vx), i);
 #pragma unroll
@@ -1731,19 +1877,21 @@ size_t static_pcg_capacity() { return kStaticPcgBytes; }
 
 // Device address of the static array for the current device. The first call on a device looks the symbol up
 // (cudaGetSymbolAddress) with that device current and caches it; later calls reuse the cached address.
+// The cache entries are atomics: two host threads making their first call on one device may both look the address
+// up, and both store the same value.
 cudaError_t static_pcg_address(void** out) {
-  static void* cache[256] = {nullptr};
+  static std::atomic<void*> cache[256];
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
-  if (cache[dev] == nullptr) {
-    void* p = nullptr;
+  void* p = cache[dev].load(std::memory_order_acquire);
+  if (p == nullptr) {
     e = cudaGetSymbolAddress(&p, g_static_pcg_scratch);
     if (e != cudaSuccess) return e;
-    cache[dev] = p;
+    cache[dev].store(p, std::memory_order_release);
   }
-  *out = cache[dev];
+  *out = p;
   return cudaSuccess;
 }
 
@@ -1901,6 +2049,25 @@ int launch_pcg(const DevArrays& d, int rhs_from_g, int mask, cudaStream_t s, cud
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   *err = cudaLaunchCooperativeKernel(k, d.pcg_grid, kTile, args, smem, s);
   return 1;
+}
+
+int launch_matvec64(const DevArrays& d, const double* x64, double* y64, int mask, cudaStream_t s) {
+  if (d.n == 0) return 0;
+  if (d.mixed) k_matvec64<float><<<blocks_for(d.n, kTile), kTile, 0, s>>>(d, x64, y64, mask);
+  else k_matvec64<double><<<blocks_for(d.n, kTile), kTile, 0, s>>>(d, x64, y64, mask);
+  return 1;
+}
+
+int launch_refine(const DevArrays& d, int first, cudaStream_t s) {
+  if (d.n == 0 || !d.refine || d.n_ptiles == 0) return 0;
+  if (d.mixed) {
+    k_refine_acc<float><<<blocks_for(d.n, 256), 256, 0, s>>>(d, first);
+    k_refine_res<float><<<d.n_ptiles, kTile, 0, s>>>(d);
+  } else {
+    k_refine_acc<double><<<blocks_for(d.n, 256), 256, 0, s>>>(d, first);
+    k_refine_res<double><<<d.n_ptiles, kTile, 0, s>>>(d);
+  }
+  return 2;
 }
 
 int launch_gdx(const DevArrays& d, cudaStream_t s) {

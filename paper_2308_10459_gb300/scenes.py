@@ -80,7 +80,8 @@ class Scene:
 def default_config(**kw) -> dict:
     c = dict(dt=1e-3, gravity=(0.0, 0.0, -9.81), newton_rel_tol=1e-6, newton_max_iter=100, pcg_max_iter=1000,
              ls_max_halvings=30, ground_z=0.0, k_ground=0.0, k_self=0.0, contact_skin=0.0, friction_slide=0.0,
-             friction_roll=0.0, optimizer=0, integrator=0, preconditioner=0, steps=100)
+             friction_roll=0.0, optimizer=0, integrator=0, preconditioner=0, newton_abs_tol=0.0, pcg_refine=4,
+             steps=100)
     c.update(kw)
     return c
 
