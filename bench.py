@@ -310,6 +310,7 @@ def pcg_probe(args, sc, sim, pkg, torch):
     if args.warmup:
         sim.step(args.warmup)
     if args.pcg_lanes:
+        sim.set_pcg_product(args.pcg_product)
         sim.set_pcg_shape(args.pcg_lanes, args.pcg_blocks)
     st = sim.read_state()
     dt = sc.config["dt"]
@@ -323,7 +324,7 @@ def pcg_probe(args, sc, sim, pkg, torch):
     line = {"probe": "pcg", "iters": int(it[0]), "seconds_incl_transfers": t, "n": sc.n, "nb": sc.nb,
             "algorithmic_bytes_per_iter_without_contacts": pcg_bytes_per_iter(sc.n, sc.nb, 0, 4),
             "fixed_bytes_per_launch": pcg_bytes_per_launch_fixed(sc.n, sc.nb),
-            "lanes": args.pcg_lanes}
+            "lanes": args.pcg_lanes, "shape": sim.pcg_shape()}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -371,11 +372,12 @@ def measure_mixed(sc, args, steps, world, torch, pkg, amg, trec, e2e_on, clocks=
     if amg:
         shape = None  # the AMG-preconditioned solve runs as host-driven kernels, not the persistent PCG
     elif args.pcg_lanes:
+        sim.set_pcg_product(args.pcg_product)
         sim.set_pcg_shape(args.pcg_lanes, args.pcg_blocks)
-        shape = {"lanes_per_row": args.pcg_lanes, "blocks": args.pcg_blocks, "autotuned": False}
+        shape = dict(sim.pcg_shape(), autotuned=False)
     else:
-        lanes, blocks = sim.autotune_pcg(30)
-        shape = {"lanes_per_row": lanes, "blocks": blocks, "autotuned": True}
+        sim.autotune_pcg(30)
+        shape = dict(sim.pcg_shape(), autotuned=True)
     sizes = np.diff(sc.scene_offsets)
     sim.step(1)  # captures the step graph for the chosen PCG shape outside the timed region
     ck = sim.read_state()
@@ -438,6 +440,8 @@ def main():
                     help="steps of the 64-scene batched workload measured beside the plate (0: skip)")
     ap.add_argument("--pcg-lanes", type=int, default=0, help="lanes per row of the PCG product (0: autotune)")
     ap.add_argument("--pcg-blocks", type=int, default=0, help="PCG grid size with --pcg-lanes (0: all resident)")
+    ap.add_argument("--pcg-product", type=int, default=1, choices=[0, 1],
+                    help="with --pcg-lanes: 1 warp-cooperative staging of the bond blocks, 0 per-lane loads")
     ap.add_argument("--pcg-probe", type=int, default=0,
                     help="time N PCG iterations of one solve (eps 0) on the workload's system and exit (profiling)")
     ap.add_argument("--workload", default="plate", choices=["plate", "batched", "impact"],

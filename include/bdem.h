@@ -29,6 +29,7 @@
 #ifndef BDEM_H
 #define BDEM_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -67,6 +68,17 @@ typedef struct {
   double tensile_strength;  /* sigma_c > 0 of the stress fracture criterion (Sec. 3.2); +inf: off */
   double shear_strength;    /* tau_c > 0 of the stress fracture criterion; +inf: off */
 } bdem_material;
+
+/* Optional device-memory hook (bdem_config.allocator): every device buffer a simulation owns is obtained from alloc
+ * and returned to free, with ctx passed through and cuda_stream the library's stream, e.g. to draw from a caller's
+ * memory pool such as PyTorch's caching allocator. alloc returns NULL on failure (the call then fails with
+ * BDEM_E_NOMEM) and must return memory aligned to 256 bytes that stays valid until free; the library clears it on its
+ * stream. The hook's functions are called from the host thread that calls the library, until bdem_destroy returns. */
+typedef struct {
+  void* (*alloc)(void* ctx, size_t bytes, void* cuda_stream);
+  void (*free)(void* ctx, void* ptr, void* cuda_stream);
+  void* ctx;
+} bdem_allocator;
 
 typedef struct {
   double dt;                /* time step > 0 */
@@ -122,6 +134,7 @@ typedef struct {
                                eps_r |b| / |r|), at most pcg_refine times, stopping early when |r| grows; the
                                line search takes the FP64 direction */
   int32_t reserved0;        /* set to 0 */
+  const bdem_allocator* allocator; /* NULL: cudaMalloc / cudaFree; else the hook, copied by bdem_create */
 } bdem_config;
 
 /* Per-scene statistics of one bdem_step call (sums over its steps, norms of the last step). */
@@ -267,9 +280,19 @@ int64_t bdem_launch_count(const bdem_sim* sim);
 bdem_status bdem_set_pcg_shape(bdem_sim* sim, int32_t lanes_per_row, int32_t blocks);
 
 
+/* How the PCG product reaches the off-diagonal bond blocks: product = 1 (default): in waves of one entry per thread,
+ * each warp first copies its wave's 32 blocks into shared memory with 16-byte asynchronous copies taken by
+ * consecutive threads from the same block (few cache lines per request); product = 0: each thread loads its own
+ * entries' blocks (with the row descriptors and incidence entries staged in shared memory when they fit). Both give
+ * the same sums in the same order. Keeps the lanes and grid (the grid shrinks if the blocks no longer fit). */
+bdem_status bdem_set_pcg_product(bdem_sim* sim, int32_t product);
+
+/* The current PCG launch shape: lanes per row, grid size and product (as bdem_set_pcg_product); NULL skips. */
+bdem_status bdem_get_pcg_shape(const bdem_sim* sim, int32_t* lanes_per_row, int32_t* blocks, int32_t* product);
+
 /* Times the PCG kernel for `iters` iterations on the system at the current committed state for each candidate shape
- * (lanes 1, 2, 4, 8 x 1..all co-resident blocks per SM), keeps the fastest, and reports it (either pointer may be
- * NULL). Host-blocking. */
+ * (product 1 and 0 x lanes 1, 2, 4, 8 x 1..all co-resident blocks per SM), keeps the fastest, and reports its lanes
+ * and grid (either pointer may be NULL; bdem_get_pcg_shape gives the product). Host-blocking. */
 bdem_status bdem_autotune_pcg(bdem_sim* sim, int32_t iters, int32_t* lanes_per_row, int32_t* blocks);
 
 /* ---- allocation-free solve ---------------------------------------------------------------------------------------

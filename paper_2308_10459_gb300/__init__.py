@@ -32,6 +32,14 @@ class bdem_material(ctypes.Structure):
                 ("shear_strength", ctypes.c_double)]
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class bdem_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
 class bdem_config(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("gravity", ctypes.c_double * 3), ("newton_rel_tol", ctypes.c_double),
                 ("newton_max_iter", ctypes.c_int32), ("pcg_max_iter", ctypes.c_int32),
@@ -40,7 +48,8 @@ class bdem_config(ctypes.Structure):
                 ("spd_mode", ctypes.c_int32), ("optimizer", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
                 ("friction_slide", ctypes.c_double), ("friction_roll", ctypes.c_double),
                 ("integrator", ctypes.c_int32), ("preconditioner", ctypes.c_int32),
-                ("newton_abs_tol", ctypes.c_double), ("pcg_refine", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+                ("newton_abs_tol", ctypes.c_double), ("pcg_refine", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("allocator", ctypes.POINTER(bdem_allocator))]
 
 
 class bdem_step_stats(ctypes.Structure):
@@ -94,6 +103,8 @@ _PROTOS = {
     "bdem_pcg_static": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int32, _ip]),
     "bdem_set_pcg_shape": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
     "bdem_autotune_pcg": (ctypes.c_int, [_vp, ctypes.c_int32, _ip, _ip]),
+    "bdem_set_pcg_product": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "bdem_get_pcg_shape": (ctypes.c_int, [_vp, _ip, _ip, _ip]),
     "bdem_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "bdem_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(bdem_profile)]),
 }
@@ -136,6 +147,36 @@ def _arr(a, dtype, shape=None):
 
 def _ptr(a, ct):
     return None if a is None else a.ctypes.data_as(ct)
+
+
+class TorchAllocator:
+    """A bdem_allocator hook that takes the library's device buffers from PyTorch's caching allocator (on the
+    library's stream) and returns them to it. Keep the object alive while a simulation created with it exists."""
+
+    def __init__(self, device=None):
+        import torch
+        self.torch = torch
+        self.device = torch.cuda.current_device() if device is None else device
+        self.live = {}
+        self.calls = 0
+
+        def _alloc(ctx, nbytes, stream):
+            try:
+                ptr = torch.cuda.caching_allocator_alloc(int(nbytes), self.device, stream or 0)
+            except Exception:
+                return None
+            self.live[ptr] = int(nbytes)
+            self.calls += 1
+            return ptr
+
+        def _free(ctx, ptr, stream):
+            if ptr in self.live:
+                del self.live[ptr]
+                torch.cuda.caching_allocator_delete(ptr)
+
+        self._alloc = ALLOC_FN(_alloc)  # the C function pointers must outlive every call through them
+        self._free = FREE_FN(_free)
+        self.struct = bdem_allocator(self._alloc, self._free, None)
 
 
 def make_config(cfg: dict, precision=BDEM_FP64, cuda_stream=None) -> bdem_config:
@@ -192,7 +233,7 @@ def bdem_create(config: bdem_config, scene_offsets, pos, quat, vel, quat_vel, ra
 class Sim:
     """Owns one bdem_sim. Methods mirror the C entry points."""
 
-    def __init__(self, scene, precision=BDEM_FP64, config=None, cuda_stream=None):
+    def __init__(self, scene, precision=BDEM_FP64, config=None, cuda_stream=None, allocator=None):
         cfg = dict(scene.config)
         if config:
             cfg.update(config)
@@ -200,6 +241,9 @@ class Sim:
         self.cfg = cfg
         self.precision = precision
         self.config = make_config(cfg, precision, cuda_stream)
+        self.allocator = allocator  # a TorchAllocator (or any object with a bdem_allocator .struct), kept alive here
+        if allocator is not None:
+            self.config.allocator = ctypes.pointer(allocator.struct)
         self.L = load()
         self.h = bdem_create(self.config, scene.scene_offsets, scene.pos, scene.quat, scene.vel, scene.quat_vel,
                              scene.radius, scene.material, scene.materials, scene.kinematic)
@@ -324,6 +368,14 @@ class Sim:
 
     def set_pcg_shape(self, lanes_per_row, blocks=0):
         self._check(self.L.bdem_set_pcg_shape(self.h, int(lanes_per_row), int(blocks)))
+
+    def set_pcg_product(self, product):
+        self._check(self.L.bdem_set_pcg_product(self.h, int(product)))
+
+    def pcg_shape(self):
+        lanes, blocks, product = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self._check(self.L.bdem_get_pcg_shape(self.h, ctypes.byref(lanes), ctypes.byref(blocks), ctypes.byref(product)))
+        return {"lanes_per_row": lanes.value, "blocks": blocks.value, "product": product.value}
 
     def autotune_pcg(self, iters=30):
         l, g = ctypes.c_int32(), ctypes.c_int32()

@@ -19,6 +19,7 @@ using namespace bdem;
 
 struct bdem_sim {
   bdem_config cfg;
+  bdem_allocator hook{};              // caller's device-memory hook (alloc == NULL: cudaMalloc)
   int32_t n = 0, n_scenes = 0;
   int64_t nb = 0;
   cudaStream_t stream = 0;
@@ -39,6 +40,7 @@ struct bdem_sim {
   std::string err;
   int64_t launches = 0;
   int pcg_blocks = 0;
+  int pcg_product = 1;                // 1: warp-cooperative staging of the bond blocks (k_pcg MODE 2); 0: per-lane
   double* dbg_buf = nullptr;          // device scratch of the inspection calls
   size_t dbg_cap = 0;
   double* stage = nullptr;            // device staging for the caller-order state arrays (14 doubles per particle)
@@ -63,7 +65,8 @@ struct bdem_sim {
   cudaGraphExec_t graph_exec = nullptr;
   DevArrays graph_d{};                // the arrays the graph was captured with (kernel arguments are by value)
   cudaStream_t cap[3] = {nullptr, nullptr, nullptr};
-  int g_pre = 0, g_body = 0, g_ls = 0, g_post = 0, g_ref = 0;  // kernels per graph segment
+  int g_pre = 0, g_body = 0, g_ls = 0, g_post = 0, g_ref = 0, g_amg = 0;  // kernels per graph segment
+  AmgDev graph_amg{};                 // the AMG hierarchy the step graph was captured with
   int64_t graph_steps = 0;
   // aggregation AMG preconditioner (bdem_config.preconditioner)
   AmgDev amg{};
@@ -155,9 +158,28 @@ static bdem_status fail(bdem_sim* s, bdem_status st, const char* fmt, ...) {
     if (st_ != BDEM_OK) return st_; \
   } while (0)
 
+// device buffers of the sim: from the caller's allocator hook when one was given, else cudaMalloc; zero-filled
+static void raw_free(bdem_sim* s, void* p) {
+  if (s->hook.alloc) s->hook.free(s->hook.ctx, p, (void*)s->stream);
+  else cudaFree(p);
+}
+
 static bdem_status dalloc(bdem_sim* s, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
+  if (s->hook.alloc) {
+    *p = s->hook.alloc(s->hook.ctx, bytes, (void*)s->stream);
+    if (!*p) return fail(s, BDEM_E_NOMEM, "the allocator hook returned NULL for %zu bytes", bytes);
+    if (reinterpret_cast<uintptr_t>(*p) % 256 != 0) {
+      raw_free(s, *p);
+      *p = nullptr;
+      return fail(s, BDEM_E_INVALID, "the allocator hook returned memory that is not 256-byte aligned");
+    }
+    s->allocs.push_back(*p);
+    cudaError_t e2 = cudaMemsetAsync(*p, 0, bytes, s->stream);
+    if (e2 != cudaSuccess) return fail(s, BDEM_E_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e2));
+    return BDEM_OK;
+  }
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -180,7 +202,7 @@ static void dfree(bdem_sim* s, void* p) {
   if (!p) return;
   auto it = std::find(s->allocs.begin(), s->allocs.end(), p);
   if (it != s->allocs.end()) s->allocs.erase(it);
-  cudaFree(p);
+  raw_free(s, p);
 }
 
 static bool fin(double x) { return std::isfinite(x); }
@@ -391,6 +413,9 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
   const int64_t per_sm = std::max(1, (grid + sms - 1) / std::max(sms, 1));
   const int64_t budget = std::min<int64_t>(200 * 1024, 227 * 1024 / per_sm - 4 * 1024);
   const int staged = max_rows * (int64_t)sizeof(int4) + max_ent * (int64_t)sizeof(int2) <= budget;
+  // the cooperative product stages the row descriptors and one bond block per thread (its grid is shrunk to what is
+  // co-resident with that shared memory by apply_pcg_shape)
+  const int mode = s->pcg_product ? 2 : (staged ? 1 : 0);
   // cuts block row ranges at scene boundaries
   auto cut = [&](const std::vector<int64_t>& bnd, std::vector<int32_t>& row, std::vector<int32_t>& scn,
                  std::vector<int32_t>& blk) {
@@ -445,14 +470,15 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
   d.pcg_lanes = lanes;
   d.pcg_max_rows = (int32_t)std::max<int64_t>(max_rows, 1);
   d.pcg_max_entries = (int32_t)std::max<int64_t>(max_ent, 1);
-  d.pcg_staged = staged;
+  d.pcg_mode = mode;
   return BDEM_OK;
 }
 
 // default PCG launch shape: 4 lanes per row, every co-resident block, at least 64 rows per block
 // co-resident PCG blocks as the registers allow (the partition's shared memory is checked in apply_pcg_shape)
 static int pcg_blocks_by_regs(const bdem_sim* s, int lanes) {
-  return pcg_max_blocks(s->d.mixed, lanes, 1024, 1);
+  int mode = s->pcg_product ? 2 : 1;
+  return pcg_max_blocks(s->d.mixed, lanes, pcg_smem_bytes_for(mode, s->d.mixed, 64, 64), mode);
 }
 
 // builds the partition for (lanes, grid) and shrinks the grid until every block is co-resident with the partition's
@@ -460,7 +486,7 @@ static int pcg_blocks_by_regs(const bdem_sim* s, int lanes) {
 static bdem_status apply_pcg_shape(bdem_sim* s, int lanes, int grid) {
   for (int tries = 0; tries < 16; ++tries) {
     TRY(build_pcg_segments(s, lanes, grid));
-    int mx = pcg_max_blocks(s->d.mixed, lanes, pcg_smem_bytes(s->d), s->d.pcg_staged);
+    int mx = pcg_max_blocks(s->d.mixed, lanes, pcg_smem_bytes(s->d), s->d.pcg_mode);
     if (mx < 1) return fail(s, BDEM_E_CUDA, "no resident blocks for the PCG kernel");
     if (s->d.pcg_grid <= mx) return BDEM_OK;
     grid = mx;
@@ -520,6 +546,14 @@ extern "C" bdem_status bdem_create(const bdem_config* config, int32_t n_scenes, 
   }
   bdem_sim* s = new bdem_sim();
   s->cfg = *config;
+  if (config->allocator) {
+    s->hook = *config->allocator;
+    if (!s->hook.alloc != !s->hook.free) {
+      delete s;
+      return fail(nullptr, BDEM_E_INVALID, "the allocator hook needs both alloc and free");
+    }
+  }
+  s->cfg.allocator = nullptr;  // copied into s->hook
   s->n = (int32_t)n;
   s->n_scenes = n_scenes;
   s->stream = (cudaStream_t)config->cuda_stream;
@@ -1064,8 +1098,32 @@ static bdem_status build_amg(bdem_sim* s) {
   return BDEM_OK;
 }
 
-// PCG with the AMG cycle as preconditioner on the assembled Newton system (host-driven: one residual read per
-// iteration). from_g: b = -g; else b is read from vr (inspection calls). The solution is left in vx.
+static cudaError_t capture_while(cudaStream_t st, cudaGraphConditionalHandle h, cudaGraph_t* body);
+
+// captures one AMG-PCG iteration (q = H p and alpha, the update with the stop test, the cycle, the new direction) on
+// stream st into `body`, closed by the kernel that sets the loop's condition h; returns the kernels per trip
+static int capture_amg_body(bdem_sim* s, const DevArrays& d, cudaGraph_t body, cudaGraphConditionalHandle h,
+                            cudaStream_t st, cudaError_t* err) {
+  *err = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (*err != cudaSuccess) return 0;
+  int k = launch_amg_iteration_begin(d, st);
+  k += launch_amg_pcg_stage(d, s->amg, 2, st);
+  k += launch_amg_pcg_stage(d, s->amg, 3, st);
+  k += launch_amg_cycle(d, s->amg, s->n_scenes, st);
+  k += launch_amg_pcg_stage(d, s->amg, 4, st);
+  k += launch_amg_loop_cond(d, (unsigned long long)h, st);
+  cudaError_t e1 = cudaGetLastError();
+  cudaGraph_t out = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(st, &out);
+  *err = e1 != cudaSuccess ? e1 : e2;
+  return k;
+}
+
+// PCG with the AMG cycle as preconditioner on the assembled Newton system. from_g: b = -g; else b is read from vr
+// (inspection calls). The solution is left in vx. The iterations run as one graph launch whose conditional while node
+// is decided on the device (every scene's stop test, at most pcg_max + 1 trips), so the host neither reads nor waits
+// between iterations; if that graph cannot be captured the same kernels run from a host loop that reads the count of
+// scenes still iterating after each iteration.
 static bdem_status run_amg_pcg(bdem_sim* s, const DevArrays& d, int from_g) {
   if (s->amg_nb != s->nb) TRY(build_amg(s));
   AmgDev& a = s->amg;
@@ -1075,45 +1133,46 @@ static bdem_status run_amg_pcg(bdem_sim* s, const DevArrays& d, int from_g) {
   TRY(check_launch(s, launch_amg_pcg_stage(d, a, from_g ? 0 : 6, st)));
   TRY(check_launch(s, launch_amg_cycle(d, a, s->n_scenes, st)));
   TRY(check_launch(s, launch_amg_pcg_stage(d, a, 1, st)));
-  // one iteration as one graph launch (captured once per set of arrays): q = H p and alpha, the update and stop
-  // test, then the cycle and the new direction (which change nothing for scenes that have stopped)
-  bool use_graph = true;
   if (!s->amg_exec || memcmp(&s->amg_gd, &d, sizeof(DevArrays)) != 0 || memcmp(&s->amg_ga, &a, sizeof(AmgDev)) != 0) {
     if (s->amg_exec) cudaGraphExecDestroy(s->amg_exec);
     s->amg_exec = nullptr;
     if (!s->amg_cap && cudaStreamCreateWithFlags(&s->amg_cap, cudaStreamNonBlocking) != cudaSuccess) s->amg_cap = nullptr;
-    cudaGraph_t g = nullptr;
-    int k = 0;
-    if (s->amg_cap && cudaStreamBeginCapture(s->amg_cap, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
-      cudaMemsetAsync(&d.cnt->n_active, 0, sizeof(int32_t), s->amg_cap);
-      k += launch_amg_pcg_stage(d, a, 2, s->amg_cap);
-      k += launch_amg_pcg_stage(d, a, 3, s->amg_cap);
-      k += launch_amg_cycle(d, a, s->n_scenes, s->amg_cap);
-      k += launch_amg_pcg_stage(d, a, 4, s->amg_cap);
-      cudaError_t e1 = cudaStreamEndCapture(s->amg_cap, &g);
-      if (e1 == cudaSuccess && g && cudaGraphInstantiate(&s->amg_exec, g, 0) == cudaSuccess) {
-        s->amg_gd = d;
-        s->amg_ga = a;
-        s->amg_gk = k;
-      } else {
-        s->amg_exec = nullptr;
-      }
-      if (g) cudaGraphDestroy(g);
+    cudaGraph_t g = nullptr, body = nullptr;
+    cudaGraphConditionalHandle h = 0;
+    cudaError_t e = s->amg_cap ? cudaGraphCreate(&g, 0) : cudaErrorNotReady;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(s->amg_cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      launch_amg_loop_init(d, (unsigned long long)h, s->amg_cap);
+      cudaError_t e1 = cudaGetLastError();
+      if (e1 == cudaSuccess) e1 = capture_while(s->amg_cap, h, &body);
+      cudaGraph_t out = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(s->amg_cap, &out);
+      e = e1 != cudaSuccess ? e1 : e2;
     }
+    int k = 0;
+    if (e == cudaSuccess) k = capture_amg_body(s, d, body, h, s->amg_cap, &e);
+    if (e == cudaSuccess && cudaGraphInstantiate(&s->amg_exec, g, 0) == cudaSuccess) {
+      s->amg_gd = d;
+      s->amg_ga = a;
+      s->amg_gk = k;
+    } else {
+      s->amg_exec = nullptr;
+    }
+    if (g) cudaGraphDestroy(g);
     cudaGetLastError();
-    use_graph = s->amg_exec != nullptr;
+  }
+  if (s->amg_exec) {
+    CUDA_TRY(s, cudaGraphLaunch(s->amg_exec, st));
+    s->launches += 1;  // the loop's kernels are counted from the device's trip count (amg_trip_launches)
+    return BDEM_OK;
   }
   for (int it = 0; it <= d.pcg_max; ++it) {
-    if (use_graph) {
-      CUDA_TRY(s, cudaGraphLaunch(s->amg_exec, st));
-      s->launches += s->amg_gk;
-    } else {
-      CUDA_TRY(s, cudaMemsetAsync(&d.cnt->n_active, 0, sizeof(int32_t), st));
-      TRY(check_launch(s, launch_amg_pcg_stage(d, a, 2, st)));  // q = H p, then alpha
-      TRY(check_launch(s, launch_amg_pcg_stage(d, a, 3, st)));
-      TRY(check_launch(s, launch_amg_cycle(d, a, s->n_scenes, st)));
-      TRY(check_launch(s, launch_amg_pcg_stage(d, a, 4, st)));
-    }
+    CUDA_TRY(s, cudaMemsetAsync(&d.cnt->n_active, 0, sizeof(int32_t), st));
+    TRY(check_launch(s, launch_amg_pcg_stage(d, a, 2, st)));  // q = H p, then alpha
+    TRY(check_launch(s, launch_amg_pcg_stage(d, a, 3, st)));
+    TRY(check_launch(s, launch_amg_cycle(d, a, s->n_scenes, st)));
+    TRY(check_launch(s, launch_amg_pcg_stage(d, a, 4, st)));
     int32_t act = 0;
     CUDA_TRY(s, cudaMemcpyAsync(&act, &d.cnt->n_active, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     TRY(sync(s));
@@ -1182,6 +1241,7 @@ static bdem_status do_step(bdem_sim* s, std::vector<SceneCtl>& ctl) {
     TRY(check_launch(s, launch_ls_commit(d, st)));
     phase_end(s);
   }
+  if (s->amg.on && s->amg_exec) s->launches += (int64_t)c.loops_amg * s->amg_gk;  // trips of the device-driven loop
   phase_begin(s, BDEM_PH_FINISH);
   TRY(check_launch(s, launch_finish(d, st)));
   phase_end(s);
@@ -1241,10 +1301,11 @@ static bool build_step_graph(bdem_sim* s) {
       s->graph_err = "cudaStreamCreateWithFlags failed";
       return false;
     }
-  cudaGraph_t G = nullptr, bodyN = nullptr, bodyL = nullptr, bodyR = nullptr;
-  cudaGraphConditionalHandle hN = 0, hL = 0, hR = 0;
+  cudaGraph_t G = nullptr, bodyN = nullptr, bodyL = nullptr, bodyR = nullptr, bodyA = nullptr;
+  cudaGraphConditionalHandle hN = 0, hL = 0, hR = 0, hA = 0;
   cudaError_t e = cudaSuccess, pe = cudaSuccess, pe2 = cudaSuccess;
-  int pre = 0, body = 0, ls = 0, post = 0, ref = 0;
+  int pre = 0, body = 0, ls = 0, post = 0, ref = 0, amgk = 0;
+  const bool amg = s->amg.on && !d.first_order;
   const char* where = "";
 #define G_TRY(what, call)        \
   do {                           \
@@ -1282,11 +1343,23 @@ static bool build_step_graph(bdem_sim* s) {
   }
   G_TRY("line-search handle", cudaGraphConditionalHandleCreate(&hL, bodyN, 0, 0));
   if (d.refine) G_TRY("refinement handle", cudaGraphConditionalHandleCreate(&hR, bodyN, 0, 0));
+  if (amg) G_TRY("AMG loop handle", cudaGraphConditionalHandleCreate(&hA, bodyN, 0, 0));
   // Newton body
   G_TRY("begin body capture", cudaStreamBeginCaptureToGraph(s->cap[1], bodyN, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   if (e == cudaSuccess) {
     cudaStream_t st = s->cap[1];
-    if (!d.first_order) {
+    if (amg) {  // the AMG-preconditioned solve: setup, first residual and cycle, WHILE(a scene iterates) { iteration }
+      body += launch_bond_hess(d, 0, st);
+      body += launch_particle_hess(d, 1, 0, st);
+      body += launch_amg_setup(d, s->amg, s->n_scenes, st);
+      body += launch_amg_pcg_stage(d, s->amg, 0, st);
+      body += launch_amg_cycle(d, s->amg, s->n_scenes, st);
+      body += launch_amg_pcg_stage(d, s->amg, 1, st);
+      body += launch_amg_loop_init(d, (unsigned long long)hA, st);
+      G_TRY("AMG launches", cudaGetLastError());
+      G_TRY("AMG while node", capture_while(st, hA, &bodyA));
+      body += launch_gdx(d, st);
+    } else if (!d.first_order) {
       body += launch_bond_hess(d, 0, st);
       body += launch_particle_hess(d, 1, 0, st);
       body += launch_pcg(d, 1, 1, st, &pe);
@@ -1340,6 +1413,12 @@ static bool build_step_graph(bdem_sim* s) {
       if (e == cudaSuccess && e2 != cudaSuccess) { e = e2; where = "end refinement capture"; }
     }
   }
+  // AMG iteration body
+  if (amg && e == cudaSuccess) {
+    cudaError_t ea = cudaSuccess;
+    amgk = capture_amg_body(s, d, bodyA, hA, s->cap[2], &ea);
+    if (ea != cudaSuccess) { e = ea; where = "AMG iteration capture"; }
+  }
   G_TRY("cudaGraphInstantiate", cudaGraphInstantiate(&s->graph_exec, G, 0));
 #undef G_TRY
   s->graph = G;
@@ -1355,6 +1434,8 @@ static bool build_step_graph(bdem_sim* s) {
   s->g_ls = ls;
   s->g_post = post;
   s->g_ref = ref;
+  s->g_amg = amgk;
+  s->graph_amg = s->amg;
   return true;
 }
 
@@ -1369,7 +1450,7 @@ static bdem_status graph_step(bdem_sim* s, std::vector<SceneCtl>& ctl, bool* red
   CUDA_TRY(s, cudaMemcpyAsync(ctl.data(), d.sc, sizeof(SceneCtl) * s->n_scenes, cudaMemcpyDeviceToHost, s->stream));
   TRY(sync(s));
   s->launches += s->g_pre + (int64_t)std::max(0, c.loops_newton - 1) * s->g_body + (int64_t)c.ls_total * s->g_ls +
-                 (int64_t)c.loops_refine * s->g_ref + s->g_post;
+                 (int64_t)c.loops_refine * s->g_ref + (int64_t)c.loops_amg * s->g_amg + s->g_post;
   if (c.timeout || c.nonfinite || c.overflow || c.runaway) {
     reset_counters(s, c.sync_gen);
     if (c.timeout) return fail(s, BDEM_E_TIMEOUT, "a device-side wait gave up; the step was rolled back");
@@ -1385,8 +1466,10 @@ static bdem_status graph_step(bdem_sim* s, std::vector<SceneCtl>& ctl, bool* red
 
 static bool graph_usable(bdem_sim* s) {
   if (!s->graph_enabled || s->graph_failed || s->prof_on || s->d.n == 0 || !s->contacts_sized) return false;
-  if (s->amg.on) return false;  // the AMG-preconditioned solve runs from the host-driven loop
-  if (s->graph_exec && memcmp(&s->graph_d, &s->d, sizeof(DevArrays)) == 0) return true;
+  if (s->amg.on && s->amg_nb != s->nb) return false;  // the host-driven step builds the AMG hierarchy first
+  if (s->graph_exec && memcmp(&s->graph_d, &s->d, sizeof(DevArrays)) == 0 &&
+      (!s->amg.on || memcmp(&s->graph_amg, &s->amg, sizeof(AmgDev)) == 0))
+    return true;
   if (build_step_graph(s)) return true;
   s->graph_failed = true;
   return false;
@@ -1543,7 +1626,8 @@ extern "C" void bdem_destroy(bdem_sim* s) {
   for (cudaStream_t c : s->cap)
     if (c) cudaStreamDestroy(c);
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
-  for (void* p : s->allocs) cudaFree(p);
+  if (s->hook.alloc) cudaStreamSynchronize(s->stream);  // the pool may hand the buffers out again at once
+  for (void* p : s->allocs) raw_free(s, p);
   s->allocs.clear();
   delete s;
 }
@@ -1733,6 +1817,7 @@ extern "C" bdem_status bdem_debug_pcg(bdem_sim* s, const double* b, double eps_r
   CUDA_TRY(s, cudaMemcpyAsync(s->dbg_buf, b, sizeof(double) * 6 * n, cudaMemcpyHostToDevice, st));
   TRY(check_launch(s, launch_convert_perm(s->dbg_buf, 1, d.vr, !d.mixed, d.perm, 0, (int)n, st)));
   if (s->amg.on) {
+    CUDA_TRY(s, cudaMemsetAsync(&d.cnt->loops_amg, 0, sizeof(int32_t), st));
     TRY(run_amg_pcg(s, d, 0));
   } else {
     TRY(run_pcg(s, d, 0, 1));
@@ -1744,6 +1829,7 @@ extern "C" bdem_status bdem_debug_pcg(bdem_sim* s, const double* b, double eps_r
   }
   Counters c{};
   TRY(read_counters(s, &c));
+  if (s->amg.on && s->amg_exec) s->launches += (int64_t)c.loops_amg * s->amg_gk;
   if (d.refine && !s->amg.on)
     TRY(check_launch(s, launch_convert_perm(d.x64, 1, s->dbg_buf + 6 * n, 1, d.perm, 1, (int)n, st)));
   else
@@ -1846,6 +1932,21 @@ extern "C" bdem_status bdem_set_pcg_shape(bdem_sim* s, int32_t lanes, int32_t bl
   return BDEM_OK;
 }
 
+extern "C" bdem_status bdem_set_pcg_product(bdem_sim* s, int32_t product) {
+  if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
+  if (product != 0 && product != 1) return fail(s, BDEM_E_INVALID, "product must be 0 or 1");
+  s->pcg_product = product;
+  return bdem_set_pcg_shape(s, s->d.pcg_lanes, s->d.pcg_grid);
+}
+
+extern "C" bdem_status bdem_get_pcg_shape(const bdem_sim* s, int32_t* lanes, int32_t* blocks, int32_t* product) {
+  if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
+  if (lanes) *lanes = s->d.pcg_lanes;
+  if (blocks) *blocks = s->d.pcg_grid;
+  if (product) *product = s->d.pcg_mode == 2 ? 1 : 0;
+  return BDEM_OK;
+}
+
 // assemble the Newton system at the committed state with xhat = x + dt v (the step's prediction)
 static bdem_status assemble_at_committed(bdem_sim* s) {
   DevArrays& d = s->d;
@@ -1871,10 +1972,13 @@ extern "C" bdem_status bdem_autotune_pcg(bdem_sim* s, int32_t iters, int32_t* la
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   float best = 1e30f;
-  int best_l = s->d.pcg_lanes, best_g = s->d.pcg_grid;
+  int best_l = s->d.pcg_lanes, best_g = s->d.pcg_grid, best_p = s->pcg_product;
   const int lanes_c[] = {1, 2, 4, 8};
+  for (int product = 1; product >= 0; --product)
   for (int lanes : lanes_c) {
+    s->pcg_product = product;
     int mx = pcg_blocks_by_regs(s, lanes);
+    if (mx < 1) continue;  // this product's shared memory leaves no resident block
     for (int per = 1; per <= std::max(1, mx / sms); ++per) {
       bdem_status sst = bdem_set_pcg_shape(s, lanes, per * sms);
       if (sst == BDEM_E_INVALID) continue;  // the block row ranges do not fit this shape's shared memory
@@ -1895,12 +1999,13 @@ extern "C" bdem_status bdem_autotune_pcg(bdem_sim* s, int32_t iters, int32_t* la
         cudaEventElapsedTime(&ms, a, b);
         t_min = std::min(t_min, ms);
       }
-      if (t_min < best) { best = t_min; best_l = lanes; best_g = s->d.pcg_grid; }
+      if (t_min < best) { best = t_min; best_l = lanes; best_g = s->d.pcg_grid; best_p = product; }
       if (s->d.pcg_grid >= (s->n + 63) / 64) break;  // larger grids are capped to the same shape
     }
   }
   s->ev_pool.push_back(a);
   s->ev_pool.push_back(b);
+  s->pcg_product = best_p;
   TRY(bdem_set_pcg_shape(s, best_l, best_g));
   if (lanes_out) *lanes_out = best_l;
   if (blocks_out) *blocks_out = best_g;

@@ -79,6 +79,8 @@ struct Counters {               // small device-side summary read by the host af
   int32_t ls_total;             // line-search trials in this step
   unsigned int never;           // written by nothing: the word the wait test waits on
   int32_t loops_refine;         // refinement rounds in this step (graph path: trips of the refinement loop)
+  int32_t loops_amg;            // AMG-PCG iterations in this step (trips of the device-driven iteration loop)
+  int32_t amg_trips;            // trips of the current AMG-PCG solve's loop
   int32_t pad_c;
 };
 
@@ -130,8 +132,8 @@ struct DevArrays {
   int32_t *btile_start, *btile_scene, *btile_begin;
   double *part_p, *part_b;      // [tiles][kPartials]
   int32_t n_seg, pcg_grid, pcg_lanes, pcg_max_rows;  // pcg_max_rows: most rows of one PCG block
-  int32_t pcg_max_entries, pcg_staged;               // most incidence entries of one PCG block's rows; 1: the
-                                                     // block's rows and entries are staged in shared memory
+  int32_t pcg_max_entries, pcg_mode;                 // most incidence entries of one PCG block's rows; how the
+                                                     // product reaches the bond blocks (k_pcg MODE 0, 1, 2)
   int32_t *seg_row, *seg_scene, *block_seg, *scene_seg;
   int32_t *useg_row, *useg_scene, *ublock_seg;      // equal-rows partition of the elementwise PCG phases
   double* part_s;               // [n_seg][kPartials]
@@ -192,8 +194,9 @@ enum ReduceMode { RED_GRAD = 0, RED_GDX = 1, RED_LS = 2, RED_FORCE_ACTIVE = 3, R
 int launch_scene_reduce(const DevArrays& d, int mode, unsigned long long cond, cudaStream_t s);
 // PCG: rhs_from_g = 1 uses b = -g; else b is read from vr (already T) and eps from sc.eps_r
 int launch_pcg(const DevArrays& d, int rhs_from_g, int mask_kin, cudaStream_t s, cudaError_t* err);
-int pcg_max_blocks(int mixed, int lanes, size_t smem, int staged);
-size_t pcg_smem_bytes(const DevArrays& d);  // shared memory of a PCG block: row descriptors + incidence entries  // co-resident PCG blocks on this device (0: none)
+int pcg_max_blocks(int mixed, int lanes, size_t smem, int mode);  // co-resident PCG blocks on this device (0: none)
+size_t pcg_smem_bytes(const DevArrays& d);  // dynamic shared memory of a PCG block in the arrays' mode
+size_t pcg_smem_bytes_for(int mode, int mixed, int max_rows, int max_entries);
 int launch_gdx(const DevArrays& d, cudaStream_t s);
 int launch_ls_trial(const DevArrays& d, cudaStream_t s);
 int launch_ls_energy(const DevArrays& d, cudaStream_t s);
@@ -234,5 +237,11 @@ int launch_amg_cycle(const DevArrays& d, const AmgDev& a, int n_scenes, cudaStre
 // 1 gamma = r.z, p = z; 2 q = H p and alpha from p.q; 3 x += alpha p, r -= alpha q, stop test (counts active scenes into
 // cnt->n_active); 4 beta from the new r.z, p = z + beta p
 int launch_amg_pcg_stage(const DevArrays& d, const AmgDev& a, int stage, cudaStream_t s);
+// the AMG-PCG iteration loop decided on the device: loop_init (before the conditional while node) starts a solve's
+// trip count and sets the loop's condition; iteration_begin opens each trip (clears the active-scene count);
+// loop_cond (closing the body) continues while a scene is still iterating, up to pcg_max + 1 trips
+int launch_amg_loop_init(const DevArrays& d, unsigned long long cond, cudaStream_t s);
+int launch_amg_iteration_begin(const DevArrays& d, cudaStream_t s);
+int launch_amg_loop_cond(const DevArrays& d, unsigned long long cond, cudaStream_t s);
 
 }  // namespace bdem

@@ -157,6 +157,7 @@ __global__ void k_step_init(DevArrays d) {
     d.cnt->loops_ls = 0;
     d.cnt->ls_total = 0;
     d.cnt->loops_refine = 0;
+    d.cnt->loops_amg = 0;
   }
   if (s >= d.n_scenes) return;
   SceneCtl c = {};
@@ -715,6 +716,33 @@ __device__ __forceinline__ void sym6_mul_as(const TS* Pg, const TA (&x)[6], TA (
     y[a] = s;
   }
 }
+// 16-byte asynchronous copy global -> shared (cp.async, L2 only) and the wait for all of this thread's copies
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// a block of NW words from shared memory (128-bit reads)
+template <int NW>
+__device__ __forceinline__ void load_words_shared(const float* src, float (&dst)[NW]) {
+  const float4* p = reinterpret_cast<const float4*>(src);
+#pragma unroll
+  for (int k = 0; k < NW / 4; ++k) {
+    float4 v = p[k];
+    dst[4 * k] = v.x; dst[4 * k + 1] = v.y; dst[4 * k + 2] = v.z; dst[4 * k + 3] = v.w;
+  }
+}
+template <int NW>
+__device__ __forceinline__ void load_words_shared(const double* src, double (&dst)[NW]) {
+  const double2* p = reinterpret_cast<const double2*>(src);
+#pragma unroll
+  for (int k = 0; k < NW / 2; ++k) {
+    double2 v = p[k];
+    dst[2 * k] = v.x; dst[2 * k + 1] = v.y;
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void sym6_mul(const T* Pg, const T (&x)[6], T (&y)[6]) {
   sym6_mul_as<T, T>(Pg, x, y);
@@ -722,6 +750,8 @@ __device__ __forceinline__ void sym6_mul(const T* Pg, const T (&x)[6], T (&y)[6]
 
 // one off-diagonal bond block (stored words of type TS) times the other endpoint's vector, added to y (arithmetic
 // of type TA)
+template <typename TA>
+__device__ __forceinline__ void bond_block_apply(const TA (&M)[36], int side, const Vec6<TA>& xo, TA (&y)[6]);
 template <typename TS, typename TA>
 __device__ __forceinline__ void bond_block_mul_as(const TS* Mg, int side, const Vec6<TA>& xo, TA (&y)[6]) {
   TS Ms[36];
@@ -729,6 +759,17 @@ __device__ __forceinline__ void bond_block_mul_as(const TS* Mg, int side, const 
   TA M[36];
 #pragma unroll
   for (int k = 0; k < 36; ++k) M[k] = (TA)Ms[k];
+  bond_block_apply<TA>(M, side, xo, y);
+}
+// the same with the block in shared memory
+template <typename T>
+__device__ __forceinline__ void bond_block_mul_shared(const T* Ms, int side, const Vec6<T>& xo, T (&y)[6]) {
+  T M[36];
+  load_words_shared<36>(Ms, M);
+  bond_block_apply<T>(M, side, xo, y);
+}
+template <typename TA>
+__device__ __forceinline__ void bond_block_apply(const TA (&M)[36], int side, const Vec6<TA>& xo, TA (&y)[6]) {
   TA a0 = xo.v[0], a1 = xo.v[1], a2 = xo.v[2], b0 = xo.v[3], b1 = xo.v[4], b2 = xo.v[5];
   TA Ah[6];
 #pragma unroll
@@ -1078,11 +1119,21 @@ __device__ __noinline__ void pcg_decide(const DevArrays& d, int k_iter, const in
   }
 }
 
-// STAGED: the block's row descriptors and incidence entries are copied to shared memory once per solve; for
-// systems whose block row ranges would not fit (about 25 KB per 1,000 rows of degree 12), they are read from global
-// memory (L2) at every product instead
-template <typename T, int G, bool STAGED>
+// MODE (DevArrays::pcg_mode) selects how the product reaches the bond blocks:
+//   0: each lane loads its own entries' blocks from L2/DRAM (128-bit loads); row descriptors and incidence entries are
+//      read from global memory at every product;
+//   1: as 0, with the block's row descriptors and incidence entries staged in shared memory once per solve (for
+//      systems whose block row ranges fit: about 25 KB per 1,000 rows of degree 12);
+//   2: row descriptors staged once per solve; the product runs in waves of one entry per lane, and before each wave
+//      the warp copies the wave's 32 bond blocks into shared memory with 16-byte cp.async copies in which
+//      consecutive lanes take consecutive 16-byte pieces of the same block, so that a copy request covers a few cache
+//      lines instead of one line per lane (with per-lane loads the L1 data pipe, not DRAM, bounds the product); each
+//      lane then multiplies its own entry's block from shared memory
+template <typename T, int G, int MODE>
 __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays d, int rhs_from_g, int mask) {
+  constexpr bool STAGED = MODE == 1;  // incidence entries in shared memory
+  constexpr bool ROWS = MODE >= 1;    // row descriptors in shared memory
+  constexpr bool COOP = MODE == 2;
   T* X = reinterpret_cast<T*>(d.vx);
   T* R = reinterpret_cast<T*>(d.vr);
   T* Z = reinterpret_cast<T*>(d.vz);
@@ -1098,6 +1149,8 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
   // and the incidence entries of those rows (staged once; every product reads them from shared memory)
   extern __shared__ int4 s_rows[];
   int2* s_ent = reinterpret_cast<int2*>(s_rows + d.pcg_max_rows);
+  // COOP: this warp's 32 block slots (36 words each) after the row descriptors
+  T* s_blk = reinterpret_cast<T*>(s_rows + d.pcg_max_rows) + (threadIdx.x >> 5) * 32 * 36;
   const int R0 = d.seg_row[seg0], R1 = d.seg_row[seg1];
   const int E0 = d.inc_start[R0], E1 = d.inc_start[R1];
   // row descriptor: first incidence entry (relative to the block's first when staged), bond count, active-contact
@@ -1108,10 +1161,10 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
     int kin = (mask && d.kin[i]) ? (1 << 30) : 0;
     return make_int4(STAGED ? a - E0 : a, d.inc_start[i + 1] - a, na | kin, d.c_start[i]);
   };
-  if (STAGED) {
+  if (ROWS)
     for (int i = R0 + threadIdx.x; i < R1; i += blockDim.x) s_rows[i - R0] = row_desc(i);
+  if (STAGED)
     for (int e = E0 + threadIdx.x; e < E1; e += blockDim.x) s_ent[e - E0] = d.inc2[e];
-  }
   const int2* ent_all = STAGED ? s_ent : d.inc2;
   __shared__ int s_sseg[kTile + 1];  // first PCG segment of each scene, for the decision (up to kTile scenes)
   const bool sseg_ok = d.n_scenes <= kTile;
@@ -1169,21 +1222,47 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
           int i = base + grp;
           bool valid = i < r1;
           T y[6] = {0, 0, 0, 0, 0, 0};
-          int4 rd = valid ? (STAGED ? s_rows[i - R0] : row_desc(i)) : make_int4(0, 0, 1 << 30, 0);
+          int4 rd = valid ? (ROWS ? s_rows[i - R0] : row_desc(i)) : make_int4(0, 0, 1 << 30, 0);
           bool live = valid && !(rd.z & (1 << 30));
-          if (live) {
-            if (sub == 0) {
-              Vec6<T> zi = load6_cg<T>(Z, i);
-              sym6_mul<T>(Dm + kDiagStride * (size_t)i, zi.v, y);
+          if (live && sub == 0) {
+            Vec6<T> zi = load6_cg<T>(Z, i);
+            sym6_mul<T>(Dm + kDiagStride * (size_t)i, zi.v, y);
+          }
+          const T* Mall = reinterpret_cast<const T*>(d.bM);
+          if (COOP) {
+            // waves of one entry per lane (warp-uniform count: every lane takes part in the copies)
+            const int lane = threadIdx.x & 31;
+            const int nwave = __reduce_max_sync(0xffffffffu, live ? (rd.y + G - 1) / G : 0);
+            constexpr int PP = 36 * (int)sizeof(T) / 16;  // 16-byte pieces of one block
+            constexpr int PW = 16 / (int)sizeof(T);       // words of one piece
+            for (int w = 0; w < nwave; ++w) {
+              const int k = w * G + sub;
+              const bool has = live && k < rd.y;
+              const int2 e = has ? __ldg(d.inc2 + rd.x + k) : make_int2(-2, 0);
+              const int bond = e.x >> 1;  // -1: no entry in this slot
+              Vec6<T> xo;
+              if (has) xo = load6_cg<T>(Z, e.y);  // in flight with the copies
+#pragma unroll
+              for (int m = 0; m < PP; ++m) {
+                const int p = lane + 32 * m, slot = p / PP, q = p - slot * PP;
+                const int bs = __shfl_sync(0xffffffffu, bond, slot);
+                if (bs >= 0) cp_async16(s_blk + 36 * slot + PW * q, Mall + 36 * (size_t)bs + PW * q);
+              }
+              cp_async_wait_all();
+              __syncwarp();
+              if (has) bond_block_mul_shared<T>(s_blk + 36 * lane, e.x & 1, xo, y);
+              __syncwarp();  // every lane has read its slot before the next wave's copies overwrite it
             }
+          } else if (live) {
             const int2* ent = ent_all + rd.x;
-            const T* Mall = reinterpret_cast<const T*>(d.bM);
 #pragma unroll 2
             for (int k = sub; k < rd.y; k += G) {
               int2 e = ent[k];
               Vec6<T> xo = load6_cg<T>(Z, e.y);
               bond_block_mul<T>(Mall + 36 * (size_t)(e.x >> 1), e.x & 1, xo, y);
             }
+          }
+          if (live) {
             int nact = rd.z & ((1 << 30) - 1);
             for (int k = sub; k < nact; k += G) {
               int e = rd.w + k;
@@ -2005,33 +2084,37 @@ int launch_scene_reduce(const DevArrays& d, int mode, unsigned long long cond, c
   return 1;
 }
 
+size_t pcg_smem_bytes_for(int mode, int mixed, int max_rows, int max_entries) {
+  size_t rows = sizeof(int4) * (size_t)(max_rows > 0 ? max_rows : 1);
+  if (mode == 1) return rows + sizeof(int2) * (size_t)(max_entries > 0 ? max_entries : 1);
+  if (mode == 2) return rows + (size_t)kTile * 36 * (mixed ? sizeof(float) : sizeof(double));
+  return 0;
+}
 size_t pcg_smem_bytes(const DevArrays& d) {
-  if (!d.pcg_staged) return 0;
-  return sizeof(int4) * (size_t)(d.pcg_max_rows > 0 ? d.pcg_max_rows : 1) +
-         sizeof(int2) * (size_t)(d.pcg_max_entries > 0 ? d.pcg_max_entries : 1);
+  return pcg_smem_bytes_for(d.pcg_mode, d.mixed, d.pcg_max_rows, d.pcg_max_entries);
 }
 
-template <typename T>
-static const void* pcg_kernel(int lanes, int staged) {
-  if (staged) switch (lanes) {
-      case 1: return (const void*)k_pcg<T, 1, true>;
-      case 2: return (const void*)k_pcg<T, 2, true>;
-      case 8: return (const void*)k_pcg<T, 8, true>;
-      default: return (const void*)k_pcg<T, 4, true>;
-    }
+template <typename T, int MODE>
+static const void* pcg_kernel_m(int lanes) {
   switch (lanes) {
-    case 1: return (const void*)k_pcg<T, 1, false>;
-    case 2: return (const void*)k_pcg<T, 2, false>;
-    case 8: return (const void*)k_pcg<T, 8, false>;
-    default: return (const void*)k_pcg<T, 4, false>;
+    case 1: return (const void*)k_pcg<T, 1, MODE>;
+    case 2: return (const void*)k_pcg<T, 2, MODE>;
+    case 8: return (const void*)k_pcg<T, 8, MODE>;
+    default: return (const void*)k_pcg<T, 4, MODE>;
   }
 }
+template <typename T>
+static const void* pcg_kernel(int lanes, int mode) {
+  if (mode == 2) return pcg_kernel_m<T, 2>(lanes);
+  if (mode == 1) return pcg_kernel_m<T, 1>(lanes);
+  return pcg_kernel_m<T, 0>(lanes);
+}
 
-int pcg_max_blocks(int mixed, int lanes, size_t smem, int staged) {
+int pcg_max_blocks(int mixed, int lanes, size_t smem, int mode) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const void* k = mixed ? pcg_kernel<float>(lanes, staged) : pcg_kernel<double>(lanes, staged);
+  const void* k = mixed ? pcg_kernel<float>(lanes, mode) : pcg_kernel<double>(lanes, mode);
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kTile, smem) != cudaSuccess) return 0;
   return sms * per;
@@ -2044,7 +2127,7 @@ int launch_pcg(const DevArrays& d, int rhs_from_g, int mask, cudaStream_t s, cud
   }
   DevArrays dd = d;
   void* args[] = {&dd, &rhs_from_g, &mask};
-  const void* k = d.mixed ? pcg_kernel<float>(d.pcg_lanes, d.pcg_staged) : pcg_kernel<double>(d.pcg_lanes, d.pcg_staged);
+  const void* k = d.mixed ? pcg_kernel<float>(d.pcg_lanes, d.pcg_mode) : pcg_kernel<double>(d.pcg_lanes, d.pcg_mode);
   size_t smem = pcg_smem_bytes(d);
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   *err = cudaLaunchCooperativeKernel(k, d.pcg_grid, kTile, args, smem, s);
@@ -3060,6 +3143,33 @@ __global__ void k_apcg_scene(DevArrays d, int stage) {
       c.rz = v;
     }
   }
+}
+
+__global__ void k_amg_loop(DevArrays d, unsigned long long cond, int what) {
+  if (what == 0) {  // a solve starts: its first trip always runs
+    d.cnt->amg_trips = 0;
+    cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 1u);
+  } else if (what == 1) {  // a trip starts
+    d.cnt->n_active = 0;
+  } else {  // a trip ends
+    int trips = ++d.cnt->amg_trips;
+    d.cnt->loops_amg += 1;
+    unsigned go = d.cnt->n_active > 0 && trips <= d.pcg_max && !step_aborted(d);
+    cudaGraphSetConditional((cudaGraphConditionalHandle)cond, go);
+  }
+}
+
+int launch_amg_loop_init(const DevArrays& d, unsigned long long cond, cudaStream_t s) {
+  k_amg_loop<<<1, 1, 0, s>>>(d, cond, 0);
+  return 1;
+}
+int launch_amg_iteration_begin(const DevArrays& d, cudaStream_t s) {
+  k_amg_loop<<<1, 1, 0, s>>>(d, 0ull, 1);
+  return 1;
+}
+int launch_amg_loop_cond(const DevArrays& d, unsigned long long cond, cudaStream_t s) {
+  k_amg_loop<<<1, 1, 0, s>>>(d, cond, 2);
+  return 1;
 }
 
 int launch_amg_pcg_stage(const DevArrays& d, const AmgDev& a, int stage, cudaStream_t s) {

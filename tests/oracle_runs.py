@@ -31,18 +31,35 @@ def split_scenes(sc):
 
 
 def _trajectory(args):
-    sc, steps, cfg = args
+    """The oracle's trajectory of one scene at Newton setting cfg; with alternative settings `alts` (name -> cfg), also
+    one step at each of them from every step's input state (the reference trajectory's previous state), recorded under
+    states[k]["alt"][name] with its status under stats[k]["alt_status"][name]."""
+    sc, steps, cfg = args[:3]
+    alts = args[3] if len(args) > 3 else {}
     if sc.n == 0:  # an empty scene has nothing to advance
-        return ([{"pos": np.zeros((0, 3)), "quat": np.zeros((0, 4)), "broken": np.zeros(0, np.uint8)}] * steps,
-                [{"newton_iters": 0, "pcg_iters": 0, "status": 0, "bonds_broken": 0}] * steps)
+        z = {"pos": np.zeros((0, 3)), "quat": np.zeros((0, 4)), "vel": np.zeros((0, 3)),
+             "quat_vel": np.zeros((0, 4)), "broken": np.zeros(0, np.uint8)}
+        st0 = {"newton_iters": 0, "pcg_iters": 0, "status": 0, "bonds_broken": 0}
+        return ([dict(z, alt={a: z for a in alts}) for _ in range(steps)],
+                [dict(st0, alt_status={a: 0 for a in alts}) for _ in range(steps)])
     import oracle
     oracle.build()
     o = oracle.OracleSim(sc, cfg)
+    others = {a: oracle.OracleSim(sc, dict(cfg or {}, **c)) for a, c in alts.items()}
     states, stats = [], []
     for _ in range(steps):
-        stats.append(o.step(1)[0][0])
+        prev = o.state()
+        alt, alt_status = {}, {}
+        for a, oa in others.items():
+            oa.set_state(prev["pos"], prev["quat"], prev["vel"], prev["quat_vel"], prev["broken"])
+            alt_status[a] = oa.step(1)[0][0]["status"]
+            sa = oa.state()
+            alt[a] = {k: sa[k] for k in ("pos", "quat", "broken")}
+        stt = o.step(1)[0][0]
+        stt["alt_status"] = alt_status
+        stats.append(stt)
         st = o.state()
-        states.append({k: st[k] for k in ("pos", "quat", "broken")})
+        states.append(dict({k: st[k] for k in ("pos", "quat", "vel", "quat_vel", "broken")}, alt=alt))
     return states, stats
 
 
@@ -59,19 +76,24 @@ def _assemble(sc, steps, res):
     off = np.asarray(sc.scene_offsets, np.int64)
     bond_scene = np.searchsorted(off, sc.bond_i, side="right") - 1
     states, stats = [], []
+    alts = list(res[0][0][0].get("alt", {})) if res and steps else []
+
+    def blank():
+        return {"pos": np.zeros((sc.n, 3)), "quat": np.zeros((sc.n, 4)), "vel": np.zeros((sc.n, 3)),
+                "quat_vel": np.zeros((sc.n, 4)), "broken": np.zeros(sc.nb, np.uint8)}
+
     for t in range(steps):
-        pos = np.zeros((sc.n, 3))
-        quat = np.zeros((sc.n, 4))
-        broken = np.zeros(sc.nb, np.uint8)
+        out = blank()
+        out["alt"] = {a: blank() for a in alts}
         for s, (st, _) in enumerate(res):
             a, b = (int(off[s]), int(off[s + 1])) if parts > 1 else (0, sc.n)
-            pos[a:b] = st[t]["pos"]
-            quat[a:b] = st[t]["quat"]
-            if parts == 1:
-                broken[:] = st[t]["broken"]
-            else:
-                broken[bond_scene == s] = st[t]["broken"]
-        states.append({"pos": pos, "quat": quat, "broken": broken})
+            sel = slice(None) if parts == 1 else (bond_scene == s)
+            for dst, src in [(out, st[t])] + [(out["alt"][n], st[t]["alt"][n]) for n in alts]:
+                for f in ("pos", "quat", "vel", "quat_vel"):
+                    if f in src:
+                        dst[f][a:b] = src[f]
+                dst["broken"][sel] = src["broken"]
+        states.append(out)
         stats.append([r[1][t] for r in res])
     return states, stats
 
@@ -86,10 +108,10 @@ class Batch:
         self.pool = mp.get_context("spawn").Pool(processes or _workers())
         self.cases = {}
 
-    def submit(self, name, sc, steps, cfg=None):
+    def submit(self, name, sc, steps, cfg=None, alts=None):
         parts = split_scenes(sc) if sc.n_scenes > 1 else [sc]
         order = sorted(range(len(parts)), key=lambda k: -(parts[k].n + parts[k].nb))
-        handles = {k: self.pool.apply_async(_trajectory, ((parts[k], steps, cfg),)) for k in order}
+        handles = {k: self.pool.apply_async(_trajectory, ((parts[k], steps, cfg, alts or {}),)) for k in order}
         self.cases[name] = (sc, steps, [handles[k] for k in range(len(parts))])
 
     def result(self, name, timeout=3600):
@@ -102,8 +124,9 @@ class Batch:
 
 
 def trajectories(sc, steps, cfg=None, processes=None):
-    """Per-step oracle states of a (possibly batched) scene: a list over steps of dicts pos [N,3], quat [N,4] and
-    broken [B] in the scene's own particle and bond order, plus per-step lists of per-scene stats."""
+    """Per-step oracle states of a (possibly batched) scene: a list over steps of dicts pos [N,3], quat [N,4], vel
+    [N,3], quat_vel [N,4] and broken [B] in the scene's own particle and bond order, plus per-step lists of per-scene
+    stats."""
     import oracle
     oracle.build()  # compile once before the workers start
     parts = split_scenes(sc) if sc.n_scenes > 1 else [sc]

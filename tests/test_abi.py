@@ -51,7 +51,8 @@ def test_binding_structs_match_the_header_layout(tmp_path):
     """Every struct of include/bdem.h has the same size and field offsets in the ctypes binding (compiled and printed
     with the host C compiler)."""
     import ctypes
-    structs = {name: getattr(pkg, name) for name in ("bdem_material", "bdem_config", "bdem_step_stats", "bdem_profile")}
+    structs = {name: getattr(pkg, name) for name in ("bdem_material", "bdem_allocator", "bdem_config", "bdem_step_stats",
+                                                   "bdem_profile")}
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "bdem.h"', 'int main(void) {']
     for name, cls in structs.items():
         lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')

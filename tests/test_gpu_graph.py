@@ -25,8 +25,8 @@ def _lib():
     pkg.load()
 
 
-def run(sc, prec, steps, graph):
-    sim = pkg.Sim(sc, precision=prec)
+def run(sc, prec, steps, graph, config=None):
+    sim = pkg.Sim(sc, precision=prec, config=config)
     sim.set_step_graph(graph)
     stats = [sim.step(1) for _ in range(steps)]
     st = sim.read_state()
@@ -112,3 +112,18 @@ def test_batched_uneven_scenes_through_the_graph():
         assert ea == "" and ga == 5
         assert_identical(x, y)
         assert [[t["newton_iters"] for t in st] for st in sx] == [[t["newton_iters"] for t in st] for st in sy]
+
+
+@pytest.mark.parametrize("prec", [pkg.BDEM_FP64, pkg.BDEM_MIXED])
+def test_graph_matches_host_loop_with_the_amg_preconditioner(prec):
+    """With the AMG preconditioner the step graph holds the AMG-PCG iterations as a device-driven while loop inside
+    the Newton loop; the host-driven step launches the same loop as a graph of its own: bit-identical results."""
+    sc = scenes.c2_plate_small(R=0.015)
+    cfg = dict(preconditioner=pkg.BDEM_PRECOND_AMG)
+    a, sa, ga, ea = run(sc, prec, 4, True, cfg)
+    b, sb, gb, eb = run(sc, prec, 4, False, cfg)
+    assert ea == "", ea
+    assert ga == 3 and gb == 0
+    assert_identical(a, b)
+    for x, y in zip(sa, sb):
+        assert x[0]["newton_iters"] == y[0]["newton_iters"] and x[0]["pcg_iters"] == y[0]["pcg_iters"]

@@ -87,12 +87,18 @@ def test_matvec_and_pcg_parity(prec, name):
     tol = 1e-11 if prec == pkg.BDEM_FP64 else 1e-5
     assert np.abs(yg - yr).max() <= tol * np.abs(yr).max()
     b = np.random.default_rng(6).normal(size=(sc.n, 6))
-    xr, itr = o.pcg_solve(p, q, phat, qhat, b, 1e-12 if prec == pkg.BDEM_FP64 else 1e-6, 2000)
-    xg, itg = sim.bdem_debug_pcg(b, 1e-12 if prec == pkg.BDEM_FP64 else 1e-6, 2000)
-    tol = 1e-8 if prec == pkg.BDEM_FP64 else 1e-3
-    assert np.abs(xg - xr).max() <= tol * np.abs(xr).max()
+    eps = 1e-12 if prec == pkg.BDEM_FP64 else 1e-6
+    xr, itr = o.pcg_solve(p, q, phat, qhat, b, eps, 2000)
+    xg, itg = sim.bdem_debug_pcg(b, eps, 2000)
+    # mixed: the refined solve meets eps on the true residual of the stored FP32 system (FP64 product), so it differs
+    # from the FP64 solution only by the FP32 rounding of the blocks, amplified by the system's conditioning
+    tol = 1e-8 if prec == pkg.BDEM_FP64 else 1e-4
+    assert np.abs(xg - xr).max() <= tol * np.abs(xr).max(), np.abs(xg - xr).max() / np.abs(xr).max()
     if prec == pkg.BDEM_FP64:
         assert abs(int(itg[0]) - itr) <= 2
+    else:
+        r = b - sim.bdem_debug_matvec(xg)
+        assert np.linalg.norm(r) <= eps * np.linalg.norm(b) * (1.0 + 1e-3), np.linalg.norm(r) / np.linalg.norm(b)
     sim.close()
 
 

@@ -1,25 +1,41 @@
 """Error of both GPU paths against the FP64 oracle, per configuration (needs a GB300; run with -s to see the table).
 
-Each configuration runs at a size the oracle finishes in seconds, built by the same generator as the full-size
-workload: the 10x10x10 cube in free fall (100 steps) and dropped onto the ground (100 steps), the plate at R = 15 mm,
-the 12x12 textile tear, three Poisson-disk boxes landing on their grounds, and a small slab hit by a ball. The
-largest position error (relative to the scene's bounding-box diagonal), quaternion error and the bond-break sets are
-compared step by step; the mixed path is held to 1e-4 and the break sets must be identical. The FP64 path is held to
-1e-9 where the method pins the answer down that far, and otherwise to how far the oracle's own trajectory moves
-when its Newton tolerance is tightened: for the slab impact and the landing boxes that spread is recorded in
-tests/golden/newton_spread.json (written by the oracle-only script beside it); for the textile, whose tighter-
-tolerance trajectories tear differently, positions are held to 1e-8 and orientations to 1e-7 (the oracle's spread
-between tolerances 1e-9 and 1e-12 before the tear is 2.6e-9 and 5.2e-8).
+Each case (tests/parity_cases.py) is built by the generator of its full-size workload at a size the oracle finishes
+in minutes: the 10x10x10 cube in free fall and on the ground, a small plate dropped fast enough to shatter, the 12x12
+textile torn apart, 64 Poisson-disk boxes of uneven sizes with an empty scene (more scenes than the PCG's few-scene
+decision path handles, so its batched decision path runs), and a small slab hit by a ball.
+
+Two comparisons per case and precision, step by step over all of its steps:
+  - shadowed: every step starts from the oracle's state of the previous step (positions, orientations, velocities,
+    bond flags written through bdem_write_state), so each of the case's steps checks the GPU's step against the
+    oracle's from the same input. A scene's step is compared where both Newton loops converged in it; a step that
+    ended at the iteration cap or with a failed line search commits the best iterate reached, which the method does
+    not pin down (the shattered plate's fragments, for one, stall near 1e-3 of |g_0| from its fifth step), so those
+    scene-steps are counted and their errors reported apart. FP64: positions (relative to the scene's bounding-box
+    diagonal) and orientations within 1e-9 and the same bonds broken at every compared step. For the two cases run
+    at a tightened tolerance the oracle also takes, from every step's input, one step with its other preconditioner
+    (AMG) and one at the configuration's own tolerance: the Newton test |g| <= tol |g_0| weighs forces (N) and
+    torques (N m) alike, so the orientations of loose particles with little rotational inertia are pinned far less
+    tightly than their positions, and two correct solvers land apart by that much; the FP64 bar is then no tighter
+    than twice the oracle's own two-solver difference. Mixed (FP32 Hessians and PCG, FP64 reductions, FP64-residual
+    refinement): within 1e-4 at the case's setting, and at the configuration's own tolerance within 1e-4 or twice
+    the distance the oracle's own solve at that tolerance lands from the tightened answer; every bond whose break
+    decision differs from the oracle's has a tensile strain within the step's own strain error of its limit (the
+    decision is the same test on a state that differs by that much);
+  - free-running: both sides advance on their own. Fracture cascades, contact switching and capped Newton loops make
+    these trajectories chaotic (a rounding-level difference grows by orders of magnitude per step once bonds break),
+    so two correct implementations separate after some steps; the report gives the largest errors and the first step
+    where the break sets differ, and asserts the free-running bars for the cases that are not chaotic.
+The report also gives, from the oracle's trajectory, the smallest distance of an intact bond's tensile strain from its
+limit over all steps (|eps - eps_c| / eps_c). The oracle trajectories are computed in spawned worker processes queued
+at the start of the session (conftest).
 """
-import json
-import os
 import numpy as np
 import pytest
 
-import oracle
 import paper_2308_10459_gb300 as pkg
 from paper_2308_10459_gb300 import build as bmod
-from paper_2308_10459_gb300 import scenes
+from parity_cases import CASES, key
 
 pytestmark = pytest.mark.gpu
 
@@ -31,57 +47,151 @@ def _lib():
         pytest.skip("no CUDA device")
     bmod.build()
     pkg.load()
-    oracle.build()
 
 
 def qerr(a, b):
     return float(np.minimum(np.abs(a - b).max(1), np.abs(a + b).max(1)).max()) if len(a) else 0.0
 
 
-with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "newton_spread.json")) as _f:
-    SPREAD = json.load(_f)
+def strains(sc, pos, l0):
+    return (np.linalg.norm(pos[sc.bond_j] - pos[sc.bond_i], axis=1) - l0) / l0
 
-# name: (scene, steps, config, FP64 position bound, FP64 quaternion bound)
-CASES = {
-    "c1 cube 10^3, free fall": (lambda: scenes.c1_cube(), 100, None, 1e-9, 1e-9),
-    "c1b cube 10^3 on the ground": (lambda: scenes.c1b_cube_contact(steps=100), 100, None, 1e-9, 1e-9),
-    "c2 plate R=15 mm": (lambda: scenes.c2_plate_small(R=0.015), 5, None, 1e-9, 1e-9),
-    "c3 textile 12x12 (tear)": (lambda: scenes.c3_textile(nx=12, steps=8), 8, dict(newton_rel_tol=1e-9), 1e-8, 1e-7),
-    "c4 3 Poisson boxes landing": (lambda: scenes.c4_batched(n_scenes=3, n_min=150, n_max=400,
-                                                             heights=(0.0002, 0.001)), 25, None,
-                                   max(1e-9, SPREAD["c4"]["pos"]), max(1e-9, SPREAD["c4"]["quat"])),
-    "c5 slab 600 + ball 80 impact": (lambda: scenes.c5_impact(n_slab=600, n_ball=80, footprint=0.035,
-                                                              ball_R=0.008), 3, None,
-                                     max(1e-9, SPREAD["c5"]["pos"]), max(1e-9, SPREAD["c5"]["quat"])),
-}
+
+def break_margin(sc, ref, l0, lim):
+    """Smallest |eps - eps_c| / eps_c over the intact bonds (before each step's test) of the oracle's trajectory."""
+    prev = np.zeros(sc.nb, bool)
+    m = np.inf
+    for st in ref:
+        e = strains(sc, st["pos"], l0)
+        act = ~prev & np.isfinite(lim)
+        if act.any():
+            m = min(m, float(np.min(np.abs(e[act] - lim[act]) / lim[act])))
+        prev = st["broken"].astype(bool)
+    return m
+
+
+def qerr_rows(a, b):
+    return np.minimum(np.abs(a - b).max(1), np.abs(a + b).max(1))
+
+
+def spread(sc, ref, ref_stats, L, alt):
+    """Largest difference, over the scene-steps where both converged, between the oracle's alternative one-step run
+    `alt` and its reference step from the same input (positions relative to L, orientations)."""
+    off = np.asarray(sc.scene_offsets, np.int64)
+    pscene = np.repeat(np.arange(sc.n_scenes), np.diff(off))
+    sp = sq = 0.0
+    for k, st in enumerate(ref):
+        conv = np.array([ref_stats[k][s]["status"] == 0 and ref_stats[k][s]["alt_status"][alt] == 0
+                         for s in range(sc.n_scenes)])
+        pin = conv[pscene]
+        if pin.any():
+            sp = max(sp, float((np.abs(st["alt"][alt]["pos"] - st["pos"]).max(1) / L)[pin].max()))
+            sq = max(sq, float(qerr_rows(st["alt"][alt]["quat"], st["quat"])[pin].max()))
+    return sp, sq
+
+
+def run_gpu(sc, prec, cfg, ref, ref_stats, L, shadow):
+    """Steps of one GPU simulation compared with the oracle's; shadow: each step from the oracle's previous state.
+    A scene's step is compared where both solvers converged in it (status 0: |g| met the Newton test); at a step that
+    ended at the iteration cap or with a failed line search the committed state is the best iterate reached, which the
+    method leaves open, so those scene-steps are counted and their errors reported apart."""
+    l0 = np.linalg.norm(sc.pos[sc.bond_j] - sc.pos[sc.bond_i], axis=1)
+    lim = np.array([sc.materials[m].break_strain for m in sc.bond_material])
+    off = np.asarray(sc.scene_offsets, np.int64)
+    pscene = np.repeat(np.arange(sc.n_scenes), np.diff(off))
+    bscene = pscene[sc.bond_i] if sc.nb else np.zeros(0, np.int64)
+    sim = pkg.Sim(sc, precision=prec, config=cfg)
+    r = dict(pos=0.0, quat=0.0, first_diff=None, flips=0, unexplained=0, pinned=0, open=0, open_pos=0.0, worst=None)
+    for k in range(len(ref)):
+        if shadow and k > 0:
+            p = ref[k - 1]
+            sim.write_state(p["pos"], p["quat"], p["vel"], p["quat_vel"], p["broken"])
+        gstats = sim.step(1)
+        st = sim.read_state()
+        conv = np.array([gstats[s]["status"] == 0 and ref_stats[k][s]["status"] == 0 for s in range(sc.n_scenes)])
+        ep = np.abs(st["pos"] - ref[k]["pos"]).max(1) / L if sc.n else np.zeros(0)
+        eq = qerr_rows(st["quat"], ref[k]["quat"]) if sc.n else np.zeros(0)
+        pin = conv[pscene]
+        if pin.any():
+            if float(ep[pin].max()) > r["pos"]:
+                i = int(np.flatnonzero(pin)[np.argmax(ep[pin])])
+                r["worst"] = (k + 1, int(pscene[i]), gstats[pscene[i]]["newton_iters"],
+                              ref_stats[k][pscene[i]]["newton_iters"])
+            r["pos"] = max(r["pos"], float(ep[pin].max()))
+            r["quat"] = max(r["quat"], float(eq[pin].max()))
+        if (~pin).any():
+            r["open_pos"] = max(r["open_pos"], float(ep[~pin].max()))
+        nonempty = np.diff(off) > 0
+        r["pinned"] += int((conv & nonempty).sum())
+        r["open"] += int((~conv & nonempty).sum())
+        diff = np.flatnonzero((st["broken"] != ref[k]["broken"]) & conv[bscene]) if sc.nb else np.zeros(0, int)
+        if diff.size:
+            if r["first_diff"] is None:
+                r["first_diff"] = k + 1
+            # a flipped decision is explained when the oracle's strain is closer to the limit than the two states'
+            # strains are to each other
+            eg, eo = strains(sc, st["pos"], l0)[diff], strains(sc, ref[k]["pos"], l0)[diff]
+            r["flips"] += diff.size
+            r["unexplained"] += int(np.sum(np.abs(eo - lim[diff]) > np.abs(eg - eo)))
+    sim.close()
+    return r
+
+
+def fmt(r):
+    b = "same" if r["first_diff"] is None else f"differ from step {r['first_diff']}"
+    if r["flips"]:
+        b += f" ({r['flips']} flips, {r['unexplained']} unexplained)"
+    s = f"pos {r['pos']:.2e} quat {r['quat']:.2e} breaks {b} [{r['pinned']} scene-steps compared"
+    if r["open"]:
+        s += f", {r['open']} not converged (pos {r['open_pos']:.1e})"
+    if r["worst"]:
+        s += ", worst at step %d scene %d, Newton %d/%d" % r["worst"]
+    return s + "]"
 
 
 @pytest.mark.parametrize("name", list(CASES))
-def test_error_against_the_oracle_per_configuration(name):
-    make, steps, cfg, ptol64, qtol64 = CASES[name]
-    sc = make()
-    o = oracle.OracleSim(sc, cfg)
-    ref = []
-    for _ in range(steps):
-        o.step(1)
-        ref.append(o.state())
+def test_error_against_the_oracle_per_configuration(name, parity_oracle):
+    case = CASES[name]
+    sc = case.make()
+    ref, ref_stats = parity_oracle.result(key(name))
     L = float(np.linalg.norm(sc.pos.max(0) - sc.pos.min(0)))
-    row = {}
-    for prec, label in ((pkg.BDEM_FP64, "fp64"), (pkg.BDEM_MIXED, "mixed")):
-        sim = pkg.Sim(sc, precision=prec, config=cfg)
-        ep = eq = 0.0
-        same = True
-        for k in range(steps):
-            sim.step(1)
-            st = sim.read_state()
-            ep = max(ep, float(np.abs(st["pos"] - ref[k]["pos"]).max()) / L)
-            eq = max(eq, qerr(st["quat"], ref[k]["quat"]))
-            same = same and bool(np.array_equal(st["broken"], ref[k]["broken"]))
-        sim.close()
-        row[label] = (ep, eq, same)
-    print(f"\nPARITY | {name} | n={sc.n} bonds={sc.nb} steps={steps} | fp64 pos {row['fp64'][0]:.2e} quat "
-          f"{row['fp64'][1]:.2e} breaks {'same' if row['fp64'][2] else 'DIFFER'} | mixed pos {row['mixed'][0]:.2e} "
-          f"quat {row['mixed'][1]:.2e} breaks {'same' if row['mixed'][2] else 'DIFFER'} | broken {int(ref[-1]['broken'].sum())}"
-          f" | fp64 bounds {ptol64:.1e} / {qtol64:.1e}")
-    assert row["fp64"][0] <= ptol64 and row["fp64"][1] <= qtol64 and row["fp64"][2]
-    assert row["mixed"][0] <= 1e-4 and row["mixed"][1] <= 1e-4 and row["mixed"][2]
+    l0 = np.linalg.norm(sc.pos[sc.bond_j] - sc.pos[sc.bond_i], axis=1)
+    lim = np.array([sc.materials[m].break_strain for m in sc.bond_material])
+    # bars: 1e-9 (FP64) and 1e-4 (mixed); for the tightened cases also no tighter than twice how far the oracle's own
+    # second solver (AMG preconditioner, same setting) and its solve at the configuration's tolerance land from its
+    # reference step from the same input
+    bar64 = (1e-9, 1e-9)
+    bar_cfg = (1e-4, 1e-4)
+    note = ""
+    if case.oracle_cfg is not None:
+        s_amg, s_cfg = spread(sc, ref, ref_stats, L, "amg"), spread(sc, ref, ref_stats, L, "config")
+        bar64 = (max(1e-9, 2 * s_amg[0]), max(1e-9, 2 * s_amg[1]))
+        bar_cfg = (max(1e-4, 2 * s_cfg[0]), max(1e-4, 2 * s_cfg[1]))
+        note = (f" | oracle spread: second solver pos {s_amg[0]:.1e} quat {s_amg[1]:.1e}, configuration tolerance pos "
+                f"{s_cfg[0]:.1e} quat {s_cfg[1]:.1e}")
+    res = {}
+    runs = [("fp64", pkg.BDEM_FP64, case.oracle_cfg), ("mixed", pkg.BDEM_MIXED, case.oracle_cfg)]
+    if case.oracle_cfg is not None:
+        runs.append(("mixed@config", pkg.BDEM_MIXED, None))
+    for label, prec, cfg in runs:
+        res[label] = {"shadow": run_gpu(sc, prec, cfg, ref, ref_stats, L, True),
+                      "free": run_gpu(sc, prec, cfg, ref, ref_stats, L, False)}
+    tol = "config" if case.oracle_cfg is None else f"{case.oracle_cfg['newton_rel_tol']:.0e}"
+    print(f"\nPARITY | {name} | n={sc.n} bonds={sc.nb} scenes={sc.n_scenes} steps={case.steps} tol={tol} | broken "
+          f"{int(ref[-1]['broken'].sum())} | margin {break_margin(sc, ref, l0, lim):.2e}{note}")
+    for label, r in res.items():
+        print(f"PARITY |   {label:12s} shadowed: {fmt(r['shadow'])} | free-running: {fmt(r['free'])}")
+    s64 = res["fp64"]["shadow"]
+    assert s64["pinned"] >= case.min_pinned
+    assert s64["pos"] <= bar64[0] and s64["quat"] <= bar64[1] and s64["first_diff"] is None
+    s = res["mixed"]["shadow"]
+    assert s["pos"] <= 1e-4 and s["quat"] <= 1e-4 and s["unexplained"] == 0
+    if "mixed@config" in res:
+        s = res["mixed@config"]["shadow"]
+        assert s["pos"] <= bar_cfg[0] and s["quat"] <= bar_cfg[1] and s["unexplained"] == 0
+    if not case.chaotic:
+        f64 = res["fp64"]["free"]
+        assert f64["pos"] <= 1e-9 and f64["quat"] <= 1e-9 and f64["first_diff"] is None
+        for label in res:
+            f = res[label]["free"]
+            assert f["pos"] <= 1e-4 and f["quat"] <= 1e-4 and f["first_diff"] is None, label

@@ -36,6 +36,7 @@ def test_staged_and_unstaged_grids_agree():
     sols, its, traj = {}, {}, {}
     for blocks in (2, 64):
         sim = pkg.Sim(sc, precision=pkg.BDEM_FP64)
+        sim.set_pcg_product(0)  # per-lane block loads: the row staging depends on the grid
         sim.set_pcg_shape(4, blocks)
         st = sim.read_state()
         dt = sc.config["dt"]
@@ -56,3 +57,29 @@ def test_staged_and_unstaged_grids_agree():
         spread = json.load(f)["plate50"]
     assert np.abs(traj[2]["pos"] - traj[64]["pos"]).max() <= 2.0 * max(1e-9, spread["pos"]) * L
     assert np.array_equal(traj[2]["broken"], traj[64]["broken"])
+
+
+@pytest.mark.parametrize("prec", [pkg.BDEM_FP64, pkg.BDEM_MIXED], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("lanes", [2, 4, 8])
+def test_cooperative_and_per_lane_products_are_bit_identical(prec, lanes):
+    """The warp-cooperative product (bond blocks copied into shared memory per wave) adds every row's terms in the
+    same order as the per-lane product, so with the same lanes and grid both give bit-identical solves and steps."""
+    sc = scenes.c2_plate_small(R=0.03)
+    out = {}
+    for product in (1, 0):
+        sim = pkg.Sim(sc, precision=prec)
+        sim.set_pcg_product(product)
+        sim.set_pcg_shape(lanes, 64)
+        shape = sim.pcg_shape()
+        assert shape["product"] == product and shape["lanes_per_row"] == lanes
+        st = sim.read_state()
+        dt = sc.config["dt"]
+        sy = sim.bdem_debug_system(st["pos"] + dt * st["vel"], st["quat"] + dt * st["quat_vel"], want_bonds=False)
+        x, it = sim.bdem_debug_pcg(-sy["g"], 1e-6, 5000)
+        sim.step(3)
+        out[product] = (x, it, sim.read_state(), shape["blocks"])
+        sim.close()
+    assert out[0][3] == out[1][3]  # same grid
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    for k in ("pos", "quat", "vel", "quat_vel", "broken"):
+        assert np.array_equal(out[0][2][k], out[1][2][k]), k

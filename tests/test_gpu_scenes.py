@@ -254,12 +254,10 @@ def test_full_size_plate_sampled_and_properties(prec):
     b = -sysd["g"]
     dx, it = sim.bdem_debug_pcg(b, 0.1, 20000)
     assert 0 < it[0] < 20000  # converged before the cap
+    # true residual b - H dx of the stored system (the inspection product is formed in FP64): in FP64 the recurrence
+    # residual agrees with it to rounding; in the mixed path the FP32 recurrence drifts on this ill-conditioned
+    # system, and the FP64-residual refinement re-solves until the true residual meets the requested 0.1
     r = b - sim.bdem_debug_matvec(dx)
-    if prec == pkg.BDEM_FP64:
-        # the recurrence residual met the tolerance and the true residual b - H dx agrees with it to rounding
-        assert np.linalg.norm(r) <= 0.1 * np.linalg.norm(b) * (1.0 + 1e-6)
-    else:
-        # FP32 recurrences drift from the true residual on this ill-conditioned system; what the Newton loop needs
-        # (its FP64 gradient refines the step) is a descent direction with a true residual clearly below |b|
-        assert np.linalg.norm(r) <= 0.6 * np.linalg.norm(b) and (b * dx).sum() > 0
+    assert np.linalg.norm(r) <= 0.1 * np.linalg.norm(b) * (1.0 + 1e-6), np.linalg.norm(r) / np.linalg.norm(b)
+    assert (b * dx).sum() > 0
     sim.close()
