@@ -282,18 +282,30 @@ bdem_status bdem_set_pcg_shape(bdem_sim* sim, int32_t lanes_per_row, int32_t blo
 
 /* How the PCG product reaches the off-diagonal bond blocks: product = 1 (default): in waves of one entry per thread,
  * each warp first copies its wave's 32 blocks into shared memory with 16-byte asynchronous copies taken by
- * consecutive threads from the same block (few cache lines per request); product = 0: each thread loads its own
- * entries' blocks (with the row descriptors and incidence entries staged in shared memory when they fit). Both give
- * the same sums in the same order. Keeps the lanes and grid (the grid shrinks if the blocks no longer fit). */
+ * consecutive threads from the same block (few cache lines per request); product = 2: the same with two buffers, the
+ * next wave's copies in flight while a wave is multiplied (twice the shared memory, fewer resident blocks);
+ * product = 0: each thread loads its own entries' blocks (with the row descriptors and incidence entries staged in
+ * shared memory when they fit). All give the same sums in the same order. Keeps the lanes and grid (the grid shrinks
+ * if the blocks no longer fit). */
 bdem_status bdem_set_pcg_product(bdem_sim* sim, int32_t product);
 
 /* The current PCG launch shape: lanes per row, grid size and product (as bdem_set_pcg_product); NULL skips. */
 bdem_status bdem_get_pcg_shape(const bdem_sim* sim, int32_t* lanes_per_row, int32_t* blocks, int32_t* product);
 
 /* Times the PCG kernel for `iters` iterations on the system at the current committed state for each candidate shape
- * (product 1 and 0 x lanes 1, 2, 4, 8 x 1..all co-resident blocks per SM), keeps the fastest, and reports its lanes
+ * (products 2, 1, 0 x lanes 1, 2, 4, 8 x 1..all co-resident blocks per SM), keeps the fastest, and reports its lanes
  * and grid (either pointer may be NULL; bdem_get_pcg_shape gives the product). Host-blocking. */
 bdem_status bdem_autotune_pcg(bdem_sim* sim, int32_t iters, int32_t* lanes_per_row, int32_t* blocks);
+
+/* ---- bond-Hessian tile ------------------------------------------------------------------------------------------
+ * The bond kernel that evaluates each bond's 12x12 reduced Hessian and its eigenvalue clamp (one thread per bond)
+ * runs in blocks of `tile` threads (64, 128 or 256; default 128); capped = 1 selects its variant compiled for 128
+ * registers per thread (twice the resident warps, with spills; FP32 path, first-order form only, else ignored). */
+bdem_status bdem_set_bond_tile(bdem_sim* sim, int32_t tile, int32_t capped);
+
+/* Times the bond-Hessian kernel `reps` times on the system at the current committed state for each tile and register
+ * variant, keeps the fastest and reports it (either pointer may be NULL). Host-blocking. */
+bdem_status bdem_autotune_bonds(bdem_sim* sim, int32_t reps, int32_t* tile, int32_t* capped);
 
 /* ---- allocation-free solve ---------------------------------------------------------------------------------------
  * The paper has no counterpart: this entry point exists for callers that cannot allocate device memory, for

@@ -104,6 +104,8 @@ _PROTOS = {
     "bdem_set_pcg_shape": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
     "bdem_autotune_pcg": (ctypes.c_int, [_vp, ctypes.c_int32, _ip, _ip]),
     "bdem_set_pcg_product": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "bdem_set_bond_tile": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
+    "bdem_autotune_bonds": (ctypes.c_int, [_vp, ctypes.c_int32, _ip, _ip]),
     "bdem_get_pcg_shape": (ctypes.c_int, [_vp, _ip, _ip, _ip]),
     "bdem_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "bdem_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(bdem_profile)]),
@@ -371,6 +373,14 @@ class Sim:
 
     def set_pcg_product(self, product):
         self._check(self.L.bdem_set_pcg_product(self.h, int(product)))
+
+    def set_bond_tile(self, tile, capped=0):
+        self._check(self.L.bdem_set_bond_tile(self.h, int(tile), int(capped)))
+
+    def autotune_bonds(self, reps=3):
+        t, c = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self.L.bdem_autotune_bonds(self.h, int(reps), ctypes.byref(t), ctypes.byref(c)))
+        return {"tile": t.value, "capped": c.value}
 
     def pcg_shape(self):
         lanes, blocks, product = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()

@@ -415,7 +415,7 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
   const int staged = max_rows * (int64_t)sizeof(int4) + max_ent * (int64_t)sizeof(int2) <= budget;
   // the cooperative product stages the row descriptors and one bond block per thread (its grid is shrunk to what is
   // co-resident with that shared memory by apply_pcg_shape)
-  const int mode = s->pcg_product ? 2 : (staged ? 1 : 0);
+  const int mode = s->pcg_product == 2 ? 3 : s->pcg_product == 1 ? 2 : (staged ? 1 : 0);
   // cuts block row ranges at scene boundaries
   auto cut = [&](const std::vector<int64_t>& bnd, std::vector<int32_t>& row, std::vector<int32_t>& scn,
                  std::vector<int32_t>& blk) {
@@ -477,7 +477,7 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
 // default PCG launch shape: 4 lanes per row, every co-resident block, at least 64 rows per block
 // co-resident PCG blocks as the registers allow (the partition's shared memory is checked in apply_pcg_shape)
 static int pcg_blocks_by_regs(const bdem_sim* s, int lanes) {
-  int mode = s->pcg_product ? 2 : 1;
+  int mode = s->pcg_product == 2 ? 3 : s->pcg_product == 1 ? 2 : 1;
   return pcg_max_blocks(s->d.mixed, lanes, pcg_smem_bytes_for(mode, s->d.mixed, 64, 64), mode);
 }
 
@@ -1934,7 +1934,7 @@ extern "C" bdem_status bdem_set_pcg_shape(bdem_sim* s, int32_t lanes, int32_t bl
 
 extern "C" bdem_status bdem_set_pcg_product(bdem_sim* s, int32_t product) {
   if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
-  if (product != 0 && product != 1) return fail(s, BDEM_E_INVALID, "product must be 0 or 1");
+  if (product < 0 || product > 2) return fail(s, BDEM_E_INVALID, "product must be 0, 1 or 2");
   s->pcg_product = product;
   return bdem_set_pcg_shape(s, s->d.pcg_lanes, s->d.pcg_grid);
 }
@@ -1943,7 +1943,7 @@ extern "C" bdem_status bdem_get_pcg_shape(const bdem_sim* s, int32_t* lanes, int
   if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
   if (lanes) *lanes = s->d.pcg_lanes;
   if (blocks) *blocks = s->d.pcg_grid;
-  if (product) *product = s->d.pcg_mode == 2 ? 1 : 0;
+  if (product) *product = s->d.pcg_mode == 3 ? 2 : s->d.pcg_mode == 2 ? 1 : 0;
   return BDEM_OK;
 }
 
@@ -1962,6 +1962,49 @@ static bdem_status assemble_at_committed(bdem_sim* s) {
   return sync(s);
 }
 
+extern "C" bdem_status bdem_set_bond_tile(bdem_sim* s, int32_t tile, int32_t capped) {
+  if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
+  if (tile != 64 && tile != 128 && tile != 256) return fail(s, BDEM_E_INVALID, "tile must be 64, 128 or 256");
+  if (capped != 0 && capped != 1) return fail(s, BDEM_E_INVALID, "capped must be 0 or 1");
+  TRY(sync(s));
+  s->d.bond_tile = tile;
+  s->d.bond_capped = capped;
+  return BDEM_OK;
+}
+
+extern "C" bdem_status bdem_autotune_bonds(bdem_sim* s, int32_t reps, int32_t* tile_out, int32_t* capped_out) {
+  if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
+  if (reps < 1) return fail(s, BDEM_E_INVALID, "reps must be >= 1");
+  if (s->nb == 0 || s->n == 0) return BDEM_OK;
+  TRY(assemble_at_committed(s));
+  cudaEvent_t a = ev_get(s), b = ev_get(s);
+  float best = 1e30f;
+  int best_t = s->d.bond_tile ? s->d.bond_tile : 128, best_c = s->d.bond_capped;
+  const int tiles[] = {64, 128, 256};
+  const int caps = (s->d.mixed && !s->d.midpoint) ? 2 : 1;  // the capped variant exists for the FP32 first-order form
+  for (int capped = 0; capped < caps; ++capped)
+    for (int tile : tiles) {
+      DevArrays d = s->d;
+      d.bond_tile = tile;
+      d.bond_capped = capped;
+      TRY(check_launch(s, launch_bond_hess(d, 1, s->stream)));  // warm-up
+      cudaEventRecord(a, s->stream);
+      for (int r = 0; r < reps; ++r) TRY(check_launch(s, launch_bond_hess(d, 1, s->stream)));
+      cudaEventRecord(b, s->stream);
+      TRY(sync(s));
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (ms < best) { best = ms; best_t = tile; best_c = capped; }
+    }
+  s->ev_pool.push_back(a);
+  s->ev_pool.push_back(b);
+  s->d.bond_tile = best_t;
+  s->d.bond_capped = best_c;
+  if (tile_out) *tile_out = best_t;
+  if (capped_out) *capped_out = best_c;
+  return BDEM_OK;
+}
+
 extern "C" bdem_status bdem_autotune_pcg(bdem_sim* s, int32_t iters, int32_t* lanes_out, int32_t* blocks_out) {
   if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
   if (iters < 1) return fail(s, BDEM_E_INVALID, "iters must be >= 1");
@@ -1974,7 +2017,7 @@ extern "C" bdem_status bdem_autotune_pcg(bdem_sim* s, int32_t iters, int32_t* la
   float best = 1e30f;
   int best_l = s->d.pcg_lanes, best_g = s->d.pcg_grid, best_p = s->pcg_product;
   const int lanes_c[] = {1, 2, 4, 8};
-  for (int product = 1; product >= 0; --product)
+  for (int product = 2; product >= 0; --product)
   for (int lanes : lanes_c) {
     s->pcg_product = product;
     int mx = pcg_blocks_by_regs(s, lanes);

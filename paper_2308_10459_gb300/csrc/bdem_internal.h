@@ -98,6 +98,8 @@ struct DevArrays {
   int32_t first_order;          // descent direction -g (Alg. 1) instead of the Newton direction
   int32_t midpoint;             // variational midpoint form: potentials at (x + x0)/2, inertia targets zhat
   int32_t refine;               // rounds of FP64-residual refinement per Newton solve (0: off; mixed + block Jacobi)
+  int32_t bond_tile;            // threads per block of the bond-Hessian kernel (64, 128, 256)
+  int32_t bond_capped;          // 1: its register-capped variant (FP32, first-order form)
   double* x64;                  // [N][6] FP64 accumulated solution of the refined solve (refine > 0)
   double* b64;                  // [N][6] FP64 right-hand side of an inspection solve (NULL: b = -g)
   // particles

@@ -524,8 +524,10 @@ __global__ void __launch_bounds__(kTile) k_particle_grad(DevArrays d, int mask, 
 // Hessian
 // ================================================================================================
 
-template <typename T, bool MID>
-__global__ void __launch_bounds__(128) k_bond_hess(DevArrays d, int all) {
+// MINB: resident 256-thread blocks the register budget is set for (1: up to 255 registers, as the 9x9 clamp wants;
+// 2: 128 registers, twice the resident warps at the price of spills); the block size is d.bond_tile (64, 128, 256)
+template <typename T, bool MID, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_bond_hess(DevArrays d, int all) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= d.nb) return;
   int s = d.bscene[b];
@@ -721,7 +723,10 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// waits until at most N of this thread's most recently committed copy groups are still pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // a block of NW words from shared memory (128-bit reads)
 template <int NW>
@@ -1128,12 +1133,22 @@ __device__ __noinline__ void pcg_decide(const DevArrays& d, int k_iter, const in
 //      the warp copies the wave's 32 bond blocks into shared memory with 16-byte cp.async copies in which
 //      consecutive lanes take consecutive 16-byte pieces of the same block, so that a copy request covers a few cache
 //      lines instead of one line per lane (with per-lane loads the L1 data pipe, not DRAM, bounds the product); each
-//      lane then multiplies its own entry's block from shared memory
+//      lane then multiplies its own entry's block from shared memory;
+//   3: as 2 with two slot buffers per warp: the copies of wave w + 1 are in flight while wave w is multiplied
+// resident blocks the register budget is set for: 4 of 256 threads per SM in FP32 (64 registers), 3 with the
+// cooperative product (85 registers; its shared-memory slots leave room for 3 or 4) and 2 with its double-buffered
+// form, 2 in FP64 (1 double-buffered)
+template <typename T, int MODE>
+constexpr int pcg_min_blocks() {
+  return sizeof(T) == 4 ? (MODE == 3 ? 2 : MODE == 2 ? 3 : 4) : (MODE == 3 ? 1 : 2);
+}
+
 template <typename T, int G, int MODE>
-__global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays d, int rhs_from_g, int mask) {
+__global__ void __launch_bounds__(kTile, pcg_min_blocks<T, MODE>()) k_pcg(DevArrays d, int rhs_from_g, int mask) {
   constexpr bool STAGED = MODE == 1;  // incidence entries in shared memory
   constexpr bool ROWS = MODE >= 1;    // row descriptors in shared memory
-  constexpr bool COOP = MODE == 2;
+  constexpr bool COOP = MODE >= 2;
+  constexpr int NB = MODE == 3 ? 2 : 1;  // slot buffers per warp of the cooperative product
   T* X = reinterpret_cast<T*>(d.vx);
   T* R = reinterpret_cast<T*>(d.vr);
   T* Z = reinterpret_cast<T*>(d.vz);
@@ -1150,7 +1165,7 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
   extern __shared__ int4 s_rows[];
   int2* s_ent = reinterpret_cast<int2*>(s_rows + d.pcg_max_rows);
   // COOP: this warp's 32 block slots (36 words each) after the row descriptors
-  T* s_blk = reinterpret_cast<T*>(s_rows + d.pcg_max_rows) + (threadIdx.x >> 5) * 32 * 36;
+  T* s_blk = reinterpret_cast<T*>(s_rows + d.pcg_max_rows) + (threadIdx.x >> 5) * NB * 32 * 36;
   const int R0 = d.seg_row[seg0], R1 = d.seg_row[seg1];
   const int E0 = d.inc_start[R0], E1 = d.inc_start[R1];
   // row descriptor: first incidence entry (relative to the block's first when staged), bond count, active-contact
@@ -1235,23 +1250,45 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) k_pcg(DevArrays
             const int nwave = __reduce_max_sync(0xffffffffu, live ? (rd.y + G - 1) / G : 0);
             constexpr int PP = 36 * (int)sizeof(T) / 16;  // 16-byte pieces of one block
             constexpr int PW = 16 / (int)sizeof(T);       // words of one piece
-            for (int w = 0; w < nwave; ++w) {
-              const int k = w * G + sub;
-              const bool has = live && k < rd.y;
-              const int2 e = has ? __ldg(d.inc2 + rd.x + k) : make_int2(-2, 0);
-              const int bond = e.x >> 1;  // -1: no entry in this slot
-              Vec6<T> xo;
-              if (has) xo = load6_cg<T>(Z, e.y);  // in flight with the copies
+            // copies of one wave's blocks (bond -1: no entry in that lane's slot) into a 32-slot buffer, as one group
+            auto copy_wave = [&](int bond, T* buf) {
 #pragma unroll
               for (int m = 0; m < PP; ++m) {
                 const int p = lane + 32 * m, slot = p / PP, q = p - slot * PP;
                 const int bs = __shfl_sync(0xffffffffu, bond, slot);
-                if (bs >= 0) cp_async16(s_blk + 36 * slot + PW * q, Mall + 36 * (size_t)bs + PW * q);
+                if (bs >= 0) cp_async16(buf + 36 * slot + PW * q, Mall + 36 * (size_t)bs + PW * q);
               }
-              cp_async_wait_all();
+              cp_async_commit();
+            };
+            // the wave's incidence entry and the other endpoint's z are loaded one wave ahead, so that the wait of a
+            // wave covers only its block copies
+            bool has = live && sub < rd.y;
+            int2 e = has ? __ldg(d.inc2 + rd.x + sub) : make_int2(-2, 0);
+            Vec6<T> xo;
+            if (has) xo = load6_cg<T>(Z, e.y);
+            if (NB == 2 && nwave > 0) copy_wave(e.x >> 1, s_blk);
+            for (int w = 0; w < nwave; ++w) {
+              T* cur = s_blk + (NB == 2 ? (w & 1) * 32 * 36 : 0);
+              if (NB == 1) copy_wave(e.x >> 1, cur);
+              const int kn = (w + 1) * G + sub;
+              const bool hasn = live && kn < rd.y;
+              const int2 en = hasn ? __ldg(d.inc2 + rd.x + kn) : make_int2(-2, 0);
+              Vec6<T> xon;
+              if (hasn) xon = load6_cg<T>(Z, en.y);
+              if (NB == 2) {
+                // the next wave's copies go to the other buffer, whose previous wave every lane has finished reading
+                if (w + 1 < nwave) copy_wave(en.x >> 1, s_blk + ((w + 1) & 1) * 32 * 36);
+                else cp_async_commit();  // an empty group keeps the count of pending groups uniform
+                cp_async_wait_group<1>();
+              } else {
+                cp_async_wait_group<0>();
+              }
               __syncwarp();
-              if (has) bond_block_mul_shared<T>(s_blk + 36 * lane, e.x & 1, xo, y);
-              __syncwarp();  // every lane has read its slot before the next wave's copies overwrite it
+              if (has) bond_block_mul_shared<T>(cur + 36 * lane, e.x & 1, xo, y);
+              __syncwarp();  // every lane has read its slot before a later wave's copies overwrite it
+              has = hasn;
+              e = en;
+              xo = xon;
             }
           } else if (live) {
             const int2* ent = ent_all + rd.x;
@@ -2062,12 +2099,16 @@ int launch_particle_grad(const DevArrays& d, int mask, int all, cudaStream_t s) 
 
 int launch_bond_hess(const DevArrays& d, int all, cudaStream_t s) {
   if (d.nb == 0) return 0;
+  const int bs = (d.bond_tile == 64 || d.bond_tile == 256) ? d.bond_tile : 128;
+  const int nbk = blocks_for(d.nb, bs);
   if (d.midpoint) {
-    if (d.mixed) k_bond_hess<float, true><<<blocks_for(d.nb, 128), 128, 0, s>>>(d, all);
-    else k_bond_hess<double, true><<<blocks_for(d.nb, 128), 128, 0, s>>>(d, all);
+    if (d.mixed) k_bond_hess<float, true, 1><<<nbk, bs, 0, s>>>(d, all);
+    else k_bond_hess<double, true, 1><<<nbk, bs, 0, s>>>(d, all);
+  } else if (d.mixed) {
+    if (d.bond_capped) k_bond_hess<float, false, 2><<<nbk, bs, 0, s>>>(d, all);
+    else k_bond_hess<float, false, 1><<<nbk, bs, 0, s>>>(d, all);
   } else {
-    if (d.mixed) k_bond_hess<float, false><<<blocks_for(d.nb, 128), 128, 0, s>>>(d, all);
-    else k_bond_hess<double, false><<<blocks_for(d.nb, 128), 128, 0, s>>>(d, all);
+    k_bond_hess<double, false, 1><<<nbk, bs, 0, s>>>(d, all);
   }
   return 1;
 }
@@ -2088,6 +2129,7 @@ size_t pcg_smem_bytes_for(int mode, int mixed, int max_rows, int max_entries) {
   size_t rows = sizeof(int4) * (size_t)(max_rows > 0 ? max_rows : 1);
   if (mode == 1) return rows + sizeof(int2) * (size_t)(max_entries > 0 ? max_entries : 1);
   if (mode == 2) return rows + (size_t)kTile * 36 * (mixed ? sizeof(float) : sizeof(double));
+  if (mode == 3) return rows + (size_t)2 * kTile * 36 * (mixed ? sizeof(float) : sizeof(double));
   return 0;
 }
 size_t pcg_smem_bytes(const DevArrays& d) {
@@ -2105,6 +2147,7 @@ static const void* pcg_kernel_m(int lanes) {
 }
 template <typename T>
 static const void* pcg_kernel(int lanes, int mode) {
+  if (mode == 3) return pcg_kernel_m<T, 3>(lanes);
   if (mode == 2) return pcg_kernel_m<T, 2>(lanes);
   if (mode == 1) return pcg_kernel_m<T, 1>(lanes);
   return pcg_kernel_m<T, 0>(lanes);

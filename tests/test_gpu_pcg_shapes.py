@@ -62,11 +62,12 @@ def test_staged_and_unstaged_grids_agree():
 @pytest.mark.parametrize("prec", [pkg.BDEM_FP64, pkg.BDEM_MIXED], ids=["fp64", "mixed"])
 @pytest.mark.parametrize("lanes", [2, 4, 8])
 def test_cooperative_and_per_lane_products_are_bit_identical(prec, lanes):
-    """The warp-cooperative product (bond blocks copied into shared memory per wave) adds every row's terms in the
-    same order as the per-lane product, so with the same lanes and grid both give bit-identical solves and steps."""
+    """The warp-cooperative products (bond blocks copied into shared memory per wave, single- and double-buffered)
+    add every row's terms in the same order as the per-lane product, so with the same lanes and grid all give
+    bit-identical solves and steps."""
     sc = scenes.c2_plate_small(R=0.03)
     out = {}
-    for product in (1, 0):
+    for product in (2, 1, 0):
         sim = pkg.Sim(sc, precision=prec)
         sim.set_pcg_product(product)
         sim.set_pcg_shape(lanes, 64)
@@ -79,7 +80,8 @@ def test_cooperative_and_per_lane_products_are_bit_identical(prec, lanes):
         sim.step(3)
         out[product] = (x, it, sim.read_state(), shape["blocks"])
         sim.close()
-    assert out[0][3] == out[1][3]  # same grid
-    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
-    for k in ("pos", "quat", "vel", "quat_vel", "broken"):
-        assert np.array_equal(out[0][2][k], out[1][2][k]), k
+    for product in (2, 1):
+        assert out[0][3] == out[product][3]  # same grid
+        assert np.array_equal(out[0][0], out[product][0]) and np.array_equal(out[0][1], out[product][1])
+        for k in ("pos", "quat", "vel", "quat_vel", "broken"):
+            assert np.array_equal(out[0][2][k], out[product][2][k]), (product, k)
