@@ -442,9 +442,10 @@ def main():
                     help="steps of the 64-scene batched workload measured beside the plate (0: skip)")
     ap.add_argument("--pcg-lanes", type=int, default=0, help="lanes per row of the PCG product (0: autotune)")
     ap.add_argument("--pcg-blocks", type=int, default=0, help="PCG grid size with --pcg-lanes (0: all resident)")
-    ap.add_argument("--pcg-product", type=int, default=1, choices=[0, 1, 2],
-                    help="with --pcg-lanes: 2 double-buffered and 1 single-buffered warp-cooperative staging of the "
-                         "bond blocks, 0 per-lane loads")
+    ap.add_argument("--pcg-product", type=int, default=1, choices=[0, 1, 2, 3],
+                    help="with --pcg-lanes: 3 one grid barrier per iteration (update fused into the next product), "
+                         "2 double-buffered and 1 single-buffered warp-cooperative staging of the bond blocks, 0 "
+                         "per-lane loads")
     ap.add_argument("--pcg-probe", type=int, default=0,
                     help="time N PCG iterations of one solve (eps 0) on the workload's system and exit (profiling)")
     ap.add_argument("--workload", default="plate", choices=["plate", "batched", "impact"],

@@ -285,15 +285,18 @@ bdem_status bdem_set_pcg_shape(bdem_sim* sim, int32_t lanes_per_row, int32_t blo
  * consecutive threads from the same block (few cache lines per request); product = 2: the same with two buffers, the
  * next wave's copies in flight while a wave is multiplied (twice the shared memory, fewer resident blocks);
  * product = 0: each thread loads its own entries' blocks (with the row descriptors and incidence entries staged in
- * shared memory when they fit). All give the same sums in the same order. Keeps the lanes and grid (the grid shrinks
- * if the blocks no longer fit). */
+ * shared memory when they fit); these three give the same sums in the same order. product = 3: the fused PCG, one
+ * grid barrier per iteration: the vector update is folded into the next product (each block keeps its rows' new z in
+ * shared memory and recomputes its halo rows' z from their previous r, s and w, which alternate between two buffers),
+ * with the bond blocks staged as in product 1; the same iterates up to rounding. Keeps the lanes and grid (the grid
+ * shrinks if the blocks no longer fit). */
 bdem_status bdem_set_pcg_product(bdem_sim* sim, int32_t product);
 
 /* The current PCG launch shape: lanes per row, grid size and product (as bdem_set_pcg_product); NULL skips. */
 bdem_status bdem_get_pcg_shape(const bdem_sim* sim, int32_t* lanes_per_row, int32_t* blocks, int32_t* product);
 
 /* Times the PCG kernel for `iters` iterations on the system at the current committed state for each candidate shape
- * (products 2, 1, 0 x lanes 1, 2, 4, 8 x 1..all co-resident blocks per SM), keeps the fastest, and reports its lanes
+ * (products 3, 2, 1, 0 x lanes 1, 2, 4, 8 x 1..all co-resident blocks per SM), keeps the fastest, and reports its lanes
  * and grid (either pointer may be NULL; bdem_get_pcg_shape gives the product). Host-blocking. */
 bdem_status bdem_autotune_pcg(bdem_sim* sim, int32_t iters, int32_t* lanes_per_row, int32_t* blocks);
 

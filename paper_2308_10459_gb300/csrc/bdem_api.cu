@@ -291,7 +291,7 @@ static bdem_status alloc_particles(bdem_sim* s) {
   TRY(dalloc_t(s, &d.g, 6 * n));
   TRY(dalloc(s, &d.D, w * kDiagStride * n));
   TRY(dalloc(s, &d.Dinv, w * kDiagStride * n));
-  void** pv[] = {&d.vx, &d.vr, &d.vz, &d.vp_, &d.vq_, &d.vs};
+  void** pv[] = {&d.vx, &d.vr, &d.vz, &d.vp_, &d.vq_, &d.vs, &d.vr2, &d.vs2, &d.vq2};
   for (void** p : pv) TRY(dalloc(s, p, w * 6 * n));
   if (d.refine) TRY(dalloc_t(s, &d.x64, 6 * n));
   int hs = 1024;
@@ -415,7 +415,7 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
   const int staged = max_rows * (int64_t)sizeof(int4) + max_ent * (int64_t)sizeof(int2) <= budget;
   // the cooperative product stages the row descriptors and one bond block per thread (its grid is shrunk to what is
   // co-resident with that shared memory by apply_pcg_shape)
-  const int mode = s->pcg_product == 2 ? 3 : s->pcg_product == 1 ? 2 : (staged ? 1 : 0);
+  const int mode = s->pcg_product == 3 ? 4 : s->pcg_product == 2 ? 3 : s->pcg_product == 1 ? 2 : (staged ? 1 : 0);
   // cuts block row ranges at scene boundaries
   auto cut = [&](const std::vector<int64_t>& bnd, std::vector<int32_t>& row, std::vector<int32_t>& scn,
                  std::vector<int32_t>& blk) {
@@ -471,14 +471,67 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
   d.pcg_max_rows = (int32_t)std::max<int64_t>(max_rows, 1);
   d.pcg_max_entries = (int32_t)std::max<int64_t>(max_ent, 1);
   d.pcg_mode = mode;
+  // the fused PCG's halo rows and local neighbour slots (the incidence of the bonds in the device's entry order)
+  {
+    void* holds[] = {d.halo_start, d.halo_rows, d.inc2_loc};
+    for (void* p : holds) dfree(s, p);
+    d.halo_start = d.halo_rows = nullptr;
+    d.inc2_loc = nullptr;
+    d.pcg_max_zslots = 0;
+  }
+  if (mode == 4) {
+    const int64_t nb = s->nb;
+    std::vector<int32_t> ist(n + 1, 0);
+    for (int64_t k = 0; k < nb; ++k) {
+      ist[s->bi[k] + 1]++;
+      ist[s->bj[k] + 1]++;
+    }
+    for (int64_t i = 0; i < n; ++i) ist[i + 1] += ist[i];
+    std::vector<int2> inc(std::max<int64_t>(2 * nb, 1));
+    {
+      std::vector<int32_t> fill(ist.begin(), ist.end() - 1);
+      for (int64_t k = 0; k < nb; ++k) {
+        inc[fill[s->bi[k]]++] = make_int2((int32_t)(k << 1), s->bj[k]);
+        inc[fill[s->bj[k]]++] = make_int2((int32_t)((k << 1) | 1), s->bi[k]);
+      }
+    }
+    std::vector<int32_t> hstart(grid + 1, 0), hrows, halo;
+    int64_t max_slots = 2;
+    for (int b = 0; b < grid; ++b) {
+      const int64_t r0 = bounds[b], r1 = bounds[b + 1];
+      hstart[b] = (int32_t)hrows.size();
+      halo.clear();
+      for (int64_t e = ist[r0]; e < ist[r1]; ++e)
+        if (inc[e].y < r0 || inc[e].y >= r1) halo.push_back(inc[e].y);
+      std::sort(halo.begin(), halo.end());
+      halo.erase(std::unique(halo.begin(), halo.end()), halo.end());
+      for (int64_t e = ist[r0]; e < ist[r1]; ++e) {
+        int32_t o = inc[e].y;
+        int64_t slot = (o >= r0 && o < r1) ? o - r0
+                                           : (r1 - r0) + (std::lower_bound(halo.begin(), halo.end(), o) - halo.begin());
+        inc[e].y = (int32_t)slot;
+      }
+      hrows.insert(hrows.end(), halo.begin(), halo.end());
+      max_slots = std::max<int64_t>(max_slots, (r1 - r0) + (int64_t)halo.size());
+    }
+    hstart[grid] = (int32_t)hrows.size();
+    TRY(dalloc_t(s, &d.halo_start, (size_t)grid + 1));
+    TRY(dalloc_t(s, &d.halo_rows, std::max<size_t>(hrows.size(), 1)));
+    TRY(dalloc_t(s, &d.inc2_loc, inc.size()));
+    CUDA_TRY(s, cudaMemcpy(d.halo_start, hstart.data(), sizeof(int32_t) * hstart.size(), cudaMemcpyHostToDevice));
+    if (!hrows.empty())
+      CUDA_TRY(s, cudaMemcpy(d.halo_rows, hrows.data(), sizeof(int32_t) * hrows.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(s, cudaMemcpy(d.inc2_loc, inc.data(), sizeof(int2) * inc.size(), cudaMemcpyHostToDevice));
+    d.pcg_max_zslots = (int32_t)((max_slots + 1) & ~int64_t(1));  // even: the bond-block slots start 16-byte aligned
+  }
   return BDEM_OK;
 }
 
 // default PCG launch shape: 4 lanes per row, every co-resident block, at least 64 rows per block
 // co-resident PCG blocks as the registers allow (the partition's shared memory is checked in apply_pcg_shape)
 static int pcg_blocks_by_regs(const bdem_sim* s, int lanes) {
-  int mode = s->pcg_product == 2 ? 3 : s->pcg_product == 1 ? 2 : 1;
-  return pcg_max_blocks(s->d.mixed, lanes, pcg_smem_bytes_for(mode, s->d.mixed, 64, 64), mode);
+  int mode = s->pcg_product == 3 ? 4 : s->pcg_product == 2 ? 3 : s->pcg_product == 1 ? 2 : 1;
+  return pcg_max_blocks(s->d.mixed, lanes, pcg_smem_bytes_for(mode, s->d.mixed, 64, 64, 128), mode);
 }
 
 // builds the partition for (lanes, grid) and shrinks the grid until every block is co-resident with the partition's
@@ -1896,6 +1949,7 @@ extern "C" bdem_status bdem_pcg_static(bdem_sim* s, const double* b_dev, double*
   void** vecs[] = {&d.vx, &d.vr, &d.vz, &d.vp_, &d.vq_, &d.vs};
   for (int k = 0; k < kVecs; ++k) *vecs[k] = b8 + off_vec + k * vec_bytes;
   d.pcg_max = max_iter;
+  if (d.pcg_mode == 4) d.pcg_mode = 2;  // the fused PCG's second buffers are not in the static array
   cudaStream_t st = s->stream;
   int k = launch_static_pcg_init(d, eps_r, st);
   k += launch_convert_perm(b_dev, 1, d.vr, !d.mixed, d.perm, 0, (int)n, st);
@@ -1934,7 +1988,7 @@ extern "C" bdem_status bdem_set_pcg_shape(bdem_sim* s, int32_t lanes, int32_t bl
 
 extern "C" bdem_status bdem_set_pcg_product(bdem_sim* s, int32_t product) {
   if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
-  if (product < 0 || product > 2) return fail(s, BDEM_E_INVALID, "product must be 0, 1 or 2");
+  if (product < 0 || product > 3) return fail(s, BDEM_E_INVALID, "product must be 0, 1, 2 or 3");
   s->pcg_product = product;
   return bdem_set_pcg_shape(s, s->d.pcg_lanes, s->d.pcg_grid);
 }
@@ -1943,7 +1997,7 @@ extern "C" bdem_status bdem_get_pcg_shape(const bdem_sim* s, int32_t* lanes, int
   if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
   if (lanes) *lanes = s->d.pcg_lanes;
   if (blocks) *blocks = s->d.pcg_grid;
-  if (product) *product = s->d.pcg_mode == 3 ? 2 : s->d.pcg_mode == 2 ? 1 : 0;
+  if (product) *product = s->d.pcg_mode == 4 ? 3 : s->d.pcg_mode == 3 ? 2 : s->d.pcg_mode == 2 ? 1 : 0;
   return BDEM_OK;
 }
 
@@ -2017,7 +2071,7 @@ extern "C" bdem_status bdem_autotune_pcg(bdem_sim* s, int32_t iters, int32_t* la
   float best = 1e30f;
   int best_l = s->d.pcg_lanes, best_g = s->d.pcg_grid, best_p = s->pcg_product;
   const int lanes_c[] = {1, 2, 4, 8};
-  for (int product = 2; product >= 0; --product)
+  for (int product = 3; product >= 0; --product)
   for (int lanes : lanes_c) {
     s->pcg_product = product;
     int mx = pcg_blocks_by_regs(s, lanes);

@@ -111,6 +111,7 @@ struct DevArrays {
   double* g;
   void *D, *Dinv;
   void *vx, *vr, *vz, *vp_, *vq_, *vs;   // x, r, z, p, w (= H z; also the inspection product), s (= H p)
+  void *vr2, *vs2, *vq2;        // second buffers of r, s, w for the fused PCG (k_pcg_fused)
   // bonds
   int2* bij;
   double4 *brest, *bstiff;
@@ -138,6 +139,12 @@ struct DevArrays {
                                                      // product reaches the bond blocks (k_pcg MODE 0, 1, 2)
   int32_t *seg_row, *seg_scene, *block_seg, *scene_seg;
   int32_t *useg_row, *useg_scene, *ublock_seg;      // equal-rows partition of the elementwise PCG phases
+  // fused PCG (pcg_mode 4): each block's halo rows (rows outside its product range that its bond entries reference),
+  // halo_start [P+1] into halo_rows; the incidence entries with their neighbour's slot in the block's shared z array
+  // (own rows first, then the halo); the most slots of one block
+  int32_t *halo_start, *halo_rows;
+  int2* inc2_loc;
+  int32_t pcg_max_zslots;
   double* part_s;               // [n_seg][kPartials]
   SceneCtl* sc;
   Counters* cnt;
@@ -198,7 +205,7 @@ int launch_scene_reduce(const DevArrays& d, int mode, unsigned long long cond, c
 int launch_pcg(const DevArrays& d, int rhs_from_g, int mask_kin, cudaStream_t s, cudaError_t* err);
 int pcg_max_blocks(int mixed, int lanes, size_t smem, int mode);  // co-resident PCG blocks on this device (0: none)
 size_t pcg_smem_bytes(const DevArrays& d);  // dynamic shared memory of a PCG block in the arrays' mode
-size_t pcg_smem_bytes_for(int mode, int mixed, int max_rows, int max_entries);
+size_t pcg_smem_bytes_for(int mode, int mixed, int max_rows, int max_entries, int max_zslots);
 int launch_gdx(const DevArrays& d, cudaStream_t s);
 int launch_ls_trial(const DevArrays& d, cudaStream_t s);
 int launch_ls_energy(const DevArrays& d, cudaStream_t s);

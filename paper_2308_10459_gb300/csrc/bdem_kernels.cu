@@ -1391,6 +1391,263 @@ __global__ void __launch_bounds__(kTile, pcg_min_blocks<T, MODE>()) k_pcg(DevArr
 }
 
 // ================================================================================================
+// fused PCG (MODE 4): the same Chronopoulos-Gear iterates with one grid barrier per iteration instead of two. The
+// vector update of iteration k (p = z + beta p, s = w + beta s, x += alpha p, r -= alpha s, z = M^-1 r) and the product
+// w = H z of iteration k + 1 run in one phase: every block updates its own rows (the product partition's) and keeps
+// their new z in shared memory, and recomputes the new z of its halo rows (the rows outside its range its bond entries
+// reference) from their previous r, s, w and block-Jacobi inverse, so that no other block's update has to be waited
+// for. r, s and w alternate between two buffers (the halo recomputation of iteration k reads the buffers of
+// iteration k - 1 while their owners write those of iteration k); x, p and z are only read by their owners and stay
+// in place. Active-contact neighbours outside the block recompute their z the same way. The bond blocks reach shared
+// memory as in MODE 2 (one wave of 32 entries per warp, warp-cooperative 16-byte copies).
+// ================================================================================================
+
+template <typename T>
+__device__ __forceinline__ void pcg_update_z(const T* Dinv, int i, const T* Rp, const T* Sp, const T* Wp, T al, T be,
+                                             T (&z)[6]) {
+  Vec6<T> r = load6_cg<T>(Rp, i), s = load6_cg<T>(Sp, i), w = load6_cg<T>(Wp, i);
+  T rn[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) rn[k] = r.v[k] - al * (w.v[k] + be * s.v[k]);
+  sym6_mul<T>(Dinv + kDiagStride * (size_t)i, rn, z);
+}
+
+template <typename T, int G>
+__global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 2 : 1) k_pcg_fused(DevArrays d, int rhs_from_g, int mask) {
+  T* X = reinterpret_cast<T*>(d.vx);
+  T* Zg = reinterpret_cast<T*>(d.vz);
+  T* P = reinterpret_cast<T*>(d.vp_);
+  T* const R_0 = reinterpret_cast<T*>(d.vr);
+  T* const R_1 = reinterpret_cast<T*>(d.vr2);
+  T* const S_0 = reinterpret_cast<T*>(d.vs);
+  T* const S_1 = reinterpret_cast<T*>(d.vs2);
+  T* const W_0 = reinterpret_cast<T*>(d.vq_);
+  T* const W_1 = reinterpret_cast<T*>(d.vq2);
+  const T* Dinv = reinterpret_cast<const T*>(d.Dinv);
+  const T* Dm = reinterpret_cast<const T*>(d.D);
+  const T* Mall = reinterpret_cast<const T*>(d.bM);
+  const int seg0 = d.block_seg[blockIdx.x], seg1 = d.block_seg[blockIdx.x + 1];
+  const int R0 = d.seg_row[seg0], R1 = d.seg_row[seg1], nown = R1 - R0;
+  const int h0 = d.halo_start[blockIdx.x], h1 = d.halo_start[blockIdx.x + 1];
+  extern __shared__ int4 s_rows[];                                      // [pcg_max_rows] row descriptors
+  T* s_z = reinterpret_cast<T*>(s_rows + d.pcg_max_rows);              // [pcg_max_zslots][6]: own rows, then halo
+  T* s_blk = s_z + 6 * (size_t)d.pcg_max_zslots + (threadIdx.x >> 5) * 32 * 36;  // this warp's 32 block slots
+  for (int i = R0 + threadIdx.x; i < R1; i += blockDim.x) {
+    int a = d.inc_start[i];
+    int na = (d.k_self > 0.0) ? d.c_act[i] : 0;
+    int kin = (mask && d.kin[i]) ? (1 << 30) : 0;
+    s_rows[i - R0] = make_int4(a, d.inc_start[i + 1] - a, na | kin, d.c_start[i]);
+  }
+  __shared__ int s_sseg[kTile + 1];
+  const bool sseg_ok = d.n_scenes <= kTile;
+  if (sseg_ok)
+    for (int x = threadIdx.x; x <= d.n_scenes; x += blockDim.x) s_sseg[x] = d.scene_seg[x];
+  __shared__ LocalPcg s_loc;
+  const bool local = d.n_scenes <= kLocalScenes;
+  if (local && threadIdx.x < d.n_scenes) {
+    const SceneCtl* c = d.sc + threadIdx.x;
+    int on = pcg_on(*c);
+    s_loc.st[threadIdx.x] = PcgState{on, on, 0, c->eps_r, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  }
+  __syncthreads();
+  const T zero6[6] = {0, 0, 0, 0, 0, 0};
+  // ---- init (own rows): x = p = s = 0, r = b, z = M^-1 r
+  for (int g = seg0; g < seg1; ++g) {
+    if (!pcg_on(d.sc[d.seg_scene[g]])) continue;
+    for (int i = d.seg_row[g] + threadIdx.x; i < d.seg_row[g + 1]; i += blockDim.x) {
+      T r[6], z[6];
+      if (rhs_from_g) {
+        const double* gg = d.g + 6 * (size_t)i;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) r[k] = (T)(-gg[k]);
+      } else {
+        Vec6<T> b = load6<T>(R_0, i);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) r[k] = b.v[k];
+      }
+      if (mask && d.kin[i])
+#pragma unroll
+        for (int k = 0; k < 6; ++k) r[k] = (T)0;
+      sym6_mul<T>(Dinv + kDiagStride * (size_t)i, r, z);
+      store6<T>(X, i, zero6);
+      store6<T>(P, i, zero6);
+      store6<T>(S_0, i, zero6);
+      store6<T>(R_0, i, r);
+      store6<T>(Zg, i, z);
+    }
+  }
+  if (!grid_barrier(d, [] {})) return;
+  const int sub = threadIdx.x % G, grp = threadIdx.x / G, rows_per_pass = blockDim.x / G, lane = threadIdx.x & 31;
+  constexpr int PP = 36 * (int)sizeof(T) / 16;
+  constexpr int PW = 16 / (int)sizeof(T);
+  for (int k_iter = 0;; ++k_iter) {
+    // this iteration's r, s, w buffers and the previous iteration's
+    const bool odd = k_iter & 1;
+    T* const Rc = odd ? R_1 : R_0;
+    T* const Sc = odd ? S_1 : S_0;
+    T* const Wc = odd ? W_1 : W_0;
+    T* const Rp = odd ? R_0 : R_1;
+    T* const Sp = odd ? S_0 : S_1;
+    T* const Wp = odd ? W_0 : W_1;
+    // the scalars of the decision that closed the previous iteration, per scene
+    auto coef = [&](int sc, T& al, T& be) -> bool {
+      if (local) {
+        al = (T)s_loc.st[sc].alpha;
+        be = (T)s_loc.st[sc].beta;
+        return s_loc.st[sc].pcg_active != 0;
+      }
+      al = (T)__ldcg(&d.sc[sc].alpha);
+      be = (T)__ldcg(&d.sc[sc].beta);
+      return pcg_on(d.sc[sc]) && (k_iter == 0 || __ldcg(&d.sc[sc].pcg_active));
+    };
+    // ---- U: own rows' update (from iteration 1 on) with their new z kept in shared memory; halo rows' new z
+    for (int g = seg0; g < seg1; ++g) {
+      T al, be;
+      if (!coef(d.seg_scene[g], al, be)) continue;
+      for (int i = d.seg_row[g] + threadIdx.x; i < d.seg_row[g + 1]; i += blockDim.x) {
+        T zn[6];
+        if (k_iter == 0) {
+          Vec6<T> z = load6_cg<T>(Zg, i);
+#pragma unroll
+          for (int k = 0; k < 6; ++k) zn[k] = z.v[k];
+        } else {
+          Vec6<T> z = load6_cg<T>(Zg, i), w = load6_cg<T>(Wp, i), p = load6_cg<T>(P, i);
+          Vec6<T> s = load6_cg<T>(Sp, i), x = load6_cg<T>(X, i), r = load6_cg<T>(Rp, i);
+          T pn[6], sn[6], xn[6], rn[6];
+#pragma unroll
+          for (int k = 0; k < 6; ++k) {
+            pn[k] = z.v[k] + be * p.v[k];
+            sn[k] = w.v[k] + be * s.v[k];
+            xn[k] = x.v[k] + al * pn[k];
+            rn[k] = r.v[k] - al * sn[k];
+          }
+          sym6_mul<T>(Dinv + kDiagStride * (size_t)i, rn, zn);
+          store6<T>(P, i, pn);
+          store6<T>(Sc, i, sn);
+          store6<T>(X, i, xn);
+          store6<T>(Rc, i, rn);
+          store6<T>(Zg, i, zn);
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s_z[6 * (i - R0) + k] = zn[k];
+      }
+    }
+    for (int h = h0 + threadIdx.x; h < h1; h += blockDim.x) {
+      const int j = d.halo_rows[h];
+      T al, be;
+      if (!coef(d.pscene[j], al, be)) continue;
+      T zn[6];
+      if (k_iter == 0) {
+        Vec6<T> z = load6_cg<T>(Zg, j);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) zn[k] = z.v[k];
+      } else {
+        pcg_update_z<T>(Dinv, j, Rp, Sp, Wp, al, be, zn);
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) s_z[6 * (nown + h - h0) + k] = zn[k];
+    }
+    __syncthreads();
+    // ---- A: w = H z from the shared z, gamma = r.z, delta = w.z, rho = r.r (per segment, deterministic)
+    for (int g = seg0; g < seg1; ++g) {
+      const int sc = d.seg_scene[g];
+      T al, be;
+      const bool act = coef(sc, al, be);
+      DotAcc<T> dg, dd, dr;
+      if (act) {
+        const int r0 = d.seg_row[g], r1 = d.seg_row[g + 1];
+        for (int base = r0; base < r1; base += rows_per_pass) {
+          const int i = base + grp;
+          const bool valid = i < r1;
+          T y[6] = {0, 0, 0, 0, 0, 0};
+          const int4 rd = valid ? s_rows[i - R0] : make_int4(0, 0, 1 << 30, 0);
+          const bool live = valid && !(rd.z & (1 << 30));
+          Vec6<T> zi;
+          if (valid)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) zi.v[k] = s_z[6 * (i - R0) + k];
+          if (live && sub == 0) sym6_mul<T>(Dm + kDiagStride * (size_t)i, zi.v, y);
+          const int nwave = __reduce_max_sync(0xffffffffu, live ? (rd.y + G - 1) / G : 0);
+          for (int w = 0; w < nwave; ++w) {
+            const int k = w * G + sub;
+            const bool has = live && k < rd.y;
+            const int2 e = has ? __ldg(d.inc2_loc + rd.x + k) : make_int2(-2, 0);
+            const int bond = e.x >> 1;
+#pragma unroll
+            for (int m = 0; m < PP; ++m) {
+              const int p = lane + 32 * m, slot = p / PP, q = p - slot * PP;
+              const int bs = __shfl_sync(0xffffffffu, bond, slot);
+              if (bs >= 0) cp_async16(s_blk + 36 * slot + PW * q, Mall + 36 * (size_t)bs + PW * q);
+            }
+            cp_async_commit();
+            Vec6<T> xo;
+            if (has)
+#pragma unroll
+              for (int c = 0; c < 6; ++c) xo.v[c] = s_z[6 * e.y + c];
+            cp_async_wait_group<0>();
+            __syncwarp();
+            if (has) bond_block_mul_shared<T>(s_blk + 36 * lane, e.x & 1, xo, y);
+            __syncwarp();
+          }
+          if (live) {
+            const int nact = rd.z & ((1 << 30) - 1);
+            for (int k = sub; k < nact; k += G) {
+              const int e = rd.w + k;
+              const int c = d.c_anbr[e];
+              T4<T> cb = reinterpret_cast<const T4<T>*>(d.c_blk)[e];
+              Vec6<T> xo;
+              if (c >= R0 && c < R1) {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) xo.v[q] = s_z[6 * (c - R0) + q];
+              } else if (k_iter == 0) {
+                xo = load6_cg<T>(Zg, c);
+              } else {
+                T a2, b2;
+                coef(d.pscene[c], a2, b2);
+                pcg_update_z<T>(Dinv, c, Rp, Sp, Wp, a2, b2, xo.v);
+              }
+              T t = cb.w * (cb.x * xo.v[0] + cb.y * xo.v[1] + cb.z * xo.v[2]);
+              y[0] -= t * cb.x;
+              y[1] -= t * cb.y;
+              y[2] -= t * cb.z;
+            }
+          }
+#pragma unroll
+          for (int o = G / 2; o >= 1; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) y[k] += __shfl_xor_sync(0xffffffffu, y[k], o, G);
+          if (valid && sub == 0) {
+            store6<T>(Wc, i, y);
+            Vec6<T> ri = load6_cg<T>(Rc, i);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+              dg.add(ri.v[k], zi.v[k]);
+              dd.add(y[k], zi.v[k]);
+              dr.add(ri.v[k], ri.v[k]);
+            }
+          }
+        }
+      }
+      double acc[3] = {dg.value(), dd.value(), dr.value()};
+      block_sum<3>(acc);
+      if (threadIdx.x == 0) {
+        d.part_s[kPartials * g] = acc[0];
+        d.part_s[kPartials * g + 1] = acc[1];
+        d.part_s[kPartials * g + 2] = acc[2];
+      }
+    }
+    if (local) {
+      if (!grid_barrier(d, [] {})) return;
+      pcg_decide_local(d, k_iter, s_sseg, s_loc);
+      if (s_loc.n_active == 0 || __ldcg(&d.cnt->timeout)) break;
+    } else {
+      if (!grid_barrier(d, [&] { pcg_decide(d, k_iter, sseg_ok ? s_sseg : nullptr); })) return;
+      if (__ldcg(&d.cnt->n_active) == 0 || __ldcg(&d.cnt->timeout)) break;
+    }
+  }
+}
+
+// ================================================================================================
 // per-scene reductions outside the PCG (Newton residual, descent check, line search decision)
 // ================================================================================================
 
@@ -2125,15 +2382,17 @@ int launch_scene_reduce(const DevArrays& d, int mode, unsigned long long cond, c
   return 1;
 }
 
-size_t pcg_smem_bytes_for(int mode, int mixed, int max_rows, int max_entries) {
+size_t pcg_smem_bytes_for(int mode, int mixed, int max_rows, int max_entries, int max_zslots) {
   size_t rows = sizeof(int4) * (size_t)(max_rows > 0 ? max_rows : 1);
+  size_t w = mixed ? sizeof(float) : sizeof(double);
   if (mode == 1) return rows + sizeof(int2) * (size_t)(max_entries > 0 ? max_entries : 1);
-  if (mode == 2) return rows + (size_t)kTile * 36 * (mixed ? sizeof(float) : sizeof(double));
-  if (mode == 3) return rows + (size_t)2 * kTile * 36 * (mixed ? sizeof(float) : sizeof(double));
+  if (mode == 2) return rows + (size_t)kTile * 36 * w;
+  if (mode == 3) return rows + (size_t)2 * kTile * 36 * w;
+  if (mode == 4) return rows + (size_t)(max_zslots > 0 ? max_zslots : 2) * 6 * w + (size_t)kTile * 36 * w;
   return 0;
 }
 size_t pcg_smem_bytes(const DevArrays& d) {
-  return pcg_smem_bytes_for(d.pcg_mode, d.mixed, d.pcg_max_rows, d.pcg_max_entries);
+  return pcg_smem_bytes_for(d.pcg_mode, d.mixed, d.pcg_max_rows, d.pcg_max_entries, d.pcg_max_zslots);
 }
 
 template <typename T, int MODE>
@@ -2147,6 +2406,12 @@ static const void* pcg_kernel_m(int lanes) {
 }
 template <typename T>
 static const void* pcg_kernel(int lanes, int mode) {
+  if (mode == 4) switch (lanes) {
+      case 1: return (const void*)k_pcg_fused<T, 1>;
+      case 2: return (const void*)k_pcg_fused<T, 2>;
+      case 8: return (const void*)k_pcg_fused<T, 8>;
+      default: return (const void*)k_pcg_fused<T, 4>;
+    }
   if (mode == 3) return pcg_kernel_m<T, 3>(lanes);
   if (mode == 2) return pcg_kernel_m<T, 2>(lanes);
   if (mode == 1) return pcg_kernel_m<T, 1>(lanes);
