@@ -289,7 +289,8 @@ bdem_status bdem_set_pcg_shape(bdem_sim* sim, int32_t lanes_per_row, int32_t blo
  * grid barrier per iteration: the vector update is folded into the next product (each block keeps its rows' new z in
  * shared memory and recomputes its halo rows' z from their previous r, s and w, which alternate between two buffers),
  * with the bond blocks staged as in product 1; the same iterates up to rounding. Keeps the lanes and grid (the grid
- * shrinks if the blocks no longer fit). */
+ * shrinks if the blocks no longer fit); BDEM_E_INVALID when no block of the product fits an SM beside its share of
+ * the rows, with the previous product kept. */
 bdem_status bdem_set_pcg_product(bdem_sim* sim, int32_t product);
 
 /* The current PCG launch shape: lanes per row, grid size and product (as bdem_set_pcg_product); NULL skips. */

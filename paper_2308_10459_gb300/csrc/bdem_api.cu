@@ -381,7 +381,14 @@ static void morton_order(const int64_t* offsets, int n_scenes, const double* pos
   }
 }
 
+// kernel variant (DevArrays::pcg_mode) of a product setting: 3 the fused one-barrier PCG, 2 and 1 the double- and
+// single-buffered cooperative staging, 0 per-lane loads (with the rows and entries staged when they fit)
+static int pcg_mode_of(int product, int staged) {
+  return product == 3 ? 4 : product == 2 ? 3 : product == 1 ? 2 : (staged ? 1 : 0);
+}
+
 // balanced PCG row ranges per block and their intersections with the scenes (segments)
+
 static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
   DevArrays& d = s->d;
   int64_t n = s->n;
@@ -415,7 +422,7 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
   const int staged = max_rows * (int64_t)sizeof(int4) + max_ent * (int64_t)sizeof(int2) <= budget;
   // the cooperative product stages the row descriptors and one bond block per thread (its grid is shrunk to what is
   // co-resident with that shared memory by apply_pcg_shape)
-  const int mode = s->pcg_product == 3 ? 4 : s->pcg_product == 2 ? 3 : s->pcg_product == 1 ? 2 : (staged ? 1 : 0);
+  const int mode = pcg_mode_of(s->pcg_product, staged);
   // cuts block row ranges at scene boundaries
   auto cut = [&](const std::vector<int64_t>& bnd, std::vector<int32_t>& row, std::vector<int32_t>& scn,
                  std::vector<int32_t>& blk) {
@@ -530,7 +537,7 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
 // default PCG launch shape: 4 lanes per row, every co-resident block, at least 64 rows per block
 // co-resident PCG blocks as the registers allow (the partition's shared memory is checked in apply_pcg_shape)
 static int pcg_blocks_by_regs(const bdem_sim* s, int lanes) {
-  int mode = s->pcg_product == 3 ? 4 : s->pcg_product == 2 ? 3 : s->pcg_product == 1 ? 2 : 1;
+  int mode = pcg_mode_of(s->pcg_product, 1);
   return pcg_max_blocks(s->d.mixed, lanes, pcg_smem_bytes_for(mode, s->d.mixed, 64, 64, 128), mode);
 }
 
@@ -540,7 +547,7 @@ static bdem_status apply_pcg_shape(bdem_sim* s, int lanes, int grid) {
   for (int tries = 0; tries < 16; ++tries) {
     TRY(build_pcg_segments(s, lanes, grid));
     int mx = pcg_max_blocks(s->d.mixed, lanes, pcg_smem_bytes(s->d), s->d.pcg_mode);
-    if (mx < 1) return fail(s, BDEM_E_CUDA, "no resident blocks for the PCG kernel");
+    if (mx < 1) return fail(s, BDEM_E_INVALID, "the PCG blocks' shared memory does not fit an SM at this shape");
     if (s->d.pcg_grid <= mx) return BDEM_OK;
     grid = mx;
   }
@@ -1989,15 +1996,23 @@ extern "C" bdem_status bdem_set_pcg_shape(bdem_sim* s, int32_t lanes, int32_t bl
 extern "C" bdem_status bdem_set_pcg_product(bdem_sim* s, int32_t product) {
   if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
   if (product < 0 || product > 3) return fail(s, BDEM_E_INVALID, "product must be 0, 1, 2 or 3");
+  const int old = s->pcg_product, lanes = s->d.pcg_lanes, grid = s->d.pcg_grid;
   s->pcg_product = product;
-  return bdem_set_pcg_shape(s, s->d.pcg_lanes, s->d.pcg_grid);
+  bdem_status st = bdem_set_pcg_shape(s, lanes, grid);
+  if (st == BDEM_E_INVALID) {  // this product does not fit the current shape: the previous setting stays
+    std::string why = s->err;
+    s->pcg_product = old;
+    TRY(bdem_set_pcg_shape(s, lanes, grid));
+    s->err = why;
+  }
+  return st;
 }
 
 extern "C" bdem_status bdem_get_pcg_shape(const bdem_sim* s, int32_t* lanes, int32_t* blocks, int32_t* product) {
   if (!s) return fail(nullptr, BDEM_E_INVALID, "sim is NULL");
   if (lanes) *lanes = s->d.pcg_lanes;
   if (blocks) *blocks = s->d.pcg_grid;
-  if (product) *product = s->d.pcg_mode == 4 ? 3 : s->d.pcg_mode == 3 ? 2 : s->d.pcg_mode == 2 ? 1 : 0;
+  if (product) *product = s->d.pcg_mode >= 2 ? s->d.pcg_mode - 1 : 0;
   return BDEM_OK;
 }
 
