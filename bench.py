@@ -85,8 +85,8 @@ def pcg_source_hash():
 
 
 def traffic_record():
-    """ncu DRAM bytes of the PCG kernel per iteration (and staged once per launch), if captured for the current
-    kernel source."""
+    """ncu DRAM bytes of the PCG kernel per iteration (and staged once per launch) for the product variants and lanes
+    per row captured, if captured for the current kernel source."""
     path = os.path.join(ROOT, "profiles", "k_pcg_traffic.json")
     try:
         with open(path) as f:
@@ -96,6 +96,16 @@ def traffic_record():
         return rec
     except Exception:
         return None
+
+
+def traffic_for_shape(trec, shape):
+    """The captured record of the launch shape's product variant and lanes per row (None: not captured)."""
+    if trec is None or shape is None:
+        return None
+    for r in trec.get("records", []):
+        if r["product"] == shape["product"] and r["lanes_per_row"] == shape["lanes_per_row"]:
+            return r
+    return None
 
 
 # ------------------------------------------------------------------------------------------------
@@ -329,7 +339,7 @@ def pcg_probe(args, sc, sim, pkg, torch):
     return 0
 
 
-def pcg_roofline(sc, rrun, sizes, trec):
+def pcg_roofline(sc, rrun, sizes, trec, shape):
     """Roofline of the persistent PCG kernel from a profiled pass: algorithmic bytes per launch (per scene and step:
     its PCG iterations x its bytes per iteration with the intact bonds after the step, plus the active contact entries
     actually in the systems, plus the once-per-launch staging) over the mean launch time from CUDA events."""
@@ -348,7 +358,8 @@ def pcg_roofline(sc, rrun, sizes, trec):
     achieved = bytes_launch / (pcg_ms_launch * 1e-3) / 1e9
     peaks, peak_kind = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    traffic = None if trec is None else trec["dram_bytes_per_pcg_iter"] * pcg_iters_launch + trec["dram_bytes_once"]
+    tr = traffic_for_shape(trec, shape)
+    traffic = None if tr is None else tr["dram_bytes_per_pcg_iter"] * pcg_iters_launch + tr["dram_bytes_once"]
     return {"bound": "hbm", "kernel": "k_pcg (persistent PCG)", "achieved": achieved, "peak": peak,
             "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
             "algorithmic_bytes_per_launch": bytes_launch,
@@ -394,7 +405,7 @@ def measure_mixed(sc, args, steps, world, torch, pkg, amg, trec, e2e_on, clocks=
     same_work = all(a[k]["newton_iters"] == b[k]["newton_iters"] and a[k]["pcg_iters"] == b[k]["pcg_iters"]
                     for a, b in zip(run["stats"], rrun["stats"]) for k in range(len(sizes)))
     prof = rrun["prof"]
-    roof = None if amg else pcg_roofline(sc, rrun, sizes, trec)
+    roof = None if amg else pcg_roofline(sc, rrun, sizes, trec, shape)
     # (3) end to end from the same state, host copies inside the timed region
     e2e = None
     if e2e_on:
