@@ -99,13 +99,15 @@ def traffic_record():
 
 
 def traffic_for_shape(trec, shape):
-    """The captured record of the launch shape's product variant and lanes per row (None: not captured)."""
+    """The captured record of the launch shape's product variant (the same lanes per row if captured, else another
+    lanes setting of that variant, which moves the same data; None: the variant was not captured)."""
     if trec is None or shape is None:
         return None
-    for r in trec.get("records", []):
-        if r["product"] == shape["product"] and r["lanes_per_row"] == shape["lanes_per_row"]:
+    recs = [r for r in trec.get("records", []) if r["product"] == shape["product"]]
+    for r in recs:
+        if r["lanes_per_row"] == shape["lanes_per_row"]:
             return r
-    return None
+    return recs[0] if recs else None
 
 
 # ------------------------------------------------------------------------------------------------
