@@ -478,6 +478,24 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
   d.pcg_max_rows = (int32_t)std::max<int64_t>(max_rows, 1);
   d.pcg_max_entries = (int32_t)std::max<int64_t>(max_ent, 1);
   d.pcg_mode = mode;
+  // many scenes: each block decides its own scenes when every block's rows (product and update partitions) span at
+  // most kDistPcgScenes scenes
+  {
+    int dist = s->n_scenes > kLocalPcgScenes;
+    for (int b = 0; b < grid && dist; ++b) {
+      int lo = 0x7fffffff, hi = -1;
+      if (block_seg[b + 1] > block_seg[b]) {
+        lo = std::min(lo, seg_scene[block_seg[b]]);
+        hi = std::max(hi, seg_scene[block_seg[b + 1] - 1]);
+      }
+      if (ublock_seg[b + 1] > ublock_seg[b]) {
+        lo = std::min(lo, useg_scene[ublock_seg[b]]);
+        hi = std::max(hi, useg_scene[ublock_seg[b + 1] - 1]);
+      }
+      if (hi >= 0 && hi - lo + 1 > kDistPcgScenes) dist = 0;
+    }
+    d.pcg_dist = dist;
+  }
   // the fused PCG's halo rows and local neighbour slots (the incidence of the bonds in the device's entry order)
   {
     void* holds[] = {d.halo_start, d.halo_rows, d.inc2_loc};

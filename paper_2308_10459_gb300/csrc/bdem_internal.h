@@ -35,6 +35,8 @@ namespace bdem {
 constexpr int kTile = 256;      // rows (particles or bonds) per tile = threads per block of tile kernels
 constexpr int kPartials = 4;    // partial sums per tile
 constexpr int kDiagStride = 24; // words per stored 6x6 symmetric block (21 used, padded for 128-bit loads)
+constexpr int kLocalPcgScenes = 4;   // up to this many scenes every PCG block decides every scene
+constexpr int kDistPcgScenes = 16;   // with more, a block decides its own scenes when its rows span at most this many
 constexpr int kPcgMaxBlocks = 2048;  // largest PCG grid (grids are at most 8 blocks of kTile threads per SM)
 
 struct SceneCtl {
@@ -81,7 +83,7 @@ struct Counters {               // small device-side summary read by the host af
   int32_t loops_refine;         // refinement rounds in this step (graph path: trips of the refinement loop)
   int32_t loops_amg;            // AMG-PCG iterations in this step (trips of the device-driven iteration loop)
   int32_t amg_trips;            // trips of the current AMG-PCG solve's loop
-  int32_t pad_c;
+  int32_t dist_active[3];       // PCG with per-block decisions: scenes still iterating after iteration k, in [k % 3]
 };
 
 struct DevArrays {
@@ -145,6 +147,8 @@ struct DevArrays {
   int32_t *halo_start, *halo_rows;
   int2* inc2_loc;
   int32_t pcg_max_zslots;
+  int32_t pcg_dist;             // 1: more scenes than kLocalPcgScenes and every PCG block's rows span at most
+                                // kDistPcgScenes scenes, so each block takes its own scenes' decisions
   double* part_s;               // [n_seg][kPartials]
   SceneCtl* sc;
   Counters* cnt;

@@ -1000,7 +1000,7 @@ __device__ bool pcg_decide_scene(const DevArrays& d, SceneCtl* c, PcgPrev pv, do
 // few scenes: every block sums every scene's partial dots in the same fixed order and takes the same decision
 // with its own copy of the solver state, so the grid needs only a plain barrier (no decision inside it, no
 // control-block reads after it); block 0 keeps the control blocks current for the host
-constexpr int kLocalScenes = 4;
+constexpr int kLocalScenes = kLocalPcgScenes;
 struct LocalPcg {
   PcgState st[kLocalScenes];
   double acc[3][kTile / 32];
@@ -1041,6 +1041,80 @@ __device__ void pcg_decide_local(const DevArrays& d, int k_iter, const int* ss, 
     __syncthreads();
   }
   if (threadIdx.x == 0) L.n_active = active;
+  __syncthreads();
+}
+
+// many scenes (DevArrays::pcg_dist): each block decides the scenes its own rows belong to (the scenes of its product
+// and update segments, a contiguous range of at most kDistPcgScenes) with its own copy of their solver state, after a
+// plain barrier. Every block sums a scene's partial dots in the same fixed order (one warp per scene, lanes over the
+// scene's segments, then the warp's shuffle tree), so all copies agree. The block holding a scene's first product
+// segment keeps its control block current and counts it, if it iterates on, in the active-scene counter of the
+// iteration (dist_active[k % 3]), which every block reads after the iteration's next barrier; block 0 clears the
+// counter two iterations ahead.
+struct DistPcg {
+  PcgState st[kDistPcgScenes];
+  int lo, n;  // first scene of the block's range, scenes in it
+};
+
+// the block's scene range and its copies of their solver states; block 0 also writes the final state of the scenes
+// without rows (no block decides them) and clears the active-scene counters
+__device__ void pcg_dist_init(const DevArrays& d, int seg0, int seg1, int useg0, int useg1, DistPcg& D) {
+  if (threadIdx.x == 0) {
+    int lo = 0x7fffffff, hi = -1;
+    if (seg1 > seg0) {
+      lo = min(lo, d.seg_scene[seg0]);
+      hi = max(hi, d.seg_scene[seg1 - 1]);
+    }
+    if (useg1 > useg0) {
+      lo = min(lo, d.useg_scene[useg0]);
+      hi = max(hi, d.useg_scene[useg1 - 1]);
+    }
+    int n = hi >= 0 ? hi - lo + 1 : 0;
+    if (n > kDistPcgScenes) {  // never taken: the host enables this path only when every range fits
+      atomicExch(&d.cnt->timeout, 1);
+      n = kDistPcgScenes;
+    }
+    D.lo = hi >= 0 ? lo : 0;
+    D.n = n;
+    if (blockIdx.x == 0) {
+      d.cnt->dist_active[0] = d.cnt->dist_active[1] = d.cnt->dist_active[2] = 0;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < D.n) {
+    const SceneCtl* c = d.sc + D.lo + threadIdx.x;
+    int on = pcg_on(*c);
+    D.st[threadIdx.x] = PcgState{on, on, 0, c->eps_r, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  }
+  if (blockIdx.x == 0)
+    for (int s = threadIdx.x; s < d.n_scenes; s += blockDim.x)
+      if (d.scene_seg[s] == d.scene_seg[s + 1] && pcg_on(d.sc[s]))
+        store_pcg_state(d.sc + s, PcgState{1, 0, 0, d.sc[s].eps_r, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0});
+}
+
+// this block's decisions of iteration k_iter (after a plain grid barrier); ss: the scenes' first product segments
+__device__ void pcg_decide_dist(const DevArrays& d, int k_iter, const int* ss, int seg0, int seg1, DistPcg& D) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = warp; j < D.n; j += nw) {
+    const int s = D.lo + j, a = ss[s], b = ss[s + 1];
+    if (lane == 0) pcg_prepare(D.st[j]);  // overlaps the partial loads below
+    double gam = 0.0, del = 0.0, rho = 0.0;
+    for (int t = a + lane; t < b; t += 32) {
+      gam += __ldcg(d.part_s + kPartials * t);
+      del += __ldcg(d.part_s + kPartials * t + 1);
+      rho += __ldcg(d.part_s + kPartials * t + 2);
+    }
+    gam = warp_sum(gam);
+    del = warp_sum(del);
+    rho = warp_sum(rho);
+    if (lane == 0 && a < b) {
+      const bool go = pcg_decision(D.st[j], gam, del, rho, k_iter, d.pcg_max);
+      if (a >= seg0 && a < seg1) {  // this block holds the scene's first product segment
+        store_pcg_state(d.sc + s, D.st[j]);
+        if (go) atomicAdd(&d.cnt->dist_active[k_iter % 3], 1);
+      }
+    }
+  }
   __syncthreads();
 }
 
@@ -1192,10 +1266,13 @@ __global__ void __launch_bounds__(kTile, pcg_min_blocks<T, MODE>()) k_pcg(DevArr
     int on = pcg_on(*c);
     s_loc.st[threadIdx.x] = PcgState{on, on, 0, c->eps_r, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   }
-  __syncthreads();
   // the elementwise phases (init and B) use the equal-rows partition: their cost is per row, while the product's
   // partition balances rows against incidence entries
   const int useg0 = d.ublock_seg[blockIdx.x], useg1 = d.ublock_seg[blockIdx.x + 1];
+  __shared__ DistPcg s_dist;
+  const bool dist = !local && d.pcg_dist;
+  if (dist) pcg_dist_init(d, seg0, seg1, useg0, useg1, s_dist);
+  __syncthreads();
   // ---- init: x = p = s = 0, r = b, z = M^-1 r
   for (int g = useg0; g < useg1; ++g) {
     int sc = d.useg_scene[g];
@@ -1228,8 +1305,9 @@ __global__ void __launch_bounds__(kTile, pcg_min_blocks<T, MODE>()) k_pcg(DevArr
     // ---- A: w = H z, gamma = r.z, delta = w.z, rho = r.r (per segment, deterministic)
     for (int g = seg0; g < seg1; ++g) {
       int sc = d.seg_scene[g];
-      bool act = local ? s_loc.st[sc].pcg_active != 0
-                       : pcg_on(d.sc[sc]) && (k_iter == 0 || __ldcg(&d.sc[sc].pcg_active));
+      bool act = local  ? s_loc.st[sc].pcg_active != 0
+                 : dist ? s_dist.st[sc - s_dist.lo].pcg_active != 0
+                        : pcg_on(d.sc[sc]) && (k_iter == 0 || __ldcg(&d.sc[sc].pcg_active));
       DotAcc<T> dg, dd, dr;
       if (act) {
         int r0 = d.seg_row[g], r1 = d.seg_row[g + 1];
@@ -1346,6 +1424,9 @@ __global__ void __launch_bounds__(kTile, pcg_min_blocks<T, MODE>()) k_pcg(DevArr
       if (!grid_barrier(d, [] {})) return;
       pcg_decide_local(d, k_iter, s_sseg, s_loc);
       if (s_loc.n_active == 0 || __ldcg(&d.cnt->timeout)) break;
+    } else if (dist) {
+      if (!grid_barrier(d, [] {})) return;
+      pcg_decide_dist(d, k_iter, sseg_ok ? s_sseg : d.scene_seg, seg0, seg1, s_dist);
     } else {
       if (!grid_barrier(d, [&] { pcg_decide(d, k_iter, sseg_ok ? s_sseg : nullptr); })) return;
       if (__ldcg(&d.cnt->n_active) == 0 || __ldcg(&d.cnt->timeout)) break;
@@ -1358,6 +1439,11 @@ __global__ void __launch_bounds__(kTile, pcg_min_blocks<T, MODE>()) k_pcg(DevArr
         if (!s_loc.st[sc].pcg_active) continue;
         al = (T)s_loc.st[sc].alpha;
         be = (T)s_loc.st[sc].beta;
+      } else if (dist) {
+        const PcgState& st = s_dist.st[sc - s_dist.lo];
+        if (!st.pcg_active) continue;
+        al = (T)st.alpha;
+        be = (T)st.beta;
       } else {
         if (!pcg_on(d.sc[sc]) || !__ldcg(&d.sc[sc].pcg_active)) continue;
         al = (T)__ldcg(&d.sc[sc].alpha);
@@ -1387,6 +1473,10 @@ __global__ void __launch_bounds__(kTile, pcg_min_blocks<T, MODE>()) k_pcg(DevArr
     prefetch_l2(Z + 6 * (size_t)R0, 6 * sizeof(T) * (size_t)(R1 - R0));
     prefetch_l2(R + 6 * (size_t)R0, 6 * sizeof(T) * (size_t)(R1 - R0));
     if (!grid_barrier(d, [] {})) return;
+    if (dist) {  // every block's decisions of this iteration are counted
+      if (__ldcg(&d.cnt->dist_active[k_iter % 3]) == 0 || __ldcg(&d.cnt->timeout)) break;
+      if (blockIdx.x == 0 && threadIdx.x == 0) d.cnt->dist_active[(k_iter + 1) % 3] = 0;
+    }
   }
 }
 
@@ -1449,6 +1539,10 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 2 : 1) k_pcg_fused(Dev
     int on = pcg_on(*c);
     s_loc.st[threadIdx.x] = PcgState{on, on, 0, c->eps_r, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   }
+  // every phase of this kernel works on the block's own rows (halo and contact neighbours are in the same scenes)
+  __shared__ DistPcg s_dist;
+  const bool dist = !local && d.pcg_dist;
+  if (dist) pcg_dist_init(d, seg0, seg1, 0, 0, s_dist);
   __syncthreads();
   const T zero6[6] = {0, 0, 0, 0, 0, 0};
   // ---- init (own rows): x = p = s = 0, r = b, z = M^-1 r
@@ -1495,6 +1589,12 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 2 : 1) k_pcg_fused(Dev
         al = (T)s_loc.st[sc].alpha;
         be = (T)s_loc.st[sc].beta;
         return s_loc.st[sc].pcg_active != 0;
+      }
+      if (dist) {
+        const PcgState& st = s_dist.st[sc - s_dist.lo];
+        al = (T)st.alpha;
+        be = (T)st.beta;
+        return st.pcg_active != 0;
       }
       al = (T)__ldcg(&d.sc[sc].alpha);
       be = (T)__ldcg(&d.sc[sc].beta);
@@ -1640,6 +1740,13 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 2 : 1) k_pcg_fused(Dev
       if (!grid_barrier(d, [] {})) return;
       pcg_decide_local(d, k_iter, s_sseg, s_loc);
       if (s_loc.n_active == 0 || __ldcg(&d.cnt->timeout)) break;
+    } else if (dist) {
+      if (!grid_barrier(d, [] {})) return;
+      pcg_decide_dist(d, k_iter, sseg_ok ? s_sseg : d.scene_seg, seg0, seg1, s_dist);
+      // the previous iteration's decisions are all counted (this iteration's may still be under way): none went on
+      // means this iteration updated and multiplied nothing, and neither will the next
+      if ((k_iter > 0 && __ldcg(&d.cnt->dist_active[(k_iter - 1) % 3]) == 0) || __ldcg(&d.cnt->timeout)) break;
+      if (blockIdx.x == 0 && threadIdx.x == 0) d.cnt->dist_active[(k_iter + 1) % 3] = 0;
     } else {
       if (!grid_barrier(d, [&] { pcg_decide(d, k_iter, sseg_ok ? s_sseg : nullptr); })) return;
       if (__ldcg(&d.cnt->n_active) == 0 || __ldcg(&d.cnt->timeout)) break;

@@ -25,8 +25,10 @@ def _lib():
     pkg.load()
 
 
-def run(sc, prec, steps, graph, config=None):
+def run(sc, prec, steps, graph, config=None, pcg_blocks=None):
     sim = pkg.Sim(sc, precision=prec, config=config)
+    if pcg_blocks is not None:
+        sim.set_pcg_shape(2, pcg_blocks)
     sim.set_step_graph(graph)
     stats = [sim.step(1) for _ in range(steps)]
     st = sim.read_state()
@@ -112,6 +114,23 @@ def test_batched_uneven_scenes_through_the_graph():
         assert ea == "" and ga == 5
         assert_identical(x, y)
         assert [[t["newton_iters"] for t in st] for st in sx] == [[t["newton_iters"] for t in st] for st in sy]
+
+
+@pytest.mark.parametrize("blocks", [3, 64])
+def test_many_scenes_through_the_graph(blocks):
+    """65 scenes (64 Poisson boxes landing, an empty scene): with 64 PCG blocks each block's rows span a few scenes
+    and every block takes its own scenes' PCG decisions; with 3 blocks a block spans more than 16 scenes and the last
+    block to reach the barrier decides every scene. Either way the graph and the host-driven loop commit
+    bit-identical states."""
+    from parity_cases import c4_boxes64
+    sc = c4_boxes64()
+    for prec in (pkg.BDEM_FP64, pkg.BDEM_MIXED):
+        x, sx, ga, ea = run(sc, prec, 4, True, pcg_blocks=blocks)
+        y, sy, _, _ = run(sc, prec, 4, False, pcg_blocks=blocks)
+        assert ea == "" and ga == 3
+        assert_identical(x, y)
+        assert [[t["newton_iters"] for t in st] for st in sx] == [[t["newton_iters"] for t in st] for st in sy]
+        assert [[t["pcg_iters"] for t in st] for st in sx] == [[t["pcg_iters"] for t in st] for st in sy]
 
 
 @pytest.mark.parametrize("prec", [pkg.BDEM_FP64, pkg.BDEM_MIXED])

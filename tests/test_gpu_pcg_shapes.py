@@ -116,3 +116,39 @@ def test_fused_pcg_matches_the_two_barrier_pcg(prec, lanes):
     L = float(np.linalg.norm(sc.pos.max(0) - sc.pos.min(0)))
     assert np.abs(s3["pos"] - s0["pos"]).max() <= (1e-9 if prec == pkg.BDEM_FP64 else 1e-5) * L
     assert np.array_equal(s3["broken"], s0["broken"])
+
+
+@pytest.mark.parametrize("prec", [pkg.BDEM_FP64, pkg.BDEM_MIXED], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("product", [1, 3])
+def test_per_block_decisions_match_the_decision_in_the_barrier(prec, product):
+    """65 scenes of uneven sizes (64 Poisson boxes and an empty scene). With 64 blocks every block's rows span a few
+    scenes, so each block decides its own scenes with its own copy of their solver state and the block holding a
+    scene's first segment reports it; with 3 blocks a block's rows span more than 16 scenes and the last block to
+    reach the barrier decides every scene. Both solve every scene to its tolerance on the true residual (an
+    independent FP64 product), report the same per-scene iteration counts up to what rounding moves (the two grids
+    group the partial dots differently), and two runs of either are bit-identical."""
+    from parity_cases import c4_boxes64
+    sc = c4_boxes64()
+    off = np.asarray(sc.scene_offsets, np.int64)
+    out = {}
+    for blocks in (64, 3):
+        sim = pkg.Sim(sc, precision=prec)
+        sim.set_pcg_product(product)
+        sim.set_pcg_shape(2, blocks)
+        assert sim.pcg_shape()["blocks"] == blocks
+        st = sim.read_state()
+        dt = sc.config["dt"]
+        sy = sim.bdem_debug_system(st["pos"] + dt * st["vel"], st["quat"] + dt * st["quat_vel"], want_bonds=False)
+        b = -sy["g"]
+        x, it = sim.bdem_debug_pcg(b, 1e-6, 5000)
+        x2, it2 = sim.bdem_debug_pcg(b, 1e-6, 5000)
+        assert np.array_equal(x, x2) and np.array_equal(it, it2)
+        r = b - sim.bdem_debug_matvec(x)
+        for s in range(sc.n_scenes):
+            rs, bs = r[off[s]:off[s + 1]], b[off[s]:off[s + 1]]
+            assert np.linalg.norm(rs) <= 1.001e-6 * np.linalg.norm(bs) + 1e-300, (blocks, s)
+        out[blocks] = np.asarray(it)
+        sim.close()
+    assert out[3][17] == 0 and out[64][17] == 0  # the empty scene
+    fp64 = prec == pkg.BDEM_FP64
+    assert np.all(np.abs(out[64] - out[3]) <= (0.10 if fp64 else 0.25) * out[3] + 2), (out[64], out[3])
