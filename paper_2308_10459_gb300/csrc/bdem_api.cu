@@ -423,6 +423,10 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
   // the cooperative product stages the row descriptors and one bond block per thread (its grid is shrunk to what is
   // co-resident with that shared memory by apply_pcg_shape)
   const int mode = pcg_mode_of(s->pcg_product, staged);
+  // the cooperative products stage the row descriptors beside their slot buffers when both fit the same budget;
+  // otherwise the rows are read from L2 and more blocks fit an SM
+  const int64_t slots = (mode == 3 ? 2 : 1) * (int64_t)kTile * 36 * (int64_t)wsize(s);
+  const int rows_sm = (mode == 2 || mode == 3) ? (max_rows * (int64_t)sizeof(int4) + slots <= budget) : 1;
   // cuts block row ranges at scene boundaries
   auto cut = [&](const std::vector<int64_t>& bnd, std::vector<int32_t>& row, std::vector<int32_t>& scn,
                  std::vector<int32_t>& blk) {
@@ -478,6 +482,7 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
   d.pcg_max_rows = (int32_t)std::max<int64_t>(max_rows, 1);
   d.pcg_max_entries = (int32_t)std::max<int64_t>(max_ent, 1);
   d.pcg_mode = mode;
+  d.pcg_rows_sm = rows_sm;
   // many scenes: each block decides its own scenes when every block's rows (product and update partitions) span at
   // most kDistPcgScenes scenes
   {

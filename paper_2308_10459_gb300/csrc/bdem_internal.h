@@ -147,6 +147,7 @@ struct DevArrays {
   int32_t *halo_start, *halo_rows;
   int2* inc2_loc;
   int32_t pcg_max_zslots;
+  int32_t pcg_rows_sm;          // pcg_mode 2, 3: 1 when each block stages its row descriptors in shared memory
   int32_t pcg_dist;             // 1: more scenes than kLocalPcgScenes and every PCG block's rows span at most
                                 // kDistPcgScenes scenes, so each block takes its own scenes' decisions
   double* part_s;               // [n_seg][kPartials]

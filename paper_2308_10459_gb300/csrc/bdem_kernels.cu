@@ -850,13 +850,6 @@ __device__ __forceinline__ bool pcg_on(const SceneCtl& c) { return c.newton_acti
 // p = z + beta p, s = w + beta s (= H p), x += alpha p, r -= alpha s, z = M^-1 r.
 // ================================================================================================
 
-// L2 prefetch of a byte range by the whole block, one 128-byte line per thread and step
-__device__ __forceinline__ void prefetch_l2(const void* base, size_t bytes) {
-  const char* p = static_cast<const char*>(base);
-  for (size_t off = (size_t)threadIdx.x * 128; off < bytes; off += (size_t)blockDim.x * 128)
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p + off));
-}
-
 // the one form of device-side waiting in the library: until *word differs from old (acquire loads), for at most
 // d.wait_ns nanoseconds; on giving up it sets the timeout flag (the host reports BDEM_E_TIMEOUT) and returns false
 __device__ bool bounded_wait_change(const DevArrays& d, const unsigned* word, unsigned old) {
@@ -1220,7 +1213,9 @@ constexpr int pcg_min_blocks() {
 template <typename T, int G, int MODE>
 __global__ void __launch_bounds__(kTile, pcg_min_blocks<T, MODE>()) k_pcg(DevArrays d, int rhs_from_g, int mask) {
   constexpr bool STAGED = MODE == 1;  // incidence entries in shared memory
-  constexpr bool ROWS = MODE >= 1;    // row descriptors in shared memory
+  // row descriptors in shared memory (always with MODE 1; with MODE 2 and 3 when the block's rows fit beside its SM's
+  // other blocks, else read from L2 at every product)
+  const bool ROWS = MODE == 1 || (MODE >= 2 && d.pcg_rows_sm);
   constexpr bool COOP = MODE >= 2;
   constexpr int NB = MODE == 3 ? 2 : 1;  // slot buffers per warp of the cooperative product
   T* X = reinterpret_cast<T*>(d.vx);
@@ -1239,7 +1234,7 @@ __global__ void __launch_bounds__(kTile, pcg_min_blocks<T, MODE>()) k_pcg(DevArr
   extern __shared__ int4 s_rows[];
   int2* s_ent = reinterpret_cast<int2*>(s_rows + d.pcg_max_rows);
   // COOP: this warp's 32 block slots (36 words each) after the row descriptors
-  T* s_blk = reinterpret_cast<T*>(s_rows + d.pcg_max_rows) + (threadIdx.x >> 5) * NB * 32 * 36;
+  T* s_blk = reinterpret_cast<T*>(s_rows + (ROWS ? d.pcg_max_rows : 1)) + (threadIdx.x >> 5) * NB * 32 * 36;
   const int R0 = d.seg_row[seg0], R1 = d.seg_row[seg1];
   const int E0 = d.inc_start[R0], E1 = d.inc_start[R1];
   // row descriptor: first incidence entry (relative to the block's first when staged), bond count, active-contact
@@ -1413,13 +1408,6 @@ __global__ void __launch_bounds__(kTile, pcg_min_blocks<T, MODE>()) k_pcg(DevArr
         d.part_s[kPartials * g + 2] = acc[2];
       }
     }
-    {  // the update phase's rows into L2 while the grid waits for the slowest product and the decision
-      const size_t u0 = d.useg_row[useg0], nu = d.useg_row[useg1] - u0;
-      T* vecs[6] = {Z, W, P, S, X, R};
-#pragma unroll
-      for (int v = 0; v < 6; ++v) prefetch_l2(vecs[v] + 6 * u0, 6 * sizeof(T) * nu);
-      prefetch_l2(Dinv + kDiagStride * u0, kDiagStride * sizeof(T) * nu);
-    }
     if (local) {
       if (!grid_barrier(d, [] {})) return;
       pcg_decide_local(d, k_iter, s_sseg, s_loc);
@@ -1468,10 +1456,6 @@ __global__ void __launch_bounds__(kTile, pcg_min_blocks<T, MODE>()) k_pcg(DevArr
         store6<T>(Z, i, zn);
       }
     }
-    // the next product's own-row data (diagonal blocks, z, r) into L2 while the grid waits
-    prefetch_l2(Dm + kDiagStride * (size_t)R0, kDiagStride * sizeof(T) * (size_t)(R1 - R0));
-    prefetch_l2(Z + 6 * (size_t)R0, 6 * sizeof(T) * (size_t)(R1 - R0));
-    prefetch_l2(R + 6 * (size_t)R0, 6 * sizeof(T) * (size_t)(R1 - R0));
     if (!grid_barrier(d, [] {})) return;
     if (dist) {  // every block's decisions of this iteration are counted
       if (__ldcg(&d.cnt->dist_active[k_iter % 3]) == 0 || __ldcg(&d.cnt->timeout)) break;
@@ -2499,7 +2483,8 @@ size_t pcg_smem_bytes_for(int mode, int mixed, int max_rows, int max_entries, in
   return 0;
 }
 size_t pcg_smem_bytes(const DevArrays& d) {
-  return pcg_smem_bytes_for(d.pcg_mode, d.mixed, d.pcg_max_rows, d.pcg_max_entries, d.pcg_max_zslots);
+  const bool rows = !(d.pcg_mode == 2 || d.pcg_mode == 3) || d.pcg_rows_sm;
+  return pcg_smem_bytes_for(d.pcg_mode, d.mixed, rows ? d.pcg_max_rows : 0, d.pcg_max_entries, d.pcg_max_zslots);
 }
 
 template <typename T, int MODE>
