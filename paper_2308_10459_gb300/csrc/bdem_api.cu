@@ -422,11 +422,27 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
   const int staged = max_rows * (int64_t)sizeof(int4) + max_ent * (int64_t)sizeof(int2) <= budget;
   // the cooperative product stages the row descriptors and one bond block per thread (its grid is shrunk to what is
   // co-resident with that shared memory by apply_pcg_shape)
-  const int mode = pcg_mode_of(s->pcg_product, staged);
+  // many scenes (at most kEvenPcgScenes) and a product that can read its rows from L2: the rows of the scenes still
+  // iterating are split evenly over the grid at every iteration, when no block's share can span more than
+  // kEvenPcgSegs scenes (a share never exceeds ceil(n / grid) rows, the smallest scene with rows bounds how many it
+  // spans)
+  int even = 0;
+  if (s->n_scenes > kLocalPcgScenes && s->n_scenes <= kEvenPcgScenes && s->pcg_product <= 2 && n > 0) {
+    int64_t min_rows = n;
+    for (int sc = 0; sc < s->n_scenes; ++sc) {
+      const int64_t r = s->offsets[sc + 1] - s->offsets[sc];
+      if (r > 0) min_rows = std::min(min_rows, r);
+    }
+    const int64_t share = (n + grid - 1) / grid;
+    even = 2 + (share + min_rows - 1) / min_rows <= kEvenPcgSegs;
+  }
+  const int mode = even && s->pcg_product == 0 ? 0 : pcg_mode_of(s->pcg_product, staged);
   // the cooperative products stage the row descriptors beside their slot buffers when both fit the same budget;
-  // otherwise the rows are read from L2 and more blocks fit an SM
+  // otherwise (and always with the even re-partition, whose rows change) the rows are read from L2 and more blocks
+  // fit an SM
   const int64_t slots = (mode == 3 ? 2 : 1) * (int64_t)kTile * 36 * (int64_t)wsize(s);
-  const int rows_sm = (mode == 2 || mode == 3) ? (max_rows * (int64_t)sizeof(int4) + slots <= budget) : 1;
+  const int rows_sm =
+      (mode == 2 || mode == 3) ? (!even && max_rows * (int64_t)sizeof(int4) + slots <= budget) : 1;
   // cuts block row ranges at scene boundaries
   auto cut = [&](const std::vector<int64_t>& bnd, std::vector<int32_t>& row, std::vector<int32_t>& scn,
                  std::vector<int32_t>& blk) {
@@ -462,7 +478,8 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
   TRY(dalloc_t(s, &d.seg_scene, ns));
   TRY(dalloc_t(s, &d.block_seg, block_seg.size()));
   TRY(dalloc_t(s, &d.scene_seg, scene_seg.size()));
-  TRY(dalloc_t(s, &d.part_s, (size_t)kPartials * ns));
+  const size_t part_slots = std::max<size_t>(ns, even ? (size_t)grid * kEvenPcgSegs + kEvenPcgScenes : 0);
+  TRY(dalloc_t(s, &d.part_s, (size_t)kPartials * part_slots));
   CUDA_TRY(s, cudaMemcpy(d.seg_row, seg_row.data(), sizeof(int32_t) * seg_row.size(), cudaMemcpyHostToDevice));
   if (!seg_scene.empty())
     CUDA_TRY(s, cudaMemcpy(d.seg_scene, seg_scene.data(), sizeof(int32_t) * seg_scene.size(), cudaMemcpyHostToDevice));
@@ -483,10 +500,14 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
   d.pcg_max_entries = (int32_t)std::max<int64_t>(max_ent, 1);
   d.pcg_mode = mode;
   d.pcg_rows_sm = rows_sm;
+  d.pcg_part_slots = (int32_t)part_slots;
+  d.pcg_even = even;
+  d.pcg_even_off = 0;
+  if (even) d.pcg_even_off = (int32_t)((pcg_smem_bytes_for(mode, d.mixed, 0, 1, 0) + 15) & ~size_t(15));
   // many scenes: each block decides its own scenes when every block's rows (product and update partitions) span at
   // most kDistPcgScenes scenes
   {
-    int dist = s->n_scenes > kLocalPcgScenes;
+    int dist = s->n_scenes > kLocalPcgScenes && !even;
     for (int b = 0; b < grid && dist; ++b) {
       int lo = 0x7fffffff, hi = -1;
       if (block_seg[b + 1] > block_seg[b]) {
@@ -1959,7 +1980,7 @@ extern "C" bdem_status bdem_pcg_static(bdem_sim* s, const double* b_dev, double*
   size_t off_sc = 0;
   size_t off_cnt = off_sc + align256(sizeof(SceneCtl) * (size_t)std::max(s->n_scenes, 1));
   size_t off_part = off_cnt + align256(sizeof(Counters));
-  size_t off_vec = off_part + align256(sizeof(double) * kPartials * (size_t)std::max(d.n_seg, 1));
+  size_t off_vec = off_part + align256(sizeof(double) * kPartials * (size_t)std::max(d.pcg_part_slots, 1));
   size_t vec_bytes = align256(w * 6 * std::max<size_t>(n, 1));
   size_t need = off_vec + kVecs * vec_bytes;
   if (need > static_pcg_capacity())

@@ -37,6 +37,8 @@ constexpr int kPartials = 4;    // partial sums per tile
 constexpr int kDiagStride = 24; // words per stored 6x6 symmetric block (21 used, padded for 128-bit loads)
 constexpr int kLocalPcgScenes = 4;   // up to this many scenes every PCG block decides every scene
 constexpr int kDistPcgScenes = 16;   // with more, a block decides its own scenes when its rows span at most this many
+constexpr int kEvenPcgScenes = 128;  // up to this many scenes the PCG can re-split the active rows every iteration
+constexpr int kEvenPcgSegs = 32;     // most scenes one block's share of the active rows may span
 constexpr int kPcgMaxBlocks = 2048;  // largest PCG grid (grids are at most 8 blocks of kTile threads per SM)
 
 struct SceneCtl {
@@ -148,6 +150,11 @@ struct DevArrays {
   int2* inc2_loc;
   int32_t pcg_max_zslots;
   int32_t pcg_rows_sm;          // pcg_mode 2, 3: 1 when each block stages its row descriptors in shared memory
+  int32_t pcg_even;             // 1: the rows of the scenes still iterating are split evenly over the grid at every
+                                // iteration, and every block decides every scene (pcg_even_off: the byte offset of
+                                // the per-block state in the dynamic shared memory)
+  int32_t pcg_even_off;
+  int32_t pcg_part_slots;       // partial-dot slots of the PCG (part_s): segments, or blocks x kEvenPcgSegs
   int32_t pcg_dist;             // 1: more scenes than kLocalPcgScenes and every PCG block's rows span at most
                                 // kDistPcgScenes scenes, so each block takes its own scenes' decisions
   double* part_s;               // [n_seg][kPartials]
@@ -211,6 +218,7 @@ int launch_pcg(const DevArrays& d, int rhs_from_g, int mask_kin, cudaStream_t s,
 int pcg_max_blocks(int mixed, int lanes, size_t smem, int mode);  // co-resident PCG blocks on this device (0: none)
 size_t pcg_smem_bytes(const DevArrays& d);  // dynamic shared memory of a PCG block in the arrays' mode
 size_t pcg_smem_bytes_for(int mode, int mixed, int max_rows, int max_entries, int max_zslots);
+size_t pcg_even_bytes();  // the per-block state of the even re-partition (in dynamic shared memory)
 int launch_gdx(const DevArrays& d, cudaStream_t s);
 int launch_ls_trial(const DevArrays& d, cudaStream_t s);
 int launch_ls_energy(const DevArrays& d, cudaStream_t s);

@@ -1111,6 +1111,147 @@ __device__ void pcg_decide_dist(const DevArrays& d, int k_iter, const int* ss, i
   __syncthreads();
 }
 
+// many scenes whose solves stop after different numbers of iterations (DevArrays::pcg_even): at every iteration the
+// rows of the scenes still iterating are split evenly over the grid (a block's share may span several scenes: its
+// segments), every block keeps every scene's solver state and takes every scene's decision from the same sums in the
+// same order, so the blocks whose scenes have stopped take rows of the others instead of waiting at the barriers. A
+// segment's partial dots go to slot blockIdx.x * kEvenPcgSegs + its index in the block; a scene's slots are found
+// from the iteration's active-row prefix (the blocks whose shares its rows fall in, its index in the first of them)
+// and summed in block order by the last block to reach the barrier, so that every other block reads one sum per
+// scene (all blocks reading every slot made the slots' L2 lines a hot spot: 19-36 us per iteration on 64 scenes).
+struct EvenPcg {
+  PcgState st[kEvenPcgScenes];
+  int off[kEvenPcgScenes + 1];    // first row of each scene
+  int pre[kEvenPcgScenes + 1];    // rows of the iterating scenes before each scene (this iteration)
+  int arank[kEvenPcgScenes + 1];  // iterating scenes with rows before each scene
+  int4 seg[kEvenPcgSegs];          // this block's segments: scene, first row, end row
+  int nseg, n_active;
+};
+size_t pcg_even_bytes() { return sizeof(EvenPcg); }
+
+// the first of the N active rows in block b's share (shares [floor(b N / G), floor((b + 1) N / G)))
+__device__ __forceinline__ long long even_share(long long b, long long N, long long G) { return b * N / G; }
+// the block whose share holds active row x: the largest b with floor(b N / G) <= x
+__device__ __forceinline__ int even_block_of(long long x, long long N, long long G) {
+  return (int)(((x + 1) * G - 1) / N);
+}
+
+__device__ void pcg_even_init(const DevArrays& d, EvenPcg& E) {
+  for (int s = threadIdx.x; s <= d.n_scenes; s += blockDim.x) E.off[s] = d.ptile_start[d.ptile_begin[s]];
+  for (int s = threadIdx.x; s < d.n_scenes; s += blockDim.x) {
+    const SceneCtl* c = d.sc + s;
+    int on = pcg_on(*c);
+    E.st[s] = PcgState{on, on, 0, c->eps_r, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  }
+}
+
+// this iteration's active-row prefix and the block's segments (thread 0; the block waits)
+__device__ void pcg_even_partition(const DevArrays& d, EvenPcg& E) {
+  if (threadIdx.x == 0) {
+    const int S = d.n_scenes;
+    int p = 0, r = 0;
+    for (int s = 0; s < S; ++s) {
+      E.pre[s] = p;
+      E.arank[s] = r;
+      const int rows = E.off[s + 1] - E.off[s];
+      if (E.st[s].pcg_active && rows > 0) {
+        p += rows;
+        ++r;
+      }
+    }
+    E.pre[S] = p;
+    E.arank[S] = r;
+    E.n_active = 0;
+    E.nseg = 0;
+    const long long N = p, G = gridDim.x;
+    const long long lo = N > 0 ? even_share(blockIdx.x, N, G) : 0, hi = N > 0 ? even_share(blockIdx.x + 1, N, G) : 0;
+    if (hi > lo) {
+      int a = 0, b = S - 1;  // the first scene with rows after lo: smallest s with pre[s + 1] > lo
+      while (a < b) {
+        const int m = (a + b) >> 1;
+        if (E.pre[m + 1] > lo) b = m;
+        else a = m + 1;
+      }
+      for (int s = a; s < S && E.pre[s] < hi; ++s) {
+        const long long x0 = lo > E.pre[s] ? lo : E.pre[s], x1 = hi < E.pre[s + 1] ? hi : E.pre[s + 1];
+        if (x1 <= x0) continue;
+        if (E.nseg < kEvenPcgSegs)
+          E.seg[E.nseg++] = make_int4(s, E.off[s] + (int)(x0 - E.pre[s]), E.off[s] + (int)(x1 - E.pre[s]), 0);
+        else
+          atomicExch(&d.cnt->timeout, 1);  // never taken: the host enables this path only when every share fits
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// the scenes' sums of this iteration's partial dots, formed by the last block to reach the barrier (all of its
+// threads): a group of threads per scene (a power of two, up to 32) strides over the scene's slots in block order
+// and adds its partial sums by a shuffle tree; the sums go to slot G * kEvenPcgSegs + scene
+__device__ void pcg_even_totals(const DevArrays& d, const EvenPcg& E) {
+  const long long N = E.pre[d.n_scenes], G = gridDim.x;
+  int T = 1;
+  while (T < 32 && 2 * T * d.n_scenes <= (int)blockDim.x) T *= 2;
+  const int lane = threadIdx.x & 31, t = threadIdx.x % T, ngroups = blockDim.x / T;
+  const unsigned gmask = (T == 32 ? 0xffffffffu : ((1u << T) - 1u)) << (lane & ~(T - 1));
+  for (int s = threadIdx.x / T; s < d.n_scenes; s += ngroups) {
+    double gam = 0.0, del = 0.0, rho = 0.0;
+    const int a = E.pre[s], b = E.pre[s + 1];
+    if (b > a) {
+      const int blo = even_block_of(a, N, G), bhi = even_block_of(b - 1, N, G);
+      // the scene's index among block blo's segments: the scenes with rows between blo's first row and this one
+      const long long x = even_share(blo, N, G);
+      int u = 0, v = s;
+      while (u < v) {
+        const int m = (u + v) >> 1;
+        if (E.pre[m + 1] > x) v = m;
+        else u = m + 1;
+      }
+      const int k0 = E.arank[s] - E.arank[u];
+      for (int bb = blo + t; bb <= bhi; bb += T) {
+        // with fewer active rows than blocks some shares are empty and wrote no slot
+        if (N < G && even_share(bb + 1, N, G) <= even_share(bb, N, G)) continue;
+        const int slot = bb * kEvenPcgSegs + (bb == blo ? k0 : 0);
+        gam += __ldcg(d.part_s + kPartials * slot);
+        del += __ldcg(d.part_s + kPartials * slot + 1);
+        rho += __ldcg(d.part_s + kPartials * slot + 2);
+      }
+    }
+    for (int o = T / 2; o >= 1; o >>= 1) {
+      gam += __shfl_xor_sync(gmask, gam, o, T);
+      del += __shfl_xor_sync(gmask, del, o, T);
+      rho += __shfl_xor_sync(gmask, rho, o, T);
+    }
+    if (t == 0) {
+      double* tot = d.part_s + kPartials * ((size_t)G * kEvenPcgSegs + s);
+      tot[0] = gam;
+      tot[1] = del;
+      tot[2] = rho;
+    }
+  }
+}
+
+// every scene's decision of iteration k_iter from the sums (after the barrier that formed them), the same in every
+// block, one thread per scene
+__device__ void pcg_decide_even(const DevArrays& d, int k_iter, EvenPcg& E) {
+  const size_t base = (size_t)gridDim.x * kEvenPcgSegs;
+  for (int s = threadIdx.x; s < d.n_scenes; s += blockDim.x) {
+    PcgState& st = E.st[s];
+    double gam = 0.0, del = 0.0, rho = 0.0;
+    if (E.pre[s + 1] > E.pre[s]) {
+      const double* tot = d.part_s + kPartials * (base + s);
+      gam = __ldcg(tot);
+      del = __ldcg(tot + 1);
+      rho = __ldcg(tot + 2);
+    }
+    pcg_prepare(st);
+    const bool go = pcg_decision(st, gam, del, rho, k_iter, d.pcg_max);
+    if (blockIdx.x == 0) store_pcg_state(d.sc + s, st);
+    if (go) atomicAdd(&E.n_active, 1);
+  }
+  __syncthreads();
+}
+
 constexpr int kBlockScene = 64;  // scenes with more PCG segments than this are reduced by the whole block
 
 // per-scene decision after the fused product, run by the last block to reach the barrier. The partial dots of a
@@ -1265,8 +1406,11 @@ __global__ void __launch_bounds__(kTile, pcg_min_blocks<T, MODE>()) k_pcg(DevArr
   // partition balances rows against incidence entries
   const int useg0 = d.ublock_seg[blockIdx.x], useg1 = d.ublock_seg[blockIdx.x + 1];
   __shared__ DistPcg s_dist;
-  const bool dist = !local && d.pcg_dist;
+  const bool even = !local && d.pcg_even;
+  const bool dist = !local && !even && d.pcg_dist;
   if (dist) pcg_dist_init(d, seg0, seg1, useg0, useg1, s_dist);
+  EvenPcg& E = *reinterpret_cast<EvenPcg*>(reinterpret_cast<char*>(s_rows) + d.pcg_even_off);
+  if (even) pcg_even_init(d, E);
   __syncthreads();
   // ---- init: x = p = s = 0, r = b, z = M^-1 r
   for (int g = useg0; g < useg1; ++g) {
@@ -1297,15 +1441,19 @@ __global__ void __launch_bounds__(kTile, pcg_min_blocks<T, MODE>()) k_pcg(DevArr
   if (!grid_barrier(d, [] {})) return;
   const int sub = threadIdx.x % G, grp = threadIdx.x / G, rows_per_pass = blockDim.x / G;
   for (int k_iter = 0;; ++k_iter) {
+    if (even) pcg_even_partition(d, E);
     // ---- A: w = H z, gamma = r.z, delta = w.z, rho = r.r (per segment, deterministic)
-    for (int g = seg0; g < seg1; ++g) {
-      int sc = d.seg_scene[g];
+    const int nseg = even ? E.nseg : seg1 - seg0;
+    for (int q = 0; q < nseg; ++q) {
+      const int g = even ? blockIdx.x * kEvenPcgSegs + q : seg0 + q;  // partial slot
+      const int sc = even ? E.seg[q].x : d.seg_scene[g];
       bool act = local  ? s_loc.st[sc].pcg_active != 0
+                 : even ? E.st[sc].pcg_active != 0
                  : dist ? s_dist.st[sc - s_dist.lo].pcg_active != 0
                         : pcg_on(d.sc[sc]) && (k_iter == 0 || __ldcg(&d.sc[sc].pcg_active));
       DotAcc<T> dg, dd, dr;
       if (act) {
-        int r0 = d.seg_row[g], r1 = d.seg_row[g + 1];
+        const int r0 = even ? E.seg[q].y : d.seg_row[g], r1 = even ? E.seg[q].z : d.seg_row[g + 1];
         for (int base = r0; base < r1; base += rows_per_pass) {
           int i = base + grp;
           bool valid = i < r1;
@@ -1412,6 +1560,10 @@ __global__ void __launch_bounds__(kTile, pcg_min_blocks<T, MODE>()) k_pcg(DevArr
       if (!grid_barrier(d, [] {})) return;
       pcg_decide_local(d, k_iter, s_sseg, s_loc);
       if (s_loc.n_active == 0 || __ldcg(&d.cnt->timeout)) break;
+    } else if (even) {
+      if (!grid_barrier(d, [&] { pcg_even_totals(d, E); })) return;
+      pcg_decide_even(d, k_iter, E);
+      if (E.n_active == 0 || __ldcg(&d.cnt->timeout)) break;
     } else if (dist) {
       if (!grid_barrier(d, [] {})) return;
       pcg_decide_dist(d, k_iter, sseg_ok ? s_sseg : d.scene_seg, seg0, seg1, s_dist);
@@ -1419,11 +1571,19 @@ __global__ void __launch_bounds__(kTile, pcg_min_blocks<T, MODE>()) k_pcg(DevArr
       if (!grid_barrier(d, [&] { pcg_decide(d, k_iter, sseg_ok ? s_sseg : nullptr); })) return;
       if (__ldcg(&d.cnt->n_active) == 0 || __ldcg(&d.cnt->timeout)) break;
     }
-    // ---- B: p = z + beta p, s = w + beta s, x += alpha p, r -= alpha s, z = M^-1 r
-    for (int g = useg0; g < useg1; ++g) {
-      int sc = d.useg_scene[g];
+    // ---- B: p = z + beta p, s = w + beta s, x += alpha p, r -= alpha s, z = M^-1 r (with the even re-partition
+    // over the product's segments, else over the equal-rows partition)
+    const int nuseg = even ? E.nseg : useg1 - useg0;
+    for (int q = 0; q < nuseg; ++q) {
+      const int g = useg0 + q;
+      const int sc = even ? E.seg[q].x : d.useg_scene[g];
+      const int u0 = even ? E.seg[q].y : d.useg_row[g], u1 = even ? E.seg[q].z : d.useg_row[g + 1];
       T al, be;
-      if (local) {
+      if (even) {
+        if (!E.st[sc].pcg_active) continue;
+        al = (T)E.st[sc].alpha;
+        be = (T)E.st[sc].beta;
+      } else if (local) {
         if (!s_loc.st[sc].pcg_active) continue;
         al = (T)s_loc.st[sc].alpha;
         be = (T)s_loc.st[sc].beta;
@@ -1437,7 +1597,7 @@ __global__ void __launch_bounds__(kTile, pcg_min_blocks<T, MODE>()) k_pcg(DevArr
         al = (T)__ldcg(&d.sc[sc].alpha);
         be = (T)__ldcg(&d.sc[sc].beta);
       }
-      for (int i = d.useg_row[g] + threadIdx.x; i < d.useg_row[g + 1]; i += blockDim.x) {
+      for (int i = u0 + threadIdx.x; i < u1; i += blockDim.x) {
         Vec6<T> z = load6_cg<T>(Z, i), w = load6_cg<T>(W, i), p = load6_cg<T>(P, i), s = load6_cg<T>(S, i);
         Vec6<T> x = load6_cg<T>(X, i), r = load6_cg<T>(R, i);
         T pn[6], sn[6], xn[6], rn[6], zn[6];
@@ -2483,6 +2643,7 @@ size_t pcg_smem_bytes_for(int mode, int mixed, int max_rows, int max_entries, in
   return 0;
 }
 size_t pcg_smem_bytes(const DevArrays& d) {
+  if (d.pcg_even) return (size_t)d.pcg_even_off + sizeof(EvenPcg);
   const bool rows = !(d.pcg_mode == 2 || d.pcg_mode == 3) || d.pcg_rows_sm;
   return pcg_smem_bytes_for(d.pcg_mode, d.mixed, rows ? d.pcg_max_rows : 0, d.pcg_max_entries, d.pcg_max_zslots);
 }

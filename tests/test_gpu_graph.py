@@ -118,10 +118,10 @@ def test_batched_uneven_scenes_through_the_graph():
 
 @pytest.mark.parametrize("blocks", [3, 64])
 def test_many_scenes_through_the_graph(blocks):
-    """65 scenes (64 Poisson boxes landing, an empty scene): with 64 PCG blocks each block's rows span a few scenes
-    and every block takes its own scenes' PCG decisions; with 3 blocks a block spans more than 16 scenes and the last
-    block to reach the barrier decides every scene. Either way the graph and the host-driven loop commit
-    bit-identical states."""
+    """65 scenes (64 Poisson boxes landing, an empty scene): with 64 PCG blocks the rows of the scenes still
+    iterating are split evenly over the grid at every PCG iteration and every block takes every scene's decision;
+    with 3 blocks a block spans more than 16 scenes and the last block to reach the barrier decides every scene.
+    Either way the graph and the host-driven loop commit bit-identical states."""
     from parity_cases import c4_boxes64
     sc = c4_boxes64()
     for prec in (pkg.BDEM_FP64, pkg.BDEM_MIXED):

@@ -88,6 +88,33 @@ def test_cooperative_and_per_lane_products_are_bit_identical(prec, lanes):
 
 
 @pytest.mark.parametrize("prec", [pkg.BDEM_FP64, pkg.BDEM_MIXED], ids=["fp64", "mixed"])
+def test_cooperative_products_with_the_rows_read_from_l2(prec):
+    """On a 2-block grid over the plate construction at R = 0.1 m (about 27,000 particles, 13,500 rows per block) a
+    block's row descriptors (16 bytes a row) do not fit beside the cooperative products' slot buffers, so those
+    products read them from L2 at every product instead of staging them; the sums are the same, so the solves and a
+    step stay bit-identical to the per-lane product's."""
+    sc = scenes.c2_plate_small(R=0.1)
+    assert sc.n // 2 * 16 > 200 * 1024
+    out = {}
+    for product in (2, 1, 0):
+        sim = pkg.Sim(sc, precision=prec)
+        sim.set_pcg_product(product)
+        sim.set_pcg_shape(4, 2)
+        assert sim.pcg_shape()["blocks"] == 2
+        st = sim.read_state()
+        dt = sc.config["dt"]
+        sy = sim.bdem_debug_system(st["pos"] + dt * st["vel"], st["quat"] + dt * st["quat_vel"], want_bonds=False)
+        x, it = sim.bdem_debug_pcg(-sy["g"], 1e-4, 5000)
+        sim.step(1)
+        out[product] = (x, it, sim.read_state())
+        sim.close()
+    for product in (2, 1):
+        assert np.array_equal(out[0][0], out[product][0]) and np.array_equal(out[0][1], out[product][1])
+        for k in ("pos", "quat", "vel", "quat_vel", "broken"):
+            assert np.array_equal(out[0][2][k], out[product][2][k]), (product, k)
+
+
+@pytest.mark.parametrize("prec", [pkg.BDEM_FP64, pkg.BDEM_MIXED], ids=["fp64", "mixed"])
 @pytest.mark.parametrize("lanes", [1, 2, 4])
 def test_fused_pcg_matches_the_two_barrier_pcg(prec, lanes):
     """The fused PCG (the vector update folded into the next product, halo rows' z recomputed from the previous
@@ -121,12 +148,13 @@ def test_fused_pcg_matches_the_two_barrier_pcg(prec, lanes):
 @pytest.mark.parametrize("prec", [pkg.BDEM_FP64, pkg.BDEM_MIXED], ids=["fp64", "mixed"])
 @pytest.mark.parametrize("product", [1, 3])
 def test_per_block_decisions_match_the_decision_in_the_barrier(prec, product):
-    """65 scenes of uneven sizes (64 Poisson boxes and an empty scene). With 64 blocks every block's rows span a few
-    scenes, so each block decides its own scenes with its own copy of their solver state and the block holding a
-    scene's first segment reports it; with 3 blocks a block's rows span more than 16 scenes and the last block to
-    reach the barrier decides every scene. Both solve every scene to its tolerance on the true residual (an
-    independent FP64 product), report the same per-scene iteration counts up to what rounding moves (the two grids
-    group the partial dots differently), and two runs of either are bit-identical."""
+    """65 scenes of uneven sizes (64 Poisson boxes and an empty scene). With 64 blocks the two-barrier PCG (product
+    1) splits the rows of the scenes still iterating evenly over the grid at every iteration and every block decides
+    every scene, while the fused PCG (product 3) keeps its row ranges and each block decides the scenes its own rows
+    belong to; with 3 blocks a block's rows span more than 16 scenes and the last block to reach the barrier decides
+    every scene. All solve every scene to its tolerance on the true residual (an independent FP64 product), report
+    the same per-scene iteration counts up to what rounding moves (the grids group the partial dots differently), and
+    two runs of any are bit-identical."""
     from parity_cases import c4_boxes64
     sc = c4_boxes64()
     off = np.asarray(sc.scene_offsets, np.int64)
