@@ -276,7 +276,9 @@ int64_t bdem_launch_count(const bdem_sim* sim);
  * lanes_per_row in {1, 2, 4, 8}: threads that share one block row of the product (the rows of a warp = 32 / lanes);
  * blocks: PCG grid size, 0 = every co-resident block (capped at one block per 64 rows). Changing the shape changes
  * the grouping of the FP64 partial sums, so results differ at rounding level between shapes; a fixed shape gives
- * bit-identical runs. */
+ * bit-identical runs. With 5 to 128 scenes and products 0-2 (bdem_set_pcg_product) the rows of the scenes still
+ * iterating are split evenly over the blocks again at every PCG iteration, when no block's share can span more than
+ * 32 scenes; that partition is part of the shape, so runs stay bit-identical. */
 bdem_status bdem_set_pcg_shape(bdem_sim* sim, int32_t lanes_per_row, int32_t blocks);
 
 
