@@ -91,8 +91,9 @@ def test_cooperative_and_per_lane_products_are_bit_identical(prec, lanes):
 def test_cooperative_products_with_the_rows_read_from_l2(prec):
     """On a 2-block grid over the plate construction at R = 0.1 m (about 27,000 particles, 13,500 rows per block) a
     block's row descriptors (16 bytes a row) do not fit beside the cooperative products' slot buffers, so those
-    products read them from L2 at every product instead of staging them; the sums are the same, so the solves and a
-    step stay bit-identical to the per-lane product's."""
+    products read them from L2 at every product instead of staging them; the sums are the same, so a fixed number of
+    iterations (and, on the FP32 path, a time step) stays bit-identical to the per-lane product's. (Two blocks make
+    the FP64 path's iterations slow, so it runs the iterations only.)"""
     sc = scenes.c2_plate_small(R=0.1)
     assert sc.n // 2 * 16 > 200 * 1024
     out = {}
@@ -104,14 +105,18 @@ def test_cooperative_products_with_the_rows_read_from_l2(prec):
         st = sim.read_state()
         dt = sc.config["dt"]
         sy = sim.bdem_debug_system(st["pos"] + dt * st["vel"], st["quat"] + dt * st["quat_vel"], want_bonds=False)
-        x, it = sim.bdem_debug_pcg(-sy["g"], 1e-4, 5000)
-        sim.step(1)
-        out[product] = (x, it, sim.read_state())
+        x, it = sim.bdem_debug_pcg(-sy["g"], 0.0, 60)
+        state = None
+        if prec == pkg.BDEM_MIXED:
+            sim.step(1)
+            state = sim.read_state()
+        out[product] = (x, it, state)
         sim.close()
     for product in (2, 1):
         assert np.array_equal(out[0][0], out[product][0]) and np.array_equal(out[0][1], out[product][1])
-        for k in ("pos", "quat", "vel", "quat_vel", "broken"):
-            assert np.array_equal(out[0][2][k], out[product][2][k]), (product, k)
+        if out[0][2] is not None:
+            for k in ("pos", "quat", "vel", "quat_vel", "broken"):
+                assert np.array_equal(out[0][2][k], out[product][2][k]), (product, k)
 
 
 @pytest.mark.parametrize("prec", [pkg.BDEM_FP64, pkg.BDEM_MIXED], ids=["fp64", "mixed"])
