@@ -478,7 +478,9 @@ static bdem_status build_pcg_segments(bdem_sim* s, int lanes, int grid) {
   TRY(dalloc_t(s, &d.seg_scene, ns));
   TRY(dalloc_t(s, &d.block_seg, block_seg.size()));
   TRY(dalloc_t(s, &d.scene_seg, scene_seg.size()));
-  const size_t part_slots = std::max<size_t>(ns, even ? (size_t)grid * kEvenPcgSegs + kEvenPcgScenes : 0);
+  // segments' partials, then the few-scene sums (n_seg + scene); or the even re-split's block slots and scene sums
+  const size_t part_slots =
+      std::max<size_t>(ns + kLocalPcgScenes, even ? (size_t)grid * kEvenPcgSegs + kEvenPcgScenes : 0);
   TRY(dalloc_t(s, &d.part_s, (size_t)kPartials * part_slots));
   CUDA_TRY(s, cudaMemcpy(d.seg_row, seg_row.data(), sizeof(int32_t) * seg_row.size(), cudaMemcpyHostToDevice));
   if (!seg_scene.empty())

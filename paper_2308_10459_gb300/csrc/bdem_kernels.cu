@@ -990,9 +990,9 @@ __device__ bool pcg_decide_scene(const DevArrays& d, SceneCtl* c, PcgPrev pv, do
   return go;
 }
 
-// few scenes: every block sums every scene's partial dots in the same fixed order and takes the same decision
-// with its own copy of the solver state, so the grid needs only a plain barrier (no decision inside it, no
-// control-block reads after it); block 0 keeps the control blocks current for the host
+// few scenes: the last block to reach the barrier sums every scene's partial dots in a fixed order, and every block
+// then takes the same decisions from those sums with its own copy of the solver state (no control-block reads after
+// the barrier); block 0 keeps the control blocks current for the host
 constexpr int kLocalScenes = kLocalPcgScenes;
 struct LocalPcg {
   PcgState st[kLocalScenes];
@@ -1000,10 +1000,11 @@ struct LocalPcg {
   int n_active;
 };
 
-__device__ void pcg_decide_local(const DevArrays& d, int k_iter, const int* ss, LocalPcg& L) {
+// the scenes' sums of this iteration's partial dots, formed by the last block to reach the barrier (threads over the
+// scene's segments, then the warps' sums in order) into slots n_seg + scene, so that the other blocks read three
+// words per scene instead of every segment's partials (all blocks reading every slot makes those lines an L2 hot spot)
+__device__ void pcg_local_totals(const DevArrays& d, const int* ss, LocalPcg& L) {
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  int active = 0;
-  if (threadIdx.x < d.n_scenes) pcg_prepare(L.st[threadIdx.x]);  // overlaps the partial loads below
   for (int s = 0; s < d.n_scenes; ++s) {
     int a = ss[s], b = ss[s + 1];
     double gam = 0.0, del = 0.0, rho = 0.0;
@@ -1028,11 +1029,28 @@ __device__ void pcg_decide_local(const DevArrays& d, int k_iter, const int* ss, 
         D += L.acc[1][w];
         R += L.acc[2][w];
       }
-      if (pcg_decision(L.st[s], G, D, R, k_iter, d.pcg_max)) ++active;
-      if (blockIdx.x == 0) store_pcg_state(d.sc + s, L.st[s]);
+      double* tot = d.part_s + kPartials * ((size_t)d.n_seg + s);
+      tot[0] = G;
+      tot[1] = D;
+      tot[2] = R;
     }
     __syncthreads();
   }
+}
+
+// every scene's decision from the sums (after the barrier that formed them), one thread per scene, the same in every
+// block
+__device__ void pcg_decide_local(const DevArrays& d, int k_iter, LocalPcg& L) {
+  bool go = false;
+  if (threadIdx.x < d.n_scenes) {
+    const int s = threadIdx.x;
+    const double* tot = d.part_s + kPartials * ((size_t)d.n_seg + s);
+    const double G = __ldcg(tot), D = __ldcg(tot + 1), R = __ldcg(tot + 2);
+    pcg_prepare(L.st[s]);
+    go = pcg_decision(L.st[s], G, D, R, k_iter, d.pcg_max);
+    if (blockIdx.x == 0) store_pcg_state(d.sc + s, L.st[s]);
+  }
+  const int active = __syncthreads_count(go);
   if (threadIdx.x == 0) L.n_active = active;
   __syncthreads();
 }
@@ -1557,8 +1575,8 @@ __global__ void __launch_bounds__(kTile, pcg_min_blocks<T, MODE>()) k_pcg(DevArr
       }
     }
     if (local) {
-      if (!grid_barrier(d, [] {})) return;
-      pcg_decide_local(d, k_iter, s_sseg, s_loc);
+      if (!grid_barrier(d, [&] { pcg_local_totals(d, s_sseg, s_loc); })) return;
+      pcg_decide_local(d, k_iter, s_loc);
       if (s_loc.n_active == 0 || __ldcg(&d.cnt->timeout)) break;
     } else if (even) {
       if (!grid_barrier(d, [&] { pcg_even_totals(d, E); })) return;
@@ -1881,8 +1899,8 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 2 : 1) k_pcg_fused(Dev
       }
     }
     if (local) {
-      if (!grid_barrier(d, [] {})) return;
-      pcg_decide_local(d, k_iter, s_sseg, s_loc);
+      if (!grid_barrier(d, [&] { pcg_local_totals(d, s_sseg, s_loc); })) return;
+      pcg_decide_local(d, k_iter, s_loc);
       if (s_loc.n_active == 0 || __ldcg(&d.cnt->timeout)) break;
     } else if (dist) {
       if (!grid_barrier(d, [] {})) return;
