@@ -299,8 +299,10 @@ bdem_status bdem_set_pcg_product(bdem_sim* sim, int32_t product);
 bdem_status bdem_get_pcg_shape(const bdem_sim* sim, int32_t* lanes_per_row, int32_t* blocks, int32_t* product);
 
 /* Times the PCG kernel for `iters` iterations on the system at the current committed state for each candidate shape
- * (products 3, 2, 1, 0 x lanes 1, 2, 4, 8 x 1..all co-resident blocks per SM), keeps the fastest, and reports its lanes
- * and grid (either pointer may be NULL; bdem_get_pcg_shape gives the product). Host-blocking. */
+ * (products 3, 2, 1, 0 x lanes 1, 2, 4, 8 x 1..all co-resident blocks per SM; shapes whose blocks do not fit an SM are
+ * skipped), keeps the fastest, and reports its lanes and grid (either pointer may be NULL; bdem_get_pcg_shape gives
+ * the product). Every scene iterates while it is timed (no stopping test), so the even re-split of many scenes is
+ * timed without the savings it makes once scenes stop. Host-blocking. */
 bdem_status bdem_autotune_pcg(bdem_sim* sim, int32_t iters, int32_t* lanes_per_row, int32_t* blocks);
 
 /* ---- bond-Hessian tile ------------------------------------------------------------------------------------------
